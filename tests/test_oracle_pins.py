@@ -1,0 +1,305 @@
+"""Pins for the FP64 oracle against what physics and mathematics fix.
+
+None of these re-types the oracle's own formula: each check compares the
+oracle with an independent fact (a closed form, an invariant, a textbook
+routine, or a different brute-force method on tiny inputs).
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_11092_gb300 import workloads
+
+
+def rand_c(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# ---------------------------------------------------------------- permanents
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
+def test_ryser_matches_permutation_sum(n):
+    rng = np.random.default_rng(n)
+    A = rand_c(rng, n, n)
+    assert abs(oracle.permanent(A) - oracle.permanent_naive(A)) <= 1e-13 * max(1.0, abs(oracle.permanent_naive(A)))
+
+
+@pytest.mark.parametrize("n", range(1, 11))
+def test_permanent_all_ones_is_factorial(n):
+    assert oracle.permanent(np.ones((n, n))) == pytest.approx(math.factorial(n), rel=1e-14)
+
+
+def test_permanent_of_diagonal_and_triangular():
+    # Per(triangular) = product of the diagonal (only the identity permutation survives)
+    rng = np.random.default_rng(7)
+    A = np.triu(rand_c(rng, 6, 6))
+    assert abs(oracle.permanent(A) - np.prod(np.diag(A))) < 1e-12
+
+
+# ---------------------------------------------------------------- Fock space
+
+@pytest.mark.parametrize("m,n", [(1, 3), (2, 4), (3, 3), (4, 2), (5, 4), (6, 3), (6, 5)])
+def test_enumeration_order_and_count(m, n):
+    out = oracle.enumerate_fock(m, n)
+    assert out.shape == (math.comb(m + n - 1, n), m)
+    assert np.all(out.sum(axis=1) == n)
+    tuples = [tuple(r) for r in out]
+    assert len(set(tuples)) == len(tuples)
+    # descending lexicographic: Python tuple order reversed
+    assert tuples == sorted(tuples, reverse=True)
+    assert tuples == oracle.enumerate_fock_recursive(m, n)
+    assert tuples[0] == (n,) + (0,) * (m - 1)
+    assert tuples[-1] == (0,) * (m - 1) + (n,)
+
+
+def test_enumeration_sampled_positions():
+    m, n = 9, 5
+    full = oracle.enumerate_fock(m, n)
+    pos = np.array([0, 3, 17, 500, full.shape[0] - 1])
+    assert np.array_equal(oracle.enumerate_fock(m, n, pos), full[pos])
+
+
+# ---------------------------------------------------------------- physics pins
+
+def test_hong_ou_mandel():
+    # 50:50 beam splitter, one photon in each input: no coincidences.
+    for B in (oracle.BS, np.array([[1, 1], [1, -1]]) / np.sqrt(2)):
+        out = oracle.enumerate_fock(2, 2)          # (2,0), (1,1), (0,2)
+        p = oracle.probabilities(B, [1, 1], out)
+        assert p[1] <= 1e-15
+        assert p[0] == pytest.approx(0.5, abs=1e-15)
+        assert p[2] == pytest.approx(0.5, abs=1e-15)
+
+
+def test_single_photon_is_column_modulus():
+    rng = np.random.default_rng(3)
+    U = workloads.haar_unitaries(7, 1, rng)[0]
+    for i in range(7):
+        s = [0] * 7
+        s[i] = 1
+        out = oracle.enumerate_fock(7, 1)
+        p = oracle.probabilities(U, s, out)
+        # output e_j has index j in descending-lex order
+        assert np.allclose(p, np.abs(U[:, i]) ** 2, atol=1e-15)
+
+
+def test_identity_and_permutation_give_delta():
+    m, s = 5, [2, 0, 1, 0, 1]
+    out = oracle.enumerate_fock(m, 4)
+    tuples = [tuple(r) for r in out]
+    p = oracle.probabilities(np.eye(m), s, out)
+    assert p[tuples.index(tuple(s))] == pytest.approx(1.0, abs=1e-15)
+    assert p.sum() == pytest.approx(1.0, abs=1e-15)
+    perm = [3, 0, 4, 1, 2]           # input mode i -> output mode perm[i]
+    P = np.zeros((m, m))
+    for i, j in enumerate(perm):
+        P[j, i] = 1.0
+    target = [0] * m
+    for i, si in enumerate(s):
+        target[perm[i]] += si
+    p = oracle.probabilities(P, s, out)
+    assert p[tuples.index(tuple(target))] == pytest.approx(1.0, abs=1e-15)
+
+
+@pytest.mark.parametrize("m,n", [(6, 3), (5, 4), (8, 4), (8, 3)])
+def test_haar_probabilities_sum_to_one(m, n):
+    rng = np.random.default_rng(100 + m + n)
+    U = workloads.haar_unitaries(m, 1, rng)[0]
+    s = [1] * n + [0] * (m - n) if n <= m else None
+    p = oracle.probabilities(U, s)
+    assert abs(p.sum() - 1.0) <= 1e-12
+    assert np.all(p >= 0)
+
+
+@pytest.mark.parametrize("m,n", [(4, 4), (6, 3), (8, 4)])
+def test_fourier_suppression_law(m, n):
+    # U_jk = e^{2 pi i jk/m}/sqrt(m); photons in modes 0, m/n, 2m/n, ...:
+    # p(t) = 0 whenever sum_j j t_j is not 0 mod n.
+    F = np.exp(2j * np.pi * np.outer(np.arange(m), np.arange(m)) / m) / np.sqrt(m)
+    s = [0] * m
+    for l in range(n):
+        s[l * m // n] = 1
+    out = oracle.enumerate_fock(m, n)
+    p = oracle.probabilities(F, s, out)
+    weight = (out * np.arange(m)[None, :]).sum(axis=1)
+    forbidden = (weight % n) != 0
+    assert forbidden.any()
+    assert np.all(p[forbidden] <= 1e-14)
+    assert abs(p.sum() - 1.0) < 1e-12
+
+
+def test_mean_photon_number_closed_form():
+    rng = np.random.default_rng(11)
+    m, s = 7, [1, 0, 2, 0, 1, 0, 0]
+    U = workloads.haar_unitaries(m, 1, rng)[0]
+    out = oracle.enumerate_fock(m, 4)
+    p = oracle.probabilities(U, s, out)
+    lhs = (out * p[:, None]).sum(axis=0)
+    rhs = (np.abs(U) ** 2) @ np.array(s, dtype=float)
+    assert np.allclose(lhs, rhs, atol=1e-13)
+
+
+def _fock_amplitudes_by_expansion(U, s):
+    """Independent brute force: expand prod_k (sum_j U[j, c_k] a_j^dag) |0> as a
+    polynomial in the creation operators, then normalise the monomials."""
+    m = U.shape[0]
+    cols = [i for i in range(m) for _ in range(s[i])]
+    poly = {tuple([0] * m): 1.0 + 0j}
+    for c in cols:
+        nxt = {}
+        for mono, coef in poly.items():
+            for j in range(m):
+                t = list(mono)
+                t[j] += 1
+                t = tuple(t)
+                nxt[t] = nxt.get(t, 0) + coef * U[j, c]
+        poly = nxt
+    sf = np.prod([math.factorial(x) for x in s])
+    return {t: coef * math.sqrt(np.prod([math.factorial(x) for x in t])) / math.sqrt(sf) for t, coef in poly.items()}
+
+
+@pytest.mark.parametrize("m,s", [(3, [1, 1, 1]), (4, [2, 0, 1, 0]), (5, [0, 3, 0, 0, 1])])
+def test_amplitudes_match_operator_expansion(m, s):
+    rng = np.random.default_rng(sum(s) + m)
+    U = workloads.haar_unitaries(m, 1, rng)[0]
+    out = oracle.enumerate_fock(m, sum(s))
+    a = oracle.amplitudes(U, s, out)
+    ref = _fock_amplitudes_by_expansion(U, s)
+    for t, amp in zip(out, a):
+        assert abs(amp - ref[tuple(t)]) < 1e-13
+
+
+def test_photon_number_spectrum_of_one_data_phase():
+    # Eq. (1): U(x) = W2 S(x) W1 with S(x) = e^{i x n_1}; every p(t) is a
+    # trigonometric polynomial in x whose frequencies satisfy |w| <= n, and with
+    # universal W1, W2 the top frequency n is present.
+    m, n = 5, 3
+    rng = np.random.default_rng(5)
+    W1, W2 = workloads.haar_unitaries(m, 2, rng)
+    s = [1, 1, 1, 0, 0]
+    N = 4 * n + 2
+    xs = 2 * np.pi * np.arange(N) / N
+    out = oracle.enumerate_fock(m, n)
+    freqs = np.fft.fftfreq(N, d=1.0 / N)
+
+    def spectrum(Ufun):
+        P = np.array([oracle.probabilities(Ufun(x), s, out) for x in xs])
+        return np.fft.fft(P, axis=0) / N
+
+    S = lambda x: np.diag([np.exp(1j * x)] + [1.0] * (m - 1))
+    spec = spectrum(lambda x: W2 @ S(x) @ W1)
+    assert np.abs(spec[np.abs(freqs) > n]).max() < 1e-12
+    assert np.abs(spec[np.abs(freqs) == n]).max() > 1e-6
+    # the same bound through the Clements mesh with one data phase
+    theta = rng.uniform(0, 2 * np.pi, m * (m - 1))
+    spec = spectrum(lambda x: oracle.mesh_unitary(m, theta, [x]))
+    assert np.abs(spec[np.abs(freqs) > n]).max() < 1e-12
+
+
+# ---------------------------------------------------------------- mesh
+
+def test_mzi_closed_form():
+    # B diag(e^{i th},1) B diag(e^{i ph},1) = i e^{i th/2} [[s, c],[c, -s]] diag(e^{i ph}, 1)
+    for th, ph in [(0.3, 1.1), (2.0, -0.7), (np.pi, 0.2), (0.0, 3.0)]:
+        sn, cs = np.sin(th / 2), np.cos(th / 2)
+        closed = 1j * np.exp(1j * th / 2) * np.array([[sn, cs], [cs, -sn]]) @ np.diag([np.exp(1j * ph), 1])
+        assert np.allclose(oracle.mzi(th, ph), closed, atol=1e-15)
+
+
+def test_mzi_cross_and_bar():
+    T0 = oracle.mzi(0.0, 0.4)
+    assert abs(abs(T0[0, 1]) - 1) < 1e-15 and abs(T0[0, 0]) < 1e-15
+    Tp = oracle.mzi(np.pi, 0.4)
+    assert abs(abs(Tp[0, 0]) - 1) < 1e-15 and abs(Tp[0, 1]) < 1e-15
+
+
+def test_mesh_m2_and_m3_brute_force():
+    rng = np.random.default_rng(1)
+    th2 = rng.uniform(0, 2 * np.pi, 2)
+    # m=2: two columns, only column 0 holds an MZI (k=0); column 1 has k=1 > m-2
+    assert oracle.mesh_layout(2) == [(0, 0)]
+    assert np.allclose(oracle.mesh_unitary(2, th2), oracle.mzi(*th2))
+    # m=3: columns 0 (k=0), 1 (k=1), 2 (k=0)
+    th3 = rng.uniform(0, 2 * np.pi, 6)
+    assert oracle.mesh_layout(3) == [(0, 0), (1, 1), (2, 0)]
+
+    def e01(T):
+        return np.array([[T[0, 0], T[0, 1], 0], [T[1, 0], T[1, 1], 0], [0, 0, 1]])
+
+    def e12(T):
+        return np.array([[1, 0, 0], [0, T[0, 0], T[0, 1]], [0, T[1, 0], T[1, 1]]])
+    U = e01(oracle.mzi(th3[4], th3[5])) @ e12(oracle.mzi(th3[2], th3[3])) @ e01(oracle.mzi(th3[0], th3[1]))
+    assert np.allclose(oracle.mesh_unitary(3, th3), U, atol=1e-15)
+    # data screen after column m//2 = 1 (between MZI 0 and MZI 1)
+    d = rng.uniform(0, 2 * np.pi, 3)
+    S = np.diag(np.exp(1j * d))
+    U = e01(oracle.mzi(th3[4], th3[5])) @ e12(oracle.mzi(th3[2], th3[3])) @ S @ e01(oracle.mzi(th3[0], th3[1]))
+    assert np.allclose(oracle.mesh_unitary(3, th3, d), U, atol=1e-15)
+
+
+@pytest.mark.parametrize("m", [2, 5, 12, 16])
+def test_mesh_is_unitary_and_counts(m):
+    rng = np.random.default_rng(m)
+    th = rng.uniform(0, 2 * np.pi, m * (m - 1))
+    assert len(oracle.mesh_layout(m)) == m * (m - 1) // 2
+    U = oracle.mesh_unitary(m, th, rng.uniform(0, 1, m))
+    assert np.abs(U @ U.conj().T - np.eye(m)).max() < 1e-14
+
+
+# ---------------------------------------------------------------- threshold
+
+def test_threshold_patterns_and_sum():
+    m, n = 6, 3
+    pats = oracle.threshold_patterns(m, n)
+    assert len(pats) == sum(math.comb(m, k) for k in range(1, n + 1))
+    assert pats[:m] == [(j,) for j in range(m)]
+    assert pats[m:m + 3] == [(0, 1), (0, 2), (1, 2)]  # colex
+    rng = np.random.default_rng(2)
+    U = workloads.haar_unitaries(m, 1, rng)[0]
+    out = oracle.enumerate_fock(m, n)
+    p = oracle.probabilities(U, [1, 1, 1, 0, 0, 0], out)
+    q = oracle.threshold_probs(p, out, m, n)
+    assert abs(q.sum() - 1.0) < 1e-12
+    # brute force: for each pattern, sum over outputs with exactly that support
+    for idx, pat in enumerate(pats):
+        mask = np.all((out > 0) == np.isin(np.arange(m), pat)[None, :], axis=1)
+        assert abs(q[idx] - p[mask].sum()) < 1e-15
+    # a single photon: threshold = PNR
+    out1 = oracle.enumerate_fock(m, 1)
+    p1 = oracle.probabilities(U, [0, 0, 1, 0, 0, 0], out1)
+    assert np.allclose(oracle.threshold_probs(p1, out1, m, 1), p1)
+
+
+# ---------------------------------------------------------------- gradients
+
+@pytest.mark.parametrize("m,s", [(4, [1, 0, 1, 0]), (5, [1, 1, 0, 1, 0]), (6, [1, 0, 2, 0, 0, 0])])
+def test_fd_gradient_matches_permanent_minor_gradient(m, s):
+    rng = np.random.default_rng(40 + m)
+    th = rng.uniform(0, 2 * np.pi, m * (m - 1))
+    d = rng.uniform(0, np.pi, m) * rng.standard_normal(m)
+    K = oracle.fock_dim(m, sum(s))
+    c = rng.standard_normal(K)
+    gt_fd, gd_fd = oracle.fd_grad_phases(m, th, d, s, c)
+    gt_an, gd_an = oracle.analytic_grad_phases(m, th, d, s, c)
+    scale = max(np.abs(gt_an).max(), 1e-3)
+    assert np.abs(gt_fd - gt_an).max() < 1e-7 * scale * 100
+    assert np.abs(gd_fd - gd_an).max() < 1e-7 * scale * 100
+
+
+def test_grad_U_minors_against_wirtinger_fd():
+    # dU = dL/dRe U + i dL/dIm U, checked entrywise by FD on Re and Im parts.
+    rng = np.random.default_rng(9)
+    m, s = 4, [1, 1, 0, 1]
+    U = workloads.haar_unitaries(m, 1, rng)[0]
+    out = oracle.enumerate_fock(m, 3)
+    c = rng.standard_normal(out.shape[0])
+    dU = oracle.grad_U_minors(U, s, c, out)
+    h = 1e-6
+    for j, i in itertools.product(range(m), range(m)):
+        E = np.zeros((m, m)); E[j, i] = 1
+        gr = (oracle.loss(U + h * E, s, c, out) - oracle.loss(U - h * E, s, c, out)) / (2 * h)
+        gi = (oracle.loss(U + 1j * h * E, s, c, out) - oracle.loss(U - 1j * h * E, s, c, out)) / (2 * h)
+        assert abs(dU[j, i] - (gr + 1j * gi)) < 1e-8
