@@ -1,0 +1,350 @@
+"""Benchmark: one training step of the m=16, n=8 photonic layer per iteration.
+
+Step (all on the GPU, through libslos.so):
+  mesh_unitary        : 256 Clements meshes (240 shared phases + 16 data phases) -> U
+  slos_forward        : 490314-state output distribution per mesh, activations kept
+                        (checkpointed: every other photon-number layer)
+  slos_backward       : loss sum_t c_t p(t), reverse recursion -> dL/dU
+  mesh_unitary_backward: dL/dU -> dL/dtheta (summed over the batch), dL/ddata
+Metric: distributions/s (forward + backward), whole job.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(Ryser permanents + permanent-minor gradients) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2602_11092_gb300 import workloads  # noqa: E402
+
+METRIC = "SLOS distributions/s fwd+bwd"
+WORKLOAD = "train16"
+M, N, BATCH = 16, 8, 256
+CKPT_BUDGET = 2_000_000  # bytes per instance -> checkpoint stride 2
+
+
+def layered_bytes_per_distribution(m: int, n: int) -> float:
+    """Forward + backward, every layer written once and read once:
+    40 * sum_{k<n} |F_k| + 24 * |F_n| bytes."""
+    F = [workloads.fock_dim(m, k) for k in range(n + 1)]
+    return 40.0 * sum(F[:n]) + 24.0 * F[n]
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2602_11092_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        h.update(fn.encode())
+        h.update(open(os.path.join(d, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it still
+    matches the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("csrc_hash") != csrc_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------- CPU oracle
+
+def oracle_step_sample(seconds_target: float = 12.0):
+    """Time the oracle (as it stands) on a bounded sample of one distribution:
+    forward probabilities by Ryser and dL/dU by permanent minors over a seeded
+    subset of outputs, plus the full mesh chain rule; extrapolated linearly in
+    the number of outputs.  Returns (distributions/s, cores, sample text)."""
+    import oracle
+
+    w = workloads.train16(batch=1)
+    mb = w["mesh"]
+    K = workloads.fock_dim(M, N)
+    rng = np.random.default_rng(7)
+    cores = oracle.default_threads()
+    # calibrate on a small subset, then size the sample for ~seconds_target
+    S = 200
+    for _ in range(3):
+        pos = np.sort(rng.choice(K, size=S, replace=False))
+        outs = oracle.enumerate_fock(M, N, pos)
+        U = oracle.mesh_unitary(M, mb.theta, mb.data[0])
+        t0 = time.perf_counter()
+        p = oracle.probabilities(U, w["s"], outs)
+        dU = oracle.grad_U_minors(U, w["s"], w["c"][pos], outs)
+        dt = time.perf_counter() - t0
+        if dt > 0.25 * seconds_target or S >= K:
+            break
+        S = min(K, int(S * max(2.0, 0.6 * seconds_target / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.phase_grad_from_dU(M, mb.theta, mb.data[0], dU)
+    t_chain = time.perf_counter() - t0
+    t_dist = dt * K / S + t_chain
+    sample = (f"1 distribution of the m=16,n=8 layer: Ryser forward + permanent-minor dL/dU over {S} of {K} "
+              f"seeded outputs ({dt:.1f} s), extrapolated x{K / S:.0f}, plus the mesh chain rule ({t_chain:.2f} s)")
+    return 1.0 / t_dist, cores, sample
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals = []
+    for _ in range(args.warmup):
+        oracle_step_sample(seconds_target=3.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, cores, sample = oracle_step_sample(seconds_target=8.0)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "distributions/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "m=16 n=8 photonic layer training step (fwd+bwd), CPU FP64 oracle",
+                   "global_batch": 1, "modes": M, "photons": N},
+        "cpu_baseline": {"value": value, "unit": "distributions/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "distributions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2602_11092_gb300 as pkg
+    B = pkg.load()
+
+    w = workloads.train16(batch=BATCH, seed=workloads.SEED_BASE + 2 + 1000 * rank)
+    mb = w["mesh"]
+    theta = torch.tensor(mb.theta, dtype=torch.float32, device=dev)
+    data = torch.tensor(mb.data, dtype=torch.float32, device=dev)
+    c = torch.tensor(w["c"], dtype=torch.float32, device=dev)
+    plan = B.Plan(M, w["s"], B.PNR, mem_budget_bytes=CKPT_BUDGET)
+    ws = plan.workspace(BATCH, training=True, device=dev)
+    probs = torch.empty((BATCH, plan.n_outputs), dtype=torch.float32, device=dev)
+    U = torch.empty((BATCH, M, M), dtype=torch.complex64, device=dev)
+    dU = torch.empty_like(U)
+    stream = torch.cuda.current_stream()
+
+    def step(theta, data, c):
+        B.mesh_unitary(M, theta, data, BATCH, out=U)
+        plan.forward(U, B.PROBS, save_for_backward=True, workspace=ws, out=probs)
+        plan.backward(U, c, ws, B.PROBS, dU=dU)
+        return B.mesh_unitary_backward(M, theta, data, BATCH, dU)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        step(theta, data, c)
+    plan.sync_status()
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    B.profile_reset()
+    B.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(theta, data, c)
+    e1.record(stream)
+    barrier()
+    B.profile_enable(False)
+    launches = B.launch_count()
+    prof = B.profile_collect()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+
+    # end to end through the public API: inputs from pinned host memory, result back
+    theta_h = torch.tensor(mb.theta, dtype=torch.float32).pin_memory()
+    data_h = torch.tensor(mb.data, dtype=torch.float32).pin_memory()
+    c_h = torch.tensor(w["c"], dtype=torch.float32).pin_memory()
+    dth_h = torch.empty(M * (M - 1), dtype=torch.float32).pin_memory()
+    dd_h = torch.empty((BATCH, M), dtype=torch.float32).pin_memory()
+    theta_d, data_d, c_d = torch.empty_like(theta), torch.empty_like(data), torch.empty_like(c)
+
+    def e2e_step():
+        theta_d.copy_(theta_h, non_blocking=True)
+        data_d.copy_(data_h, non_blocking=True)
+        c_d.copy_(c_h, non_blocking=True)
+        dth, dd = step(theta_d, data_d, c_d)
+        dth_h.copy_(dth, non_blocking=True)
+        dd_h.copy_(dd, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms_e2e], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_e2e = float(t.item())
+    h2d = (theta_h.numel() + data_h.numel() + c_h.numel()) * 4
+    d2h = (dth_h.numel() + dd_h.numel()) * 4
+
+    peak, peak_kind = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, tot_ms, tot_bytes) = dom
+    achieved = tot_bytes / (tot_ms * 1e-3) / 1e9
+    step_bytes = layered_bytes_per_distribution(M, N) * BATCH
+    value = world * BATCH / (ms * 1e-3)
+    kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
+                   "gbs": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None} for k, v in prof.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = oracle_step_sample(seconds_target=12.0)
+        cpu = {"value": v, "unit": "distributions/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "distributions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64/f32", "data": "synthetic",
+        "config": {"workload": "m=16 n=8 photonic layer training step (mesh -> SLOS fwd -> loss sum c_t p_t -> "
+                               "SLOS bwd -> mesh bwd), 240 shared + 16 data phases, checkpoint stride "
+                               f"{plan.checkpoint_stride}",
+                   "global_batch": BATCH * world, "per_gpu_batch": BATCH, "modes": M, "photons": N,
+                   "fock_states": plan.n_outputs, "parallelism": f"replicas x{world}" if world > 1 else "single",
+                   "l2": "working set > L2 (probs 502 MB/step), no flush needed"},
+        "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": ncu_traffic(name),
+                     "launches_per_step": nl / args.steps},
+        "step_hbm": {"layered_bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
+                     "frac": step_bytes / (ms * 1e-3) / 1e9 / peak},
+        "kernels": kernels,
+        "e2e": {"value": world * BATCH / (ms_e2e * 1e-3), "unit": "distributions/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

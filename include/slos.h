@@ -1,0 +1,230 @@
+/*
+ * libslos — batched strong simulation of linear-optical layers on one GPU.
+ *
+ * C ABI.  Plain pointers and sizes only; no framework types.  Every device
+ * pointer is owned by the caller (allocate it however you like); a plan owns
+ * only its small device-side status word.  Every call that takes a `stream`
+ * (a cudaStream_t passed as void*, NULL = legacy default stream) is
+ * asynchronous on that stream, allocates nothing and does not synchronise, so
+ * it can be captured in a CUDA graph.  Errors are returned as status codes and
+ * never thrown; `slos_last_error()` gives a message for the calling thread.
+ *
+ * Physics (Sec. II-A.1 "Essentials of linear optics"): an n-photon Fock state
+ * |s> = |s_1..s_m> over m modes evolves through an m x m unitary U; the
+ * amplitude of output Fock state t is
+ *      <t|U|s> = Per(U[rows(t), cols(s)]) / sqrt(prod_j t_j! prod_i s_i!),
+ * and there are C(m+n-1, n) output states.  The library computes all of them
+ * at once by the photon-by-photon recursion of Sec. II-A.2/II-A.3 (SLOS): with
+ * the input photons in modes c_1 <= ... <= c_n,
+ *      a_0 = 1 on the vacuum,
+ *      a_k(t) = sum_{j : t_j > 0} U[j, c_k] * a_{k-1}(t - e_j),
+ * so a_n(t) = Per(...)/prod t_j!, p(t) = |a_n(t)|^2 prod t_j! / prod s_i!.
+ *
+ * Conventions used by every call:
+ *   complex64  interleaved (re, im) float32.
+ *   U          complex64 [batch][m][m] row-major, U[b][j][i] = U_{j,i}: input
+ *              mode i is mapped to sum_j U_{j,i} |j>.
+ *   outputs    index of Fock state t = its position in descending
+ *              lexicographic order over compositions of n into m parts
+ *              (first (n,0,...,0), last (0,...,0,n)).
+ *   threshold  outcome b = set of occupied modes, 1 <= |b| <= min(n, m),
+ *              ordered by |b| ascending then by colex rank of the subset;
+ *              q(b) = sum of p(t) over t whose occupied set is b.
+ *   gradients  PyTorch convention for complex tensors:
+ *              dZ = dL/dRe Z + i dL/dIm Z.
+ *   limits     2 <= m <= 24, 1 <= n <= 12, C(m+n-1, n) < 2^31; larger
+ *              problems return SLOS_ERR_UNSUPPORTED.
+ */
+#ifndef SLOS_H
+#define SLOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slos_plan_s *slos_plan_t;
+
+typedef enum {
+    SLOS_OK = 0,
+    SLOS_ERR_INVALID_ARG = 1,
+    SLOS_ERR_UNSUPPORTED = 2,
+    SLOS_ERR_OOM = 3,
+    SLOS_ERR_CUDA = 4,
+    SLOS_ERR_TIMEOUT = 5,
+    SLOS_ERR_INTERNAL = 6
+} slos_status_t;
+
+typedef enum { SLOS_DETECT_PNR = 0, SLOS_DETECT_THRESHOLD = 1 } slos_detection_t;
+typedef enum { SLOS_OUT_PROBS = 0, SLOS_OUT_AMPS = 1 } slos_output_t;
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *slos_last_error(void);
+
+/* Library version string. */
+const char *slos_version(void);
+
+/* ----------------------------------------------------------------------
+ * Interferometer mesh -> unitary (Sec. II-A.3: trainable parameters are the
+ * phases of the physical components; Sec. II-C.1: U(x, theta) =
+ * W2(theta2) S(x) W1(theta1) with data phases between two trainable
+ * interferometers).
+ *
+ * Mesh: rectangular (Clements) layout of m columns; column c holds a
+ * Mach-Zehnder interferometer on modes (k, k+1) for k = c mod 2, c mod 2 + 2,
+ * ..., k <= m-2: m(m-1)/2 MZIs, P = m(m-1) phases.  MZI(theta, phi) =
+ * B diag(e^{i theta}, 1) B diag(e^{i phi}, 1) with B = [[1, i], [i, 1]]/sqrt 2.
+ * Phases are ordered column by column, k ascending, (theta, phi) per MZI;
+ * U = T_last ... T_first.  If n_data > 0 the data screen
+ * diag(e^{i x_0}, ..., e^{i x_{n_data-1}}, 1, ...) sits after the first
+ * `data_col` columns (0 <= data_col <= m).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int m;        /* modes, 2..24 */
+    int n_data;   /* data phases, 0..m, on modes 0..n_data-1 */
+    int data_col; /* number of mesh columns before the data screen */
+} slos_mesh_desc_t;
+
+/* theta: float32 device [batch][m(m-1)] with row stride theta_stride_b
+ *        floats (0 = one phase vector shared by the whole batch).
+ * data:  float32 device [batch][n_data] with row stride data_stride_b
+ *        (NULL allowed when n_data == 0).
+ * U:     complex64 device [batch][m][m], fully written. */
+slos_status_t mesh_unitary(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
+                           const float *data, int64_t data_stride_b, int batch, void *U, void *stream);
+
+/* Scratch bytes needed by mesh_unitary_backward for this shape. */
+slos_status_t mesh_unitary_backward_workspace(const slos_mesh_desc_t *desc, int batch,
+                                              int64_t theta_stride_b, size_t *bytes);
+
+/* Reverse sweep through the mesh.  dU: complex64 device [batch][m][m].
+ * dtheta: float32 device; [m(m-1)] (summed over the batch, in a fixed order)
+ * when theta_stride_b == 0, otherwise [batch][m(m-1)].  ddata: float32 device
+ * [batch][n_data] (NULL allowed when n_data == 0).  Both outputs are
+ * overwritten.  workspace: device scratch of the size reported above (may be
+ * NULL when that size is 0). */
+slos_status_t mesh_unitary_backward(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
+                                    const float *data, int64_t data_stride_b, int batch, const void *dU,
+                                    float *dtheta, float *ddata, void *workspace, size_t workspace_bytes,
+                                    void *stream);
+
+/* ----------------------------------------------------------------------
+ * Plans (Sec. II-A.3: the transition structure between photon-number
+ * layers depends only on the input state and is built once; only the
+ * U-dependent coefficients change per call).
+ * ---------------------------------------------------------------------- */
+
+/* Build a plan for input Fock state `input_state` (host, m ints summing to n).
+ * mem_budget_bytes: per-instance budget for the activations that
+ * slos_forward(save_for_backward=1) keeps for slos_backward; 0 = keep every
+ * photon-number layer.  With a budget, only every s-th layer below n-1 is
+ * kept (s as small as fits) and the others are recomputed in the backward
+ * pass.  Allocates a 64-byte device status word on the current device. */
+slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t detection,
+                        size_t mem_budget_bytes, slos_plan_t *out);
+
+/* n_outputs: values per instance written by slos_forward (PNR: C(m+n-1, n);
+ * threshold: sum_{k=1}^{min(n,m)} C(m, k)).  fock_dim: C(m+n-1, n).
+ * checkpoint_stride: the s chosen from the budget (1 = every layer kept). */
+slos_status_t slos_plan_query(slos_plan_t plan, int64_t *n_outputs, int64_t *fock_dim, int *checkpoint_stride);
+
+/* Device scratch bytes that slos_forward / slos_backward need for `batch`
+ * instances.  training = 0: forward only; training = 1: forward with
+ * save_for_backward and the matching backward (same buffer for both). */
+slos_status_t slos_workspace_bytes(slos_plan_t plan, int batch, int training, size_t *bytes);
+
+/* Forward pass for a batch of unitaries (all with this plan's m, n, input).
+ * out: PNR + SLOS_OUT_PROBS  -> float32 [batch][n_outputs] probabilities;
+ *      PNR + SLOS_OUT_AMPS   -> complex64 [batch][n_outputs] amplitudes <t|U|s>;
+ *      threshold (PROBS only) -> float32 [batch][n_outputs] q(b).
+ * save_for_backward = 1 keeps the activations slos_backward needs inside
+ * `workspace` (sized with training = 1); the caller must hand the same
+ * workspace, untouched, to slos_backward. */
+slos_status_t slos_forward(slos_plan_t plan, const void *U, int batch, slos_output_t output, void *out,
+                           int save_for_backward, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Backward pass.  dout: gradient of the loss w.r.t. slos_forward's output,
+ * float32 (probabilities / threshold) or complex64 (amplitudes), row stride
+ * dout_stride_b elements between instances (0 = the same row for every
+ * instance).  dU: complex64 device [batch][m][m], fully overwritten
+ * (columns of modes without input photons are zero). */
+slos_status_t slos_backward(slos_plan_t plan, const void *U, int batch, slos_output_t output, const void *dout,
+                            int64_t dout_stride_b, void *dU, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Reads the plan's device status word (waits for `stream`), clears it, and
+ * returns SLOS_ERR_TIMEOUT / SLOS_ERR_INTERNAL if a kernel reported one. */
+slos_status_t slos_sync_status(slos_plan_t plan, void *stream);
+
+slos_status_t slos_plan_destroy(slos_plan_t plan);
+
+/* ----------------------------------------------------------------------
+ * Uneven batches: instances with different (m, n, input, detection) in one
+ * persistent launch.  Instances are packed: U of instance i is complex64
+ * [m_i][m_i] at element offset u_offset[i]; its output is float32 [K_i] at
+ * element offset out_offset[i] (PNR: probabilities, threshold: q(b)).
+ * ---------------------------------------------------------------------- */
+slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int *const *input_states,
+                                const slos_detection_t *detection, slos_plan_t *out);
+
+/* u_offsets / out_offsets: host arrays of count + 1 int64 (the last entry is
+ * the total).  workspace_bytes: device scratch for slos_batched_forward. */
+slos_status_t slos_batched_query(slos_plan_t plan, int64_t *u_offsets, int64_t *out_offsets,
+                                 size_t *workspace_bytes);
+
+/* One launch of a persistent kernel over every (instance, layer, tile) work
+ * item; graph-capturable.  Waits between layers are bounded: a wait that runs
+ * out sets the plan's status word (read it with slos_sync_status). */
+slos_status_t slos_batched_forward(slos_plan_t plan, const void *U_packed, float *out_packed, void *workspace,
+                                   size_t workspace_bytes, void *stream);
+
+/* Times the launch configurations of slos_batched_forward on this GPU and
+ * keeps the fastest in the plan; results are cached in the JSON file
+ * `cache_path` (NULL = no cache), keyed by device name and problem shape. */
+slos_status_t slos_batched_autotune(slos_plan_t plan, const void *U_packed, float *out_packed, void *workspace,
+                                    size_t workspace_bytes, const char *cache_path, void *stream);
+
+/* ----------------------------------------------------------------------
+ * Index arithmetic, exposed for exact (bit-for-bit) testing.
+ * ---------------------------------------------------------------------- */
+
+/* Host: rank of composition t (m ints summing to k) in descending-lex order. */
+int64_t slos_host_rank(int m, const int *t);
+/* Host: inverse of slos_host_rank; writes m ints. */
+slos_status_t slos_host_unrank(int m, int k, int64_t rank, int *t);
+
+/* Device: for ranks [first, first + count) of layer k (k photons, m modes)
+ * write the composition (uint8 [count][m]) and the parent index
+ * rank_{k-1}(t - e_j) for every mode j (int32 [count][m], -1 where t_j = 0),
+ * computed by the same device code the SLOS kernels use.  Either output may
+ * be NULL. */
+slos_status_t slos_device_index_table(int m, int k, int64_t first, int64_t count, uint8_t *compositions,
+                                      int32_t *parents, void *stream);
+
+
+/* ----------------------------------------------------------------------
+ * Tracing.  Every kernel the library launches increments a process-wide
+ * counter.  With profiling enabled, each launch is also bracketed by two CUDA
+ * events recorded on its own stream and tagged with a name and the number of
+ * algorithmic bytes the launch moves (layered model: every photon-number
+ * layer written once and read once, complex64 amplitudes, float32
+ * probabilities).  Do not enable it while capturing a CUDA graph.
+ * ---------------------------------------------------------------------- */
+slos_status_t slos_profile_enable(int enable);
+/* Drops every recorded launch and resets the launch counter. */
+slos_status_t slos_profile_reset(void);
+/* Kernels launched since the last reset (counted with or without profiling). */
+int64_t slos_launch_count(void);
+/* Waits for the recorded events and aggregates them by name.  Returns the
+ * number of distinct names; entry i (0 <= i < count) is read with
+ * slos_profile_entry. */
+int slos_profile_collect(void);
+slos_status_t slos_profile_entry(int i, char *name, size_t name_len, int64_t *launches, double *total_ms,
+                                 double *total_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLOS_H */

@@ -1,0 +1,312 @@
+"""ctypes binding of libslos.so (include/slos.h): argument marshalling only.
+
+Every computation happens inside the CUDA library; this module turns torch
+tensors into device pointers and the current torch stream into a
+cudaStream_t.  There is no CPU fallback: if the library is missing or a call
+fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libslos.so")
+
+PNR, THRESHOLD = 0, 1
+PROBS, AMPS = 0, 1
+
+_status_names = {0: "SLOS_OK", 1: "SLOS_ERR_INVALID_ARG", 2: "SLOS_ERR_UNSUPPORTED", 3: "SLOS_ERR_OOM",
+                 4: "SLOS_ERR_CUDA", 5: "SLOS_ERR_TIMEOUT", 6: "SLOS_ERR_INTERNAL"}
+
+
+class SlosError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_names.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n_data", ctypes.c_int), ("data_col", ctypes.c_int)]
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_sz = ctypes.c_size_t
+_int = ctypes.c_int
+
+# name -> argtypes (restype slos_status_t = int unless noted)
+_SIGNATURES = {
+    "slos_last_error": ([], ctypes.c_char_p),
+    "slos_version": ([], ctypes.c_char_p),
+    "mesh_unitary": ([ctypes.POINTER(MeshDesc), _vp, _i64, _vp, _i64, _int, _vp, _vp], _int),
+    "mesh_unitary_backward_workspace": ([ctypes.POINTER(MeshDesc), _int, _i64, ctypes.POINTER(_sz)], _int),
+    "mesh_unitary_backward": ([ctypes.POINTER(MeshDesc), _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp, _vp, _sz, _vp],
+                              _int),
+    "slos_plan": ([_int, _int, ctypes.POINTER(_int), _int, _sz, ctypes.POINTER(_vp)], _int),
+    "slos_plan_query": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_int)], _int),
+    "slos_workspace_bytes": ([_vp, _int, _int, ctypes.POINTER(_sz)], _int),
+    "slos_forward": ([_vp, _vp, _int, _int, _vp, _int, _vp, _sz, _vp], _int),
+    "slos_backward": ([_vp, _vp, _int, _int, _vp, _i64, _vp, _vp, _sz, _vp], _int),
+    "slos_sync_status": ([_vp, _vp], _int),
+    "slos_plan_destroy": ([_vp], _int),
+    "slos_batched_plan": ([_int, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(ctypes.POINTER(_int)),
+                           ctypes.POINTER(_int), ctypes.POINTER(_vp)], _int),
+    "slos_batched_query": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_sz)], _int),
+    "slos_batched_forward": ([_vp, _vp, _vp, _vp, _sz, _vp], _int),
+    "slos_batched_autotune": ([_vp, _vp, _vp, _vp, _sz, ctypes.c_char_p, _vp], _int),
+    "slos_host_rank": ([_int, ctypes.POINTER(_int)], _i64),
+    "slos_host_unrank": ([_int, _int, _i64, ctypes.POINTER(_int)], _int),
+    "slos_device_index_table": ([_int, _int, _i64, _i64, _vp, _vp, _vp], _int),
+    "slos_profile_enable": ([_int], _int),
+    "slos_profile_reset": ([], _int),
+    "slos_launch_count": ([], _i64),
+    "slos_profile_collect": ([], _int),
+    "slos_profile_entry": ([_int, ctypes.c_char_p, _sz, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double)], _int),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libslos.so (build it first with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libslos.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+def _check(status: int):
+    if status != 0:
+        raise SlosError(status, load().slos_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t: torch.Tensor, dtype, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+# ------------------------------------------------------------------ mesh
+
+def mesh_unitary(m: int, theta: torch.Tensor, data: torch.Tensor | None, batch: int, data_col: int | None = None,
+                 out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """theta: float32 [P] (shared) or [B, P]; data: float32 [B, n_data] or None."""
+    lib = load()
+    _need(theta, torch.float32, "theta")
+    n_data = 0 if data is None else data.shape[-1]
+    if data is not None:
+        _need(data, torch.float32, "data")
+    desc = MeshDesc(m, n_data, m // 2 if data_col is None else data_col)
+    if out is None:
+        out = torch.empty((batch, m, m), dtype=torch.complex64, device=theta.device)
+    ts = 0 if theta.dim() == 1 else theta.shape[-1]
+    ds = 0 if data is None else data.shape[-1]
+    _check(lib.mesh_unitary(ctypes.byref(desc), _ptr(theta), ts, _ptr(data), ds, batch, _ptr(out), _stream(stream)))
+    return out
+
+
+def mesh_unitary_backward(m: int, theta, data, batch: int, dU: torch.Tensor, data_col=None, stream=None):
+    lib = load()
+    _need(dU, torch.complex64, "dU")
+    n_data = 0 if data is None else data.shape[-1]
+    desc = MeshDesc(m, n_data, m // 2 if data_col is None else data_col)
+    shared = theta.dim() == 1
+    ts = 0 if shared else theta.shape[-1]
+    P = m * (m - 1)
+    dtheta = torch.empty((P,) if shared else (batch, P), dtype=torch.float32, device=dU.device)
+    ddata = torch.empty((batch, n_data), dtype=torch.float32, device=dU.device) if n_data else None
+    nbytes = ctypes.c_size_t()
+    _check(lib.mesh_unitary_backward_workspace(ctypes.byref(desc), batch, ts, ctypes.byref(nbytes)))
+    ws = torch.empty(max(1, nbytes.value), dtype=torch.uint8, device=dU.device)
+    ds = 0 if data is None else data.shape[-1]
+    _check(lib.mesh_unitary_backward(ctypes.byref(desc), _ptr(theta), ts, _ptr(data), ds, batch, _ptr(dU),
+                                     _ptr(dtheta), _ptr(ddata), _ptr(ws), nbytes.value, _stream(stream)))
+    return dtheta, ddata
+
+
+# ------------------------------------------------------------------ plans
+
+class Plan:
+    """Owns a slos_plan_t for one (m, n, input state, detection)."""
+
+    def __init__(self, m: int, input_state, detection: int = PNR, mem_budget_bytes: int = 0):
+        lib = load()
+        s = [int(x) for x in input_state]
+        assert len(s) == m
+        self.m, self.n, self.input_state, self.detection = m, sum(s), s, detection
+        arr = (ctypes.c_int * m)(*s)
+        h = ctypes.c_void_p()
+        _check(lib.slos_plan(m, self.n, arr, detection, mem_budget_bytes, ctypes.byref(h)))
+        self._h = h
+        K, F, st = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib.slos_plan_query(h, ctypes.byref(K), ctypes.byref(F), ctypes.byref(st)))
+        self.n_outputs, self.fock_dim, self.checkpoint_stride = K.value, F.value, st.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_bytes(self, batch: int, training: bool) -> int:
+        b = ctypes.c_size_t()
+        _check(load().slos_workspace_bytes(self._h, batch, 1 if training else 0, ctypes.byref(b)))
+        return b.value
+
+    def workspace(self, batch: int, training: bool, device="cuda") -> torch.Tensor:
+        return torch.empty(max(1, self.workspace_bytes(batch, training)), dtype=torch.uint8, device=device)
+
+    def forward(self, U: torch.Tensor, output: int = PROBS, save_for_backward: bool = False,
+                workspace: torch.Tensor | None = None, out: torch.Tensor | None = None, stream=None):
+        _need(U, torch.complex64, "U")
+        B = U.shape[0]
+        if workspace is None:
+            workspace = self.workspace(B, save_for_backward, U.device)
+        if out is None:
+            dt = torch.complex64 if output == AMPS else torch.float32
+            out = torch.empty((B, self.n_outputs), dtype=dt, device=U.device)
+        _check(load().slos_forward(self._h, _ptr(U), B, output, _ptr(out), 1 if save_for_backward else 0,
+                                   _ptr(workspace), workspace.numel(), _stream(stream)))
+        return out
+
+    def backward(self, U: torch.Tensor, dout: torch.Tensor, workspace: torch.Tensor, output: int = PROBS,
+                 dU: torch.Tensor | None = None, stream=None):
+        """dout: [B, K] or [K] (shared by the batch, stride 0)."""
+        B = U.shape[0]
+        stride = 0 if dout.dim() == 1 else dout.shape[-1]
+        if not dout.is_contiguous():
+            raise ValueError("dout must be contiguous")
+        if dU is None:
+            dU = torch.empty_like(U)
+        _check(load().slos_backward(self._h, _ptr(U), B, output, _ptr(dout), stride, _ptr(dU), _ptr(workspace),
+                                    workspace.numel(), _stream(stream)))
+        return dU
+
+    def sync_status(self, stream=None):
+        _check(load().slos_sync_status(self._h, _stream(stream)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.slos_plan_destroy(h)
+            self._h = None
+
+
+class BatchedPlan:
+    """Uneven batch of (m_i, n_i, input_i, detection_i) instances."""
+
+    def __init__(self, ms, ns, inputs, detections):
+        lib = load()
+        cnt = len(ms)
+        self.count = cnt
+        m_arr = (ctypes.c_int * cnt)(*ms)
+        n_arr = (ctypes.c_int * cnt)(*ns)
+        d_arr = (ctypes.c_int * cnt)(*detections)
+        self._rows = [(ctypes.c_int * len(s))(*s) for s in inputs]
+        rows = (ctypes.POINTER(ctypes.c_int) * cnt)(*[ctypes.cast(r, ctypes.POINTER(ctypes.c_int)) for r in self._rows])
+        h = ctypes.c_void_p()
+        _check(lib.slos_batched_plan(cnt, m_arr, n_arr, rows, d_arr, ctypes.byref(h)))
+        self._h = h
+        uo = (ctypes.c_int64 * (cnt + 1))()
+        oo = (ctypes.c_int64 * (cnt + 1))()
+        wb = ctypes.c_size_t()
+        _check(lib.slos_batched_query(h, uo, oo, ctypes.byref(wb)))
+        self.u_offsets = list(uo)
+        self.out_offsets = list(oo)
+        self.workspace_bytes = wb.value
+
+    def forward(self, U_packed, out_packed, workspace, stream=None):
+        _check(load().slos_batched_forward(self._h, _ptr(U_packed), _ptr(out_packed), _ptr(workspace),
+                                           workspace.numel(), _stream(stream)))
+        return out_packed
+
+    def autotune(self, U_packed, out_packed, workspace, cache_path=None, stream=None):
+        cp = cache_path.encode() if cache_path else None
+        _check(load().slos_batched_autotune(self._h, _ptr(U_packed), _ptr(out_packed), _ptr(workspace),
+                                            workspace.numel(), cp, _stream(stream)))
+
+    def sync_status(self, stream=None):
+        _check(load().slos_sync_status(self._h, _stream(stream)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.slos_plan_destroy(h)
+            self._h = None
+
+
+# ------------------------------------------------------------------ index tables
+
+def host_rank(m: int, t) -> int:
+    arr = (ctypes.c_int * m)(*[int(x) for x in t])
+    return load().slos_host_rank(m, arr)
+
+
+def host_unrank(m: int, k: int, rank: int):
+    arr = (ctypes.c_int * m)()
+    _check(load().slos_host_unrank(m, k, rank, arr))
+    return list(arr)
+
+
+def device_index_table(m: int, k: int, first: int, count: int, device="cuda", stream=None):
+    comp = torch.empty((count, m), dtype=torch.uint8, device=device)
+    par = torch.empty((count, m), dtype=torch.int32, device=device)
+    _check(load().slos_device_index_table(m, k, first, count, _ptr(comp), _ptr(par), _stream(stream)))
+    return comp, par
+
+
+# ------------------------------------------------------------------ tracing
+
+def profile_enable(on: bool = True):
+    _check(load().slos_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(load().slos_profile_reset())
+
+
+def launch_count() -> int:
+    return int(load().slos_launch_count())
+
+
+def profile_collect() -> dict:
+    """{kernel name: (launches, total_ms, total_algorithmic_bytes)}"""
+    lib = load()
+    n = lib.slos_profile_collect()
+    out = {}
+    buf = ctypes.create_string_buffer(128)
+    for i in range(n):
+        L, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        _check(lib.slos_profile_entry(i, buf, 128, ctypes.byref(L), ctypes.byref(ms), ctypes.byref(by)))
+        out[buf.value.decode()] = (L.value, ms.value, by.value)
+    return out

@@ -1,0 +1,666 @@
+// C-ABI entry points: plans, forward/backward orchestration, mesh calls and
+// the exact index tables.  Every stream operation is asynchronous; nothing
+// here allocates on the forward/backward path.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/slos.h"
+#include "common.cuh"
+#include "mesh.h"
+#include "plan.h"
+#include "profile.h"
+#include "slos_kernels.cuh"
+
+namespace slos {
+
+SLOS_DECLARE_LAUNCHERS(8)
+SLOS_DECLARE_LAUNCHERS(12)
+SLOS_DECLARE_LAUNCHERS(16)
+SLOS_DECLARE_LAUNCHERS(20)
+SLOS_DECLARE_LAUNCHERS(24)
+
+static thread_local std::string g_last_error;
+
+slos_status_t fail(slos_status_t st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+#define SLOS_CUDA(call)                                                                             \
+    do {                                                                                            \
+        cudaError_t e__ = (call);                                                                   \
+        if (e__ != cudaSuccess)                                                                     \
+            return fail(SLOS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__));     \
+    } while (0)
+
+static int mmax_for(int m) {
+    if (m <= 8) return 8;
+    if (m <= 12) return 12;
+    if (m <= 16) return 16;
+    if (m <= 20) return 20;
+    return 24;
+}
+
+cudaError_t launch_fwd(int m, const FwdArgs &a, int epi, bool save, int bx, cudaStream_t s) {
+    switch (mmax_for(m)) {
+        case 8: return slos_launch_fwd_m8(a, epi, save, bx, s);
+        case 12: return slos_launch_fwd_m12(a, epi, save, bx, s);
+        case 16: return slos_launch_fwd_m16(a, epi, save, bx, s);
+        case 20: return slos_launch_fwd_m20(a, epi, save, bx, s);
+        default: return slos_launch_fwd_m24(a, epi, save, bx, s);
+    }
+}
+cudaError_t launch_bwd(int m, const BwdArgs &a, int seed, int bx, cudaStream_t s) {
+    switch (mmax_for(m)) {
+        case 8: return slos_launch_bwd_m8(a, seed, bx, s);
+        case 12: return slos_launch_bwd_m12(a, seed, bx, s);
+        case 16: return slos_launch_bwd_m16(a, seed, bx, s);
+        case 20: return slos_launch_bwd_m20(a, seed, bx, s);
+        default: return slos_launch_bwd_m24(a, seed, bx, s);
+    }
+}
+cudaError_t launch_prep(int m, const PrepArgs &a, int bx, cudaStream_t s) {
+    switch (mmax_for(m)) {
+        case 8: return slos_launch_prep_m8(a, bx, s);
+        case 12: return slos_launch_prep_m12(a, bx, s);
+        case 16: return slos_launch_prep_m16(a, bx, s);
+        case 20: return slos_launch_prep_m20(a, bx, s);
+        default: return slos_launch_prep_m24(a, bx, s);
+    }
+}
+
+static cudaError_t init_device_once(int dev) {
+    static bool done[64] = {false};
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (done[dev]) return cudaSuccess;
+    cudaError_t e;
+    if ((e = slos_init_m8()) != cudaSuccess) return e;
+    if ((e = slos_init_m12()) != cudaSuccess) return e;
+    if ((e = slos_init_m16()) != cudaSuccess) return e;
+    if ((e = slos_init_m20()) != cudaSuccess) return e;
+    if ((e = slos_init_m24()) != cudaSuccess) return e;
+    done[dev] = true;
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------------ host index
+int64_t binom_host(int a, int e) {
+    if (e < 0 || a < 0 || e > a) return 0;
+    int64_t r = 1;
+    for (int i = 1; i <= e; ++i) r = r * (a - e + i) / i;
+    return r;
+}
+
+// rank(t) = sum_b C(p_b, m-1-b), p_b = distance of bar b from the string end.
+int64_t host_rank(int m, const int *t) {
+    int64_t r = 0;
+    int after = 0;  // stars after bar b
+    // p_b = (stars after bar b) + (bars after bar b) = R_b + (m-2-b)
+    for (int b = m - 2; b >= 0; --b) {
+        after += t[b + 1];
+        r += binom_host(after + (m - 2 - b), m - 1 - b);
+    }
+    return r;
+}
+
+void host_unrank(int m, int k, int64_t r, int *t) {
+    const int L = k + m - 1;
+    std::vector<int> p(m + 1);
+    int x = L - 1;
+    for (int b = 0; b < m - 1; ++b) {
+        const int e = m - 1 - b;
+        while (binom_host(x, e) > r) --x;
+        p[b] = x;
+        r -= binom_host(x, e);
+        --x;
+    }
+    for (int j = 0; j < m; ++j) {
+        const int hi = (j == 0) ? L : p[j - 1];
+        const int lo = (j < m - 1) ? p[j] : -1;
+        t[j] = hi - lo - 1;
+    }
+}
+
+// ------------------------------------------------------------------ layouts
+static int groups_for(int batch) { return (batch + kLanes - 1) / kLanes; }
+
+static int blocks_for(const slos_plan_s *p, int64_t states, int chunk, int NG) {
+    const int64_t nchunks = (states + chunk - 1) / chunk;
+    const int64_t need = (nchunks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int64_t target = std::max<int64_t>(1, (int64_t)p->sm_count * 4 / std::max(1, NG));
+    return (int)std::max<int64_t>(1, std::min(need, std::max<int64_t>(target, 1)));
+}
+
+constexpr int kChunkStore = 64;
+constexpr int kChunkFinal = 32;
+constexpr int kChunkBwd = 64;
+
+static Layout make_layout(const slos_plan_s *p, int batch, bool training) {
+    Layout L;
+    const int n = p->n;
+    const int NG = groups_for(batch);
+    const size_t row = (size_t)NG * kLanes * sizeof(float2);  // bytes per Fock state
+    L.layer.assign(n + 1, SIZE_MAX);
+    L.g[0] = L.g[1] = SIZE_MAX;
+    L.seedT = SIZE_MAX;
+    L.dupart.assign(n + 1, SIZE_MAX);
+    L.bwd_blocks.assign(n + 1, 0);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    if (!training) {
+        // ping-pong: layer k in buffer (n-1-k) % 2
+        size_t b0 = n >= 2 ? take(row * p->F[n - 1]) : SIZE_MAX;
+        size_t b1 = n >= 3 ? take(row * p->F[n - 2]) : SIZE_MAX;
+        for (int k = 1; k < n; ++k) L.layer[k] = ((n - 1 - k) % 2 == 0) ? b0 : b1;
+    } else {
+        // kept layers + one segment buffer of (stride-1) slots for the rest
+        int64_t fmax_ns = 0;
+        for (int k = 1; k < n; ++k) {
+            if (p->stored[k]) L.layer[k] = take(row * p->F[k]);
+            else fmax_ns = std::max(fmax_ns, p->F[k]);
+        }
+        L.layer[n] = take(row * p->F[n]);
+        std::vector<size_t> slot(std::max(1, p->stride - 1), SIZE_MAX);
+        if (fmax_ns > 0)
+            for (auto &s : slot) s = take(row * fmax_ns);
+        int base = 0;
+        for (int k = 1; k < n; ++k) {
+            if (p->stored[k]) {
+                base = k;
+            } else {
+                L.layer[k] = slot[k - base - 1];
+            }
+        }
+        if (n >= 2) L.g[0] = take(row * p->F[n - 1]);
+        if (n >= 3) L.g[1] = take(row * p->F[n - 2]);
+        L.seedT = take(row * p->F[n]);  // c64-sized: enough for either seed kind
+        for (int k = 1; k <= n; ++k) {
+            const int bx = blocks_for(p, p->F[k - 1], kChunkBwd, NG);
+            L.bwd_blocks[k] = bx;
+            L.dupart[k] = take((size_t)NG * bx * kLanes * p->m * sizeof(float2));
+        }
+    }
+    L.total = off;
+    return L;
+}
+
+static void fill_pat_off(const slos_plan_s *p, int *dst) {
+    for (int i = 0; i < kMaxPhotons + 2; ++i) dst[i] = p->pat_off[std::min(i, 15)];
+}
+
+// dU[b][j][i] = sum over layers k with c_k = i and over blocks of the partials.
+struct ReduceArgs {
+    const float2 *part[kMaxPhotons + 1];
+    int blocks[kMaxPhotons + 1];
+    int cols[kMaxPhotons + 1];
+    int n, m, B;
+    float2 *dU;
+};
+
+__global__ void dU_reduce_kernel(ReduceArgs a) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)a.B * a.m * a.m;
+    if (tid >= total) return;
+    const int i = (int)(tid % a.m);
+    const int j = (int)((tid / a.m) % a.m);
+    const int b = (int)(tid / ((int64_t)a.m * a.m));
+    const int grp = b / kLanes, lane = b % kLanes;
+    float2 s = make_float2(0.f, 0.f);
+    for (int k = 1; k <= a.n; ++k) {
+        if (a.cols[k] != i) continue;
+        const int bx = a.blocks[k];
+        const float2 *base = a.part[k] + ((int64_t)grp * bx * kLanes) * a.m;
+        for (int blk = 0; blk < bx; ++blk) {
+            const float2 v = base[((int64_t)blk * kLanes + lane) * a.m + j];
+            s.x += v.x;
+            s.y += v.y;
+        }
+    }
+    a.dU[tid] = s;
+}
+
+// Device index table (tests): same unrank / occupation / parent arithmetic as
+// the SLOS kernels, one thread per state.
+template <int MMAX>
+__global__ void index_table_kernel(int m, int k, int64_t first, int64_t count, uint8_t *comp, int32_t *par) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t c = first + i;
+    const int L = k + m - 1;
+    int p[MMAX];
+    unrank_bars<MMAX>(c, m, L, p);
+    int64_t S = 0;
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j) {
+        if (j < m) {
+            const int tj = occupation<MMAX>(j, m, L, p);
+            if (comp) comp[i * m + j] = (uint8_t)tj;
+            if (par) par[i * m + j] = tj > 0 ? (int32_t)(c - S) : -1;
+            if (j < m - 1) S += (int64_t)binom_m1(p[j], m - 2 - j);
+        }
+    }
+}
+
+}  // namespace slos
+
+using namespace slos;
+
+// ==================================================================== ABI
+extern "C" {
+
+const char *slos_last_error(void) { return g_last_error.c_str(); }
+const char *slos_version(void) { return "libslos 0.1 (sm_103a)"; }
+
+static slos_status_t check_mesh(const slos_mesh_desc_t *d, int batch) {
+    if (!d) return fail(SLOS_ERR_INVALID_ARG, "mesh desc is NULL");
+    if (d->m < 2 || d->m > kMaxModes) return fail(SLOS_ERR_UNSUPPORTED, "mesh: m must be in [2, 24]");
+    if (d->n_data < 0 || d->n_data > d->m) return fail(SLOS_ERR_INVALID_ARG, "mesh: n_data must be in [0, m]");
+    if (d->data_col < 0 || d->data_col > d->m) return fail(SLOS_ERR_INVALID_ARG, "mesh: data_col must be in [0, m]");
+    if (batch < 0) return fail(SLOS_ERR_INVALID_ARG, "mesh: negative batch");
+    return SLOS_OK;
+}
+
+slos_status_t mesh_unitary(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
+                           const float *data, int64_t data_stride_b, int batch, void *U, void *stream) {
+    slos_status_t st = check_mesh(desc, batch);
+    if (st != SLOS_OK) return st;
+    if (batch == 0) return SLOS_OK;
+    if (!theta || !U) return fail(SLOS_ERR_INVALID_ARG, "mesh_unitary: NULL theta or U");
+    if (desc->n_data > 0 && !data) return fail(SLOS_ERR_INVALID_ARG, "mesh_unitary: NULL data with n_data > 0");
+    MeshArgs a;
+    a.theta = theta;
+    a.theta_stride = theta_stride_b;
+    a.data = desc->n_data > 0 ? data : nullptr;
+    a.data_stride = data_stride_b;
+    a.U = reinterpret_cast<float2 *>(U);
+    a.m = desc->m;
+    a.n_data = desc->n_data;
+    a.data_col = desc->data_col;
+    a.B = batch;
+    {
+        ProfScope ps("mesh_fwd", (double)batch * 8.0 * desc->m * desc->m, (cudaStream_t)stream);
+        SLOS_CUDA(mesh_forward_launch(a, (cudaStream_t)stream));
+    }
+    return SLOS_OK;
+}
+
+slos_status_t mesh_unitary_backward_workspace(const slos_mesh_desc_t *desc, int batch, int64_t theta_stride_b,
+                                              size_t *bytes) {
+    slos_status_t st = check_mesh(desc, batch);
+    if (st != SLOS_OK) return st;
+    if (!bytes) return fail(SLOS_ERR_INVALID_ARG, "NULL bytes");
+    *bytes = theta_stride_b == 0 ? (size_t)batch * desc->m * (desc->m - 1) * sizeof(float) : 0;
+    return SLOS_OK;
+}
+
+slos_status_t mesh_unitary_backward(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
+                                    const float *data, int64_t data_stride_b, int batch, const void *dU,
+                                    float *dtheta, float *ddata, void *workspace, size_t workspace_bytes,
+                                    void *stream) {
+    slos_status_t st = check_mesh(desc, batch);
+    if (st != SLOS_OK) return st;
+    const int m = desc->m;
+    const int P = m * (m - 1);
+    if (batch == 0) {
+        if (theta_stride_b == 0 && dtheta) SLOS_CUDA(cudaMemsetAsync(dtheta, 0, P * sizeof(float), (cudaStream_t)stream));
+        return SLOS_OK;
+    }
+    if (!theta || !dU || !dtheta) return fail(SLOS_ERR_INVALID_ARG, "mesh_unitary_backward: NULL pointer");
+    if (desc->n_data > 0 && (!data || !ddata))
+        return fail(SLOS_ERR_INVALID_ARG, "mesh_unitary_backward: NULL data/ddata with n_data > 0");
+    size_t need = 0;
+    mesh_unitary_backward_workspace(desc, batch, theta_stride_b, &need);
+    if (workspace_bytes < need || (need > 0 && !workspace))
+        return fail(SLOS_ERR_INVALID_ARG, "mesh_unitary_backward: workspace too small");
+    MeshBwdArgs a;
+    a.theta = theta;
+    a.theta_stride = theta_stride_b;
+    a.data = desc->n_data > 0 ? data : nullptr;
+    a.data_stride = data_stride_b;
+    a.dU = reinterpret_cast<const float2 *>(dU);
+    a.dtheta = theta_stride_b == 0 ? reinterpret_cast<float *>(workspace) : dtheta;
+    a.dtheta_stride = P;
+    a.ddata = ddata;
+    a.m = m;
+    a.n_data = desc->n_data;
+    a.data_col = desc->data_col;
+    a.B = batch;
+    {
+        ProfScope ps("mesh_bwd", (double)batch * (8.0 * m * m + 4.0 * P), (cudaStream_t)stream);
+        SLOS_CUDA(mesh_backward_launch(a, theta_stride_b == 0 ? dtheta : nullptr, (cudaStream_t)stream));
+    }
+    return SLOS_OK;
+}
+
+slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t detection, size_t mem_budget_bytes,
+                        slos_plan_t *out) {
+    if (!out) return fail(SLOS_ERR_INVALID_ARG, "slos_plan: NULL out");
+    *out = nullptr;
+    if (!input_state) return fail(SLOS_ERR_INVALID_ARG, "slos_plan: NULL input_state");
+    if (m < 2 || m > kMaxModes) return fail(SLOS_ERR_UNSUPPORTED, "slos_plan: m must be in [2, 24]");
+    if (n < 1 || n > kMaxPhotons) return fail(SLOS_ERR_UNSUPPORTED, "slos_plan: n must be in [1, 12]");
+    if (detection != SLOS_DETECT_PNR && detection != SLOS_DETECT_THRESHOLD)
+        return fail(SLOS_ERR_INVALID_ARG, "slos_plan: unknown detection");
+    int tot = 0;
+    for (int i = 0; i < m; ++i) {
+        if (input_state[i] < 0) return fail(SLOS_ERR_INVALID_ARG, "slos_plan: negative occupation");
+        tot += input_state[i];
+    }
+    if (tot != n) return fail(SLOS_ERR_INVALID_ARG, "slos_plan: input_state does not hold n photons");
+    if (binom_host(m + n - 1, n) >= (int64_t)1 << 31)
+        return fail(SLOS_ERR_UNSUPPORTED, "slos_plan: Fock space too large (>= 2^31 states)");
+    slos_plan_s *p = new (std::nothrow) slos_plan_s();
+    if (!p) return fail(SLOS_ERR_OOM, "slos_plan: host allocation failed");
+    p->kind = 0;
+    p->m = m;
+    p->n = n;
+    p->s.assign(input_state, input_state + m);
+    for (int i = 0; i < m; ++i)
+        for (int q = 0; q < input_state[i]; ++q) p->cols.push_back(i);
+    p->det = detection;
+    p->F.resize(n + 1);
+    for (int k = 0; k <= n; ++k) p->F[k] = binom_host(m + k - 1, k);
+    double sf = 1.0;
+    for (int i = 0; i < m; ++i)
+        for (int q = 2; q <= input_state[i]; ++q) sf *= q;
+    p->inv_sfact = (float)(1.0 / sf);
+    memset(p->pat_off, 0, sizeof(p->pat_off));
+    {
+        int64_t acc = 0;
+        for (int i = 1; i <= std::min(n, m) && i < 16; ++i) {
+            p->pat_off[i] = (int)acc;
+            acc += binom_host(m, i);
+        }
+        p->K = detection == SLOS_DETECT_PNR ? p->F[n] : acc;
+    }
+    // checkpoint schedule: keep layers k = n-1, n-1-s, n-1-2s, ... (s minimal within budget)
+    auto bytes_for = [&](int s) {
+        int64_t states = p->F[n];  // a_n
+        int64_t fmax_ns = 0;
+        for (int k = 1; k < n; ++k) {
+            if ((n - 1 - k) % s == 0) states += p->F[k];
+            else fmax_ns = std::max(fmax_ns, p->F[k]);
+        }
+        states += (int64_t)(s - 1) * fmax_ns;
+        return (size_t)states * sizeof(float2);
+    };
+    int s = 1;
+    if (mem_budget_bytes > 0) {
+        while (s < n && bytes_for(s) > mem_budget_bytes) ++s;
+    }
+    p->stride = s;
+    p->stored.assign(n + 1, 0);
+    for (int k = 1; k < n; ++k) p->stored[k] = ((n - 1 - k) % s == 0);
+    p->stored[n] = 1;
+    p->batched = nullptr;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return fail(SLOS_ERR_CUDA, "slos_plan: no CUDA device");
+    }
+    cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    if (p->sm_count <= 0) p->sm_count = 148;
+    cudaError_t e = init_device_once(p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return fail(SLOS_ERR_CUDA, std::string("slos_plan: kernel attributes: ") + cudaGetErrorString(e));
+    }
+    if (cudaMalloc(&p->d_status, 64) != cudaSuccess) {
+        delete p;
+        return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the status word");
+    }
+    cudaMemset(p->d_status, 0, 64);
+    *out = p;
+    return SLOS_OK;
+}
+
+slos_status_t slos_plan_query(slos_plan_t p, int64_t *n_outputs, int64_t *fock_dim, int *checkpoint_stride) {
+    if (!p || p->kind != 0) return fail(SLOS_ERR_INVALID_ARG, "slos_plan_query: not a single-shape plan");
+    if (n_outputs) *n_outputs = p->K;
+    if (fock_dim) *fock_dim = p->F[p->n];
+    if (checkpoint_stride) *checkpoint_stride = p->stride;
+    return SLOS_OK;
+}
+
+slos_status_t slos_workspace_bytes(slos_plan_t p, int batch, int training, size_t *bytes) {
+    if (!p || p->kind != 0 || !bytes || batch < 0)
+        return fail(SLOS_ERR_INVALID_ARG, "slos_workspace_bytes: bad argument");
+    *bytes = batch == 0 ? 0 : make_layout(p, batch, training != 0).total;
+    return SLOS_OK;
+}
+
+static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws, const float2 *U, int batch, int k,
+                                      int epi, bool save, void *out, cudaStream_t s, bool recompute = false) {
+    const int NG = groups_for(batch);
+    FwdArgs a;
+    memset(&a, 0, sizeof(a));
+    a.prev = k >= 2 ? reinterpret_cast<const float2 *>(ws + Ly.layer[k - 1]) : nullptr;
+    a.next = (epi == EPI_STORE || save) ? reinterpret_cast<float2 *>(ws + Ly.layer[k]) : nullptr;
+    a.U = U;
+    a.out = out;
+    a.Fk = p->F[k];
+    a.Fprev = p->F[k - 1];
+    a.K = p->K;
+    a.m = p->m;
+    a.k = k;
+    a.col = p->cols[k - 1];
+    a.B = batch;
+    a.NG = NG;
+    a.chunk = epi == EPI_STORE ? kChunkStore : kChunkFinal;
+    a.inv_sfact = p->inv_sfact;
+    fill_pat_off(p, a.pat_off);
+    const int bx = blocks_for(p, a.Fk, a.chunk, NG);
+    // layered-model bytes: read a_{k-1}, write a_k and/or the output
+    double bytes = (k >= 2 ? 8.0 * a.Fprev : 0.0);
+    const char *name = recompute ? "slos_fwd_recompute" : "slos_fwd_layer";
+    if (epi == EPI_STORE) {
+        bytes += 8.0 * a.Fk;
+    } else {
+        name = "slos_fwd_final";
+        bytes += (epi == EPI_AMPS ? 8.0 : 4.0) * p->K + (save ? 8.0 * a.Fk : 0.0);
+    }
+    ProfScope ps(name, bytes * batch, s);
+    SLOS_CUDA(launch_fwd(p->m, a, epi, save, bx, s));
+    return SLOS_OK;
+}
+
+slos_status_t slos_forward(slos_plan_t p, const void *U, int batch, slos_output_t output, void *out,
+                           int save_for_backward, void *workspace, size_t workspace_bytes, void *stream) {
+    if (!p || p->kind != 0) return fail(SLOS_ERR_INVALID_ARG, "slos_forward: not a single-shape plan");
+    if (batch < 0) return fail(SLOS_ERR_INVALID_ARG, "slos_forward: negative batch");
+    if (output != SLOS_OUT_PROBS && output != SLOS_OUT_AMPS) return fail(SLOS_ERR_INVALID_ARG, "slos_forward: bad output");
+    if (output == SLOS_OUT_AMPS && p->det != SLOS_DETECT_PNR)
+        return fail(SLOS_ERR_INVALID_ARG, "slos_forward: amplitudes are only defined before detection (use PNR plan)");
+    if (batch == 0) return SLOS_OK;
+    if (!U || !out) return fail(SLOS_ERR_INVALID_ARG, "slos_forward: NULL U or out");
+    const bool save = save_for_backward != 0;
+    const Layout Ly = make_layout(p, batch, save);
+    if (workspace_bytes < Ly.total || (Ly.total > 0 && !workspace))
+        return fail(SLOS_ERR_INVALID_ARG, "slos_forward: workspace too small (" + std::to_string(workspace_bytes) +
+                                               " < " + std::to_string(Ly.total) + ")");
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = reinterpret_cast<char *>(workspace);
+    const float2 *Ud = reinterpret_cast<const float2 *>(U);
+    const int n = p->n;
+    if (p->det == SLOS_DETECT_THRESHOLD) SLOS_CUDA(cudaMemsetAsync(out, 0, (size_t)batch * p->K * sizeof(float), s));
+    for (int k = 1; k < n; ++k) {
+        slos_status_t st = launch_layer_fwd(p, Ly, ws, Ud, batch, k, EPI_STORE, true, nullptr, s);
+        if (st != SLOS_OK) return st;
+    }
+    const int epi = p->det == SLOS_DETECT_THRESHOLD ? EPI_THRESH : (output == SLOS_OUT_AMPS ? EPI_AMPS : EPI_PROBS);
+    return launch_layer_fwd(p, Ly, ws, Ud, batch, n, epi, save, out, s);
+}
+
+slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output_t output, const void *dout,
+                            int64_t dout_stride_b, void *dU, void *workspace, size_t workspace_bytes, void *stream) {
+    if (!p || p->kind != 0) return fail(SLOS_ERR_INVALID_ARG, "slos_backward: not a single-shape plan");
+    if (batch < 0) return fail(SLOS_ERR_INVALID_ARG, "slos_backward: negative batch");
+    if (output == SLOS_OUT_AMPS && p->det != SLOS_DETECT_PNR)
+        return fail(SLOS_ERR_INVALID_ARG, "slos_backward: amplitudes need a PNR plan");
+    if (batch == 0) return SLOS_OK;
+    if (!U || !dout || !dU) return fail(SLOS_ERR_INVALID_ARG, "slos_backward: NULL pointer");
+    if (dout_stride_b < 0) return fail(SLOS_ERR_INVALID_ARG, "slos_backward: negative dout stride");
+    const Layout Ly = make_layout(p, batch, true);
+    if (workspace_bytes < Ly.total || !workspace)
+        return fail(SLOS_ERR_INVALID_ARG, "slos_backward: workspace too small (need the training size)");
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = reinterpret_cast<char *>(workspace);
+    const float2 *Ud = reinterpret_cast<const float2 *>(U);
+    const int n = p->n, m = p->m;
+    const int NG = groups_for(batch);
+
+    // seed
+    int seed;
+    const void *seed_ptr;
+    if (output == SLOS_OUT_PROBS && p->det == SLOS_DETECT_PNR && dout_stride_b == 0) {
+        seed = SEED_PROBS_BCAST;
+        seed_ptr = dout;
+    } else {
+        PrepArgs pa;
+        memset(&pa, 0, sizeof(pa));
+        pa.dout = dout;
+        pa.stride = dout_stride_b;
+        pa.outT = ws + Ly.seedT;
+        pa.Fn = p->F[n];
+        pa.m = m;
+        pa.n = n;
+        pa.B = batch;
+        pa.NG = NG;
+        pa.chunk = kChunkStore;
+        pa.kind = output == SLOS_OUT_AMPS ? 1 : (p->det == SLOS_DETECT_THRESHOLD ? 2 : 0);
+        fill_pat_off(p, pa.pat_off);
+        ProfScope ps("slos_seed_prep", (double)batch * (4.0 * p->K + (pa.kind == 1 ? 16.0 : 4.0) * p->F[n]), s);
+        SLOS_CUDA(launch_prep(m, pa, blocks_for(p, pa.Fn, pa.chunk, NG), s));
+        seed = output == SLOS_OUT_AMPS ? SEED_AMPS_T : SEED_PROBS_T;
+        seed_ptr = ws + Ly.seedT;
+    }
+
+    int have_base = -1;  // segment currently recomputed (its kept base layer)
+    ReduceArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    for (int k = n; k >= 1; --k) {
+        const int kp = k - 1;
+        if (kp >= 1 && !p->stored[kp]) {
+            int base = kp;
+            while (base >= 1 && !p->stored[base]) --base;
+            if (base != have_base) {
+                int top = kp;
+                while (top + 1 < n && !p->stored[top + 1]) ++top;
+                for (int q = base + 1; q <= top; ++q) {
+                    slos_status_t st = launch_layer_fwd(p, Ly, ws, Ud, batch, q, EPI_STORE, true, nullptr, s, true);
+                    if (st != SLOS_OK) return st;
+                }
+                have_base = base;
+            }
+        }
+        BwdArgs a;
+        memset(&a, 0, sizeof(a));
+        a.aprev = kp >= 1 ? reinterpret_cast<const float2 *>(ws + Ly.layer[kp]) : nullptr;
+        a.Gk = k < n ? reinterpret_cast<const float2 *>(ws + Ly.g[(n - 1 - k) % 2]) : nullptr;
+        a.Gprev = kp >= 1 ? reinterpret_cast<float2 *>(ws + Ly.g[(n - 1 - kp) % 2]) : nullptr;
+        a.an = k == n ? reinterpret_cast<const float2 *>(ws + Ly.layer[n]) : nullptr;
+        a.seed = seed_ptr;
+        a.U = Ud;
+        a.dUpart = reinterpret_cast<float2 *>(ws + Ly.dupart[k]);
+        a.Fk = p->F[k];
+        a.Fprev = p->F[kp];
+        a.m = m;
+        a.k = k;
+        a.col = p->cols[k - 1];
+        a.B = batch;
+        a.NG = NG;
+        a.chunk = kChunkBwd;
+        a.inv_sfact = p->inv_sfact;
+        {
+            // layered-model bytes: read a_{k-1} and G_k (or a_n and dL/dout), write G_{k-1}
+            double bytes = (kp >= 1 ? 16.0 * a.Fprev : 0.0) + (k == n ? 12.0 : 8.0) * a.Fk;
+            ProfScope ps(k == n ? "slos_bwd_final" : "slos_bwd_layer", bytes * batch, s);
+            SLOS_CUDA(launch_bwd(m, a, k == n ? seed : SEED_G, Ly.bwd_blocks[k], s));
+        }
+        ra.part[k] = a.dUpart;
+        ra.blocks[k] = Ly.bwd_blocks[k];
+        ra.cols[k] = a.col;
+    }
+    ra.n = n;
+    ra.m = m;
+    ra.B = batch;
+    ra.dU = reinterpret_cast<float2 *>(dU);
+    const int64_t tot = (int64_t)batch * m * m;
+    {
+        ProfScope ps("slos_dU_reduce", 16.0 * tot, s);
+        dU_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ra);
+        SLOS_CUDA(cudaGetLastError());
+    }
+    return SLOS_OK;
+}
+
+slos_status_t slos_sync_status(slos_plan_t p, void *stream) {
+    if (!p) return fail(SLOS_ERR_INVALID_ARG, "slos_sync_status: NULL plan");
+    int h[16];
+    cudaStream_t s = (cudaStream_t)stream;
+    SLOS_CUDA(cudaMemcpyAsync(h, p->d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SLOS_CUDA(cudaStreamSynchronize(s));
+    SLOS_CUDA(cudaMemsetAsync(p->d_status, 0, 64, s));
+    SLOS_CUDA(cudaStreamSynchronize(s));
+    if (h[0] == SLOS_ERR_TIMEOUT)
+        return fail(SLOS_ERR_TIMEOUT, "a bounded wait between layers ran out (work item " + std::to_string(h[1]) + ")");
+    if (h[0] != 0) return fail(SLOS_ERR_INTERNAL, "device status " + std::to_string(h[0]));
+    return SLOS_OK;
+}
+
+slos_status_t slos_plan_destroy(slos_plan_t p) {
+    if (!p) return SLOS_OK;
+    if (p->d_status) cudaFree(p->d_status);
+    if (p->batched) batched_destroy(p);
+    delete p;
+    return SLOS_OK;
+}
+
+int64_t slos_host_rank(int m, const int *t) {
+    if (!t || m < 1 || m > kMaxModes) return -1;
+    return host_rank(m, t);
+}
+
+slos_status_t slos_host_unrank(int m, int k, int64_t rank, int *t) {
+    if (!t || m < 1 || m > kMaxModes || k < 0 || k > 40) return fail(SLOS_ERR_INVALID_ARG, "slos_host_unrank: bad argument");
+    if (rank < 0 || rank >= binom_host(m + k - 1, k)) return fail(SLOS_ERR_INVALID_ARG, "slos_host_unrank: rank out of range");
+    if (m == 1) {
+        t[0] = k;
+        return SLOS_OK;
+    }
+    host_unrank(m, k, rank, t);
+    return SLOS_OK;
+}
+
+slos_status_t slos_device_index_table(int m, int k, int64_t first, int64_t count, uint8_t *compositions,
+                                      int32_t *parents, void *stream) {
+    if (m < 2 || m > kMaxModes || k < 1 || k > kMaxPhotons)
+        return fail(SLOS_ERR_UNSUPPORTED, "slos_device_index_table: m in [2,24], k in [1,12]");
+    const int64_t F = binom_host(m + k - 1, k);
+    if (first < 0 || count < 0 || first + count > F) return fail(SLOS_ERR_INVALID_ARG, "slos_device_index_table: range");
+    if (count == 0) return SLOS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned blocks = (unsigned)((count + 127) / 128);
+    ProfScope ps("slos_index_table", 0.0, s);
+    switch (mmax_for(m)) {
+        case 8: index_table_kernel<8><<<blocks, 128, 0, s>>>(m, k, first, count, compositions, parents); break;
+        case 12: index_table_kernel<12><<<blocks, 128, 0, s>>>(m, k, first, count, compositions, parents); break;
+        case 16: index_table_kernel<16><<<blocks, 128, 0, s>>>(m, k, first, count, compositions, parents); break;
+        case 20: index_table_kernel<20><<<blocks, 128, 0, s>>>(m, k, first, count, compositions, parents); break;
+        default: index_table_kernel<24><<<blocks, 128, 0, s>>>(m, k, first, count, compositions, parents); break;
+    }
+    SLOS_CUDA(cudaGetLastError());
+    return SLOS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,255 @@
+// Batched interferometer mesh -> unitary (forward) and its reverse sweep
+// (backward).  Sec. II-A.3: the trainable parameters are the phases of the
+// physical components; Sec. II-C.1: U(x, theta) = W2(theta2) S(x) W1(theta1).
+//
+// One warp per instance.  Lane i carries column i of the running product
+// X = T_l ... T_1 in registers; an MZI on modes (k, k+1) only mixes entries
+// k and k+1 of every column, so each lane updates its own column and no data
+// moves between lanes.  The rectangular layout is regular (column c holds the
+// pairs k = c mod 2, c mod 2 + 2, ...), so the pair index k is a compile-time
+// constant inside the unrolled inner loop and the column stays in registers.
+//
+// MZI(theta, phi) = B diag(e^{i theta}, 1) B diag(e^{i phi}, 1),
+// B = [[1, i], [i, 1]]/sqrt 2, which multiplies out to
+//     i e^{i theta/2} [[sin(theta/2) e^{i phi},  cos(theta/2)],
+//                      [cos(theta/2) e^{i phi}, -sin(theta/2)]].
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "mesh.h"
+#include "profile.h"
+
+namespace slos {
+
+struct Mzi {
+    float2 t00, t01, t10, t11;
+    float2 eth, eph;  // e^{i theta}, e^{i phi}
+};
+
+__device__ __forceinline__ Mzi make_mzi(float theta, float phi) {
+    float sh, chh, sp, cp, st, ct;
+    sincosf(0.5f * theta, &sh, &chh);
+    sincosf(phi, &sp, &cp);
+    sincosf(theta, &st, &ct);
+    // g = i e^{i theta/2} = (-sin(theta/2), cos(theta/2))
+    const float2 g = make_float2(-sh, chh);
+    const float2 eph = make_float2(cp, sp);
+    Mzi z;
+    z.t01 = cscale(g, chh);
+    z.t11 = cscale(g, -sh);
+    z.t00 = cmul(cscale(g, sh), eph);
+    z.t10 = cmul(cscale(g, chh), eph);
+    z.eth = make_float2(ct, st);
+    z.eph = eph;
+    return z;
+}
+
+__device__ __forceinline__ int mzi_offset(int c, int m) {
+    const int ne = m / 2, no = (m - 1) / 2;  // MZIs in even / odd columns
+    return ((c + 1) / 2) * ne + (c / 2) * no;
+}
+
+// Forward sweep for one column of U (lane = input mode), all in registers.
+template <int MMAX>
+__device__ __forceinline__ void mesh_column(const float *th, const float *dd, int m, int n_data, int data_col,
+                                            int lane, float2 (&x)[MMAX]) {
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j) x[j] = make_float2(j == lane ? 1.f : 0.f, 0.f);
+    for (int c = 0; c <= m; ++c) {
+        if (c == data_col && n_data > 0) {
+#pragma unroll
+            for (int j = 0; j < MMAX; ++j) {
+                if (j < n_data) {
+                    float s, co;
+                    sincosf(dd[j], &s, &co);
+                    x[j] = cmul(make_float2(co, s), x[j]);
+                }
+            }
+        }
+        if (c == m) break;
+        const int base = mzi_offset(c, m);
+        const int par = c & 1;
+#pragma unroll
+        for (int k = 0; k < MMAX - 1; ++k) {
+            if ((k & 1) == par && k + 1 < m) {
+                const int idx = base + (k - par) / 2;
+                const Mzi z = make_mzi(th[2 * idx], th[2 * idx + 1]);
+                const float2 xk = x[k], xk1 = x[k + 1];
+                x[k] = cfma(z.t01, xk1, cmul(z.t00, xk));
+                x[k + 1] = cfma(z.t11, xk1, cmul(z.t10, xk));
+            }
+        }
+    }
+}
+
+template <int MMAX>
+__global__ void mesh_fwd_kernel(MeshArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= a.B) return;
+    const int m = a.m;
+    const float *th = a.theta + (int64_t)b * a.theta_stride;
+    const float *dd = a.data ? a.data + (int64_t)b * a.data_stride : nullptr;
+    float2 x[MMAX];
+    mesh_column<MMAX>(th, dd, m, a.n_data, a.data_col, lane, x);
+    if (lane < m) {
+        float2 *U = a.U + (int64_t)b * m * m;
+#pragma unroll
+        for (int j = 0; j < MMAX; ++j)
+            if (j < m) U[j * m + lane] = x[j];
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Reverse sweep.  With U = Y_l T_l X_{l-1} (X_{l-1} = T_{l-1}..T_1,
+// Y_l = T_L..T_{l+1}) and M_l = Y_l^H dU, the gradient w.r.t. the 2x2 block
+// is G = M_l X_{l-1}^H on rows/cols (k, k+1), and
+//      dL/dx = Re sum_ab conj(G_ab) dT_ab/dx.
+// Going down: X_{l-1} = T_l^H X_l, M_{l-1} = T_l^H M_l.
+template <int MMAX>
+__global__ void mesh_bwd_kernel(MeshBwdArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= a.B) return;
+    const int m = a.m;
+    const float *th = a.theta + (int64_t)b * a.theta_stride;
+    const float *dd = a.data ? a.data + (int64_t)b * a.data_stride : nullptr;
+    float *gth = a.dtheta + (int64_t)b * a.dtheta_stride;
+    float2 x[MMAX], mm[MMAX];
+    mesh_column<MMAX>(th, dd, m, a.n_data, a.data_col, lane, x);  // X = U, recomputed
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j) {
+        mm[j] = make_float2(0.f, 0.f);
+        if (j < m && lane < m) mm[j] = a.dU[((int64_t)b * m + j) * m + lane];
+        if (lane >= m) x[j] = make_float2(0.f, 0.f);
+    }
+    for (int c = m; c >= 0; --c) {
+        if (c < m) {
+            const int base = mzi_offset(c, m);
+            const int par = c & 1;
+#pragma unroll
+            for (int k = 0; k < MMAX - 1; ++k) {
+                if ((k & 1) == par && k + 1 < m) {
+                    const int idx = base + (k - par) / 2;
+                    const float theta = th[2 * idx], phi = th[2 * idx + 1];
+                    const Mzi z = make_mzi(theta, phi);
+                    // X_before = T^H X
+                    const float2 xk = x[k], xk1 = x[k + 1];
+                    const float2 bk = cfma_conj_a(z.t10, xk1, make_float2(z.t00.x * xk.x + z.t00.y * xk.y,
+                                                                           z.t00.x * xk.y - z.t00.y * xk.x));
+                    const float2 bk1 = cfma_conj_a(z.t11, xk1, make_float2(z.t01.x * xk.x + z.t01.y * xk.y,
+                                                                            z.t01.x * xk.y - z.t01.y * xk.x));
+                    x[k] = bk;
+                    x[k + 1] = bk1;
+                    // G_ab = sum_i M[a][i] conj(Xb[b][i])
+                    const float2 mk = mm[k], mk1 = mm[k + 1];
+                    float g00x = mk.x * bk.x + mk.y * bk.y, g00y = mk.y * bk.x - mk.x * bk.y;
+                    float g01x = mk.x * bk1.x + mk.y * bk1.y, g01y = mk.y * bk1.x - mk.x * bk1.y;
+                    float g10x = mk1.x * bk.x + mk1.y * bk.y, g10y = mk1.y * bk.x - mk1.x * bk.y;
+                    float g11x = mk1.x * bk1.x + mk1.y * bk1.y, g11y = mk1.y * bk1.x - mk1.x * bk1.y;
+                    g00x = warp_sum(g00x); g00y = warp_sum(g00y);
+                    g01x = warp_sum(g01x); g01y = warp_sum(g01y);
+                    g10x = warp_sum(g10x); g10y = warp_sum(g10y);
+                    g11x = warp_sum(g11x); g11y = warp_sum(g11y);
+                    // dT/dtheta = [[ (i/2) e^{i th} e^{i ph}, -(1/2) e^{i th}],
+                    //              [-(1/2) e^{i th} e^{i ph}, -(i/2) e^{i th}]]
+                    const float2 e2 = cmul(z.eth, z.eph);
+                    const float2 d00 = make_float2(-0.5f * e2.y, 0.5f * e2.x);
+                    const float2 d01 = make_float2(-0.5f * z.eth.x, -0.5f * z.eth.y);
+                    const float2 d10 = make_float2(-0.5f * e2.x, -0.5f * e2.y);
+                    const float2 d11 = make_float2(0.5f * z.eth.y, -0.5f * z.eth.x);
+                    // Re(conj(G) d) = Gx dx + Gy dy
+                    const float dth = g00x * d00.x + g00y * d00.y + g01x * d01.x + g01y * d01.y +
+                                      g10x * d10.x + g10y * d10.y + g11x * d11.x + g11y * d11.y;
+                    // dT/dphi = [[i t00, 0], [i t10, 0]]
+                    const float2 p00 = make_float2(-z.t00.y, z.t00.x);
+                    const float2 p10 = make_float2(-z.t10.y, z.t10.x);
+                    const float dph = g00x * p00.x + g00y * p00.y + g10x * p10.x + g10y * p10.y;
+                    if (lane == 0) {
+                        gth[2 * idx] = dth;
+                        gth[2 * idx + 1] = dph;
+                    }
+                    // M_before = T^H M
+                    mm[k] = cfma_conj_a(z.t10, mk1, make_float2(z.t00.x * mk.x + z.t00.y * mk.y,
+                                                                z.t00.x * mk.y - z.t00.y * mk.x));
+                    mm[k + 1] = cfma_conj_a(z.t11, mk1, make_float2(z.t01.x * mk.x + z.t01.y * mk.y,
+                                                                    z.t01.x * mk.y - z.t01.y * mk.x));
+                }
+            }
+        }
+        if (c == a.data_col && a.n_data > 0) {
+#pragma unroll
+            for (int j = 0; j < MMAX; ++j) {
+                if (j < a.n_data) {
+                    float s, co;
+                    sincosf(dd[j], &s, &co);
+                    const float2 e = make_float2(co, s);
+                    // X_before = conj(e) X ; G = sum_i M conj(X_before)
+                    const float2 xb = make_float2(e.x * x[j].x + e.y * x[j].y, e.x * x[j].y - e.y * x[j].x);
+                    x[j] = xb;
+                    float gx = mm[j].x * xb.x + mm[j].y * xb.y;
+                    float gy = mm[j].y * xb.x - mm[j].x * xb.y;
+                    gx = warp_sum(gx);
+                    gy = warp_sum(gy);
+                    // dS_jj/dx_j = i e ; Re(conj(G) i e) = Gx (-e.y) + Gy e.x
+                    if (lane == 0) a.ddata[(int64_t)b * a.n_data + j] = -gx * e.y + gy * e.x;
+                    mm[j] = make_float2(e.x * mm[j].x + e.y * mm[j].y, e.x * mm[j].y - e.y * mm[j].x);
+                }
+            }
+        }
+    }
+}
+
+// dtheta[p] = sum_b part[b][p], in batch order.
+__global__ void mesh_reduce_kernel(const float *part, int B, int P, float *out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += part[(int64_t)b * P + p];
+    out[p] = s;
+}
+
+template <int MMAX>
+static cudaError_t launch_fwd(const MeshArgs &a, cudaStream_t s) {
+    const int wpb = 4;
+    mesh_fwd_kernel<MMAX><<<(a.B + wpb - 1) / wpb, wpb * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int MMAX>
+static cudaError_t launch_bwd(const MeshBwdArgs &a, cudaStream_t s) {
+    const int wpb = 4;
+    mesh_bwd_kernel<MMAX><<<(a.B + wpb - 1) / wpb, wpb * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t mesh_forward_launch(const MeshArgs &a, cudaStream_t s) {
+    if (a.B == 0) return cudaSuccess;
+    if (a.m <= 8) return launch_fwd<8>(a, s);
+    if (a.m <= 16) return launch_fwd<16>(a, s);
+    return launch_fwd<24>(a, s);
+}
+
+cudaError_t mesh_backward_launch(const MeshBwdArgs &a, float *dtheta_shared, cudaStream_t s) {
+    if (a.B == 0) return cudaSuccess;
+    cudaError_t e;
+    if (a.m <= 8) e = launch_bwd<8>(a, s);
+    else if (a.m <= 16) e = launch_bwd<16>(a, s);
+    else e = launch_bwd<24>(a, s);
+    if (e != cudaSuccess) return e;
+    if (dtheta_shared) {
+        const int P = a.m * (a.m - 1);
+        count_launch();
+        mesh_reduce_kernel<<<(P + 127) / 128, 128, 0, s>>>(a.dtheta, a.B, P, dtheta_shared);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace slos

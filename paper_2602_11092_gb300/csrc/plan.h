@@ -1,0 +1,63 @@
+// Host-side plan: Fock-lattice sizes, photon columns, checkpoint schedule and
+// workspace layout.  Built once per (m, n, input state, detection); only the
+// unitaries change between calls (Sec. II-A.3).
+#pragma once
+
+#include <stdint.h>
+#include <stddef.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/slos.h"
+
+namespace slos {
+
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int64_t binom_host(int a, int e);
+
+// Host rank/unrank in descending-lex order (same closed form as the device).
+int64_t host_rank(int m, const int *t);
+void host_unrank(int m, int k, int64_t r, int *t);
+
+struct BatchedPlan;  // uneven batches (batched.cu)
+
+struct Layout {
+    // byte offsets into the workspace (SIZE_MAX = absent)
+    std::vector<size_t> layer;  // [0..n]: where a_k lives (layer[0] unused)
+    size_t g[2];                // G ping-pong
+    size_t seedT;               // transposed output gradient
+    std::vector<size_t> dupart; // [1..n]: dU partials of layer k
+    std::vector<int> bwd_blocks;  // [1..n]: blocks_x of the backward launch of layer k
+    size_t total;
+};
+
+struct slos_plan_impl;
+
+}  // namespace slos
+
+struct slos_plan_s;
+namespace slos {
+void batched_destroy(slos_plan_s *p);
+}
+
+struct slos_plan_s {
+    int kind;  // 0 = single-shape plan, 1 = uneven batch
+    int m, n;
+    std::vector<int> s;     // input occupations
+    std::vector<int> cols;  // c_1 <= ... <= c_n
+    slos_detection_t det;
+    int64_t K;              // outputs per instance
+    std::vector<int64_t> F; // |F(m, k)| for k = 0..n
+    float inv_sfact;
+    int stride;             // checkpoint stride s (1 = every layer kept)
+    std::vector<char> stored;  // [0..n]: layer kept by a saving forward
+    int pat_off[16];
+    int device;
+    int sm_count;
+    int *d_status;          // device status word (owned)
+    slos::BatchedPlan *batched;
+};

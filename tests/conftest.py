@@ -24,4 +24,4 @@ def cuda_available() -> bool:
 def slos():
     """The CUDA binding; GPU tests fail loudly if the library is missing."""
     import paper_2602_11092_gb300 as pkg
-    return pkg.binding()
+    return pkg.load()

@@ -1,0 +1,87 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+declared in include/slos.h, and its host-side Fock ranking is bit-exact
+against the oracle's brute-force enumeration."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for mt in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                              text, flags=re.M):
+            names.add(mt.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_11092_gb300 import buildlib as pkg_build
+    pkg_build.build()
+    from paper_2602_11092_gb300 import binding
+    return binding.load()
+
+
+def test_library_exports_every_declared_function(lib):
+    names = header_functions()
+    assert "slos_forward" in names and "mesh_unitary" in names
+    for name in names:
+        assert hasattr(lib, name), f"libslos.so does not export {name}"
+    from paper_2602_11092_gb300 import binding
+    assert set(binding.exported_symbols()) >= set(names)
+
+
+@pytest.mark.parametrize("m", range(2, 13))
+def test_host_rank_matches_enumeration(lib, m):
+    from paper_2602_11092_gb300 import binding
+    for k in range(0, 7):
+        states = oracle.enumerate_fock(m, k)
+        if states.shape[0] > 20000:
+            states = states[:: max(1, states.shape[0] // 5000)]
+            idx = np.arange(0, oracle.fock_dim(m, k), max(1, oracle.fock_dim(m, k) // 5000))[: states.shape[0]]
+        else:
+            idx = np.arange(states.shape[0])
+        for r, t in zip(idx, states):
+            assert binding.host_rank(m, t) == r
+            assert binding.host_unrank(m, k, int(r)) == list(t)
+
+
+def test_host_rank_large_sample(lib):
+    from paper_2602_11092_gb300 import binding
+    m, k = 20, 10
+    total = math.comb(m + k - 1, k)
+    rng = np.random.default_rng(0)
+    pos = np.sort(rng.choice(total, size=300, replace=False))
+    pos = np.concatenate([[0], pos, [total - 1]])
+    states = oracle.enumerate_fock(m, k, pos)
+    for r, t in zip(pos, states):
+        assert binding.host_rank(m, t) == r
+        assert binding.host_unrank(m, k, int(r)) == list(t)
+
+
+def test_plan_argument_validation_without_gpu(lib):
+    from paper_2602_11092_gb300 import binding
+    with pytest.raises(binding.SlosError) as e:
+        binding.Plan(25, [1] + [0] * 24)
+    assert e.value.status == 2
+    with pytest.raises(binding.SlosError) as e:
+        binding.Plan(4, [1, 1, 0, 0], detection=7)
+    assert e.value.status == 1
+    with pytest.raises(binding.SlosError) as e:
+        binding.Plan(4, [13, 0, 0, 0])
+    assert e.value.status == 2
+    with pytest.raises(binding.SlosError) as e:
+        binding.host_unrank(5, 3, 10 ** 6)
+    assert e.value.status == 1

@@ -1,0 +1,392 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (stated by the target): max |dp| <= 1e-5 and total variation
+<= 1e-5 for distributions, gradient relative error <= 1e-3, integer Fock
+indexing bit-exact.  The oracle evaluates the complex64-rounded unitary the
+GPU received (upcast to complex128), so the gap is the device arithmetic.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2602_11092_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+P_TOL = 1e-5
+TV_TOL = 1e-5
+G_TOL = 1e-3
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def c64(U):
+    return torch.tensor(np.asarray(U), dtype=torch.complex64, device=dev())
+
+
+def up(Ut):
+    return Ut.detach().cpu().numpy().astype(np.complex128)
+
+
+def check_dist(p_gpu, p_ref, tol=P_TOL, tv_tol=TV_TOL):
+    d = np.abs(p_gpu.astype(np.float64) - p_ref)
+    assert d.max() <= tol, f"max |dp| = {d.max():.3e}"
+    assert 0.5 * d.sum() <= tv_tol, f"TV = {0.5 * d.sum():.3e}"
+
+
+# ------------------------------------------------------------------ indexing
+
+@pytest.mark.parametrize("m,k", [(2, 1), (3, 3), (6, 3), (8, 4), (12, 6), (16, 5), (24, 3), (7, 12)])
+def test_device_index_table_bit_exact(slos, m, k):
+    F = math.comb(m + k - 1, k)
+    count = min(F, 40000)
+    comp, par = slos.device_index_table(m, k, 0, count)
+    comp = comp.cpu().numpy().astype(np.int32)
+    par = par.cpu().numpy()
+    ref = oracle.enumerate_fock(m, k, np.arange(count))
+    assert np.array_equal(comp, ref)
+    prev = [tuple(t) for t in oracle.enumerate_fock(m, k - 1)] if math.comb(m + k - 2, k - 1) <= 400000 else None
+    if prev is not None:
+        index = {t: i for i, t in enumerate(prev)}
+        for i in range(0, count, max(1, count // 3000)):
+            for j in range(m):
+                if ref[i, j] == 0:
+                    assert par[i, j] == -1
+                else:
+                    t = list(ref[i]); t[j] -= 1
+                    assert par[i, j] == index[tuple(t)]
+
+
+def test_device_index_table_large_layer_sampled(slos):
+    m, k = 20, 10
+    F = math.comb(m + k - 1, k)
+    rng = np.random.default_rng(4)
+    for first in sorted(rng.choice(F - 64, size=5, replace=False)):
+        comp, _ = slos.device_index_table(m, k, int(first), 64)
+        ref = oracle.enumerate_fock(m, k, np.arange(first, first + 64))
+        assert np.array_equal(comp.cpu().numpy().astype(np.int32), ref)
+
+
+# ------------------------------------------------------------------ mesh
+
+@pytest.mark.parametrize("m,B", [(2, 3), (6, 5), (12, 33), (16, 8), (24, 2)])
+def test_mesh_unitary_matches_oracle(slos, m, B):
+    mb = workloads.mesh_batch(m, B, seed=77 + m)
+    theta = torch.tensor(mb.theta, dtype=torch.float32, device=dev())
+    data = torch.tensor(mb.data, dtype=torch.float32, device=dev())
+    U = slos.mesh_unitary(m, theta, data, B).cpu().numpy()
+    for b in range(B):
+        ref = oracle.mesh_unitary(m, mb.theta.astype(np.float32).astype(np.float64),
+                                  mb.data[b].astype(np.float32).astype(np.float64))
+        assert np.abs(U[b] - ref).max() < 2e-5
+
+
+def test_mesh_per_instance_theta_and_no_data(slos):
+    m, B = 8, 4
+    rng = np.random.default_rng(3)
+    th = rng.uniform(0, 2 * np.pi, (B, m * (m - 1)))
+    U = slos.mesh_unitary(m, torch.tensor(th, dtype=torch.float32, device=dev()), None, B).cpu().numpy()
+    for b in range(B):
+        ref = oracle.mesh_unitary(m, th[b].astype(np.float32).astype(np.float64))
+        assert np.abs(U[b] - ref).max() < 1e-5
+
+
+@pytest.mark.parametrize("m,B,shared", [(4, 3, True), (6, 2, False), (12, 5, True), (16, 3, True)])
+def test_mesh_backward_matches_oracle_chain_rule(slos, m, B, shared):
+    rng = np.random.default_rng(m + B)
+    th = rng.uniform(0, 2 * np.pi, m * (m - 1) if shared else (B, m * (m - 1))).astype(np.float32)
+    d = rng.standard_normal((B, m)).astype(np.float32)
+    dU = (rng.standard_normal((B, m, m)) + 1j * rng.standard_normal((B, m, m))).astype(np.complex64)
+    dth, dd = slos.mesh_unitary_backward(m, torch.tensor(th, device=dev()), torch.tensor(d, device=dev()), B,
+                                         torch.tensor(dU, device=dev()))
+    dth = dth.cpu().numpy()
+    dd = dd.cpu().numpy()
+    acc = 0
+    for b in range(B):
+        tb = th if shared else th[b]
+        gt, gd = oracle.phase_grad_from_dU(m, tb.astype(np.float64), d[b].astype(np.float64),
+                                           dU[b].astype(np.complex128))
+        if shared:
+            acc = acc + gt
+        else:
+            assert np.linalg.norm(dth[b] - gt) / np.linalg.norm(gt) < 1e-4
+        assert np.linalg.norm(dd[b] - gd) / np.linalg.norm(gd) < 1e-4
+    if shared:
+        assert np.linalg.norm(dth - acc) / np.linalg.norm(acc) < 1e-4
+
+
+# ------------------------------------------------------------------ forward
+
+def test_tiny_config_probs_and_amps(slos):
+    w = workloads.tiny()
+    U = c64(w["U"])
+    plan = slos.Plan(6, w["s"])
+    assert plan.n_outputs == 56
+    p = plan.forward(U).cpu().numpy()[0]
+    a = plan.forward(U, output=slos.AMPS).cpu().numpy()[0]
+    outs = oracle.enumerate_fock(6, 3)
+    ref_a = oracle.amplitudes(up(U)[0], w["s"], outs)
+    check_dist(p, np.abs(ref_a) ** 2)
+    assert np.abs(a - ref_a).max() <= 1e-5
+    # error against the unrounded FP64 unitary is stated, not bounded by the GPU
+    ref64 = oracle.probabilities(w["U"][0], w["s"], outs)
+    assert np.abs(p - ref64).max() < 1e-5
+
+
+@pytest.mark.parametrize("m,s,B", [
+    (2, [1, 1], 3),
+    (3, [1, 1, 1], 1),
+    (5, [2, 0, 1, 0, 1], 7),
+    (8, [1, 0, 1, 0, 1, 0, 1, 0], 33),
+    (12, [1, 0] * 6, 40),
+    (9, [3, 0, 0, 0, 0, 0, 0, 0, 1], 5),
+    (24, [1] + [0] * 23, 4),
+    (20, [1, 0, 1] + [0] * 17, 2),
+    (4, [6, 0, 0, 0], 3),
+])
+def test_forward_probs_match_oracle(slos, m, s, B):
+    rng = np.random.default_rng(m * 31 + B)
+    Us = workloads.haar_unitaries(m, B, rng)
+    U = c64(Us)
+    plan = slos.Plan(m, s)
+    p = plan.forward(U).cpu().numpy()
+    outs = oracle.enumerate_fock(m, sum(s))
+    Uh = up(U)
+    for b in range(B):
+        ref = oracle.probabilities(Uh[b], s, outs)
+        check_dist(p[b], ref)
+        assert abs(p[b].astype(np.float64).sum() - 1.0) < 1e-5
+
+
+def test_layer12_subset_against_oracle(slos):
+    """The m=12, n=6 layer: 40 meshes (two groups, ragged tail), all 12376 outputs."""
+    w = workloads.layer12(batch=40)
+    mb = w["mesh"]
+    theta = torch.tensor(mb.theta, dtype=torch.float32, device=dev())
+    data = torch.tensor(mb.data, dtype=torch.float32, device=dev())
+    U = slos.mesh_unitary(12, theta, data, 40)
+    plan = slos.Plan(12, w["s"])
+    p = plan.forward(U).cpu().numpy()
+    outs = oracle.enumerate_fock(12, 6)
+    Uh = up(U)
+    for b in range(40):
+        check_dist(p[b], oracle.probabilities(Uh[b], w["s"], outs))
+
+
+def test_train16_full_size_sampled_outputs(slos):
+    """m=16, n=8, batch 256 in the bench's launch configuration; sampled outputs."""
+    w = workloads.train16(batch=256)
+    mb = w["mesh"]
+    theta = torch.tensor(mb.theta, dtype=torch.float32, device=dev())
+    data = torch.tensor(mb.data, dtype=torch.float32, device=dev())
+    U = slos.mesh_unitary(16, theta, data, 256)
+    plan = slos.Plan(16, w["s"], mem_budget_bytes=2_000_000)
+    ws = plan.workspace(256, training=True)
+    p = plan.forward(U, save_for_backward=True, workspace=ws).cpu().numpy()
+    K = plan.n_outputs
+    assert K == 490314
+    rng = np.random.default_rng(8)
+    pos = np.sort(rng.choice(K, size=300, replace=False))
+    pos = np.concatenate([[0, 1, K - 2, K - 1], pos])
+    pos = np.unique(pos)
+    outs = oracle.enumerate_fock(16, 8, pos)
+    Uh = up(U)
+    for b in [0, 1, 31, 32, 100, 255]:
+        ref = oracle.probabilities(Uh[b], w["s"], outs)
+        assert np.abs(p[b, pos] - ref).max() <= P_TOL
+    # properties that hold at any size: normalisation and mean photon numbers
+    tot = p.astype(np.float64).sum(axis=1)
+    assert np.abs(tot - 1).max() < 1e-4
+
+
+@pytest.mark.parametrize("m,n,B", [(8, 4, 5), (16, 3, 3), (6, 6, 2)])
+def test_threshold_matches_oracle(slos, m, n, B):
+    rng = np.random.default_rng(m + n)
+    s = workloads.even_mode_input(m, n) if 2 * n <= m else [1] * n + [0] * (m - n)
+    Us = workloads.haar_unitaries(m, B, rng)
+    U = c64(Us)
+    plan = slos.Plan(m, s, slos.THRESHOLD)
+    q = plan.forward(U).cpu().numpy()
+    outs = oracle.enumerate_fock(m, n)
+    Uh = up(U)
+    for b in range(B):
+        ref = oracle.threshold_probs(oracle.probabilities(Uh[b], s, outs), outs, m, n)
+        assert q.shape[1] == ref.shape[0]
+        check_dist(q[b], ref)
+
+
+def test_empty_batch_is_noop(slos):
+    plan = slos.Plan(4, [1, 1, 0, 0])
+    U = torch.empty((0, 4, 4), dtype=torch.complex64, device=dev())
+    out = plan.forward(U)
+    assert out.shape == (0, plan.n_outputs)
+
+
+# ------------------------------------------------------------------ backward
+
+def _grad_U_ref(Uh, s, c, outs):
+    return oracle.grad_U_minors(Uh, s, c, outs)
+
+
+@pytest.mark.parametrize("m,s,B,shared", [
+    (6, [1, 1, 1, 0, 0, 0], 3, True),
+    (5, [2, 0, 1, 0, 0], 2, False),
+    (8, [1, 0, 1, 0, 1, 0, 1, 0], 33, True),
+    (4, [1, 0, 0, 0], 2, False),
+])
+def test_backward_dU_matches_permanent_minors(slos, m, s, B, shared):
+    rng = np.random.default_rng(5 + m + B)
+    U = c64(workloads.haar_unitaries(m, B, rng))
+    plan = slos.Plan(m, s)
+    K = plan.n_outputs
+    c = rng.standard_normal(K if shared else (B, K)).astype(np.float32)
+    ws = plan.workspace(B, training=True)
+    plan.forward(U, save_for_backward=True, workspace=ws)
+    dU = plan.backward(U, torch.tensor(c, device=dev()), ws).cpu().numpy()
+    outs = oracle.enumerate_fock(m, sum(s))
+    Uh = up(U)
+    for b in range(B):
+        cb = c if shared else c[b]
+        ref = _grad_U_ref(Uh[b], s, cb.astype(np.float64), outs)
+        rel = np.linalg.norm(dU[b] - ref) / np.linalg.norm(ref)
+        assert rel <= G_TOL, f"instance {b}: rel err {rel:.2e}"
+
+
+def test_backward_amplitudes(slos):
+    m, s, B = 5, [1, 1, 0, 1, 0], 3
+    rng = np.random.default_rng(12)
+    U = c64(workloads.haar_unitaries(m, B, rng))
+    plan = slos.Plan(m, s)
+    K = plan.n_outputs
+    g = (rng.standard_normal((B, K)) + 1j * rng.standard_normal((B, K))).astype(np.complex64)
+    ws = plan.workspace(B, training=True)
+    plan.forward(U, output=slos.AMPS, save_for_backward=True, workspace=ws)
+    dU = plan.backward(U, torch.tensor(g, device=dev()), ws, output=slos.AMPS).cpu().numpy()
+    # L = Re sum conj(g) a  => dL/dU via FD on the oracle amplitudes
+    outs = oracle.enumerate_fock(m, 3)
+    Uh = up(U)
+    h = 1e-6
+    for b in range(B):
+        def L(V):
+            return float(np.real(np.sum(np.conj(g[b].astype(np.complex128)) * oracle.amplitudes(V, s, outs))))
+        ref = np.zeros((m, m), dtype=np.complex128)
+        for j in range(m):
+            for i in range(m):
+                E = np.zeros((m, m)); E[j, i] = 1
+                ref[j, i] = (L(Uh[b] + h * E) - L(Uh[b] - h * E)) / (2 * h) + \
+                    1j * (L(Uh[b] + 1j * h * E) - L(Uh[b] - 1j * h * E)) / (2 * h)
+        assert np.linalg.norm(dU[b] - ref) / np.linalg.norm(ref) <= G_TOL
+
+
+def test_backward_threshold(slos):
+    m, n, B = 8, 4, 3
+    s = workloads.even_mode_input(m, n)
+    rng = np.random.default_rng(21)
+    U = c64(workloads.haar_unitaries(m, B, rng))
+    plan = slos.Plan(m, s, slos.THRESHOLD)
+    Kq = plan.n_outputs
+    cq = rng.standard_normal((B, Kq)).astype(np.float32)
+    ws = plan.workspace(B, training=True)
+    plan.forward(U, save_for_backward=True, workspace=ws)
+    dU = plan.backward(U, torch.tensor(cq, device=dev()), ws).cpu().numpy()
+    outs = oracle.enumerate_fock(m, n)
+    pats = oracle.threshold_patterns(m, n)
+    index = {pat: i for i, pat in enumerate(pats)}
+    pat_of = np.array([index[tuple(np.nonzero(t)[0])] for t in outs])
+    Uh = up(U)
+    for b in range(B):
+        c_states = cq[b][pat_of].astype(np.float64)  # dL/dp(t) = dL/dq(pattern(t))
+        ref = _grad_U_ref(Uh[b], s, c_states, outs)
+        assert np.linalg.norm(dU[b] - ref) / np.linalg.norm(ref) <= G_TOL
+
+
+def test_checkpointing_is_bitwise_equal_to_full_store(slos):
+    m, s, B = 10, [1, 0] * 5, 40
+    rng = np.random.default_rng(2)
+    U = c64(workloads.haar_unitaries(m, B, rng))
+    full = slos.Plan(m, s)
+    ck = slos.Plan(m, s, mem_budget_bytes=1)  # forces the largest stride
+    assert full.checkpoint_stride == 1 and ck.checkpoint_stride > 1
+    c = torch.tensor(rng.standard_normal(full.n_outputs), dtype=torch.float32, device=dev())
+    res = []
+    for plan in (full, ck):
+        ws = plan.workspace(B, training=True)
+        p = plan.forward(U, save_for_backward=True, workspace=ws)
+        res.append((p, plan.backward(U, c, ws)))
+    assert torch.equal(res[0][0], res[1][0])
+    assert torch.equal(res[0][1], res[1][1])
+    for budget in (200_000, 50_000):
+        mid = slos.Plan(m, s, mem_budget_bytes=budget)
+        ws = mid.workspace(B, training=True)
+        mid.forward(U, save_for_backward=True, workspace=ws)
+        assert torch.equal(mid.backward(U, c, ws), res[0][1])
+
+
+def test_autograd_phase_gradient_against_fd_and_minors(slos):
+    """End-to-end d loss / d phases through MeshFn and SlosFn (m=6, n=3)."""
+    from paper_2602_11092_gb300 import functions
+    m, s, B = 6, [1, 1, 1, 0, 0, 0], 4
+    mb = workloads.mesh_batch(m, B, seed=1000)
+    theta = torch.tensor(mb.theta, dtype=torch.float32, device=dev(), requires_grad=True)
+    data = torch.tensor(mb.data, dtype=torch.float32, device=dev(), requires_grad=True)
+    plan = slos.Plan(m, s)
+    rng = np.random.default_rng(1)
+    c = torch.tensor(rng.standard_normal(plan.n_outputs), dtype=torch.float32, device=dev())
+    p = functions.slos(functions.mesh_unitary(theta, data, m, B), plan)
+    (p * c).sum().backward()
+    th64 = theta.detach().cpu().double().numpy()
+    gt_sum = 0
+    for b in range(B):
+        d64 = data.detach().cpu().double().numpy()[b]
+        gt_fd, gd_fd = oracle.fd_grad_phases(m, th64, d64, s, c.cpu().double().numpy())
+        gt_an, gd_an = oracle.analytic_grad_phases(m, th64, d64, s, c.cpu().double().numpy())
+        assert np.linalg.norm(gt_fd - gt_an) / np.linalg.norm(gt_an) < 1e-6
+        gd = data.grad.cpu().double().numpy()[b]
+        assert np.linalg.norm(gd - gd_fd) / np.linalg.norm(gd_fd) <= G_TOL
+        gt_sum = gt_sum + gt_fd
+    g = theta.grad.cpu().double().numpy()
+    assert np.linalg.norm(g - gt_sum) / np.linalg.norm(gt_sum) <= G_TOL
+
+
+def test_train16_gradients_against_fd_on_8_samples(slos):
+    """m=16, n=8 training step with checkpointing on: gradients w.r.t. all 256
+    phases of 8 samples against FP64 central differences (h=1e-6) of the
+    oracle.  The loss weights c_t are N(0,1) on a seeded set of 1000 outputs
+    (zero elsewhere) so the oracle's Ryser evaluations stay cheap; the GPU
+    still runs the full recursion over all 490314 states."""
+    from paper_2602_11092_gb300 import functions
+    w = workloads.train16(batch=8)
+    mb = w["mesh"]
+    m, s = 16, w["s"]
+    plan = slos.Plan(m, s, mem_budget_bytes=2_000_000)
+    assert plan.checkpoint_stride > 1
+    K = plan.n_outputs
+    rng = np.random.default_rng(1002)
+    pos = np.sort(rng.choice(K, size=1000, replace=False))
+    c_full = np.zeros(K, dtype=np.float32)
+    c_full[pos] = rng.standard_normal(pos.size).astype(np.float32)
+    theta = torch.tensor(mb.theta, dtype=torch.float32, device=dev(), requires_grad=True)
+    data = torch.tensor(mb.data, dtype=torch.float32, device=dev(), requires_grad=True)
+    c = torch.tensor(c_full, device=dev())
+    p = functions.slos(functions.mesh_unitary(theta, data, m, 8), plan)
+    (p * c).sum().backward()
+    th64 = theta.detach().cpu().double().numpy()
+    d64 = data.detach().cpu().double().numpy()
+    outs = oracle.enumerate_fock(m, 8, pos)
+    cs = c_full[pos].astype(np.float64)
+    gt_sum = np.zeros_like(th64)
+    for b in range(8):
+        gt, gd = oracle.fd_grad_phases(m, th64, d64[b], s, cs, h=1e-6, outputs=outs)
+        gt_sum += gt
+        gdat = data.grad.cpu().double().numpy()[b]
+        assert np.linalg.norm(gdat - gd) / np.linalg.norm(gd) <= G_TOL
+        if b == 0:
+            gt_an, _ = oracle.analytic_grad_phases(m, th64, d64[0], s, cs, outputs=outs)
+            assert np.linalg.norm(gt - gt_an) / np.linalg.norm(gt_an) < 1e-6
+    g = theta.grad.cpu().double().numpy()
+    assert np.linalg.norm(g - gt_sum) / np.linalg.norm(gt_sum) <= G_TOL
