@@ -241,12 +241,14 @@ def mesh_factors(m: int, theta, data=None, data_col=None):
         d[: len(data)] = np.exp(1j * np.asarray(data, dtype=np.float64))
         return ("data", None, np.diag(d))
 
-    for idx, (c, k) in enumerate(layout):
-        if has_data and c == data_col and (idx == 0 or layout[idx - 1][0] != c):
+    idx = 0
+    for c in range(m + 1):
+        if has_data and c == data_col:
             facs.append(screen())
-        facs.append(("mzi", idx, embed(m, k, mzi(theta[2 * idx], theta[2 * idx + 1]))))
-    if has_data and data_col >= m:
-        facs.append(screen())
+        while idx < len(layout) and layout[idx][0] == c:
+            k = layout[idx][1]
+            facs.append(("mzi", idx, embed(m, k, mzi(theta[2 * idx], theta[2 * idx + 1]))))
+            idx += 1
     return facs
 
 

@@ -222,6 +222,11 @@ def test_mesh_m2_and_m3_brute_force():
     # m=2: two columns, only column 0 holds an MZI (k=0); column 1 has k=1 > m-2
     assert oracle.mesh_layout(2) == [(0, 0)]
     assert np.allclose(oracle.mesh_unitary(2, th2), oracle.mzi(*th2))
+    # with data phases the screen follows the first m//2 = 1 column, even
+    # though column 1 holds no MZI
+    d2 = rng.uniform(0, 2 * np.pi, 2)
+    assert np.allclose(oracle.mesh_unitary(2, th2, d2), np.diag(np.exp(1j * d2)) @ oracle.mzi(*th2))
+    assert np.allclose(oracle.mesh_unitary(2, th2, d2, data_col=0), oracle.mzi(*th2) @ np.diag(np.exp(1j * d2)))
     # m=3: columns 0 (k=0), 1 (k=1), 2 (k=0)
     th3 = rng.uniform(0, 2 * np.pi, 6)
     assert oracle.mesh_layout(3) == [(0, 0), (1, 1), (2, 0)]
