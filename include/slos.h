@@ -117,11 +117,13 @@ slos_status_t mesh_unitary_backward(const slos_mesh_desc_t *desc, const float *t
  * ---------------------------------------------------------------------- */
 
 /* Build a plan for input Fock state `input_state` (host, m ints summing to n).
- * mem_budget_bytes: per-instance budget for the activations that
- * slos_forward(save_for_backward=1) keeps for slos_backward; 0 = keep every
- * photon-number layer.  With a budget, only every s-th layer below n-1 is
- * kept (s as small as fits) and the others are recomputed in the backward
- * pass.  Allocates a 64-byte device status word on the current device. */
+ * mem_budget_bytes: per-instance budget (bytes) for the intermediate
+ * photon-number layers 1..n-1 that slos_forward(save_for_backward=1) keeps
+ * for slos_backward; 0 = keep them all.  With a budget, only layers n-1,
+ * n-1-s, n-1-2s, ... are kept (s as small as fits, counting one recompute
+ * segment) and the others are recomputed in the backward pass; the final
+ * layer a_n is always kept.  Allocates a 64-byte device status word on the
+ * current device. */
 slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t detection,
                         size_t mem_budget_bytes, slos_plan_t *out);
 

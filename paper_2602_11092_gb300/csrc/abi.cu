@@ -164,22 +164,27 @@ static Layout make_layout(const slos_plan_s *p, int batch, bool training) {
         size_t b1 = n >= 3 ? take(row * p->F[n - 2]) : SIZE_MAX;
         for (int k = 1; k < n; ++k) L.layer[k] = ((n - 1 - k) % 2 == 0) ? b0 : b1;
     } else {
-        // kept layers + one segment buffer of (stride-1) slots for the rest
-        int64_t fmax_ns = 0;
-        for (int k = 1; k < n; ++k) {
-            if (p->stored[k]) L.layer[k] = take(row * p->F[k]);
-            else fmax_ns = std::max(fmax_ns, p->F[k]);
+        // kept layers + one recompute segment: slot i of a segment holds the
+        // i-th non-kept layer above the segment's kept base layer
+        std::vector<int64_t> slot_states(n + 1, 0);
+        {
+            int base = 0;
+            for (int k = 1; k < n; ++k) {
+                if (p->stored[k]) base = k;
+                else slot_states[k - base - 1] = std::max(slot_states[k - base - 1], p->F[k]);
+            }
         }
+        for (int k = 1; k < n; ++k)
+            if (p->stored[k]) L.layer[k] = take(row * p->F[k]);
         L.layer[n] = take(row * p->F[n]);
-        std::vector<size_t> slot(std::max(1, p->stride - 1), SIZE_MAX);
-        if (fmax_ns > 0)
-            for (auto &s : slot) s = take(row * fmax_ns);
-        int base = 0;
-        for (int k = 1; k < n; ++k) {
-            if (p->stored[k]) {
-                base = k;
-            } else {
-                L.layer[k] = slot[k - base - 1];
+        std::vector<size_t> slot(n + 1, SIZE_MAX);
+        for (int i = 0; i <= n; ++i)
+            if (slot_states[i] > 0) slot[i] = take(row * slot_states[i]);
+        {
+            int base = 0;
+            for (int k = 1; k < n; ++k) {
+                if (p->stored[k]) base = k;
+                else L.layer[k] = slot[k - base - 1];
             }
         }
         if (n >= 2) L.g[0] = take(row * p->F[n - 1]);
@@ -384,16 +389,21 @@ slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t d
         }
         p->K = detection == SLOS_DETECT_PNR ? p->F[n] : acc;
     }
-    // checkpoint schedule: keep layers k = n-1, n-1-s, n-1-2s, ... (s minimal within budget)
+    // checkpoint schedule: keep layers k = n-1, n-1-s, n-1-2s, ... with the
+    // smallest s whose kept layers plus one recompute segment fit the budget
+    // (a_n is always kept: it seeds the backward pass)
     auto bytes_for = [&](int s) {
-        int64_t states = p->F[n];  // a_n
-        int64_t fmax_ns = 0;
+        int64_t states = 0, seg = 0, seg_max = 0;
         for (int k = 1; k < n; ++k) {
-            if ((n - 1 - k) % s == 0) states += p->F[k];
-            else fmax_ns = std::max(fmax_ns, p->F[k]);
+            if ((n - 1 - k) % s == 0) {
+                states += p->F[k];
+                seg = 0;
+            } else {
+                seg += p->F[k];
+                seg_max = std::max(seg_max, seg);
+            }
         }
-        states += (int64_t)(s - 1) * fmax_ns;
-        return (size_t)states * sizeof(float2);
+        return (size_t)(states + seg_max) * sizeof(float2);
     };
     int s = 1;
     if (mem_budget_bytes > 0) {

@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace slos {
 
 constexpr int kMaxModes = 24;
@@ -155,6 +157,43 @@ __device__ __forceinline__ uint32_t colex_rank(uint32_t mask) {
         mask &= mask - 1;
     }
     return r;
+}
+
+
+// ---------------------------------------------------------------- bar masks
+// The same state as a bitmask of bar positions (bit p_b set).  Descending-lex
+// order on compositions is colex order on bar sets, i.e. increasing integer
+// order among masks with m-1 bits set, so the successor is the next larger
+// integer with the same popcount (Gosper's next-combination step).
+template <int MMAX>
+struct BarMask {
+    // up to 20 modes and 12 photons the string has at most 31 symbols
+    using T = typename std::conditional<(MMAX + kMaxPhotons - 1 <= 32), uint32_t, unsigned long long>::type;
+};
+
+__device__ __forceinline__ uint32_t next_comb(uint32_t z) {
+    const uint32_t c = z & (0u - z);
+    const uint32_t r = z + c;
+    return r | (((r ^ z) >> 2) >> (__ffs(z) - 1));
+}
+__device__ __forceinline__ unsigned long long next_comb(unsigned long long z) {
+    const unsigned long long c = z & (0ull - z);
+    const unsigned long long r = z + c;
+    return r | (((r ^ z) >> 2) >> (__ffsll((long long)z) - 1));
+}
+// Highest set bit position of a nonzero mask.
+__device__ __forceinline__ int top_bit(uint32_t z) { return 31 - __clz(z); }
+__device__ __forceinline__ int top_bit(unsigned long long z) { return 63 - __clzll((long long)z); }
+
+template <int MMAX, typename Z>
+__device__ __forceinline__ Z unrank_mask(int64_t r, int m, int L) {
+    int p[MMAX];
+    unrank_bars<MMAX>(r, m, L, p);
+    Z z = 0;
+#pragma unroll
+    for (int b = 0; b < MMAX - 1; ++b)
+        if (b < m - 1) z |= (Z)1 << p[b];
+    return z;
 }
 
 }  // namespace slos

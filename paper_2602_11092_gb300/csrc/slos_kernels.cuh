@@ -63,11 +63,21 @@ struct PrepArgs {
 };
 
 constexpr int kWarpsPerBlock = 8;
+constexpr int kCStore = 8;  // states per warp iteration, intermediate layers
+constexpr int kCFinal = 8;  // final layer
+constexpr int kCBwd = 4;    // parents per warp iteration, backward
 constexpr int kThreads = kWarpsPerBlock * 32;
 
 // ------------------------------------------------------------------ forward
-template <int MMAX, int EPI, bool SAVE>
+// Each warp walks a chunk of consecutive Fock states of layer k, C states at a
+// time.  The mode loop is outermost and warp-uniform (so U[j, c_k] of the
+// lane's instance is a register), and for each mode the C states' parent
+// loads are independent, which keeps 8+ coalesced 256-byte loads in flight
+// per warp.  A state is carried as its bar mask; the next state is the next
+// larger mask with the same popcount.
+template <int MMAX, int EPI, bool SAVE, int C>
 __global__ void __launch_bounds__(kThreads) slos_fwd_kernel(FwdArgs a) {
+    using Z = typename BarMask<MMAX>::T;
     extern __shared__ float4 smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -83,68 +93,86 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_kernel(FwdArgs a) {
         u[j] = make_float2(0.f, 0.f);
         if (j < m && valid) u[j] = a.U[((int64_t)inst * m + j) * m + a.col];
     }
-
-    const int64_t gprev = (int64_t)grp * a.Fprev;
-    const int64_t gnext = (int64_t)grp * a.Fk;
+    const float2 *prevg = a.prev + (int64_t)grp * a.Fprev * kLanes + lane;
+    float2 *nextg = a.next + (int64_t)grp * a.Fk * kLanes + lane;
     const int64_t nchunks = (a.Fk + a.chunk - 1) / a.chunk;
     const int64_t wstride = (int64_t)gridDim.x * kWarpsPerBlock;
-
-    // per-warp staging tile for the [B][K] output: tile[lane(instance)][33]
     float *tile = reinterpret_cast<float *>(smem_raw) + warp * (32 * 33 * (EPI == EPI_AMPS ? 2 : 1));
 
     for (int64_t ch = (int64_t)blockIdx.x * kWarpsPerBlock + warp; ch < nchunks; ch += wstride) {
         const int64_t c0 = ch * a.chunk;
         const int64_t c1 = min(c0 + (int64_t)a.chunk, a.Fk);
-        int p[MMAX];
-        unrank_bars<MMAX>(c0, m, L, p);
+        Z z = unrank_mask<MMAX, Z>(c0, m, L);
         int run_pat = -1;
         float run_val = 0.f;
-        for (int64_t c = c0; c < c1; ++c) {
-            float2 acc = make_float2(0.f, 0.f);
-            int64_t S = 0;
-            float fprod = 1.f;
-            uint32_t supp = 0;
+        for (int64_t cb = c0; cb < c1; cb += C) {
+            Z rem[C];
+            int prevbar[C], S[C];
+            float2 acc[C];
+            float fp[C];
+            uint32_t supp[C];
+            bool live[C];
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                live[i] = cb + i < c1;
+                rem[i] = z;
+                z = next_comb(z);
+                prevbar[i] = L;
+                S[i] = 0;
+                acc[i] = make_float2(0.f, 0.f);
+                fp[i] = 1.f;
+                supp[i] = 0u;
+            }
+#pragma unroll
+            for (int i = 0; i < C; ++i)
+                if (!live[i]) rem[i] = rem[0];  // keep index arithmetic in range
 #pragma unroll
             for (int j = 0; j < MMAX; ++j) {
                 if (j < m) {
-                    const int tj = occupation<MMAX>(j, m, L, p);
-                    if (tj > 0) {
-                        float2 v;
-                        if (a.k == 1) {
-                            v = make_float2(1.f, 0.f);
-                        } else {
-                            v = __ldg(&a.prev[(gprev + (c - S)) * kLanes + lane]);
+#pragma unroll
+                    for (int i = 0; i < C; ++i) {
+                        int pb = -1;
+                        if (j < m - 1) {
+                            pb = top_bit(rem[i]);
+                            rem[i] ^= (Z)1 << pb;
                         }
-                        acc = cfma(u[j], v, acc);
-                        if (EPI != EPI_STORE) {
-                            fprod *= c_fact.v[tj];
-                            supp |= 1u << j;
+                        const int tj = prevbar[i] - pb - 1;
+                        prevbar[i] = pb;
+                        if (tj > 0 && live[i]) {
+                            const float2 v = (a.k == 1) ? make_float2(1.f, 0.f)
+                                                        : __ldg(prevg + (int64_t)(cb + i - S[i]) * kLanes);
+                            acc[i] = cfma(u[j], v, acc[i]);
+                            if (EPI != EPI_STORE) {
+                                fp[i] *= c_fact.v[tj];
+                                supp[i] |= 1u << j;
+                            }
                         }
+                        if (j < m - 1) S[i] += (int)binom_m1(pb, m - 2 - j);
                     }
-                    if (j < m - 1) S += (int64_t)binom_m1(p[j], m - 2 - j);
                 }
             }
-            if (SAVE || EPI == EPI_STORE) a.next[(gnext + c) * kLanes + lane] = acc;
-            if (EPI == EPI_PROBS) {
-                const float w = fprod * a.inv_sfact;
-                tile[lane * 33 + (int)(c - c0)] = w * (acc.x * acc.x + acc.y * acc.y);
-            } else if (EPI == EPI_AMPS) {
-                const float sw = sqrtf(fprod * a.inv_sfact);
-                float2 *t2 = reinterpret_cast<float2 *>(tile);
-                t2[lane * 33 + (int)(c - c0)] = cscale(acc, sw);
-            } else if (EPI == EPI_THRESH) {
-                const float w = fprod * a.inv_sfact;
-                const float pr = w * (acc.x * acc.x + acc.y * acc.y);
-                const int pat = a.pat_off[__popc(supp)] + (int)colex_rank(supp);
-                if (pat != run_pat) {
-                    if (run_pat >= 0 && valid)
-                        atomicAdd(reinterpret_cast<float *>(a.out) + (int64_t)inst * a.K + run_pat, run_val);
-                    run_pat = pat;
-                    run_val = 0.f;
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                if (!live[i]) continue;
+                const int64_t c = cb + i;
+                if (SAVE || EPI == EPI_STORE) nextg[c * kLanes] = acc[i];
+                if (EPI == EPI_PROBS) {
+                    tile[lane * 33 + (int)(c - c0)] = fp[i] * a.inv_sfact * (acc[i].x * acc[i].x + acc[i].y * acc[i].y);
+                } else if (EPI == EPI_AMPS) {
+                    float2 *t2 = reinterpret_cast<float2 *>(tile);
+                    t2[lane * 33 + (int)(c - c0)] = cscale(acc[i], sqrtf(fp[i] * a.inv_sfact));
+                } else if (EPI == EPI_THRESH) {
+                    const float pr = fp[i] * a.inv_sfact * (acc[i].x * acc[i].x + acc[i].y * acc[i].y);
+                    const int pat = a.pat_off[__popc(supp[i])] + (int)colex_rank(supp[i]);
+                    if (pat != run_pat) {
+                        if (run_pat >= 0 && valid)
+                            atomicAdd(reinterpret_cast<float *>(a.out) + (int64_t)inst * a.K + run_pat, run_val);
+                        run_pat = pat;
+                        run_val = 0.f;
+                    }
+                    run_val += pr;
                 }
-                run_val += pr;
             }
-            next_bars<MMAX>(m, L, p);
         }
         if (EPI == EPI_THRESH) {
             if (run_pat >= 0 && valid)
@@ -175,9 +203,10 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_kernel(FwdArgs a) {
 //      G_{k-1}(t') = sum_j conj(U[j, c_k]) G_k(t' + e_j)
 //      dU[j, c_k] += conj(a_{k-1}(t')) G_k(t' + e_j)
 // For k == n the child gradient is formed on the fly from a_n and the output
-// gradient (seed).
-template <int MMAX, int SEED>
+// gradient (seed).  C parents per warp iteration, mode loop outermost.
+template <int MMAX, int SEED, int C>
 __global__ void __launch_bounds__(kThreads) slos_bwd_kernel(BwdArgs a) {
+    using Z = typename BarMask<MMAX>::T;
     __shared__ float2 red[kWarpsPerBlock][32];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -194,56 +223,101 @@ __global__ void __launch_bounds__(kThreads) slos_bwd_kernel(BwdArgs a) {
         dU[j] = make_float2(0.f, 0.f);
         if (j < m && valid) u[j] = a.U[((int64_t)inst * m + j) * m + a.col];
     }
-    const int64_t gprev = (int64_t)grp * a.Fprev;
-    const int64_t gk = (int64_t)grp * a.Fk;
+    const int64_t gofs_prev = (int64_t)grp * a.Fprev * kLanes + lane;
+    const int64_t gofs_k = (int64_t)grp * a.Fk * kLanes + lane;
     const int64_t nchunks = (a.Fprev + a.chunk - 1) / a.chunk;
     const int64_t wstride = (int64_t)gridDim.x * kWarpsPerBlock;
 
     for (int64_t ch = (int64_t)blockIdx.x * kWarpsPerBlock + warp; ch < nchunks; ch += wstride) {
         const int64_t c0 = ch * a.chunk;
         const int64_t c1 = min(c0 + (int64_t)a.chunk, a.Fprev);
-        int p[MMAX];
-        unrank_bars<MMAX>(c0, m, L, p);
-        for (int64_t c = c0; c < c1; ++c) {
-            const float2 av = (a.k == 1) ? make_float2(1.f, 0.f) : __ldg(&a.aprev[(gprev + c) * kLanes + lane]);
-            float fp = 1.f;
-            if (SEED != SEED_G) {
+        Z z = unrank_mask<MMAX, Z>(c0, m, L);
+        for (int64_t cb = c0; cb < c1; cb += C) {
+            Z rem[C];
+            int prevbar[C], S[C];
+            float2 av[C], gacc[C];
+            float fp[C];
+            bool live[C];
 #pragma unroll
-                for (int j = 0; j < MMAX; ++j)
-                    if (j < m) fp *= c_fact.v[occupation<MMAX>(j, m, L, p)];
+            for (int i = 0; i < C; ++i) {
+                live[i] = cb + i < c1;
+                rem[i] = z;
+                z = next_comb(z);
+                prevbar[i] = L;
+                S[i] = 0;
+                gacc[i] = make_float2(0.f, 0.f);
+                fp[i] = 1.f;
             }
-            float2 gacc = make_float2(0.f, 0.f);
-            int64_t S = 0;
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                if (!live[i]) rem[i] = rem[0];
+                av[i] = make_float2(0.f, 0.f);
+                if (live[i]) av[i] = (a.k == 1) ? make_float2(1.f, 0.f) : __ldg(a.aprev + gofs_prev + (cb + i) * kLanes);
+            }
+            if (SEED != SEED_G) {
+                // prod_l t'_l! of each parent
+#pragma unroll
+                for (int i = 0; i < C; ++i) {
+                    Z r2 = rem[i];
+                    int pv = L;
+#pragma unroll
+                    for (int j = 0; j < MMAX; ++j) {
+                        if (j < m) {
+                            int pb = -1;
+                            if (j < m - 1) {
+                                pb = top_bit(r2);
+                                r2 ^= (Z)1 << pb;
+                            }
+                            fp[i] *= c_fact.v[pv - pb - 1];
+                            pv = pb;
+                        }
+                    }
+                }
+            }
 #pragma unroll
             for (int j = 0; j < MMAX; ++j) {
                 if (j < m) {
-                    const int64_t cidx = c + S;
-                    const int64_t off = (gk + cidx) * kLanes + lane;
-                    float2 g;
-                    if (SEED == SEED_G) {
-                        g = __ldg(&a.Gk[off]);
-                    } else {
-                        const int tj = occupation<MMAX>(j, m, L, p);
-                        const float w = fp * (float)(tj + 1) * a.inv_sfact;
-                        const float2 an = __ldg(&a.an[off]);
-                        if (SEED == SEED_PROBS_BCAST) {
-                            const float dp = __ldg(reinterpret_cast<const float *>(a.seed) + cidx);
-                            g = cscale(an, 2.f * dp * w);
-                        } else if (SEED == SEED_PROBS_T) {
-                            const float dp = __ldg(reinterpret_cast<const float *>(a.seed) + off);
-                            g = cscale(an, 2.f * dp * w);
-                        } else {
-                            const float2 d = __ldg(reinterpret_cast<const float2 *>(a.seed) + off);
-                            g = cscale(d, sqrtf(w));
+#pragma unroll
+                    for (int i = 0; i < C; ++i) {
+                        int pb = -1;
+                        if (j < m - 1) {
+                            pb = top_bit(rem[i]);
+                            rem[i] ^= (Z)1 << pb;
                         }
+                        const int tj = prevbar[i] - pb - 1;
+                        prevbar[i] = pb;
+                        const int64_t cidx = cb + i + S[i];
+                        const int64_t off = gofs_k + cidx * kLanes;
+                        float2 g = make_float2(0.f, 0.f);
+                        if (live[i]) {
+                            if (SEED == SEED_G) {
+                                g = __ldg(a.Gk + off);
+                            } else {
+                                const float w = fp[i] * (float)(tj + 1) * a.inv_sfact;
+                                const float2 an = __ldg(a.an + off);
+                                if (SEED == SEED_PROBS_BCAST) {
+                                    const float dp = __ldg(reinterpret_cast<const float *>(a.seed) + cidx);
+                                    g = cscale(an, 2.f * dp * w);
+                                } else if (SEED == SEED_PROBS_T) {
+                                    const float dp = __ldg(reinterpret_cast<const float *>(a.seed) + off);
+                                    g = cscale(an, 2.f * dp * w);
+                                } else {
+                                    const float2 d = __ldg(reinterpret_cast<const float2 *>(a.seed) + off);
+                                    g = cscale(d, sqrtf(w));
+                                }
+                            }
+                        }
+                        gacc[i] = cfma_conj_a(u[j], g, gacc[i]);
+                        dU[j] = cfma_conj_a(av[i], g, dU[j]);
+                        if (j < m - 1) S[i] += (int)binom(pb, m - 2 - j);
                     }
-                    gacc = cfma_conj_a(u[j], g, gacc);
-                    dU[j] = cfma_conj_a(av, g, dU[j]);
-                    if (j < m - 1) S += (int64_t)binom(p[j], m - 2 - j);
                 }
             }
-            if (a.k > 1) a.Gprev[(gprev + c) * kLanes + lane] = gacc;
-            next_bars<MMAX>(m, L, p);
+            if (a.k > 1) {
+#pragma unroll
+                for (int i = 0; i < C; ++i)
+                    if (live[i]) a.Gprev[gofs_prev + (cb + i) * kLanes] = gacc[i];
+            }
         }
     }
     // reduce dU over the warps of this block, one mode at a time
@@ -322,10 +396,10 @@ inline size_t fwd_smem_bytes(int epi) {
 #define SLOS_DEFINE_LAUNCHERS(MM)                                                                            \
     cudaError_t slos_init_m##MM() {                                                                          \
         const int sm = (int)fwd_smem_bytes(EPI_AMPS);                                                        \
-        cudaError_t e = cudaFuncSetAttribute(slos_fwd_kernel<MM, EPI_AMPS, false>,                          \
+        cudaError_t e = cudaFuncSetAttribute(slos_fwd_kernel<MM, EPI_AMPS, false, kCFinal>,                          \
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm);               \
         if (e != cudaSuccess) return e;                                                                      \
-        return cudaFuncSetAttribute(slos_fwd_kernel<MM, EPI_AMPS, true>,                                    \
+        return cudaFuncSetAttribute(slos_fwd_kernel<MM, EPI_AMPS, true, kCFinal>,                                    \
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, sm);                        \
     }                                                                                                        \
     cudaError_t slos_launch_fwd_m##MM(const FwdArgs &a, int epi, bool save, int blocks_x, cudaStream_t s) { \
@@ -333,13 +407,13 @@ inline size_t fwd_smem_bytes(int epi) {
         const size_t sm = fwd_smem_bytes(epi);                                                               \
         switch (epi * 2 + (save ? 1 : 0)) {                                                                  \
             case 0:                                                                                          \
-            case 1: slos_fwd_kernel<MM, EPI_STORE, true><<<grid, kThreads, 0, s>>>(a); break;               \
-            case 2: slos_fwd_kernel<MM, EPI_PROBS, false><<<grid, kThreads, sm, s>>>(a); break;             \
-            case 3: slos_fwd_kernel<MM, EPI_PROBS, true><<<grid, kThreads, sm, s>>>(a); break;              \
-            case 4: slos_fwd_kernel<MM, EPI_AMPS, false><<<grid, kThreads, sm, s>>>(a); break;              \
-            case 5: slos_fwd_kernel<MM, EPI_AMPS, true><<<grid, kThreads, sm, s>>>(a); break;               \
-            case 6: slos_fwd_kernel<MM, EPI_THRESH, false><<<grid, kThreads, 0, s>>>(a); break;             \
-            case 7: slos_fwd_kernel<MM, EPI_THRESH, true><<<grid, kThreads, 0, s>>>(a); break;              \
+            case 1: slos_fwd_kernel<MM, EPI_STORE, true, kCStore><<<grid, kThreads, 0, s>>>(a); break;               \
+            case 2: slos_fwd_kernel<MM, EPI_PROBS, false, kCFinal><<<grid, kThreads, sm, s>>>(a); break;             \
+            case 3: slos_fwd_kernel<MM, EPI_PROBS, true, kCFinal><<<grid, kThreads, sm, s>>>(a); break;              \
+            case 4: slos_fwd_kernel<MM, EPI_AMPS, false, kCFinal><<<grid, kThreads, sm, s>>>(a); break;              \
+            case 5: slos_fwd_kernel<MM, EPI_AMPS, true, kCFinal><<<grid, kThreads, sm, s>>>(a); break;               \
+            case 6: slos_fwd_kernel<MM, EPI_THRESH, false, kCFinal><<<grid, kThreads, 0, s>>>(a); break;             \
+            case 7: slos_fwd_kernel<MM, EPI_THRESH, true, kCFinal><<<grid, kThreads, 0, s>>>(a); break;              \
             default: return cudaErrorInvalidValue;                                                           \
         }                                                                                                    \
         return cudaGetLastError();                                                                           \
@@ -347,10 +421,10 @@ inline size_t fwd_smem_bytes(int epi) {
     cudaError_t slos_launch_bwd_m##MM(const BwdArgs &a, int seed, int blocks_x, cudaStream_t s) {           \
         dim3 grid(blocks_x, a.NG);                                                                           \
         switch (seed) {                                                                                      \
-            case SEED_G: slos_bwd_kernel<MM, SEED_G><<<grid, kThreads, 0, s>>>(a); break;                   \
-            case SEED_PROBS_BCAST: slos_bwd_kernel<MM, SEED_PROBS_BCAST><<<grid, kThreads, 0, s>>>(a); break; \
-            case SEED_PROBS_T: slos_bwd_kernel<MM, SEED_PROBS_T><<<grid, kThreads, 0, s>>>(a); break;       \
-            case SEED_AMPS_T: slos_bwd_kernel<MM, SEED_AMPS_T><<<grid, kThreads, 0, s>>>(a); break;         \
+            case SEED_G: slos_bwd_kernel<MM, SEED_G, kCBwd><<<grid, kThreads, 0, s>>>(a); break;                   \
+            case SEED_PROBS_BCAST: slos_bwd_kernel<MM, SEED_PROBS_BCAST, kCBwd><<<grid, kThreads, 0, s>>>(a); break; \
+            case SEED_PROBS_T: slos_bwd_kernel<MM, SEED_PROBS_T, kCBwd><<<grid, kThreads, 0, s>>>(a); break;       \
+            case SEED_AMPS_T: slos_bwd_kernel<MM, SEED_AMPS_T, kCBwd><<<grid, kThreads, 0, s>>>(a); break;         \
             default: return cudaErrorInvalidValue;                                                           \
         }                                                                                                    \
         return cudaGetLastError();                                                                           \

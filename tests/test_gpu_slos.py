@@ -185,7 +185,7 @@ def test_train16_full_size_sampled_outputs(slos):
     theta = torch.tensor(mb.theta, dtype=torch.float32, device=dev())
     data = torch.tensor(mb.data, dtype=torch.float32, device=dev())
     U = slos.mesh_unitary(16, theta, data, 256)
-    plan = slos.Plan(16, w["s"], mem_budget_bytes=2_000_000)
+    plan = slos.Plan(16, w["s"], mem_budget_bytes=1_950_000)
     ws = plan.workspace(256, training=True)
     p = plan.forward(U, save_for_backward=True, workspace=ws).cpu().numpy()
     K = plan.n_outputs
@@ -320,8 +320,10 @@ def test_checkpointing_is_bitwise_equal_to_full_store(slos):
         res.append((p, plan.backward(U, c, ws)))
     assert torch.equal(res[0][0], res[1][0])
     assert torch.equal(res[0][1], res[1][1])
-    for budget in (200_000, 50_000):
+    # m=10, n=5: keeping layers 1..4 takes 8000 bytes; 7950 forces stride 2
+    for budget, stride in ((7950, 2), (8000, 1)):
         mid = slos.Plan(m, s, mem_budget_bytes=budget)
+        assert mid.checkpoint_stride == stride
         ws = mid.workspace(B, training=True)
         mid.forward(U, save_for_backward=True, workspace=ws)
         assert torch.equal(mid.backward(U, c, ws), res[0][1])
@@ -363,7 +365,7 @@ def test_train16_gradients_against_fd_on_8_samples(slos):
     w = workloads.train16(batch=8)
     mb = w["mesh"]
     m, s = 16, w["s"]
-    plan = slos.Plan(m, s, mem_budget_bytes=2_000_000)
+    plan = slos.Plan(m, s, mem_budget_bytes=1_950_000)
     assert plan.checkpoint_stride > 1
     K = plan.n_outputs
     rng = np.random.default_rng(1002)
