@@ -6,7 +6,8 @@
  * only its small device-side status word.  Every call that takes a `stream`
  * (a cudaStream_t passed as void*, NULL = legacy default stream) is
  * asynchronous on that stream, allocates nothing and does not synchronise, so
- * it can be captured in a CUDA graph.  Errors are returned as status codes and
+ * it can be captured in a CUDA graph.  A plan additionally owns its transition
+ * tables (allocated and filled once by slos_plan).  Errors are returned as status codes and
  * never thrown; `slos_last_error()` gives a message for the calling thread.
  *
  * Physics (Sec. II-A.1 "Essentials of linear optics"): an n-photon Fock state
@@ -195,6 +196,14 @@ slos_status_t slos_batched_autotune(slos_plan_t plan, const void *U_packed, floa
 int64_t slos_host_rank(int m, const int *t);
 /* Host: inverse of slos_host_rank; writes m ints. */
 slos_status_t slos_host_unrank(int m, int k, int64_t rank, int *t);
+
+/* Host: the transition graph of layer k (Sec. II-A.3) that plans build
+ * once and reuse.  rowptr: int32 [C(m+k-1,k) + 1]; entries: uint32
+ * [m * C(m+k-2,k-1)], child c owns entries rowptr[c] .. rowptr[c+1]-1, each
+ * (parent rank << 6) | (mode << 1) | last; ctab: int32 [C(m+k-2,k-1)][m],
+ * ctab[c'][j] = rank_k(t' + e_j).  Host buffers owned by the caller; any may
+ * be NULL.  SLOS_ERR_UNSUPPORTED when parent ranks do not fit 26 bits. */
+slos_status_t slos_host_transition_table(int m, int k, int32_t *rowptr, uint32_t *entries, int32_t *ctab);
 
 /* Device: for ranks [first, first + count) of layer k (k photons, m modes)
  * write the composition (uint8 [count][m]) and the parent index

@@ -61,6 +61,7 @@ _SIGNATURES = {
     "slos_host_rank": ([_int, ctypes.POINTER(_int)], _i64),
     "slos_host_unrank": ([_int, _int, _i64, ctypes.POINTER(_int)], _int),
     "slos_device_index_table": ([_int, _int, _i64, _i64, _vp, _vp, _vp], _int),
+    "slos_host_transition_table": ([_int, _int, _vp, _vp, _vp], _int),
     "slos_profile_enable": ([_int], _int),
     "slos_profile_reset": ([], _int),
     "slos_launch_count": ([], _i64),
@@ -276,6 +277,18 @@ def host_unrank(m: int, k: int, rank: int):
     arr = (ctypes.c_int * m)()
     _check(load().slos_host_unrank(m, k, rank, arr))
     return list(arr)
+
+
+def host_transition_table(m: int, k: int):
+    """(rowptr, entries, ctab) numpy arrays of layer k, built by the library."""
+    import math
+    import numpy as np
+    Fk, Fp = math.comb(m + k - 1, k), math.comb(m + k - 2, k - 1)
+    rowptr = np.zeros(Fk + 1, dtype=np.int32)
+    entries = np.zeros(m * Fp, dtype=np.uint32)
+    ctab = np.zeros(Fp * m, dtype=np.int32)
+    _check(load().slos_host_transition_table(m, k, rowptr.ctypes.data, entries.ctypes.data, ctab.ctypes.data))
+    return rowptr, entries, ctab.reshape(Fp, m)
 
 
 def device_index_table(m: int, k: int, first: int, count: int, device="cuda", stream=None):

@@ -17,6 +17,7 @@
 #include "plan.h"
 #include "profile.h"
 #include "slos_kernels.cuh"
+#include "tab_launch.h"
 
 namespace slos {
 
@@ -66,13 +67,22 @@ cudaError_t launch_bwd(int m, const BwdArgs &a, int seed, int bx, cudaStream_t s
         default: return slos_launch_bwd_m24(a, seed, bx, s);
     }
 }
-cudaError_t launch_prep(int m, const PrepArgs &a, int bx, cudaStream_t s) {
+cudaError_t launch_prep(int m, const PrepArgs &a, int bx, bool bcast, cudaStream_t s) {
     switch (mmax_for(m)) {
-        case 8: return slos_launch_prep_m8(a, bx, s);
-        case 12: return slos_launch_prep_m12(a, bx, s);
-        case 16: return slos_launch_prep_m16(a, bx, s);
-        case 20: return slos_launch_prep_m20(a, bx, s);
-        default: return slos_launch_prep_m24(a, bx, s);
+        case 8: return slos_launch_prep_m8(a, bx, bcast, s);
+        case 12: return slos_launch_prep_m12(a, bx, bcast, s);
+        case 16: return slos_launch_prep_m16(a, bx, bcast, s);
+        case 20: return slos_launch_prep_m20(a, bx, bcast, s);
+        default: return slos_launch_prep_m24(a, bx, bcast, s);
+    }
+}
+cudaError_t launch_bwd_tab(int m, const BwdArgs &a, const int32_t *ctab, int seed, int bx, cudaStream_t s) {
+    switch (mmax_for(m)) {
+        case 8: return slos_launch_bwd_tab_m8(a, ctab, seed, bx, s);
+        case 12: return slos_launch_bwd_tab_m12(a, ctab, seed, bx, s);
+        case 16: return slos_launch_bwd_tab_m16(a, ctab, seed, bx, s);
+        case 20: return slos_launch_bwd_tab_m20(a, ctab, seed, bx, s);
+        default: return slos_launch_bwd_tab_m24(a, ctab, seed, bx, s);
     }
 }
 
@@ -86,6 +96,7 @@ static cudaError_t init_device_once(int dev) {
     if ((e = slos_init_m16()) != cudaSuccess) return e;
     if ((e = slos_init_m20()) != cudaSuccess) return e;
     if ((e = slos_init_m24()) != cudaSuccess) return e;
+    if ((e = slos_tab_init()) != cudaSuccess) return e;
     done[dev] = true;
     return cudaSuccess;
 }
@@ -128,6 +139,159 @@ void host_unrank(int m, int k, int64_t r, int *t) {
     }
 }
 
+
+// ------------------------------------------------------------------ transition graph
+// Built on the host by walking each layer in descending-lex order with the
+// bar mask (next larger integer with the same popcount) and the closed-form
+// parent/child rank offsets, then uploaded once.
+static uint64_t next_comb_host(uint64_t z) {
+    const uint64_t c = z & (0ull - z);
+    const uint64_t r = z + c;
+    return r | (((r ^ z) >> 2) >> __builtin_ctzll(z));
+}
+
+static void bars_of(uint64_t z, int m, int L, int *p, int *t) {
+    // p[b]: b-th highest set bit; t[j] = p[j-1] - p[j] - 1
+    int b = 0;
+    for (int q = L - 1; q >= 0 && b < m - 1; --q)
+        if ((z >> q) & 1ull) p[b++] = q;
+    for (int j = 0; j < m; ++j) {
+        const int hi = (j == 0) ? L : p[j - 1];
+        const int lo = (j < m - 1) ? p[j] : -1;
+        t[j] = hi - lo - 1;
+    }
+}
+
+static void free_tables(slos_plan_s *p) {
+    for (auto &L : p->tab.layer) {
+        if (L.rowptr) cudaFree(L.rowptr);
+        if (L.entries) cudaFree(L.entries);
+        if (L.ctab) cudaFree(L.ctab);
+        L = LayerTables();
+    }
+    if (p->tab.w) cudaFree(p->tab.w);
+    if (p->tab.pat) cudaFree(p->tab.pat);
+    p->tab.w = nullptr;
+    p->tab.pat = nullptr;
+    p->tab.enabled = false;
+}
+
+// Transition graph of layer k (k photons, m modes) on the host: CSR parent
+// entries of every child state and the child table of every parent state.
+static void build_layer_host(int m, int k, std::vector<int32_t> &rowptr, std::vector<uint32_t> &entries,
+                             std::vector<int32_t> &ctab) {
+    const int64_t Fk = binom_host(m + k - 1, k), Fp = binom_host(m + k - 2, k - 1);
+    std::vector<int> bar(m + 1), t(m + 1);
+    uint64_t first = 0;  // (k, 0, ..., 0): all bars packed at the end of the string
+    for (int b = 0; b < m - 1; ++b) first |= 1ull << b;
+    const int L = k + m - 1;
+    rowptr.assign(Fk + 1, 0);
+    entries.clear();
+    entries.reserve((size_t)m * Fp);
+    uint64_t z = first;
+    for (int64_t c = 0; c < Fk; ++c) {
+        bars_of(z, m, L, bar.data(), t.data());
+        rowptr[c] = (int32_t)entries.size();
+        int64_t S = 0;
+        for (int j = 0; j < m; ++j) {
+            if (t[j] > 0) entries.push_back((uint32_t)((c - S) << 6) | (uint32_t)(j << 1));
+            if (j < m - 1) S += bar[j] > 0 ? binom_host(bar[j] - 1, m - 2 - j) : 0;
+        }
+        entries.back() |= 1u;
+        z = next_comb_host(z);
+    }
+    rowptr[Fk] = (int32_t)entries.size();
+    const int Lp = (k - 1) + m - 1;
+    ctab.assign((size_t)Fp * m, 0);
+    if (k == 1) {
+        for (int j = 0; j < m; ++j) ctab[j] = j;  // vacuum -> e_j has rank j
+        return;
+    }
+    z = first;
+    for (int64_t c = 0; c < Fp; ++c) {
+        bars_of(z, m, Lp, bar.data(), t.data());
+        int64_t S = 0;
+        for (int j = 0; j < m; ++j) {
+            ctab[(size_t)c * m + j] = (int32_t)(c + S);
+            if (j < m - 1) S += binom_host(bar[j], m - 2 - j);
+        }
+        z = next_comb_host(z);
+    }
+}
+
+static slos_status_t build_tables(slos_plan_s *p) {
+    const int m = p->m, n = p->n;
+    size_t bytes = 0;
+    for (int k = 1; k <= n; ++k) {
+        if (p->F[k - 1] >= kMaxTableParent || p->F[k] >= ((int64_t)1 << 31) / m) return SLOS_OK;  // too large
+        bytes += 4 * (size_t)(p->F[k] + 1) + 8 * (size_t)m * p->F[k - 1];
+    }
+    bytes += 8 * (size_t)p->F[n];
+    if (bytes > kTableBudgetBytes) return SLOS_OK;
+    p->tab.layer.assign(n + 1, LayerTables());
+    std::vector<int> bar(m + 1), t(m + 1);
+    auto init_mask = [&](int k) {
+        // first state (k, 0, ..., 0): all bars at the end of the string
+        uint64_t z = 0;
+        for (int b = 0; b < m - 1; ++b) z |= 1ull << b;
+        (void)k;
+        return z;
+    };
+    for (int k = 1; k <= n; ++k) {
+        std::vector<int32_t> rowptr, ctab;
+        std::vector<uint32_t> entries;
+        build_layer_host(m, k, rowptr, entries, ctab);
+        LayerTables &LT = p->tab.layer[k];
+        if (cudaMalloc(&LT.rowptr, rowptr.size() * 4) != cudaSuccess ||
+            cudaMalloc(&LT.entries, entries.size() * 4) != cudaSuccess ||
+            cudaMalloc(&LT.ctab, ctab.size() * 4) != cudaSuccess) {
+            free_tables(p);
+            return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the transition tables");
+        }
+        cudaMemcpy(LT.rowptr, rowptr.data(), rowptr.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(LT.entries, entries.data(), entries.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(LT.ctab, ctab.data(), ctab.size() * 4, cudaMemcpyHostToDevice);
+    }
+    // final-layer weights and threshold patterns
+    {
+        const int L = n + m - 1;
+        std::vector<float> w(p->F[n]);
+        std::vector<int32_t> pat(p->F[n]);
+        uint64_t z = init_mask(n);
+        for (int64_t c = 0; c < p->F[n]; ++c) {
+            bars_of(z, m, L, bar.data(), t.data());
+            double f = 1.0;
+            uint32_t supp = 0;
+            for (int j = 0; j < m; ++j) {
+                for (int q = 2; q <= t[j]; ++q) f *= q;
+                if (t[j] > 0) supp |= 1u << j;
+            }
+            w[c] = (float)(f * (double)p->inv_sfact);
+            int64_t r = 0;
+            int i = 1;
+            for (int q = 0; q < m; ++q)
+                if ((supp >> q) & 1u) r += binom_host(q, i++);
+            pat[c] = p->pat_off[__builtin_popcount(supp)] + (int32_t)r;
+            z = next_comb_host(z);
+        }
+        if (cudaMalloc(&p->tab.w, w.size() * 4) != cudaSuccess) {
+            free_tables(p);
+            return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the weight table");
+        }
+        cudaMemcpy(p->tab.w, w.data(), w.size() * 4, cudaMemcpyHostToDevice);
+        if (p->det == SLOS_DETECT_THRESHOLD) {
+            if (cudaMalloc(&p->tab.pat, pat.size() * 4) != cudaSuccess) {
+                free_tables(p);
+                return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the pattern table");
+            }
+            cudaMemcpy(p->tab.pat, pat.data(), pat.size() * 4, cudaMemcpyHostToDevice);
+        }
+    }
+    p->tab.bytes = bytes;
+    p->tab.enabled = true;
+    return SLOS_OK;
+}
+
 // ------------------------------------------------------------------ layouts
 static int groups_for(int batch) { return (batch + kLanes - 1) / kLanes; }
 
@@ -151,6 +315,7 @@ static Layout make_layout(const slos_plan_s *p, int batch, bool training) {
     L.g[0] = L.g[1] = SIZE_MAX;
     L.seedT = SIZE_MAX;
     L.dupart.assign(n + 1, SIZE_MAX);
+    L.dpw = SIZE_MAX;
     L.bwd_blocks.assign(n + 1, 0);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -190,8 +355,9 @@ static Layout make_layout(const slos_plan_s *p, int batch, bool training) {
         if (n >= 2) L.g[0] = take(row * p->F[n - 1]);
         if (n >= 3) L.g[1] = take(row * p->F[n - 2]);
         L.seedT = take(row * p->F[n]);  // c64-sized: enough for either seed kind
+        L.dpw = L.seedT;
         for (int k = 1; k <= n; ++k) {
-            const int bx = blocks_for(p, p->F[k - 1], kChunkBwd, NG);
+            const int bx = blocks_for(p, p->F[k - 1], p->tab.enabled ? 1 : kChunkBwd, NG);
             L.bwd_blocks[k] = bx;
             L.dupart[k] = take((size_t)NG * bx * kLanes * p->m * sizeof(float2));
         }
@@ -430,6 +596,12 @@ slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t d
         return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the status word");
     }
     cudaMemset(p->d_status, 0, 64);
+    slos_status_t tst = build_tables(p);
+    if (tst != SLOS_OK) {
+        cudaFree(p->d_status);
+        delete p;
+        return tst;
+    }
     *out = p;
     return SLOS_OK;
 }
@@ -480,7 +652,16 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
         bytes += (epi == EPI_AMPS ? 8.0 : 4.0) * p->K + (save ? 8.0 * a.Fk : 0.0);
     }
     ProfScope ps(name, bytes * batch, s);
-    SLOS_CUDA(launch_fwd(p->m, a, epi, save, bx, s));
+    if (p->tab.enabled) {
+        TabArgs t;
+        t.rowptr = p->tab.layer[k].rowptr;
+        t.entries = p->tab.layer[k].entries;
+        t.w = p->tab.w;
+        t.pat = p->tab.pat;
+        SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, NG), s));
+    } else {
+        SLOS_CUDA(launch_fwd(p->m, a, epi, save, bx, s));
+    }
     return SLOS_OK;
 }
 
@@ -529,30 +710,30 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
     const int n = p->n, m = p->m;
     const int NG = groups_for(batch);
 
-    // seed
+    // seed: the factorial weights are folded in here (see Seed)
     int seed;
     const void *seed_ptr;
-    if (output == SLOS_OUT_PROBS && p->det == SLOS_DETECT_PNR && dout_stride_b == 0) {
-        seed = SEED_PROBS_BCAST;
-        seed_ptr = dout;
-    } else {
+    {
         PrepArgs pa;
         memset(&pa, 0, sizeof(pa));
         pa.dout = dout;
         pa.stride = dout_stride_b;
-        pa.outT = ws + Ly.seedT;
         pa.Fn = p->F[n];
         pa.m = m;
         pa.n = n;
         pa.B = batch;
         pa.NG = NG;
         pa.chunk = kChunkStore;
+        pa.inv_sfact = p->inv_sfact;
         pa.kind = output == SLOS_OUT_AMPS ? 1 : (p->det == SLOS_DETECT_THRESHOLD ? 2 : 0);
         fill_pat_off(p, pa.pat_off);
-        ProfScope ps("slos_seed_prep", (double)batch * (4.0 * p->K + (pa.kind == 1 ? 16.0 : 4.0) * p->F[n]), s);
-        SLOS_CUDA(launch_prep(m, pa, blocks_for(p, pa.Fn, pa.chunk, NG), s));
-        seed = output == SLOS_OUT_AMPS ? SEED_AMPS_T : SEED_PROBS_T;
-        seed_ptr = ws + Ly.seedT;
+        const bool bcast = dout_stride_b == 0 && pa.kind != 1;
+        pa.outT = ws + (bcast ? Ly.dpw : Ly.seedT);
+        ProfScope ps("slos_seed_prep", bcast ? 8.0 * p->F[n]
+                                            : (double)batch * ((pa.kind == 1 ? 16.0 : 8.0) * p->F[n]), s);
+        SLOS_CUDA(launch_prep(m, pa, blocks_for(p, pa.Fn, pa.chunk, NG), bcast, s));
+        seed = bcast ? SEED_BCAST : (pa.kind == 1 ? SEED_AMPS_T : SEED_T);
+        seed_ptr = pa.outT;
     }
 
     int have_base = -1;  // segment currently recomputed (its kept base layer)
@@ -595,7 +776,10 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
             // layered-model bytes: read a_{k-1} and G_k (or a_n and dL/dout), write G_{k-1}
             double bytes = (kp >= 1 ? 16.0 * a.Fprev : 0.0) + (k == n ? 12.0 : 8.0) * a.Fk;
             ProfScope ps(k == n ? "slos_bwd_final" : "slos_bwd_layer", bytes * batch, s);
-            SLOS_CUDA(launch_bwd(m, a, k == n ? seed : SEED_G, Ly.bwd_blocks[k], s));
+            if (p->tab.enabled)
+                SLOS_CUDA(launch_bwd_tab(m, a, p->tab.layer[k].ctab, k == n ? seed : SEED_G, Ly.bwd_blocks[k], s));
+            else
+                SLOS_CUDA(launch_bwd(m, a, k == n ? seed : SEED_G, Ly.bwd_blocks[k], s));
         }
         ra.part[k] = a.dUpart;
         ra.blocks[k] = Ly.bwd_blocks[k];
@@ -631,6 +815,7 @@ slos_status_t slos_sync_status(slos_plan_t p, void *stream) {
 slos_status_t slos_plan_destroy(slos_plan_t p) {
     if (!p) return SLOS_OK;
     if (p->d_status) cudaFree(p->d_status);
+    free_tables(p);
     if (p->batched) batched_destroy(p);
     delete p;
     return SLOS_OK;
@@ -649,6 +834,20 @@ slos_status_t slos_host_unrank(int m, int k, int64_t rank, int *t) {
         return SLOS_OK;
     }
     host_unrank(m, k, rank, t);
+    return SLOS_OK;
+}
+
+slos_status_t slos_host_transition_table(int m, int k, int32_t *rowptr, uint32_t *entries, int32_t *ctab) {
+    if (m < 2 || m > kMaxModes || k < 1 || k > kMaxPhotons)
+        return fail(SLOS_ERR_UNSUPPORTED, "slos_host_transition_table: m in [2,24], k in [1,12]");
+    if (binom_host(m + k - 2, k - 1) >= kMaxTableParent)
+        return fail(SLOS_ERR_UNSUPPORTED, "slos_host_transition_table: parent layer too large for packed entries");
+    std::vector<int32_t> rp, ct;
+    std::vector<uint32_t> en;
+    build_layer_host(m, k, rp, en, ct);
+    if (rowptr) memcpy(rowptr, rp.data(), rp.size() * 4);
+    if (entries) memcpy(entries, en.data(), en.size() * 4);
+    if (ctab) memcpy(ctab, ct.data(), ct.size() * 4);
     return SLOS_OK;
 }
 

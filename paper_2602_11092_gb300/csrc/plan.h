@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/slos.h"
+#include "tables.h"
 
 namespace slos {
 
@@ -32,6 +33,7 @@ struct Layout {
     size_t seedT;               // transposed output gradient
     std::vector<size_t> dupart; // [1..n]: dU partials of layer k
     std::vector<int> bwd_blocks;  // [1..n]: blocks_x of the backward launch of layer k
+    size_t dpw;                   // shared seed [F_n] floats (aliases seedT)
     size_t total;
 };
 
@@ -59,5 +61,6 @@ struct slos_plan_s {
     int device;
     int sm_count;
     int *d_status;          // device status word (owned)
+    slos::PlanTables tab;   // transition graph (owned; empty when too large)
     slos::BatchedPlan *batched;
 };

@@ -22,11 +22,15 @@ enum Epilogue : int {
     EPI_THRESH = 3,  // final layer: q(pattern(t)) += p(t)                -> out [B][Kq]
 };
 
+// Output-gradient seed of the final backward layer.  The prep step folds the
+// weight w_t = prod t_j! / prod s_i! into it, so that
+//      probabilities / threshold: G_n(t) = seed(t) * a_n(t), seed = 2 w_t dL/dp(t)
+//      amplitudes:                G_n(t) = seed(t),          seed = sqrt(w_t) dL/d(amp)
 enum Seed : int {
-    SEED_G = 0,            // k < n: read G_k
-    SEED_PROBS_BCAST = 1,  // k == n: dL/dp shared by the batch, float [K]
-    SEED_PROBS_T = 2,      // k == n: dL/dp per instance, transposed float [NG][F_n][32]
-    SEED_AMPS_T = 3,       // k == n: dL/d(amp) per instance, transposed c64 [NG][F_n][32]
+    SEED_G = 0,       // k < n: read G_k
+    SEED_BCAST = 1,   // k == n: float [F_n], the same for every instance
+    SEED_T = 2,       // k == n: float [NG][F_n][32]
+    SEED_AMPS_T = 3,  // k == n: complex64 [NG][F_n][32]
 };
 
 struct FwdArgs {
@@ -56,9 +60,10 @@ struct BwdArgs {
 struct PrepArgs {
     const void *dout;    // [B][stride] float or c64
     int64_t stride;      // elements between instances (0 = shared)
-    void *outT;          // [NG][Fn][32] float or c64
+    void *outT;          // [NG][Fn][32] float or c64, or [Fn] float (shared seed)
     int64_t Fn;
     int m, n, B, NG, chunk, kind;  // kind: 0 PNR probs, 1 amps, 2 threshold
+    float inv_sfact;
     int pat_off[kMaxPhotons + 2];
 };
 
@@ -197,6 +202,18 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_kernel(FwdArgs a) {
     }
 }
 
+// Gradient of child state cidx (element offset `off` in the [NG][F_k][32]
+// layout) for the reverse recursion.
+template <int SEED>
+__device__ __forceinline__ float2 load_child_grad(const BwdArgs &a, int64_t off, int64_t cidx) {
+    if (SEED == SEED_G) return __ldg(a.Gk + off);
+    if (SEED == SEED_AMPS_T) return __ldg(reinterpret_cast<const float2 *>(a.seed) + off);
+    const float2 an = __ldg(a.an + off);
+    const float sc = (SEED == SEED_BCAST) ? __ldg(reinterpret_cast<const float *>(a.seed) + cidx)
+                                          : __ldg(reinterpret_cast<const float *>(a.seed) + off);
+    return cscale(an, sc);
+}
+
 // ------------------------------------------------------------------ backward
 // Layer k: for every parent t' in F_{k-1} and every mode j (all children
 // t' + e_j exist):
@@ -236,7 +253,6 @@ __global__ void __launch_bounds__(kThreads) slos_bwd_kernel(BwdArgs a) {
             Z rem[C];
             int prevbar[C], S[C];
             float2 av[C], gacc[C];
-            float fp[C];
             bool live[C];
 #pragma unroll
             for (int i = 0; i < C; ++i) {
@@ -246,33 +262,12 @@ __global__ void __launch_bounds__(kThreads) slos_bwd_kernel(BwdArgs a) {
                 prevbar[i] = L;
                 S[i] = 0;
                 gacc[i] = make_float2(0.f, 0.f);
-                fp[i] = 1.f;
             }
 #pragma unroll
             for (int i = 0; i < C; ++i) {
                 if (!live[i]) rem[i] = rem[0];
                 av[i] = make_float2(0.f, 0.f);
                 if (live[i]) av[i] = (a.k == 1) ? make_float2(1.f, 0.f) : __ldg(a.aprev + gofs_prev + (cb + i) * kLanes);
-            }
-            if (SEED != SEED_G) {
-                // prod_l t'_l! of each parent
-#pragma unroll
-                for (int i = 0; i < C; ++i) {
-                    Z r2 = rem[i];
-                    int pv = L;
-#pragma unroll
-                    for (int j = 0; j < MMAX; ++j) {
-                        if (j < m) {
-                            int pb = -1;
-                            if (j < m - 1) {
-                                pb = top_bit(r2);
-                                r2 ^= (Z)1 << pb;
-                            }
-                            fp[i] *= c_fact.v[pv - pb - 1];
-                            pv = pb;
-                        }
-                    }
-                }
             }
 #pragma unroll
             for (int j = 0; j < MMAX; ++j) {
@@ -288,25 +283,9 @@ __global__ void __launch_bounds__(kThreads) slos_bwd_kernel(BwdArgs a) {
                         prevbar[i] = pb;
                         const int64_t cidx = cb + i + S[i];
                         const int64_t off = gofs_k + cidx * kLanes;
+                        (void)tj;
                         float2 g = make_float2(0.f, 0.f);
-                        if (live[i]) {
-                            if (SEED == SEED_G) {
-                                g = __ldg(a.Gk + off);
-                            } else {
-                                const float w = fp[i] * (float)(tj + 1) * a.inv_sfact;
-                                const float2 an = __ldg(a.an + off);
-                                if (SEED == SEED_PROBS_BCAST) {
-                                    const float dp = __ldg(reinterpret_cast<const float *>(a.seed) + cidx);
-                                    g = cscale(an, 2.f * dp * w);
-                                } else if (SEED == SEED_PROBS_T) {
-                                    const float dp = __ldg(reinterpret_cast<const float *>(a.seed) + off);
-                                    g = cscale(an, 2.f * dp * w);
-                                } else {
-                                    const float2 d = __ldg(reinterpret_cast<const float2 *>(a.seed) + off);
-                                    g = cscale(d, sqrtf(w));
-                                }
-                            }
-                        }
+                        if (live[i]) g = load_child_grad<SEED>(a, off, cidx);
                         gacc[i] = cfma_conj_a(u[j], g, gacc[i]);
                         dU[j] = cfma_conj_a(av[i], g, dU[j]);
                         if (j < m - 1) S[i] += (int)binom(pb, m - 2 - j);
@@ -342,9 +321,10 @@ __global__ void __launch_bounds__(kThreads) slos_bwd_kernel(BwdArgs a) {
 }
 
 // ------------------------------------------------------------------ seed prep
-// Gathers the output gradient into the state-major layout of layer n:
-// outT[g][t][lane] = dout[inst][idx(t)], idx(t) = t (PNR, amps) or the
-// threshold pattern of t.
+// Per-instance seeds in the state-major layout of layer n:
+//   kind 0 (PNR probs):  outT[g][t][lane] = 2 w_t dout[inst][t]
+//   kind 2 (threshold):  outT[g][t][lane] = 2 w_t dout[inst][pattern(t)]
+//   kind 1 (amplitudes): outT[g][t][lane] = sqrt(w_t) dout[inst][t]   (complex)
 template <int MMAX>
 __global__ void __launch_bounds__(kThreads) slos_seed_prep_kernel(PrepArgs a) {
     const int lane = threadIdx.x & 31;
@@ -363,23 +343,114 @@ __global__ void __launch_bounds__(kThreads) slos_seed_prep_kernel(PrepArgs a) {
         int p[MMAX];
         unrank_bars<MMAX>(c0, m, L, p);
         for (int64_t c = c0; c < c1; ++c) {
-            int64_t idx = c;
-            if (a.kind == 2) {
-                uint32_t supp = 0;
+            uint32_t supp = 0;
+            float fp = 1.f;
 #pragma unroll
-                for (int j = 0; j < MMAX; ++j)
-                    if (j < m && occupation<MMAX>(j, m, L, p) > 0) supp |= 1u << j;
-                idx = a.pat_off[__popc(supp)] + (int64_t)colex_rank(supp);
+            for (int j = 0; j < MMAX; ++j) {
+                if (j < m) {
+                    const int tj = occupation<MMAX>(j, m, L, p);
+                    fp *= c_fact.v[tj];
+                    if (tj > 0) supp |= 1u << j;
+                }
             }
+            const float w = fp * a.inv_sfact;
+            int64_t idx = c;
+            if (a.kind == 2) idx = a.pat_off[__popc(supp)] + (int64_t)colex_rank(supp);
             const int64_t src = (valid ? (int64_t)inst * a.stride : 0) + idx;
             if (a.kind == 1) {
                 float2 v = valid ? __ldg(reinterpret_cast<const float2 *>(a.dout) + src) : make_float2(0.f, 0.f);
-                reinterpret_cast<float2 *>(a.outT)[(base + c) * kLanes + lane] = v;
+                reinterpret_cast<float2 *>(a.outT)[(base + c) * kLanes + lane] = cscale(v, sqrtf(w));
             } else {
                 float v = valid ? __ldg(reinterpret_cast<const float *>(a.dout) + src) : 0.f;
-                reinterpret_cast<float *>(a.outT)[(base + c) * kLanes + lane] = v;
+                reinterpret_cast<float *>(a.outT)[(base + c) * kLanes + lane] = 2.f * w * v;
             }
             next_bars<MMAX>(m, L, p);
+        }
+    }
+}
+
+// Shared seed (dout row stride 0): dpw[t] = 2 w_t dout[t] (PNR) or
+// 2 w_t dout[pattern(t)] (threshold); one thread per state.
+template <int MMAX>
+__global__ void slos_seed_bcast_kernel(PrepArgs a) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.Fn) return;
+    const int m = a.m;
+    const int L = a.n + m - 1;
+    int p[MMAX];
+    unrank_bars<MMAX>(c, m, L, p);
+    uint32_t supp = 0;
+    float fp = 1.f;
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j) {
+        if (j < m) {
+            const int tj = occupation<MMAX>(j, m, L, p);
+            fp *= c_fact.v[tj];
+            if (tj > 0) supp |= 1u << j;
+        }
+    }
+    int64_t idx = c;
+    if (a.kind == 2) idx = a.pat_off[__popc(supp)] + (int64_t)colex_rank(supp);
+    reinterpret_cast<float *>(a.outT)[c] = 2.f * fp * a.inv_sfact * __ldg(reinterpret_cast<const float *>(a.dout) + idx);
+}
+
+// ------------------------------------------------------------------ table mode
+// Backward with the precomputed child table: per parent, lane j < m fetches
+// rank_k(t' + e_j); the warp then broadcasts each child index and gathers the
+// 16 child gradients with independent coalesced loads.
+template <int MMAX, int SEED>
+__global__ void __launch_bounds__(kThreads) slos_bwd_tab_kernel(BwdArgs a, const int32_t *ctab) {
+    __shared__ float2 red[kWarpsPerBlock][32];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int grp = blockIdx.y;
+    const int inst = grp * kLanes + lane;
+    const bool valid = inst < a.B;
+    const int m = a.m;
+    float2 u[MMAX], dU[MMAX];
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j) {
+        u[j] = make_float2(0.f, 0.f);
+        dU[j] = make_float2(0.f, 0.f);
+        if (j < m && valid) u[j] = a.U[((int64_t)inst * m + j) * m + a.col];
+    }
+    const int64_t gofs_prev = (int64_t)grp * a.Fprev * kLanes + lane;
+    const int64_t gofs_k = (int64_t)grp * a.Fk * kLanes + lane;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + warp; c < a.Fprev; c += nwarps) {
+        const int mine = lane < m ? __ldg(ctab + c * m + lane) : 0;
+        const float2 av = (a.k == 1) ? make_float2(1.f, 0.f) : __ldg(a.aprev + gofs_prev + c * kLanes);
+        float2 g[MMAX];
+#pragma unroll
+        for (int j = 0; j < MMAX; ++j) {
+            const int cidx = __shfl_sync(0xffffffffu, mine, j);
+            g[j] = make_float2(0.f, 0.f);
+            if (j < m) g[j] = load_child_grad<SEED>(a, gofs_k + (int64_t)cidx * kLanes, cidx);
+        }
+        float2 gacc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < MMAX; ++j) {
+            gacc = cfma_conj_a(u[j], g[j], gacc);
+            dU[j] = cfma_conj_a(av, g[j], dU[j]);
+        }
+        if (a.k > 1) a.Gprev[gofs_prev + c * kLanes] = gacc;
+    }
+    float2 *dst = a.dUpart + (((int64_t)grp * gridDim.x + blockIdx.x) * kLanes) * m;
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j) {
+        if (j < m) {
+            red[warp][lane] = dU[j];
+            __syncthreads();
+            if (warp == 0) {
+                float2 sacc = red[0][lane];
+#pragma unroll
+                for (int w = 1; w < kWarpsPerBlock; ++w) {
+                    sacc.x += red[w][lane].x;
+                    sacc.y += red[w][lane].y;
+                }
+                dst[lane * m + j] = sacc;
+            }
+            __syncthreads();
         }
     }
 }
@@ -422,16 +493,32 @@ inline size_t fwd_smem_bytes(int epi) {
         dim3 grid(blocks_x, a.NG);                                                                           \
         switch (seed) {                                                                                      \
             case SEED_G: slos_bwd_kernel<MM, SEED_G, kCBwd><<<grid, kThreads, 0, s>>>(a); break;                   \
-            case SEED_PROBS_BCAST: slos_bwd_kernel<MM, SEED_PROBS_BCAST, kCBwd><<<grid, kThreads, 0, s>>>(a); break; \
-            case SEED_PROBS_T: slos_bwd_kernel<MM, SEED_PROBS_T, kCBwd><<<grid, kThreads, 0, s>>>(a); break;       \
+            case SEED_BCAST: slos_bwd_kernel<MM, SEED_BCAST, kCBwd><<<grid, kThreads, 0, s>>>(a); break;             \
+            case SEED_T: slos_bwd_kernel<MM, SEED_T, kCBwd><<<grid, kThreads, 0, s>>>(a); break;                     \
             case SEED_AMPS_T: slos_bwd_kernel<MM, SEED_AMPS_T, kCBwd><<<grid, kThreads, 0, s>>>(a); break;         \
             default: return cudaErrorInvalidValue;                                                           \
         }                                                                                                    \
         return cudaGetLastError();                                                                           \
     }                                                                                                        \
-    cudaError_t slos_launch_prep_m##MM(const PrepArgs &a, int blocks_x, cudaStream_t s) {                   \
+    cudaError_t slos_launch_prep_m##MM(const PrepArgs &a, int blocks_x, bool bcast, cudaStream_t s) {       \
+        if (bcast) {                                                                                         \
+            slos_seed_bcast_kernel<MM><<<(unsigned)((a.Fn + 255) / 256), 256, 0, s>>>(a);                    \
+        } else {                                                                                             \
+            dim3 grid(blocks_x, a.NG);                                                                       \
+            slos_seed_prep_kernel<MM><<<grid, kThreads, 0, s>>>(a);                                          \
+        }                                                                                                    \
+        return cudaGetLastError();                                                                           \
+    }                                                                                                        \
+    cudaError_t slos_launch_bwd_tab_m##MM(const BwdArgs &a, const int32_t *ctab, int seed, int blocks_x,    \
+                                          cudaStream_t s) {                                                  \
         dim3 grid(blocks_x, a.NG);                                                                           \
-        slos_seed_prep_kernel<MM><<<grid, kThreads, 0, s>>>(a);                                              \
+        switch (seed) {                                                                                      \
+            case SEED_G: slos_bwd_tab_kernel<MM, SEED_G><<<grid, kThreads, 0, s>>>(a, ctab); break;         \
+            case SEED_BCAST: slos_bwd_tab_kernel<MM, SEED_BCAST><<<grid, kThreads, 0, s>>>(a, ctab); break; \
+            case SEED_T: slos_bwd_tab_kernel<MM, SEED_T><<<grid, kThreads, 0, s>>>(a, ctab); break;         \
+            case SEED_AMPS_T: slos_bwd_tab_kernel<MM, SEED_AMPS_T><<<grid, kThreads, 0, s>>>(a, ctab); break; \
+            default: return cudaErrorInvalidValue;                                                           \
+        }                                                                                                    \
         return cudaGetLastError();                                                                           \
     }
 
@@ -439,6 +526,8 @@ inline size_t fwd_smem_bytes(int epi) {
     cudaError_t slos_init_m##MM();                                                                  \
     cudaError_t slos_launch_fwd_m##MM(const FwdArgs &a, int epi, bool save, int blocks_x, cudaStream_t s); \
     cudaError_t slos_launch_bwd_m##MM(const BwdArgs &a, int seed, int blocks_x, cudaStream_t s);  \
-    cudaError_t slos_launch_prep_m##MM(const PrepArgs &a, int blocks_x, cudaStream_t s);
+    cudaError_t slos_launch_prep_m##MM(const PrepArgs &a, int blocks_x, bool bcast, cudaStream_t s);      \
+    cudaError_t slos_launch_bwd_tab_m##MM(const BwdArgs &a, const int32_t *ctab, int seed, int blocks_x,  \
+                                          cudaStream_t s);
 
 }  // namespace slos

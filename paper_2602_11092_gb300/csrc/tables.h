@@ -1,0 +1,38 @@
+// Transition graph of a plan (Sec. II-A.3: the k -> k+1 transitions depend
+// only on the input state, so they are built once and reused for every batch
+// of unitaries; only the U coefficients change per call).
+//
+// For layer k (k photons, built for k = 1..n):
+//   forward:  CSR parent lists.  rowptr[c] .. rowptr[c+1] index the entries of
+//             child state c; entry = (parent rank << 6) | (mode << 1) | last,
+//             where `last` marks the final entry of a child.  Parent ranks are
+//             < 2^26.
+//   backward: dense child table ctab[c'][j] = rank_k(t' + e_j) for every
+//             parent c' of layer k-1 and every mode j.
+// For the final layer n: w[t] = prod t_j! / prod s_i! and, for threshold
+// detection, pat[t] = index of the occupied-mode pattern of t.
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+namespace slos {
+
+struct LayerTables {
+    int32_t *rowptr = nullptr;   // [F_k + 1]
+    uint32_t *entries = nullptr; // [m * F_{k-1}]
+    int32_t *ctab = nullptr;     // [F_{k-1} * m]
+};
+
+struct PlanTables {
+    bool enabled = false;
+    std::vector<LayerTables> layer;  // [0..n], layer[0] unused
+    float *w = nullptr;              // [F_n]
+    int32_t *pat = nullptr;          // [F_n] (threshold only)
+    size_t bytes = 0;
+};
+
+constexpr size_t kTableBudgetBytes = size_t(1) << 30;  // per plan
+constexpr int64_t kMaxTableParent = int64_t(1) << 26;
+
+}  // namespace slos

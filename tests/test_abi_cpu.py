@@ -85,3 +85,40 @@ def test_plan_argument_validation_without_gpu(lib):
     with pytest.raises(binding.SlosError) as e:
         binding.host_unrank(5, 3, 10 ** 6)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("m,k", [(2, 1), (2, 5), (3, 3), (6, 3), (8, 4), (12, 6), (16, 4), (16, 8), (24, 3)])
+def test_transition_graph_matches_enumeration(lib, m, k):
+    """The plan's transition tables (Sec. II-A.3) against brute-force
+    enumeration: CSR parent entries of every child, child table of every
+    parent, all indices in range."""
+    from paper_2602_11092_gb300 import binding
+    rowptr, entries, ctab = binding.host_transition_table(m, k)
+    child = oracle.enumerate_fock(m, k)
+    parent = oracle.enumerate_fock(m, k - 1)
+    Fk, Fp = child.shape[0], parent.shape[0]
+    assert rowptr[0] == 0 and rowptr[-1] == m * Fp == entries.size
+    assert np.all(np.diff(rowptr) >= 1)
+    pidx = (entries >> 6).astype(np.int64)
+    mode = ((entries >> 1) & 31).astype(np.int64)
+    last = (entries & 1).astype(bool)
+    assert pidx.max() < Fp and mode.max() < m
+    assert np.array_equal(np.nonzero(last)[0], rowptr[1:] - 1)
+    # expected: for child c, the nonzero modes in increasing order, parent = rank(t - e_j)
+    pkey = {tuple(t): i for i, t in enumerate(parent)}
+    ckey = {tuple(t): i for i, t in enumerate(child)}
+    step = max(1, Fk // 4000)
+    for c in range(0, Fk, step):
+        t = child[c]
+        js = np.nonzero(t)[0]
+        seg = slice(rowptr[c], rowptr[c + 1])
+        assert list(mode[seg]) == list(js)
+        for j, pi in zip(js, pidx[seg]):
+            tt = t.copy(); tt[j] -= 1
+            assert pkey[tuple(tt)] == pi
+    stepp = max(1, Fp // 4000)
+    assert ctab.min() >= 0 and ctab.max() < Fk
+    for cp in range(0, Fp, stepp):
+        for j in range(m):
+            tt = parent[cp].copy(); tt[j] += 1
+            assert ctab[cp, j] == ckey[tuple(tt)]
