@@ -302,6 +302,14 @@ static int blocks_for(const slos_plan_s *p, int64_t states, int chunk, int NG) {
     return (int)std::max<int64_t>(1, std::min(need, std::max<int64_t>(target, 1)));
 }
 
+// Table-mode backward: one parent per warp per step, 4-warp blocks, about
+// 6 resident blocks per SM (80 registers) spread over the groups.
+static int bwd_tab_blocks(const slos_plan_s *p, int64_t parents, int NG) {
+    const int64_t need = (parents + kBwdTabWarps - 1) / kBwdTabWarps;
+    const int64_t target = std::max<int64_t>(1, (int64_t)p->sm_count * 6 / std::max(1, NG));
+    return (int)std::max<int64_t>(1, std::min(need, target));
+}
+
 constexpr int kChunkStore = 64;
 constexpr int kChunkFinal = 32;
 constexpr int kChunkBwd = 64;
@@ -357,7 +365,8 @@ static Layout make_layout(const slos_plan_s *p, int batch, bool training) {
         L.seedT = take(row * p->F[n]);  // c64-sized: enough for either seed kind
         L.dpw = L.seedT;
         for (int k = 1; k <= n; ++k) {
-            const int bx = blocks_for(p, p->F[k - 1], p->tab.enabled ? 1 : kChunkBwd, NG);
+            const int bx = p->tab.enabled ? bwd_tab_blocks(p, p->F[k - 1], NG)
+                                          : blocks_for(p, p->F[k - 1], kChunkBwd, NG);
             L.bwd_blocks[k] = bx;
             L.dupart[k] = take((size_t)NG * bx * kLanes * p->m * sizeof(float2));
         }

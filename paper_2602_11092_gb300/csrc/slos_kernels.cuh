@@ -396,42 +396,53 @@ __global__ void slos_seed_bcast_kernel(PrepArgs a) {
 
 // ------------------------------------------------------------------ table mode
 // Backward with the precomputed child table: per parent, lane j < m fetches
-// rank_k(t' + e_j); the warp then broadcasts each child index and gathers the
-// 16 child gradients with independent coalesced loads.
+// rank_k(t' + e_j); the warp broadcasts each child index and gathers the child
+// gradients with independent coalesced loads, 8 modes at a time.  U[j, c_k]
+// lives in shared memory and only dU stays in registers, which keeps the
+// kernel near 80 registers (more resident warps, more loads in flight).
+constexpr int kBwdTabWarps = 4;
+
 template <int MMAX, int SEED>
-__global__ void __launch_bounds__(kThreads) slos_bwd_tab_kernel(BwdArgs a, const int32_t *ctab) {
-    __shared__ float2 red[kWarpsPerBlock][32];
+__global__ void __launch_bounds__(kBwdTabWarps * 32) slos_bwd_tab_kernel(BwdArgs a, const int32_t *ctab) {
+    __shared__ float2 red[kBwdTabWarps][32];
+    __shared__ float2 us[MMAX][32];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int grp = blockIdx.y;
     const int inst = grp * kLanes + lane;
     const bool valid = inst < a.B;
     const int m = a.m;
-    float2 u[MMAX], dU[MMAX];
+    for (int j = warp; j < m; j += kBwdTabWarps)
+        us[j][lane] = valid ? a.U[((int64_t)inst * m + j) * m + a.col] : make_float2(0.f, 0.f);
+    __syncthreads();
+    float2 dU[MMAX];
 #pragma unroll
-    for (int j = 0; j < MMAX; ++j) {
-        u[j] = make_float2(0.f, 0.f);
-        dU[j] = make_float2(0.f, 0.f);
-        if (j < m && valid) u[j] = a.U[((int64_t)inst * m + j) * m + a.col];
-    }
+    for (int j = 0; j < MMAX; ++j) dU[j] = make_float2(0.f, 0.f);
     const int64_t gofs_prev = (int64_t)grp * a.Fprev * kLanes + lane;
     const int64_t gofs_k = (int64_t)grp * a.Fk * kLanes + lane;
-    const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + warp; c < a.Fprev; c += nwarps) {
+    const int64_t nwarps = (int64_t)gridDim.x * kBwdTabWarps;
+    for (int64_t c = (int64_t)blockIdx.x * kBwdTabWarps + warp; c < a.Fprev; c += nwarps) {
         const int mine = lane < m ? __ldg(ctab + c * m + lane) : 0;
         const float2 av = (a.k == 1) ? make_float2(1.f, 0.f) : __ldg(a.aprev + gofs_prev + c * kLanes);
-        float2 g[MMAX];
-#pragma unroll
-        for (int j = 0; j < MMAX; ++j) {
-            const int cidx = __shfl_sync(0xffffffffu, mine, j);
-            g[j] = make_float2(0.f, 0.f);
-            if (j < m) g[j] = load_child_grad<SEED>(a, gofs_k + (int64_t)cidx * kLanes, cidx);
-        }
         float2 gacc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int j = 0; j < MMAX; ++j) {
-            gacc = cfma_conj_a(u[j], g[j], gacc);
-            dU[j] = cfma_conj_a(av, g[j], dU[j]);
+        for (int h = 0; h < MMAX; h += 8) {
+            float2 g[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int j = h + r;
+                const int cidx = __shfl_sync(0xffffffffu, mine, j < 32 ? j : 0);
+                g[r] = make_float2(0.f, 0.f);
+                if (j < m) g[r] = load_child_grad<SEED>(a, gofs_k + (int64_t)cidx * kLanes, cidx);
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int j = h + r;
+                if (j < MMAX && j < m) {
+                    gacc = cfma_conj_a(us[j][lane], g[r], gacc);
+                    dU[j] = cfma_conj_a(av, g[r], dU[j]);
+                }
+            }
         }
         if (a.k > 1) a.Gprev[gofs_prev + c * kLanes] = gacc;
     }
@@ -444,7 +455,7 @@ __global__ void __launch_bounds__(kThreads) slos_bwd_tab_kernel(BwdArgs a, const
             if (warp == 0) {
                 float2 sacc = red[0][lane];
 #pragma unroll
-                for (int w = 1; w < kWarpsPerBlock; ++w) {
+                for (int w = 1; w < kBwdTabWarps; ++w) {
                     sacc.x += red[w][lane].x;
                     sacc.y += red[w][lane].y;
                 }
@@ -513,10 +524,10 @@ inline size_t fwd_smem_bytes(int epi) {
                                           cudaStream_t s) {                                                  \
         dim3 grid(blocks_x, a.NG);                                                                           \
         switch (seed) {                                                                                      \
-            case SEED_G: slos_bwd_tab_kernel<MM, SEED_G><<<grid, kThreads, 0, s>>>(a, ctab); break;         \
-            case SEED_BCAST: slos_bwd_tab_kernel<MM, SEED_BCAST><<<grid, kThreads, 0, s>>>(a, ctab); break; \
-            case SEED_T: slos_bwd_tab_kernel<MM, SEED_T><<<grid, kThreads, 0, s>>>(a, ctab); break;         \
-            case SEED_AMPS_T: slos_bwd_tab_kernel<MM, SEED_AMPS_T><<<grid, kThreads, 0, s>>>(a, ctab); break; \
+            case SEED_G: slos_bwd_tab_kernel<MM, SEED_G><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;         \
+            case SEED_BCAST: slos_bwd_tab_kernel<MM, SEED_BCAST><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break; \
+            case SEED_T: slos_bwd_tab_kernel<MM, SEED_T><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;         \
+            case SEED_AMPS_T: slos_bwd_tab_kernel<MM, SEED_AMPS_T><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break; \
             default: return cudaErrorInvalidValue;                                                           \
         }                                                                                                    \
         return cudaGetLastError();                                                                           \

@@ -58,50 +58,52 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_tab_kernel(FwdArgs a, TabAr
         float run_val = 0.f;
         for (int qb = e0; qb < e1; qb += 32) {
             const int cnt = min(32, e1 - qb);
+            // entries past this chunk read as 0: no load, no contribution, no `last` bit
+            // (a real entry is never 0: the only entry with parent 0 and mode 0 is
+            // the single, hence last, entry of state (k, 0, ..., 0))
             const uint32_t mine = lane < cnt ? __ldg(t.entries + qb + lane) : 0u;
-            for (int r0 = 0; r0 < cnt; r0 += 8) {
+            const int nb = (cnt + 7) >> 3;
+            for (int r0 = 0; r0 < 8 * nb; r0 += 8) {
                 uint32_t e[8];
                 float2 v[8];
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
                     e[r] = __shfl_sync(0xffffffffu, mine, r0 + r);
                     v[r] = make_float2(0.f, 0.f);
-                    if (r0 + r < cnt) {
+                    if (e[r] != 0u) {
                         v[r] = first_layer ? make_float2(1.f, 0.f)
                                            : __ldg(reinterpret_cast<const float2 *>(prevb + ((size_t)(e[r] >> 6) << 8)));
                     }
                 }
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    if (r0 + r < cnt) {
-                        const float2 uu = *reinterpret_cast<const float2 *>(usb + (((e[r] >> 1) & 31u) << 8));
-                        acc = cfma(uu, v[r], acc);
-                        if (e[r] & 1u) {
-                            // child c0 + ci is complete
-                            const int64_t c = c0 + ci;
-                            if (SAVE || EPI == EPI_STORE) nextg[c * kLanes] = acc;
-                            if (EPI != EPI_STORE) {
-                                const float w = __shfl_sync(0xffffffffu, wl, ci);
-                                if (EPI == EPI_PROBS) {
-                                    tile[lane * 33 + ci] = w * (acc.x * acc.x + acc.y * acc.y);
-                                } else if (EPI == EPI_AMPS) {
-                                    reinterpret_cast<float2 *>(tile)[lane * 33 + ci] = cscale(acc, sqrtf(w));
-                                } else {
-                                    const float pr = w * (acc.x * acc.x + acc.y * acc.y);
-                                    const int pat = __shfl_sync(0xffffffffu, patl, ci);
-                                    if (pat != run_pat) {
-                                        if (run_pat >= 0 && valid)
-                                            atomicAdd(reinterpret_cast<float *>(a.out) + (int64_t)inst * a.K + run_pat,
-                                                      run_val);
-                                        run_pat = pat;
-                                        run_val = 0.f;
-                                    }
-                                    run_val += pr;
+                    const float2 uu = *reinterpret_cast<const float2 *>(usb + (((e[r] >> 1) & 31u) << 8));
+                    acc = cfma(uu, v[r], acc);
+                    if (e[r] & 1u) {
+                        // child c0 + ci is complete
+                        const int64_t c = c0 + ci;
+                        if (SAVE || EPI == EPI_STORE) nextg[c * kLanes] = acc;
+                        if (EPI != EPI_STORE) {
+                            const float w = __shfl_sync(0xffffffffu, wl, ci);
+                            if (EPI == EPI_PROBS) {
+                                tile[lane * 33 + ci] = w * (acc.x * acc.x + acc.y * acc.y);
+                            } else if (EPI == EPI_AMPS) {
+                                reinterpret_cast<float2 *>(tile)[lane * 33 + ci] = cscale(acc, sqrtf(w));
+                            } else {
+                                const float pr = w * (acc.x * acc.x + acc.y * acc.y);
+                                const int pat = __shfl_sync(0xffffffffu, patl, ci);
+                                if (pat != run_pat) {
+                                    if (run_pat >= 0 && valid)
+                                        atomicAdd(reinterpret_cast<float *>(a.out) + (int64_t)inst * a.K + run_pat,
+                                                  run_val);
+                                    run_pat = pat;
+                                    run_val = 0.f;
                                 }
+                                run_val += pr;
                             }
-                            acc = make_float2(0.f, 0.f);
-                            ++ci;
                         }
+                        acc = make_float2(0.f, 0.f);
+                        ++ci;
                     }
                 }
             }
