@@ -234,6 +234,31 @@ int slos_profile_collect(void);
 slos_status_t slos_profile_entry(int i, char *name, size_t name_len, int64_t *launches, double *total_ms,
                                  double *total_bytes);
 
+/* ----------------------------------------------------------------------
+ * Allocation-free forward pass.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory themselves,
+ * such as a plugin inside a host application whose memory pool owns all
+ * device allocations, or a latency-critical loop that must never wait on a
+ * cudaMalloc.
+ *
+ * Same computation and output as slos_forward(plan, U, batch, output, out,
+ * save_for_backward = 0, ...), but the intermediate photon-number layers live
+ * in a scratch array built into the library (slos_noalloc_scratch_bytes(),
+ * 32 MiB, held by every GPU that loads the library until the process exits).
+ * The caller still passes U and out.  Calls no cudaMalloc / cudaFree.
+ *
+ * - Returns SLOS_ERR_UNSUPPORTED, with a message naming both sizes, when the
+ *   batch needs more scratch than that (slos_workspace_bytes(plan, batch, 0)).
+ * - The first call on a device looks up the array's device address with that
+ *   device current; make that first call before any stream capture.
+ * - Every call uses the same array: calls that overlap on the GPU (different
+ *   streams, or several host threads) race and must be serialised by the
+ *   caller.  No state carries over between calls.
+ * ---------------------------------------------------------------------- */
+size_t slos_noalloc_scratch_bytes(void);
+slos_status_t slos_forward_noalloc(slos_plan_t plan, const void *U, int batch, slos_output_t output, void *out,
+                                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,8 @@ _SIGNATURES = {
     "slos_host_unrank": ([_int, _int, _i64, ctypes.POINTER(_int)], _int),
     "slos_device_index_table": ([_int, _int, _i64, _i64, _vp, _vp, _vp], _int),
     "slos_host_transition_table": ([_int, _int, _vp, _vp, _vp], _int),
+    "slos_noalloc_scratch_bytes": ([], _sz),
+    "slos_forward_noalloc": ([_vp, _vp, _int, _int, _vp, _vp], _int),
     "slos_profile_enable": ([_int], _int),
     "slos_profile_reset": ([], _int),
     "slos_launch_count": ([], _i64),
@@ -198,6 +200,12 @@ class Plan:
             out = torch.empty((B, self.n_outputs), dtype=dt, device=U.device)
         _check(load().slos_forward(self._h, _ptr(U), B, output, _ptr(out), 1 if save_for_backward else 0,
                                    _ptr(workspace), workspace.numel(), _stream(stream)))
+        return out
+
+    def forward_noalloc(self, U: torch.Tensor, out: torch.Tensor, output: int = PROBS, stream=None):
+        """slos_forward_noalloc: the library's built-in scratch, no workspace."""
+        _need(U, torch.complex64, "U")
+        _check(load().slos_forward_noalloc(self._h, _ptr(U), U.shape[0], output, _ptr(out), _stream(stream)))
         return out
 
     def backward(self, U: torch.Tensor, dout: torch.Tensor, workspace: torch.Tensor, output: int = PROBS,
