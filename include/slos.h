@@ -182,6 +182,13 @@ slos_status_t slos_batched_query(slos_plan_t plan, int64_t *u_offsets, int64_t *
 slos_status_t slos_batched_forward(slos_plan_t plan, const void *U_packed, float *out_packed, void *workspace,
                                    size_t workspace_bytes, void *stream);
 
+/* Fault injection for tests of the bounded waits: while enabled, every
+ * slos_batched_forward launch starts one layer's completion counter so that
+ * it never completes and shortens the wait limit to about a millisecond; the
+ * items waiting on it give up, the launch ends, and slos_sync_status returns
+ * SLOS_ERR_TIMEOUT.  No fault, trap or hang is involved. */
+slos_status_t slos_batched_inject_stall(slos_plan_t plan, int enable);
+
 /* Times the launch configurations of slos_batched_forward on this GPU and
  * keeps the fastest in the plan; results are cached in the JSON file
  * `cache_path` (NULL = no cache), keyed by device name and problem shape. */

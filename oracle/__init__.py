@@ -190,6 +190,32 @@ def threshold_probs(p: np.ndarray, outputs: np.ndarray, m: int, n: int) -> np.nd
     return q
 
 
+def threshold_prob_of_pattern(U: np.ndarray, s, pattern, nthreads=None) -> float:
+    """q(b) for one occupied-mode set b: the sum of p(t) over every output t
+    whose occupied modes are exactly b (all compositions of n into |b|
+    positive parts, placed on b)."""
+    U = np.asarray(U)
+    m = U.shape[0]
+    n = int(np.sum(s))
+    b = list(pattern)
+
+    def positive_parts(total, parts):
+        if parts == 1:
+            yield (total,)
+            return
+        for first in range(1, total - parts + 2):
+            for rest in positive_parts(total - first, parts - 1):
+                yield (first,) + rest
+
+    outs = []
+    for occ in positive_parts(n, len(b)):
+        t = [0] * m
+        for mode, c in zip(b, occ):
+            t[mode] = c
+        outs.append(t)
+    return float(probabilities(U, s, np.array(outs, dtype=np.int32), nthreads).sum())
+
+
 # --------------------------------------------------------------------------
 # Interferometer mesh (Sec. II-A.3: trainable parameters are the phases of the
 # physical components; Sec. II-C.1: U(x, theta) = W2(theta2) S(x) W1(theta1)).

@@ -58,6 +58,7 @@ _SIGNATURES = {
     "slos_batched_query": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_sz)], _int),
     "slos_batched_forward": ([_vp, _vp, _vp, _vp, _sz, _vp], _int),
     "slos_batched_autotune": ([_vp, _vp, _vp, _vp, _sz, ctypes.c_char_p, _vp], _int),
+    "slos_batched_inject_stall": ([_vp, _int], _int),
     "slos_host_rank": ([_int, ctypes.POINTER(_int)], _i64),
     "slos_host_unrank": ([_int, _int, _i64, ctypes.POINTER(_int)], _int),
     "slos_device_index_table": ([_int, _int, _i64, _i64, _vp, _vp, _vp], _int),
@@ -266,6 +267,9 @@ class BatchedPlan:
 
     def sync_status(self, stream=None):
         _check(load().slos_sync_status(self._h, _stream(stream)))
+
+    def inject_stall(self, enable: bool):
+        _check(load().slos_batched_inject_stall(self._h, 1 if enable else 0))
 
     def __del__(self):
         h = getattr(self, "_h", None)

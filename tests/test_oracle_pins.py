@@ -278,6 +278,18 @@ def test_threshold_patterns_and_sum():
     assert np.allclose(oracle.threshold_probs(p1, out1, m, 1), p1)
 
 
+def test_threshold_single_pattern_matches_aggregation():
+    m, n = 7, 4
+    rng = np.random.default_rng(17)
+    U = workloads.haar_unitaries(m, 1, rng)[0]
+    s = [1, 0, 1, 0, 1, 0, 1]
+    out = oracle.enumerate_fock(m, n)
+    q = oracle.threshold_probs(oracle.probabilities(U, s, out), out, m, n)
+    pats = oracle.threshold_patterns(m, n)
+    for idx in [0, 3, 10, 40, len(pats) - 1]:
+        assert abs(oracle.threshold_prob_of_pattern(U, s, pats[idx]) - q[idx]) < 1e-15
+
+
 # ---------------------------------------------------------------- gradients
 
 @pytest.mark.parametrize("m,s", [(4, [1, 0, 1, 0]), (5, [1, 1, 0, 1, 0]), (6, [1, 0, 2, 0, 0, 0])])
