@@ -1,0 +1,77 @@
+/*
+ * libslos — learned surrogate of a photonic layer (BF16 MLP on the tensor
+ * cores), trained on distributions the exact simulator produces.
+ *
+ * The differentiable layers of the paper (Sec. II-A.3, II-B) map phases to an
+ * output distribution; this model approximates that map for one fixed layer
+ * (here the m=12, n=6 layer): features [sin phi, cos phi] -> n_hidden GELU
+ * layers of width `hidden` -> logits over the n_outputs Fock states ->
+ * softmax.  It is trained with the KL divergence KL(p_exact || q); the exact
+ * path (slos_forward) stays the judge of its total-variation error and the
+ * fallback for samples that fail the check.
+ *
+ * Conventions: all pointers are device pointers owned by the caller unless
+ * stated otherwise; a model owns its weights, Adam moments and activation
+ * buffers (allocated once by surr_create for batches up to max_batch, so the
+ * forward and training calls allocate nothing).  Every call is asynchronous
+ * on `stream` (cudaStream_t as void*); errors are status codes with a message
+ * from slos_last_error().
+ */
+#ifndef SLOS_SURROGATE_H
+#define SLOS_SURROGATE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "slos.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct surr_model_s *surr_model_t;
+
+/* Tensor-core GEMM (tcgen05 + TMA + TMEM): C[M][N] = A[M][K] . B[N][K]^T with
+ * A, B BF16 row-major (row strides lda, ldb elements; K, lda, ldb multiples
+ * of 8; 16-byte aligned), FP32 accumulation.  Epilogue `epi`:
+ *   0: C = acc (float [M][ldc])          1: C = acc + bias[n] (float)
+ *   2: aux = bf16(acc + bias[n]), C = bf16(gelu(aux))   (GELU, tanh form)
+ *   3: C = bf16(acc * gelu'(aux))         4: C += acc (float)
+ * The kernel's pipeline waits are bounded; a wait that runs out is reported
+ * by surr_sync_status. */
+slos_status_t surr_gemm_bf16(int epi, int M, int N, int K, const void *A, int64_t lda, const void *B, int64_t ldb,
+                             void *C, int ldc, const float *bias, void *aux, void *stream);
+
+/* Waits for `stream`, then returns SLOS_ERR_TIMEOUT (and clears the flag) if
+ * a tensor-core GEMM reported a pipeline wait that ran out. */
+slos_status_t surr_sync_status(void *stream);
+
+/* Model with n_phases phase inputs (2*n_phases features), n_hidden_layers of
+ * width `hidden`, n_outputs logits; weights He-uniform from `seed`, biases 0.
+ * 2*n_phases, hidden, n_outputs and max_batch must be multiples of 8. */
+slos_status_t surr_create(int n_phases, int hidden, int n_hidden_layers, int n_outputs, int max_batch,
+                          unsigned long long seed, surr_model_t *out);
+slos_status_t surr_destroy(surr_model_t model);
+
+/* phases: float [B][n_phases]; probs: float [B][n_outputs] = softmax(logits).
+ * B a multiple of 8, <= max_batch. */
+slos_status_t surr_forward(surr_model_t model, const float *phases, int B, float *probs, void *stream);
+
+/* One Adam step (lr; beta 0.9/0.999; eps 1e-8) on the batch mean of
+ * KL(target || softmax(logits)); target: float [B][n_outputs] (rows sum to 1).
+ * loss_rows: float [B] per-sample KL (may be NULL). */
+slos_status_t surr_train_step(surr_model_t model, const float *phases, const float *target, int B, float lr,
+                              float *loss_rows, void *stream);
+
+/* Host copies of layer `layer` (0 .. n_hidden_layers; the last is the output
+ * layer): W float [fan_out][fan_in], b float [fan_out]; grads are those of
+ * the last surr_train_step (before its Adam update).  Synchronous. */
+slos_status_t surr_get_param(surr_model_t model, int layer, float *w_host, float *b_host);
+slos_status_t surr_set_param(surr_model_t model, int layer, const float *w_host, const float *b_host);
+slos_status_t surr_get_grad(surr_model_t model, int layer, float *gw_host, float *gb_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLOS_SURROGATE_H */

@@ -1,0 +1,264 @@
+// Tensor-core GEMM for sm_103a: C[M][N] = A[M][K] . B[N][K]^T, BF16 inputs
+// (both K-major), FP32 accumulation in tensor memory (TMEM), fused epilogues.
+//
+// One CTA = 128 threads computes one 128 x 128 output tile.
+//   warp 0, lane 0: TMA producer.  cp.async.bulk.tensor loads 128x64 tiles of
+//                   A and B (128-byte swizzle) into a 4-stage ring; each stage
+//                   has a `full` mbarrier (transaction bytes) and an `empty`
+//                   mbarrier (arrived by tcgen05.commit when the MMAs that
+//                   read the stage are done).
+//   warp 1, lane 0: MMA issuer.  Four tcgen05.mma.kind::f16 (K = 16 each) per
+//                   stage into one 128 x 128 FP32 accumulator in TMEM.
+//   all 4 warps:    epilogue.  tcgen05.ld 32x32b: warp w reads TMEM lanes
+//                   32w..32w+31 (= output rows), 16 columns per load.
+// Every mbarrier wait has an iteration limit; a wait that runs out sets the
+// error word, the CTA still frees its TMEM and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace slos {
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int A_TILE = BM * BK * 2;  // bytes
+constexpr int B_TILE = BN * BK * 2;
+constexpr int STAGE_BYTES = A_TILE + B_TILE;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr uint32_t TMEM_COLS = 128;
+constexpr long long kWaitLimit = 1ll << 26;
+
+enum TcEpi : int {
+    TC_F32 = 0,        // C = acc                         (float)
+    TC_F32_BIAS = 1,   // C = acc + bias[n]               (float)
+    TC_GELU = 2,       // Z = acc + bias[n] (bf16, aux), C = gelu(Z) (bf16)
+    TC_GELU_BWD = 3,   // C = acc * gelu'(Z), Z = aux (bf16 in), C bf16
+    TC_F32_ACCUM = 4,  // C += acc                        (float)
+};
+
+struct TcArgs {
+    int M, N, K;
+    void *C;              // [M][ldc]
+    int ldc;
+    const float *bias;    // [N]
+    __nv_bfloat16 *aux;   // [M][ldc] (Z for TC_GELU out, TC_GELU_BWD in)
+    int *err;             // error word (device)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: true if the phase completed, false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (long long i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major operand with 128-byte swizzle:
+// start address >> 4 (bits 0-13), leading byte offset 16 B (unused for this
+// layout, bits 16-29), stride byte offset 1024 B between 8-row groups
+// (bits 32-45), fixed 0b001 (bits 46-48), swizzle mode 2 = 128 B (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
+// BF16 (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 (bits 17-22),
+// M >> 4 (bits 24-28).
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// GELU, tanh form, and its derivative (the surrogate's activation).
+__device__ __forceinline__ float gelu_f(float z) {
+    const float c = 0.7978845608028654f;  // sqrt(2/pi)
+    const float u = c * (z + 0.044715f * z * z * z);
+    return 0.5f * z * (1.f + tanhf(u));
+}
+__device__ __forceinline__ float gelu_grad(float z) {
+    const float c = 0.7978845608028654f;
+    const float u = c * (z + 0.044715f * z * z * z);
+    const float t = tanhf(u);
+    return 0.5f * (1.f + t) + 0.5f * z * (1.f - t * t) * c * (1.f + 3.f * 0.044715f * z * z);
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, TcArgs g) {
+    extern __shared__ uint8_t smem_tc[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_tc) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = base;
+    uint8_t *sB = base + STAGES * A_TILE;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + STAGES * B_TILE);
+    uint64_t *empty = full + STAGES;
+    uint64_t *done = empty + STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nk = (g.K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        int issued = 0;
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % STAGES;
+            const uint32_t ph = (kt / STAGES) & 1;
+            if (kt >= STAGES && !mbar_wait(empty + s, ph ^ 1)) {
+                atomicExch(g.err, 1);
+                *abort_flag = 1;
+                break;
+            }
+            if (*abort_flag) break;
+            mbar_expect_tx(full + s, STAGE_BYTES);
+            tma_load_2d(sA + s * A_TILE, &ta, kt * BK, m0, full + s);
+            tma_load_2d(sB + s * B_TILE, &tb, kt * BK, n0, full + s);
+            issued = kt + 1;
+        }
+        // never leave with copies in flight: wait (bounded) for the last loads
+        for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
+            mbar_wait(full + (kt % STAGES), (kt / STAGES) & 1);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % STAGES;
+            const uint32_t ph = (kt / STAGES) & 1;
+            if (*abort_flag || !mbar_wait(full + s, ph)) {
+                atomicExch(g.err, 2);
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA + s * A_TILE), b0 = smem_u32(sB + s * B_TILE);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kt > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(empty + s);
+        }
+        mma_commit(done);  // arrives once every MMA issued above has completed
+    }
+    __syncwarp();
+    // epilogue
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0) && !*abort_flag);
+    if (!ok && lane == 0) atomicExch(g.err, 3);
+    tc_fence_after();
+    const int row = m0 + warp * 32 + lane;
+    if (ok) {
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            if (row < g.M) {
+                const int col0 = n0 + c;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int col = col0 + i;
+                    if (col >= g.N) break;
+                    const int64_t o = (int64_t)row * g.ldc + col;
+                    float x = v[i];
+                    if (EPI == TC_F32) {
+                        reinterpret_cast<float *>(g.C)[o] = x;
+                    } else if (EPI == TC_F32_ACCUM) {
+                        reinterpret_cast<float *>(g.C)[o] += x;
+                    } else if (EPI == TC_F32_BIAS) {
+                        reinterpret_cast<float *>(g.C)[o] = x + g.bias[col];
+                    } else if (EPI == TC_GELU) {
+                        const float z = x + g.bias[col];
+                        const __nv_bfloat16 zb = __float2bfloat16(z);
+                        g.aux[o] = zb;
+                        reinterpret_cast<__nv_bfloat16 *>(g.C)[o] = __float2bfloat16(gelu_f(__bfloat162float(zb)));
+                    } else {  // TC_GELU_BWD
+                        const float z = __bfloat162float(g.aux[o]);
+                        reinterpret_cast<__nv_bfloat16 *>(g.C)[o] = __float2bfloat16(x * gelu_grad(z));
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+}  // namespace tc
+}  // namespace slos

@@ -320,3 +320,52 @@ def test_grad_U_minors_against_wirtinger_fd():
         gr = (oracle.loss(U + h * E, s, c, out) - oracle.loss(U - h * E, s, c, out)) / (2 * h)
         gi = (oracle.loss(U + 1j * h * E, s, c, out) - oracle.loss(U - 1j * h * E, s, c, out)) / (2 * h)
         assert abs(dU[j, i] - (gr + 1j * gi)) < 1e-8
+
+
+# ---------------------------------------------------------------- surrogate reference
+
+def test_mlp_reference_gradients_match_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(12)
+    sizes = [(6, 8), (6, 6), (5, 6)]  # (out, in): 4 phases -> 8 features -> 6 -> 6 -> 5
+    params = [(rng.standard_normal(s) * 0.5, rng.standard_normal(s[0]) * 0.1) for s in sizes]
+    phases = rng.uniform(0, 2 * np.pi, (3, 4))
+    target = rng.dirichlet(np.ones(5), size=3)
+    _, _, grads = mlp.loss_and_grads(params, phases, target, bf=False)
+    h = 1e-6
+    for l, (W, b) in enumerate(params):
+        for idx in [(0, 0), (1, 2), (W.shape[0] - 1, W.shape[1] - 1)]:
+            Wp, Wm = W.copy(), W.copy()
+            Wp[idx] += h
+            Wm[idx] -= h
+            pp = list(params); pp[l] = (Wp, b)
+            pm = list(params); pm[l] = (Wm, b)
+            fd = (mlp.loss_and_grads(pp, phases, target, bf=False)[0] -
+                  mlp.loss_and_grads(pm, phases, target, bf=False)[0]) / (2 * h)
+            assert abs(fd - grads[l][0][idx]) < 1e-7
+        bp, bm = b.copy(), b.copy()
+        bp[0] += h
+        bm[0] -= h
+        pp = list(params); pp[l] = (W, bp)
+        pm = list(params); pm[l] = (W, bm)
+        fd = (mlp.loss_and_grads(pp, phases, target, bf=False)[0] -
+              mlp.loss_and_grads(pm, phases, target, bf=False)[0]) / (2 * h)
+        assert abs(fd - grads[l][1][0]) < 1e-7
+
+
+def test_mlp_reference_invariants():
+    from oracle import mlp
+    z = np.array([[0.3, -1.0, 2.0], [5.0, 5.0, 5.0]])
+    q = mlp.softmax(z)
+    assert np.allclose(q.sum(axis=1), 1.0) and np.allclose(q[1], 1 / 3)
+    # GELU: gelu(0) = 0, gelu(z) -> z for large z, gelu' by FD
+    assert mlp.gelu(0.0) == 0.0 and abs(mlp.gelu(10.0) - 10.0) < 1e-12
+    zz = np.linspace(-4, 4, 17)
+    fd = (mlp.gelu(zz + 1e-6) - mlp.gelu(zz - 1e-6)) / 2e-6
+    assert np.abs(fd - mlp.gelu_grad(zz)).max() < 1e-8
+    # KL(p || softmax(log p)) = 0
+    rng = np.random.default_rng(0)
+    p = rng.dirichlet(np.ones(4), size=2)
+    params = [(np.zeros((4, 2)), np.log(p[0]))]
+    loss, _, _ = mlp.loss_and_grads(params, np.zeros((1, 1)), p[:1], bf=False)
+    assert abs(loss) < 1e-12
