@@ -29,7 +29,7 @@ constexpr int B_TILE = BN * BK * 2;
 constexpr int STAGE_BYTES = A_TILE + B_TILE;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr uint32_t TMEM_COLS = 128;
-constexpr long long kWaitLimit = 1ll << 26;
+constexpr long long kWaitLimit = 1ll << 22;  // tries; a few seconds at most
 
 enum TcEpi : int {
     TC_F32 = 0,        // C = acc                         (float)
