@@ -307,6 +307,12 @@ def run_gpu(args):
         v, cores, sample = oracle_step_sample(seconds_target=12.0)
         cpu = {"value": v, "unit": "distributions/s", "cores": cores, "kind": "oracle", "sample": sample}
 
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        del ws, probs
+        torch.cuda.empty_cache()
+        extras = run_extras(B, dev, peaks()[0], args)
+
     line = {
         "metric": METRIC, "value": value, "unit": "distributions/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -328,12 +334,132 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "extras": extras,
     }
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------- other workloads
+
+def _timed(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_extras(B, dev, peak_hbm, args):
+    """Forward throughput of the m=12 n=6 layer, the 1024-instance uneven
+    launch, and the learned surrogate against the exact path."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = {}
+    # --- m=12, n=6, batch 4096 meshes, forward only
+    w = workloads.layer12(batch=4096)
+    mb = w["mesh"]
+    theta = torch.tensor(mb.theta, dtype=torch.float32, device=dev)
+    data = torch.tensor(mb.data, dtype=torch.float32, device=dev)
+    plan = B.Plan(12, w["s"])
+    ws = plan.workspace(4096, training=False, device=dev)
+    probs = torch.empty((4096, plan.n_outputs), dtype=torch.float32, device=dev)
+    U = torch.empty((4096, 12, 12), dtype=torch.complex64, device=dev)
+
+    def fwd12():
+        B.mesh_unitary(12, theta, data, 4096, out=U)
+        plan.forward(U, workspace=ws, out=probs)
+    for _ in range(3):
+        fwd12()
+    B.profile_reset()
+    B.profile_enable(True)
+    ms = _timed(fwd12, 20, stream)
+    B.profile_enable(False)
+    prof = B.profile_collect()
+    nl, tms, tby = prof["slos_fwd_final"]
+    out["layer12_forward"] = {"workload": "m=12 n=6, 4096 Clements meshes (132 shared + 12 data phases), forward",
+                              "value": 4096 / (ms * 1e-3), "unit": "distributions/s", "ms_per_batch": ms,
+                              "final_layer_gbs": tby / (tms * 1e-3) / 1e9,
+                              "final_layer_frac": tby / (tms * 1e-3) / 1e9 / peak_hbm}
+    exact12_rate = 4096 / (ms * 1e-3)
+    del ws, probs
+    # --- uneven: 1024 instances, one persistent launch, autotuned
+    inst, Us = workloads.uneven()
+    bp = B.BatchedPlan([it.m for it in inst], [it.n for it in inst], [it.s for it in inst],
+                       [B.THRESHOLD if it.threshold else B.PNR for it in inst])
+    flat = np.concatenate([np.asarray(U_, dtype=np.complex64).reshape(-1) for U_ in Us])
+    Up = torch.tensor(flat, dtype=torch.complex64, device=dev)
+    wsb = torch.empty(bp.workspace_bytes, dtype=torch.uint8, device=dev)
+    outb = torch.empty((bp.out_offsets[-1],), dtype=torch.float32, device=dev)
+    cache = os.path.join(ROOT, "gpurun_out", "autotune_cache.json") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else None
+    t0 = time.perf_counter()
+    bp.autotune(Up, outb, wsb, cache_path=cache)
+    tune_s = time.perf_counter() - t0
+    bp.forward(Up, outb, wsb)
+    bp.sync_status()
+    msb = _timed(lambda: bp.forward(Up, outb, wsb), 5, stream)
+    bp.sync_status()
+    states = sum(workloads.fock_dim(it.m, it.n) for it in inst)
+    out["uneven_batched"] = {"workload": "1024 instances, m in 8..20, n in 2..min(10, m/2), threshold for m>=16, "
+                                         "one persistent launch",
+                             "value": 1024 / (msb * 1e-3), "unit": "instances/s", "ms_per_launch": msb,
+                             "final_states_per_s": states / (msb * 1e-3), "autotune_s": tune_s}
+    del wsb, outb, Up
+    # --- surrogate vs exact on the m=12, n=6 layer
+    if not args.no_surrogate:
+        from paper_2602_11092_gb300 import surrogate as S
+        t0 = time.perf_counter()
+        layer = S.SurrogateLayer(hidden=2048, n_hidden_layers=4, max_batch=65536)
+        hist = layer.train(n_samples=args.surrogate_samples, batch=4096, lr=1e-3)
+        train_s = time.perf_counter() - t0
+        ev = layer.evaluate(count=10000)
+        rng = np.random.default_rng(2024)
+        dinf = layer.sample_data(65536, rng)
+        layer.infer(dinf, seed=0)
+        torch.cuda.synchronize()
+        B.profile_reset()
+        B.profile_enable(True)
+        t0 = time.perf_counter()
+        reps = 3
+        for r in range(reps):
+            _, st = layer.infer(dinf, rho=1 / 64, tv_tol=0.02, seed=r)
+        torch.cuda.synchronize()
+        surr_s = (time.perf_counter() - t0) / reps
+        B.profile_enable(False)
+        prof = B.profile_collect()
+        g = prof.get("tc_gemm", (0, 0.0, 0.0))
+        tflops = g[2] / (g[1] * 1e-3) / 1e12 if g[1] > 0 else None
+        peaks_d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        bf16_peak = float(peaks_d.get("bf16_tflops", 1900.0))
+        # exact path at the same batch
+        def ex():
+            for o in range(0, 65536, 4096):
+                layer.exact(dinf[o:o + 4096])
+        ex()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ex()
+        torch.cuda.synchronize()
+        exact_s = time.perf_counter() - t0
+        out["surrogate"] = {
+            "workload": "BF16 MLP 288 -> 4x2048 GELU -> 12376 softmax on the m=12 n=6 layer, trained on "
+                        f"{args.surrogate_samples} exact distributions; inference batch 65536, spot check 1/64, "
+                        "exact fallback at TV > 0.02",
+            "train_s": train_s, "train_loss": hist, "heldout_tv": ev, "inference": st,
+            "checked_evals_per_s": 65536 / surr_s, "exact_evals_per_s": 65536 / exact_s,
+            "gain": exact_s / surr_s,
+            "tensor": {"bound": "tensor", "achieved_tflops": tflops, "peak_tflops": bf16_peak,
+                       "frac": tflops / bf16_peak if tflops else None, "peak_kind": "measured bf16 burst"}}
+        del layer
+    return out
 
 
 def main():
@@ -345,6 +471,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="instances per GPU (small cases for ncu captures)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads (rank 0, 1 GPU only)")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate among the extras")
+    ap.add_argument("--surrogate-samples", type=int, default=2_000_000)
     args = ap.parse_args()
     global BATCH
     BATCH = args.batch

@@ -70,6 +70,24 @@ slos_status_t surr_get_param(surr_model_t model, int layer, float *w_host, float
 slos_status_t surr_set_param(surr_model_t model, int layer, const float *w_host, const float *b_host);
 slos_status_t surr_get_grad(surr_model_t model, int layer, float *gw_host, float *gb_host);
 
+/* ---- checks used by the inference driver (exact path as judge) ---- */
+
+/* tv[i] = 1/2 sum_t |q[rows[i]][t] - p[i][t]| : total variation of checked
+ * rows.  q float [*][K], rows int [n], p float [n][K] (exact), tv float [n]. */
+slos_status_t surr_tv_rows(const float *q, const int *rows, const float *p, int n, int K, float *tv, void *stream);
+
+/* Cheap screen for every sample: the surrogate's mean photon number per mode,
+ * sum_t q[b][t] t_j (occ: uint8 [K][m] occupations of the output states),
+ * against the exact value sum_i |U[b][j][i]|^2 s_i (Sec. II-A.1); flag[b] is
+ * set to 1 (never cleared) when some mode differs by more than tol.
+ * input_state: host, m ints.  marg_scratch: float [B][m]. */
+slos_status_t surr_screen(const float *q, int B, int K, const uint8_t *occ, int m, const void *U, const int *input_state,
+                          float tol, float *marg_scratch, int *flag, void *stream);
+
+/* dst[rows[i]][:] = src[i][:] (K floats) and dst[i][:] = src[rows[i]][:]. */
+slos_status_t surr_scatter_rows(const float *src, const int *rows, int n, int K, float *dst, void *stream);
+slos_status_t surr_gather_rows(const float *src, const int *rows, int n, int W, float *dst, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -246,6 +246,89 @@ __global__ void adam_kernel(AdamArgs a) {
 }
 
 
+
+// ---------------------------------------------------------------- checks
+// tv[i] = 1/2 sum_t |q[rows[i]][t] - p[i][t]|   (one block per checked row)
+__global__ void tv_rows_kernel(const float *q, const int *rows, const float *p, int K, float *tv) {
+    const int i = blockIdx.x;
+    const float *qr = q + (int64_t)rows[i] * K;
+    const float *pr = p + (int64_t)i * K;
+    float s = 0.f;
+    for (int t = threadIdx.x; t < K; t += blockDim.x) s += fabsf(qr[t] - pr[t]);
+    __shared__ float red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float v = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+        tv[i] = 0.5f * v;
+    }
+}
+
+// marg[b][j] = sum_t q[b][t] * occ[t][j]    (one block per row)
+__global__ void marginals_kernel(const float *q, int K, const uint8_t *occ, int m, float *marg) {
+    const int b = blockIdx.x;
+    __shared__ float acc[32][33];
+    float loc[32];
+    for (int j = 0; j < 32; ++j) loc[j] = 0.f;
+    const float *qr = q + (int64_t)b * K;
+    for (int t = threadIdx.x; t < K; t += blockDim.x) {
+        const float v = qr[t];
+        for (int j = 0; j < m; ++j) loc[j] += v * (float)occ[(int64_t)t * m + j];
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int j = 0; j < m; ++j) {
+        float v = loc[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (l == 0) acc[w][j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        float v = 0.f;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) v += acc[ww][threadIdx.x];
+        marg[(int64_t)b * m + threadIdx.x] = v;
+    }
+}
+
+// exact mean photon numbers <n_j> = sum_i |U[b][j][i]|^2 s_i; flag[b] = 1 if
+// max_j |marg[b][j] - <n_j>| > tol (flag is OR-ed, never cleared here)
+struct ScreenArgs {
+    const float2 *U;
+    const float *marg;
+    int B, m;
+    float s[24];
+    float tol;
+    int *flag;
+};
+__global__ void screen_kernel(ScreenArgs a) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= a.B) return;
+    float worst = 0.f;
+    for (int j = 0; j < a.m; ++j) {
+        float nj = 0.f;
+        for (int i = 0; i < a.m; ++i) {
+            const float2 u = a.U[((int64_t)b * a.m + j) * a.m + i];
+            nj += (u.x * u.x + u.y * u.y) * a.s[i];
+        }
+        worst = fmaxf(worst, fabsf(nj - a.marg[(int64_t)b * a.m + j]));
+    }
+    if (worst > a.tol) a.flag[b] = 1;
+}
+
+// dst[rows[i]] = src[i] (K floats per row)
+__global__ void scatter_rows_kernel(const float *src, const int *rows, int K, float *dst) {
+    const int i = blockIdx.x;
+    const float *sr = src + (int64_t)i * K;
+    float *dr = dst + (int64_t)rows[i] * K;
+    for (int t = threadIdx.x; t < K; t += blockDim.x) dr[t] = sr[t];
+}
+// dst[i] = src[rows[i]] (n_phases floats per row)
+__global__ void gather_rows_kernel(const float *src, const int *rows, int W, float *dst) {
+    const int i = blockIdx.x;
+    for (int t = threadIdx.x; t < W; t += blockDim.x) dst[(int64_t)i * W + t] = src[(int64_t)rows[i] * W + t];
+}
+
 }  // namespace
 
 // ======================================================================== model
@@ -541,6 +624,56 @@ slos_status_t surr_set_param(surr_model_t M, int layer, const float *w_host, con
     }
     if (b_host) cudaMemcpy(M->b[layer], b_host, fo * 4, cudaMemcpyHostToDevice);
     return SLOS_OK;
+}
+
+slos_status_t surr_tv_rows(const float *q, const int *rows, const float *p, int n, int K, float *tv, void *stream) {
+    if (n <= 0) return SLOS_OK;
+    if (!q || !rows || !p || !tv) return fail(SLOS_ERR_INVALID_ARG, "surr_tv_rows: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    ProfScope ps("surr_tv", 8.0 * n * K, s);
+    tv_rows_kernel<<<n, 256, 0, s>>>(q, rows, p, K, tv);
+    return launch_check("tv_rows");
+}
+
+slos_status_t surr_screen(const float *q, int B, int K, const uint8_t *occ, int m, const void *U, const int *input_state,
+                          float tol, float *marg_scratch, int *flag, void *stream) {
+    if (B <= 0) return SLOS_OK;
+    if (m < 1 || m > 24 || !q || !occ || !U || !input_state || !marg_scratch || !flag)
+        return fail(SLOS_ERR_INVALID_ARG, "surr_screen: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        ProfScope ps("surr_marginals", 4.0 * B * K + (double)K * m, s);
+        marginals_kernel<<<B, 256, 0, s>>>(q, K, occ, m, marg_scratch);
+    }
+    slos_status_t st = launch_check("marginals");
+    if (st) return st;
+    ScreenArgs a;
+    a.U = reinterpret_cast<const float2 *>(U);
+    a.marg = marg_scratch;
+    a.B = B;
+    a.m = m;
+    for (int i = 0; i < 24; ++i) a.s[i] = i < m ? (float)input_state[i] : 0.f;
+    a.tol = tol;
+    a.flag = flag;
+    ProfScope ps("surr_screen", 8.0 * B * m * m, s);
+    screen_kernel<<<(B + 127) / 128, 128, 0, s>>>(a);
+    return launch_check("screen");
+}
+
+slos_status_t surr_scatter_rows(const float *src, const int *rows, int n, int K, float *dst, void *stream) {
+    if (n <= 0) return SLOS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    ProfScope ps("surr_scatter", 8.0 * n * K, s);
+    scatter_rows_kernel<<<n, 256, 0, s>>>(src, rows, K, dst);
+    return launch_check("scatter_rows");
+}
+
+slos_status_t surr_gather_rows(const float *src, const int *rows, int n, int W, float *dst, void *stream) {
+    if (n <= 0) return SLOS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    ProfScope ps("surr_gather", 8.0 * n * W, s);
+    gather_rows_kernel<<<n, 128, 0, s>>>(src, rows, W, dst);
+    return launch_check("gather_rows");
 }
 
 }  // extern "C"

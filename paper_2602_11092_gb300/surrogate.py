@@ -21,6 +21,10 @@ _SIG = {
     "surr_get_param": ([_vp, _int, _vp, _vp], _int),
     "surr_set_param": ([_vp, _int, _vp, _vp], _int),
     "surr_get_grad": ([_vp, _int, _vp, _vp], _int),
+    "surr_tv_rows": ([_vp, _vp, _vp, _int, _int, _vp, _vp], _int),
+    "surr_screen": ([_vp, _int, _int, _vp, _int, _vp, ctypes.POINTER(_int), _f, _vp, _vp, _vp], _int),
+    "surr_scatter_rows": ([_vp, _vp, _int, _int, _vp, _vp], _int),
+    "surr_gather_rows": ([_vp, _vp, _int, _int, _vp, _vp], _int),
 }
 
 _done = False
@@ -113,3 +117,119 @@ class Surrogate:
         if h is not None and B._lib is not None:
             B._lib.surr_destroy(h)
             self._h = None
+
+
+# ---------------------------------------------------------------------- driver
+
+class SurrogateLayer:
+    """Surrogate of the m=12, n=6 layer (132 shared trainable phases + 12
+    data phases x*w), trained on exact SLOS distributions; at inference the
+    exact path screens every sample, spot-checks a seeded fraction and
+    replaces every sample that fails (total variation > tv_tol)."""
+
+    def __init__(self, hidden=2048, n_hidden_layers=4, max_batch=4096, seed=1004, device="cuda"):
+        import numpy as np
+
+        from . import workloads
+        w = workloads.layer12(batch=1)
+        self.m, self.n, self.s = 12, 6, w["s"]
+        mb = w["mesh"]
+        self.device = torch.device(device)
+        self.theta = torch.tensor(mb.theta, dtype=torch.float32, device=self.device)
+        self.wdata = mb.w
+        self.plan = B.Plan(self.m, self.s)
+        self.K = self.plan.n_outputs
+        self.model = Surrogate(n_phases=self.theta.numel() + self.m, hidden=hidden, n_hidden_layers=n_hidden_layers,
+                               n_outputs=self.K, max_batch=max_batch, seed=seed)
+        self.max_batch = max_batch
+        occ, _ = B.device_index_table(self.m, self.n, 0, self.K, device=self.device)
+        self.occ = occ
+        self._np = np
+
+    # data phases x*w for a seeded stream of samples
+    def sample_data(self, count: int, rng):
+        x = rng.standard_normal((count, self.m))
+        return torch.tensor(x * self.wdata[None, :], dtype=torch.float32, device=self.device)
+
+    def phases(self, data: torch.Tensor) -> torch.Tensor:
+        return torch.cat([self.theta.expand(data.shape[0], -1), data], dim=1).contiguous()
+
+    def exact(self, data: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        U = B.mesh_unitary(self.m, self.theta, data.contiguous(), data.shape[0])
+        return self.plan.forward(U, out=out)
+
+    def train(self, n_samples: int, batch: int = 4096, lr: float = 1e-3, seed: int = 1004, lr_min: float = 1e-5):
+        import math
+        rng = self._np.random.default_rng(seed)
+        steps = max(1, n_samples // batch)
+        losses = torch.zeros(batch, dtype=torch.float32, device=self.device)
+        hist = []
+        for it in range(steps):
+            data = self.sample_data(batch, rng)
+            p = self.exact(data)
+            cur = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * it / steps))
+            self.model.train_step(self.phases(data), p, cur, losses)
+            if it % max(1, steps // 20) == 0 or it == steps - 1:
+                hist.append((it, float(losses.mean().item())))
+        sync_status()
+        return hist
+
+    def evaluate(self, count: int = 10000, seed: int = 1005, batch: int = 2048):
+        """Held-out total variation of the bare surrogate against exact SLOS."""
+        rng = self._np.random.default_rng(seed)
+        tvs = []
+        L = lib()
+        for off in range(0, count, batch):
+            nb = min(batch, count - off)
+            nb8 = (nb + 7) // 8 * 8
+            data = self.sample_data(nb8, rng)
+            q = self.model.forward(self.phases(data))
+            p = self.exact(data)
+            rows = torch.arange(nb8, dtype=torch.int32, device=self.device)
+            tv = torch.empty(nb8, dtype=torch.float32, device=self.device)
+            B._check(L.surr_tv_rows(B._ptr(q), B._ptr(rows), B._ptr(p), nb8, self.K, B._ptr(tv), B._stream()))
+            tvs.append(tv[:nb].cpu().numpy())
+        tv = self._np.concatenate(tvs)
+        return {"p50": float(self._np.median(tv)), "p99": float(self._np.percentile(tv, 99)), "max": float(tv.max()),
+                "frac_gt_0.02": float((tv > 0.02).mean()), "count": int(tv.size)}
+
+    def infer(self, data: torch.Tensor, rho: float = 1 / 64, tv_tol: float = 0.02, seed: int = 0):
+        """Surrogate outputs with the exact path as judge: a mean-photon-number
+        screen on every sample (a difference above 2 n tv_tol proves TV >
+        tv_tol), an exact spot check of a seeded fraction rho, exact fallback
+        for every sample that failed either."""
+        L = lib()
+        Bn = data.shape[0]
+        q = self.model.forward(self.phases(data))
+        U = B.mesh_unitary(self.m, self.theta, data, Bn)
+        flag = torch.zeros(Bn, dtype=torch.int32, device=self.device)
+        marg = torch.empty((Bn, self.m), dtype=torch.float32, device=self.device)
+        s_host = (ctypes.c_int * self.m)(*self.s)
+        B._check(L.surr_screen(B._ptr(q), Bn, self.K, B._ptr(self.occ), self.m, B._ptr(U), s_host,
+                               2.0 * self.n * tv_tol, B._ptr(marg), B._ptr(flag), B._stream()))
+        rng = self._np.random.default_rng(seed)
+        n_chk = max(1, int(round(rho * Bn)))
+        chk = torch.tensor(self._np.sort(rng.choice(Bn, size=n_chk, replace=False)), dtype=torch.int32,
+                           device=self.device)
+        dchk = torch.empty((n_chk, self.m), dtype=torch.float32, device=self.device)
+        B._check(L.surr_gather_rows(B._ptr(data), B._ptr(chk), n_chk, self.m, B._ptr(dchk), B._stream()))
+        pchk = self.exact(dchk)
+        tv = torch.empty(n_chk, dtype=torch.float32, device=self.device)
+        B._check(L.surr_tv_rows(B._ptr(q), B._ptr(chk), B._ptr(pchk), n_chk, self.K, B._ptr(tv), B._stream()))
+        # decisions on the host: which samples fall back
+        fl = flag.cpu().numpy().astype(bool)
+        tvh = tv.cpu().numpy()
+        ch = chk.cpu().numpy()
+        fl[ch[tvh > tv_tol]] = True
+        # checked samples that passed keep the surrogate; the checked exact rows are free to reuse
+        bad = self._np.nonzero(fl)[0]
+        if bad.size:
+            rows = torch.tensor(bad, dtype=torch.int32, device=self.device)
+            dbad = torch.empty((bad.size, self.m), dtype=torch.float32, device=self.device)
+            B._check(L.surr_gather_rows(B._ptr(data), B._ptr(rows), bad.size, self.m, B._ptr(dbad), B._stream()))
+            pbad = self.exact(dbad)
+            B._check(L.surr_scatter_rows(B._ptr(pbad), B._ptr(rows), bad.size, self.K, B._ptr(q), B._stream()))
+        stats = {"batch": Bn, "screen_flagged": int(flag.sum().item()), "checked": n_chk,
+                 "check_failed": int((tvh > tv_tol).sum()), "fallback": int(bad.size),
+                 "fallback_rate": float(bad.size / Bn), "checked_tv_max": float(tvh.max())}
+        return q, stats
