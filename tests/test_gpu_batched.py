@@ -169,4 +169,5 @@ def test_bounded_wait_reports_timeout_and_context_survives(slos):
     bp.sync_status()
     ref = torch.empty_like(out)
     bp.forward(U, ref, ws)
-    assert torch.allclose(out, ref, atol=0, rtol=0)
+    # threshold outcomes accumulate with float atomics: equal up to summation order
+    assert torch.allclose(out, ref, atol=P_TOL, rtol=0)
