@@ -324,6 +324,7 @@ static Layout make_layout(const slos_plan_s *p, int batch, bool training) {
     L.seedT = SIZE_MAX;
     L.dupart.assign(n + 1, SIZE_MAX);
     L.dpw = SIZE_MAX;
+    L.dulayer = SIZE_MAX;
     L.bwd_blocks.assign(n + 1, 0);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -370,6 +371,7 @@ static Layout make_layout(const slos_plan_s *p, int batch, bool training) {
             L.bwd_blocks[k] = bx;
             L.dupart[k] = take((size_t)NG * bx * kLanes * p->m * sizeof(float2));
         }
+        L.dulayer = take((size_t)(n + 1) * NG * kLanes * p->m * sizeof(float2));
     }
     L.total = off;
     return L;
@@ -379,16 +381,36 @@ static void fill_pat_off(const slos_plan_s *p, int *dst) {
     for (int i = 0; i < kMaxPhotons + 2; ++i) dst[i] = p->pat_off[std::min(i, 15)];
 }
 
-// dU[b][j][i] = sum over layers k with c_k = i and over blocks of the partials.
+// dU reduction, in a fixed order.  Pass 1 (grid: layer x group, threads:
+// lane x mode): sum the per-block partials of layer k, reading contiguous
+// rows.  Pass 2 (thread per dU entry): dU[b][j][i] = sum over the layers k
+// whose photon sits in mode i (c_k = i) of the per-layer sums.
 struct ReduceArgs {
     const float2 *part[kMaxPhotons + 1];
     int blocks[kMaxPhotons + 1];
     int cols[kMaxPhotons + 1];
-    int n, m, B;
+    int n, m, B, NG;
+    float2 *layer;  // [n + 1][NG][32][m]
     float2 *dU;
 };
 
-__global__ void dU_reduce_kernel(ReduceArgs a) {
+__global__ void dU_layer_sum_kernel(ReduceArgs a) {
+    const int k = blockIdx.x + 1, grp = blockIdx.y;
+    const int per = kLanes * a.m;
+    const int bx = a.blocks[k];
+    const float2 *base = a.part[k] + (int64_t)grp * bx * per;
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int blk = 0; blk < bx; ++blk) {
+            const float2 v = base[(int64_t)blk * per + e];
+            s.x += v.x;
+            s.y += v.y;
+        }
+        a.layer[((int64_t)k * a.NG + grp) * per + e] = s;
+    }
+}
+
+__global__ void dU_assemble_kernel(ReduceArgs a) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)a.B * a.m * a.m;
     if (tid >= total) return;
@@ -399,13 +421,9 @@ __global__ void dU_reduce_kernel(ReduceArgs a) {
     float2 s = make_float2(0.f, 0.f);
     for (int k = 1; k <= a.n; ++k) {
         if (a.cols[k] != i) continue;
-        const int bx = a.blocks[k];
-        const float2 *base = a.part[k] + ((int64_t)grp * bx * kLanes) * a.m;
-        for (int blk = 0; blk < bx; ++blk) {
-            const float2 v = base[((int64_t)blk * kLanes + lane) * a.m + j];
-            s.x += v.x;
-            s.y += v.y;
-        }
+        const float2 v = a.layer[(((int64_t)k * a.NG + grp) * kLanes + lane) * a.m + j];
+        s.x += v.x;
+        s.y += v.y;
     }
     a.dU[tid] = s;
 }
@@ -667,7 +685,8 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
         t.entries = p->tab.layer[k].entries;
         t.w = p->tab.w;
         t.pat = p->tab.pat;
-        SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, NG), s));
+        const int gpw = NG >= 2 ? p->fwd_gpw : 1;
+        SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, (NG + gpw - 1) / gpw), gpw, s));
     } else {
         SLOS_CUDA(launch_fwd(p->m, a, epi, save, bx, s));
     }
@@ -797,11 +816,18 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
     ra.n = n;
     ra.m = m;
     ra.B = batch;
+    ra.NG = NG;
+    ra.layer = reinterpret_cast<float2 *>(ws + Ly.dulayer);
     ra.dU = reinterpret_cast<float2 *>(dU);
     const int64_t tot = (int64_t)batch * m * m;
     {
-        ProfScope ps("slos_dU_reduce", 16.0 * tot, s);
-        dU_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ra);
+        double bytes = 0.0;
+        for (int k = 1; k <= n; ++k) bytes += 8.0 * NG * Ly.bwd_blocks[k] * kLanes * m;
+        ProfScope ps("slos_dU_reduce", bytes + 8.0 * tot, s);
+        dU_layer_sum_kernel<<<dim3(n, NG), 256, 0, s>>>(ra);
+        SLOS_CUDA(cudaGetLastError());
+        count_launch();
+        dU_assemble_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ra);
         SLOS_CUDA(cudaGetLastError());
     }
     return SLOS_OK;

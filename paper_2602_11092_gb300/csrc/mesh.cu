@@ -101,23 +101,24 @@ __global__ void mesh_fwd_kernel(MeshArgs a) {
     }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // Reverse sweep.  With U = Y_l T_l X_{l-1} (X_{l-1} = T_{l-1}..T_1,
 // Y_l = T_L..T_{l+1}) and M_l = Y_l^H dU, the gradient w.r.t. the 2x2 block
 // is G = M_l X_{l-1}^H on rows/cols (k, k+1), and
-//      dL/dx = Re sum_ab conj(G_ab) dT_ab/dx.
-// Going down: X_{l-1} = T_l^H X_l, M_{l-1} = T_l^H M_l.
+//      dL/dx = Re sum_ab conj(G_ab) dT_ab/dx
+//            = sum_i Re sum_ab conj(M_l[a][i]) X_{l-1}[b][i] dT_ab/dx,
+// a sum over the columns i (lanes) of per-lane scalars.  Going down:
+// X_{l-1} = T_l^H X_l, M_{l-1} = T_l^H M_l.  Each lane writes its scalar for
+// every phase to shared memory during the sweep (no cross-lane traffic in
+// the sequential part); the column sums are formed at the end, one phase per
+// lane at a time, in a fixed order.
 template <int MMAX>
 __global__ void mesh_bwd_kernel(MeshBwdArgs a) {
+    extern __shared__ float contrib[];  // [P + n_data][33]
     const int lane = threadIdx.x & 31;
-    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int b = blockIdx.x;
     if (b >= a.B) return;
     const int m = a.m;
+    const int P = m * (m - 1);
     const float *th = a.theta + (int64_t)b * a.theta_stride;
     const float *dd = a.data ? a.data + (int64_t)b * a.data_stride : nullptr;
     float *gth = a.dtheta + (int64_t)b * a.dtheta_stride;
@@ -137,8 +138,7 @@ __global__ void mesh_bwd_kernel(MeshBwdArgs a) {
             for (int k = 0; k < MMAX - 1; ++k) {
                 if ((k & 1) == par && k + 1 < m) {
                     const int idx = base + (k - par) / 2;
-                    const float theta = th[2 * idx], phi = th[2 * idx + 1];
-                    const Mzi z = make_mzi(theta, phi);
+                    const Mzi z = make_mzi(th[2 * idx], th[2 * idx + 1]);
                     // X_before = T^H X
                     const float2 xk = x[k], xk1 = x[k + 1];
                     const float2 bk = cfma_conj_a(z.t10, xk1, make_float2(z.t00.x * xk.x + z.t00.y * xk.y,
@@ -147,16 +147,7 @@ __global__ void mesh_bwd_kernel(MeshBwdArgs a) {
                                                                             z.t01.x * xk.y - z.t01.y * xk.x));
                     x[k] = bk;
                     x[k + 1] = bk1;
-                    // G_ab = sum_i M[a][i] conj(Xb[b][i])
                     const float2 mk = mm[k], mk1 = mm[k + 1];
-                    float g00x = mk.x * bk.x + mk.y * bk.y, g00y = mk.y * bk.x - mk.x * bk.y;
-                    float g01x = mk.x * bk1.x + mk.y * bk1.y, g01y = mk.y * bk1.x - mk.x * bk1.y;
-                    float g10x = mk1.x * bk.x + mk1.y * bk.y, g10y = mk1.y * bk.x - mk1.x * bk.y;
-                    float g11x = mk1.x * bk1.x + mk1.y * bk1.y, g11y = mk1.y * bk1.x - mk1.x * bk1.y;
-                    g00x = warp_sum(g00x); g00y = warp_sum(g00y);
-                    g01x = warp_sum(g01x); g01y = warp_sum(g01y);
-                    g10x = warp_sum(g10x); g10y = warp_sum(g10y);
-                    g11x = warp_sum(g11x); g11y = warp_sum(g11y);
                     // dT/dtheta = [[ (i/2) e^{i th} e^{i ph}, -(1/2) e^{i th}],
                     //              [-(1/2) e^{i th} e^{i ph}, -(i/2) e^{i th}]]
                     const float2 e2 = cmul(z.eth, z.eph);
@@ -164,17 +155,17 @@ __global__ void mesh_bwd_kernel(MeshBwdArgs a) {
                     const float2 d01 = make_float2(-0.5f * z.eth.x, -0.5f * z.eth.y);
                     const float2 d10 = make_float2(-0.5f * e2.x, -0.5f * e2.y);
                     const float2 d11 = make_float2(0.5f * z.eth.y, -0.5f * z.eth.x);
-                    // Re(conj(G) d) = Gx dx + Gy dy
-                    const float dth = g00x * d00.x + g00y * d00.y + g01x * d01.x + g01y * d01.y +
-                                      g10x * d10.x + g10y * d10.y + g11x * d11.x + g11y * d11.y;
                     // dT/dphi = [[i t00, 0], [i t10, 0]]
                     const float2 p00 = make_float2(-z.t00.y, z.t00.x);
                     const float2 p10 = make_float2(-z.t10.y, z.t10.x);
-                    const float dph = g00x * p00.x + g00y * p00.y + g10x * p10.x + g10y * p10.y;
-                    if (lane == 0) {
-                        gth[2 * idx] = dth;
-                        gth[2 * idx + 1] = dph;
-                    }
+                    // per-lane Re( conj(M_a) sum_b Xb_b dT_ab )
+                    const float2 r0 = cfma(bk1, d01, cmul(bk, d00));
+                    const float2 r1 = cfma(bk1, d11, cmul(bk, d10));
+                    const float cth = mk.x * r0.x + mk.y * r0.y + mk1.x * r1.x + mk1.y * r1.y;
+                    const float2 q0 = cmul(bk, p00), q1 = cmul(bk, p10);
+                    const float cph = mk.x * q0.x + mk.y * q0.y + mk1.x * q1.x + mk1.y * q1.y;
+                    contrib[(2 * idx) * 33 + lane] = cth;
+                    contrib[(2 * idx + 1) * 33 + lane] = cph;
                     // M_before = T^H M
                     mm[k] = cfma_conj_a(z.t10, mk1, make_float2(z.t00.x * mk.x + z.t00.y * mk.y,
                                                                 z.t00.x * mk.y - z.t00.y * mk.x));
@@ -190,19 +181,22 @@ __global__ void mesh_bwd_kernel(MeshBwdArgs a) {
                     float s, co;
                     sincosf(dd[j], &s, &co);
                     const float2 e = make_float2(co, s);
-                    // X_before = conj(e) X ; G = sum_i M conj(X_before)
+                    // X_before = conj(e) X ; contribution Re(conj(M) Xb (i e))
                     const float2 xb = make_float2(e.x * x[j].x + e.y * x[j].y, e.x * x[j].y - e.y * x[j].x);
                     x[j] = xb;
-                    float gx = mm[j].x * xb.x + mm[j].y * xb.y;
-                    float gy = mm[j].y * xb.x - mm[j].x * xb.y;
-                    gx = warp_sum(gx);
-                    gy = warp_sum(gy);
-                    // dS_jj/dx_j = i e ; Re(conj(G) i e) = Gx (-e.y) + Gy e.x
-                    if (lane == 0) a.ddata[(int64_t)b * a.n_data + j] = -gx * e.y + gy * e.x;
+                    const float2 r = cmul(xb, make_float2(-e.y, e.x));
+                    contrib[(P + j) * 33 + lane] = mm[j].x * r.x + mm[j].y * r.y;
                     mm[j] = make_float2(e.x * mm[j].x + e.y * mm[j].y, e.x * mm[j].y - e.y * mm[j].x);
                 }
             }
         }
+    }
+    __syncwarp();
+    for (int q = lane; q < P + a.n_data; q += 32) {
+        float sum = 0.f;
+        for (int l = 0; l < 32; ++l) sum += contrib[q * 33 + l];
+        if (q < P) gth[q] = sum;
+        else a.ddata[(int64_t)b * a.n_data + (q - P)] = sum;
     }
 }
 
@@ -224,8 +218,15 @@ static cudaError_t launch_fwd(const MeshArgs &a, cudaStream_t s) {
 
 template <int MMAX>
 static cudaError_t launch_bwd(const MeshBwdArgs &a, cudaStream_t s) {
-    const int wpb = 4;
-    mesh_bwd_kernel<MMAX><<<(a.B + wpb - 1) / wpb, wpb * 32, 0, s>>>(a);
+    const size_t smem = (size_t)(a.m * (a.m - 1) + a.n_data) * 33 * sizeof(float);
+    static bool attr_set = false;  // largest case: m = 24 needs 76 KB
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(mesh_bwd_kernel<MMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((24 * 23 + 24) * 33 * sizeof(float)));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    mesh_bwd_kernel<MMAX><<<a.B, 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 

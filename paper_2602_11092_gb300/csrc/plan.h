@@ -34,6 +34,7 @@ struct Layout {
     std::vector<size_t> dupart; // [1..n]: dU partials of layer k
     std::vector<int> bwd_blocks;  // [1..n]: blocks_x of the backward launch of layer k
     size_t dpw;                   // shared seed [F_n] floats (aliases seedT)
+    size_t dulayer;               // per-layer dU sums [n][NG][32][m] c64
     size_t total;
 };
 
@@ -62,5 +63,6 @@ struct slos_plan_s {
     int sm_count;
     int *d_status;          // device status word (owned)
     slos::PlanTables tab;   // transition graph (owned; empty when too large)
+    int fwd_gpw = 2;        // instance groups per warp in the table-driven forward
     slos::BatchedPlan *batched;
 };

@@ -19,23 +19,40 @@
 
 namespace slos {
 
-template <int EPI, bool SAVE>
+template <int EPI, bool SAVE, int GPW>
 __global__ void __launch_bounds__(kThreads) slos_fwd_tab_kernel(FwdArgs a, TabArgs t) {
-    __shared__ float2 us[kMaxModes][32];
+    // GPW groups of 32 instances per warp: lane l serves instance l of each
+    // group, so the entry stream and its decoding are shared by 32*GPW instances.
+    __shared__ float2 us[GPW][kMaxModes][32];
     extern __shared__ float4 smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int grp = blockIdx.y;
-    const int inst = grp * kLanes + lane;
-    const bool valid = inst < a.B;
-    for (int j = warp; j < a.m; j += kWarpsPerBlock)
-        us[j][lane] = valid ? a.U[((int64_t)inst * a.m + j) * a.m + a.col] : make_float2(0.f, 0.f);
+    const int grp0 = blockIdx.y * GPW;
+    bool valid[GPW];
+    int inst[GPW];
+#pragma unroll
+    for (int q = 0; q < GPW; ++q) {
+        inst[q] = (grp0 + q) * kLanes + lane;
+        valid[q] = (grp0 + q) < a.NG && inst[q] < a.B;
+    }
+    for (int j = warp; j < a.m; j += kWarpsPerBlock) {
+#pragma unroll
+        for (int q = 0; q < GPW; ++q)
+            us[q][j][lane] = valid[q] ? a.U[((int64_t)inst[q] * a.m + j) * a.m + a.col] : make_float2(0.f, 0.f);
+    }
     __syncthreads();
 
-    const char *prevb = reinterpret_cast<const char *>(a.prev + (int64_t)grp * a.Fprev * kLanes + lane);
-    float2 *nextg = a.next + (int64_t)grp * a.Fk * kLanes + lane;
-    const char *usb = reinterpret_cast<const char *>(&us[0][lane]);
-    float *tile = reinterpret_cast<float *>(smem_raw) + warp * (32 * 33 * (EPI == EPI_AMPS ? 2 : 1));
+    const char *prevb[GPW];
+    float2 *nextg[GPW];
+#pragma unroll
+    for (int q = 0; q < GPW; ++q) {
+        const int g = min(grp0 + q, a.NG - 1);  // a missing second group reads group NG-1 and writes nothing
+        prevb[q] = reinterpret_cast<const char *>(a.prev + (int64_t)g * a.Fprev * kLanes + lane);
+        nextg[q] = a.next + (int64_t)g * a.Fk * kLanes + lane;
+    }
+    const char *usb = reinterpret_cast<const char *>(&us[0][0][lane]);
+    constexpr int kUsGroup = kMaxModes * 32 * 8;  // bytes between the groups' U tables
+    float *tile = reinterpret_cast<float *>(smem_raw) + warp * (GPW * 32 * 33 * (EPI == EPI_AMPS ? 2 : 1));
     const int64_t nchunks = (a.Fk + 31) / 32;
     const int64_t wstride = (int64_t)gridDim.x * kWarpsPerBlock;
     const bool first_layer = a.k == 1;
@@ -45,17 +62,22 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_tab_kernel(FwdArgs a, TabAr
         const int nc = (int)min((int64_t)32, a.Fk - c0);
         const int e0 = __ldg(t.rowptr + c0);
         const int e1 = __ldg(t.rowptr + c0 + nc);
-        // per-child epilogue data of this chunk, one child per lane
         float wl = 0.f;
         int patl = 0;
         if (EPI != EPI_STORE && lane < nc) {
             wl = __ldg(t.w + c0 + lane);
             if (EPI == EPI_THRESH) patl = __ldg(t.pat + c0 + lane);
         }
-        int ci = 0;  // child index within the chunk
-        float2 acc = make_float2(0.f, 0.f);
-        int run_pat = -1;
-        float run_val = 0.f;
+        int ci = 0;
+        float2 acc[GPW];
+        int run_pat[GPW];
+        float run_val[GPW];
+#pragma unroll
+        for (int q = 0; q < GPW; ++q) {
+            acc[q] = make_float2(0.f, 0.f);
+            run_pat[q] = -1;
+            run_val[q] = 0.f;
+        }
         for (int qb = e0; qb < e1; qb += 32) {
             const int cnt = min(32, e1 - qb);
             // entries past this chunk read as 0: no load, no contribution, no `last` bit
@@ -65,63 +87,78 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_tab_kernel(FwdArgs a, TabAr
             const int nb = (cnt + 7) >> 3;
             for (int r0 = 0; r0 < 8 * nb; r0 += 8) {
                 uint32_t e[8];
-                float2 v[8];
+                float2 v[8][GPW];
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
                     e[r] = __shfl_sync(0xffffffffu, mine, r0 + r);
-                    v[r] = make_float2(0.f, 0.f);
-                    if (e[r] != 0u) {
-                        v[r] = first_layer ? make_float2(1.f, 0.f)
-                                           : __ldg(reinterpret_cast<const float2 *>(prevb + ((size_t)(e[r] >> 6) << 8)));
+                    const size_t off = (size_t)(e[r] >> 6) << 8;
+#pragma unroll
+                    for (int q = 0; q < GPW; ++q) {
+                        v[r][q] = make_float2(0.f, 0.f);
+                        if (e[r] != 0u)
+                            v[r][q] = first_layer ? make_float2(1.f, 0.f)
+                                                  : __ldg(reinterpret_cast<const float2 *>(prevb[q] + off));
                     }
                 }
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    const float2 uu = *reinterpret_cast<const float2 *>(usb + (((e[r] >> 1) & 31u) << 8));
-                    acc = cfma(uu, v[r], acc);
+                    const uint32_t uoff = ((e[r] >> 1) & 31u) << 8;
+#pragma unroll
+                    for (int q = 0; q < GPW; ++q) {
+                        const float2 uu = *reinterpret_cast<const float2 *>(usb + q * kUsGroup + uoff);
+                        acc[q] = cfma(uu, v[r][q], acc[q]);
+                    }
                     if (e[r] & 1u) {
                         // child c0 + ci is complete
                         const int64_t c = c0 + ci;
-                        if (SAVE || EPI == EPI_STORE) nextg[c * kLanes] = acc;
-                        if (EPI != EPI_STORE) {
-                            const float w = __shfl_sync(0xffffffffu, wl, ci);
-                            if (EPI == EPI_PROBS) {
-                                tile[lane * 33 + ci] = w * (acc.x * acc.x + acc.y * acc.y);
-                            } else if (EPI == EPI_AMPS) {
-                                reinterpret_cast<float2 *>(tile)[lane * 33 + ci] = cscale(acc, sqrtf(w));
-                            } else {
-                                const float pr = w * (acc.x * acc.x + acc.y * acc.y);
-                                const int pat = __shfl_sync(0xffffffffu, patl, ci);
-                                if (pat != run_pat) {
-                                    if (run_pat >= 0 && valid)
-                                        atomicAdd(reinterpret_cast<float *>(a.out) + (int64_t)inst * a.K + run_pat,
-                                                  run_val);
-                                    run_pat = pat;
-                                    run_val = 0.f;
-                                }
-                                run_val += pr;
+                        const float w = (EPI != EPI_STORE) ? __shfl_sync(0xffffffffu, wl, ci) : 0.f;
+                        const int pat = (EPI == EPI_THRESH) ? __shfl_sync(0xffffffffu, patl, ci) : 0;
+#pragma unroll
+                        for (int q = 0; q < GPW; ++q) {
+                            if (SAVE || EPI == EPI_STORE) {
+                                if (grp0 + q < a.NG) nextg[q][c * kLanes] = acc[q];
                             }
+                            if (EPI == EPI_PROBS) {
+                                tile[(q * 32 + lane) * 33 + ci] = w * (acc[q].x * acc[q].x + acc[q].y * acc[q].y);
+                            } else if (EPI == EPI_AMPS) {
+                                reinterpret_cast<float2 *>(tile)[(q * 32 + lane) * 33 + ci] = cscale(acc[q], sqrtf(w));
+                            } else if (EPI == EPI_THRESH) {
+                                const float pr = w * (acc[q].x * acc[q].x + acc[q].y * acc[q].y);
+                                if (pat != run_pat[q]) {
+                                    if (run_pat[q] >= 0 && valid[q])
+                                        atomicAdd(reinterpret_cast<float *>(a.out) + (int64_t)inst[q] * a.K + run_pat[q],
+                                                  run_val[q]);
+                                    run_pat[q] = pat;
+                                    run_val[q] = 0.f;
+                                }
+                                run_val[q] += pr;
+                            }
+                            acc[q] = make_float2(0.f, 0.f);
                         }
-                        acc = make_float2(0.f, 0.f);
                         ++ci;
                     }
                 }
             }
         }
         if (EPI == EPI_THRESH) {
-            if (run_pat >= 0 && valid)
-                atomicAdd(reinterpret_cast<float *>(a.out) + (int64_t)inst * a.K + run_pat, run_val);
+#pragma unroll
+            for (int q = 0; q < GPW; ++q)
+                if (run_pat[q] >= 0 && valid[q])
+                    atomicAdd(reinterpret_cast<float *>(a.out) + (int64_t)inst[q] * a.K + run_pat[q], run_val[q]);
         }
         if (EPI == EPI_PROBS || EPI == EPI_AMPS) {
             __syncwarp();
-            for (int i = 0; i < kLanes; ++i) {
-                const int ii = grp * kLanes + i;
-                if (ii < a.B && lane < nc) {
-                    if (EPI == EPI_PROBS) {
-                        reinterpret_cast<float *>(a.out)[(int64_t)ii * a.K + c0 + lane] = tile[i * 33 + lane];
-                    } else {
-                        reinterpret_cast<float2 *>(a.out)[(int64_t)ii * a.K + c0 + lane] =
-                            reinterpret_cast<const float2 *>(tile)[i * 33 + lane];
+#pragma unroll
+            for (int q = 0; q < GPW; ++q) {
+                for (int i = 0; i < kLanes; ++i) {
+                    const int ii = (grp0 + q) * kLanes + i;
+                    if (grp0 + q < a.NG && ii < a.B && lane < nc) {
+                        if (EPI == EPI_PROBS) {
+                            reinterpret_cast<float *>(a.out)[(int64_t)ii * a.K + c0 + lane] = tile[(q * 32 + i) * 33 + lane];
+                        } else {
+                            reinterpret_cast<float2 *>(a.out)[(int64_t)ii * a.K + c0 + lane] =
+                                reinterpret_cast<const float2 *>(tile)[(q * 32 + i) * 33 + lane];
+                        }
                     }
                 }
             }
@@ -130,29 +167,52 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_tab_kernel(FwdArgs a, TabAr
     }
 }
 
-cudaError_t slos_tab_init() {
-    const int sm = (int)fwd_smem_bytes(EPI_AMPS);
-    cudaError_t e = cudaFuncSetAttribute(slos_fwd_tab_kernel<EPI_AMPS, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(slos_fwd_tab_kernel<EPI_AMPS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+template <int GPW>
+static size_t tab_smem(int epi) {
+    return GPW * fwd_smem_bytes(epi);
 }
 
-cudaError_t slos_launch_fwd_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, cudaStream_t s) {
-    dim3 grid(blocks_x, a.NG);
-    const size_t sm = fwd_smem_bytes(epi);
+template <int GPW>
+static cudaError_t tab_attrs() {
+    cudaError_t e;
+    const int sp = (int)tab_smem<GPW>(EPI_PROBS), sa = (int)tab_smem<GPW>(EPI_AMPS);
+    if ((e = cudaFuncSetAttribute(slos_fwd_tab_kernel<EPI_PROBS, false, GPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sp)))
+        return e;
+    if ((e = cudaFuncSetAttribute(slos_fwd_tab_kernel<EPI_PROBS, true, GPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sp)))
+        return e;
+    if ((e = cudaFuncSetAttribute(slos_fwd_tab_kernel<EPI_AMPS, false, GPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa)))
+        return e;
+    return cudaFuncSetAttribute(slos_fwd_tab_kernel<EPI_AMPS, true, GPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa);
+}
+
+cudaError_t slos_tab_init() {
+    cudaError_t e = tab_attrs<1>();
+    if (e != cudaSuccess) return e;
+    return tab_attrs<2>();
+}
+
+template <int GPW>
+static cudaError_t launch_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, cudaStream_t s) {
+    dim3 grid(blocks_x, (a.NG + GPW - 1) / GPW);
+    const size_t sm = tab_smem<GPW>(epi);
     switch (epi * 2 + (save ? 1 : 0)) {
         case 0:
-        case 1: slos_fwd_tab_kernel<EPI_STORE, true><<<grid, kThreads, 0, s>>>(a, t); break;
-        case 2: slos_fwd_tab_kernel<EPI_PROBS, false><<<grid, kThreads, sm, s>>>(a, t); break;
-        case 3: slos_fwd_tab_kernel<EPI_PROBS, true><<<grid, kThreads, sm, s>>>(a, t); break;
-        case 4: slos_fwd_tab_kernel<EPI_AMPS, false><<<grid, kThreads, sm, s>>>(a, t); break;
-        case 5: slos_fwd_tab_kernel<EPI_AMPS, true><<<grid, kThreads, sm, s>>>(a, t); break;
-        case 6: slos_fwd_tab_kernel<EPI_THRESH, false><<<grid, kThreads, 0, s>>>(a, t); break;
-        case 7: slos_fwd_tab_kernel<EPI_THRESH, true><<<grid, kThreads, 0, s>>>(a, t); break;
+        case 1: slos_fwd_tab_kernel<EPI_STORE, true, GPW><<<grid, kThreads, 0, s>>>(a, t); break;
+        case 2: slos_fwd_tab_kernel<EPI_PROBS, false, GPW><<<grid, kThreads, sm, s>>>(a, t); break;
+        case 3: slos_fwd_tab_kernel<EPI_PROBS, true, GPW><<<grid, kThreads, sm, s>>>(a, t); break;
+        case 4: slos_fwd_tab_kernel<EPI_AMPS, false, GPW><<<grid, kThreads, sm, s>>>(a, t); break;
+        case 5: slos_fwd_tab_kernel<EPI_AMPS, true, GPW><<<grid, kThreads, sm, s>>>(a, t); break;
+        case 6: slos_fwd_tab_kernel<EPI_THRESH, false, GPW><<<grid, kThreads, 0, s>>>(a, t); break;
+        case 7: slos_fwd_tab_kernel<EPI_THRESH, true, GPW><<<grid, kThreads, 0, s>>>(a, t); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t slos_launch_fwd_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, int gpw,
+                                cudaStream_t s) {
+    if (gpw == 2) return launch_tab<2>(a, t, epi, save, blocks_x, s);
+    return launch_tab<1>(a, t, epi, save, blocks_x, s);
 }
 
 }  // namespace slos

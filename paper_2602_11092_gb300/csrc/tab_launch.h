@@ -15,6 +15,8 @@ struct TabArgs {
 };
 
 cudaError_t slos_tab_init();
-cudaError_t slos_launch_fwd_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, cudaStream_t s);
+// gpw: instance groups served by one warp (1 or 2)
+cudaError_t slos_launch_fwd_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, int gpw,
+                                cudaStream_t s);
 
 }  // namespace slos
