@@ -50,22 +50,39 @@ __device__ __forceinline__ int mzi_offset(int c, int m) {
     return ((c + 1) / 2) * ne + (c / 2) * no;
 }
 
+// The 2x2 blocks of every MZI (and the data-screen phase factors) of one
+// instance, computed in parallel by the warp's lanes into shared memory, so
+// the sequential sweeps below only read them.
+struct MziTab {
+    float2 t00, t01, t10, t11, eth, eph;
+};
+
+__device__ __forceinline__ void fill_mzi_table(const float *th, const float *dd, int m, int n_data, int lane,
+                                               MziTab *tab, float2 *ed) {
+    const int nmzi = m * (m - 1) / 2;
+    for (int idx = lane; idx < nmzi; idx += 32) {
+        const Mzi z = make_mzi(th[2 * idx], th[2 * idx + 1]);
+        tab[idx] = MziTab{z.t00, z.t01, z.t10, z.t11, z.eth, z.eph};
+    }
+    for (int j = lane; j < n_data; j += 32) {
+        float s, c;
+        sincosf(dd[j], &s, &c);
+        ed[j] = make_float2(c, s);
+    }
+    __syncwarp();
+}
+
 // Forward sweep for one column of U (lane = input mode), all in registers.
 template <int MMAX>
-__device__ __forceinline__ void mesh_column(const float *th, const float *dd, int m, int n_data, int data_col,
+__device__ __forceinline__ void mesh_column(const MziTab *tab, const float2 *ed, int m, int n_data, int data_col,
                                             int lane, float2 (&x)[MMAX]) {
 #pragma unroll
     for (int j = 0; j < MMAX; ++j) x[j] = make_float2(j == lane ? 1.f : 0.f, 0.f);
     for (int c = 0; c <= m; ++c) {
         if (c == data_col && n_data > 0) {
 #pragma unroll
-            for (int j = 0; j < MMAX; ++j) {
-                if (j < n_data) {
-                    float s, co;
-                    sincosf(dd[j], &s, &co);
-                    x[j] = cmul(make_float2(co, s), x[j]);
-                }
-            }
+            for (int j = 0; j < MMAX; ++j)
+                if (j < n_data) x[j] = cmul(ed[j], x[j]);
         }
         if (c == m) break;
         const int base = mzi_offset(c, m);
@@ -73,8 +90,7 @@ __device__ __forceinline__ void mesh_column(const float *th, const float *dd, in
 #pragma unroll
         for (int k = 0; k < MMAX - 1; ++k) {
             if ((k & 1) == par && k + 1 < m) {
-                const int idx = base + (k - par) / 2;
-                const Mzi z = make_mzi(th[2 * idx], th[2 * idx + 1]);
+                const MziTab z = tab[base + (k - par) / 2];
                 const float2 xk = x[k], xk1 = x[k + 1];
                 x[k] = cfma(z.t01, xk1, cmul(z.t00, xk));
                 x[k + 1] = cfma(z.t11, xk1, cmul(z.t10, xk));
@@ -83,16 +99,31 @@ __device__ __forceinline__ void mesh_column(const float *th, const float *dd, in
     }
 }
 
+// per-warp shared memory: MZI table + data-screen factors
+template <int MMAX>
+struct MeshSmem {
+    MziTab tab[MMAX * (MMAX - 1) / 2];
+    float2 ed[MMAX];
+};
+
+// warps (instances) per block of the forward mesh kernel: the per-warp MZI
+// tables must stay under the 48 KB static shared-memory limit
+template <int MMAX>
+constexpr int mesh_fwd_warps() { return MMAX > 16 ? 2 : 4; }
+
 template <int MMAX>
 __global__ void mesh_fwd_kernel(MeshArgs a) {
+    __shared__ MeshSmem<MMAX> sm[mesh_fwd_warps<MMAX>()];
     const int lane = threadIdx.x & 31;
-    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int w = threadIdx.x >> 5;
+    const int b = blockIdx.x * (blockDim.x >> 5) + w;
     if (b >= a.B) return;
     const int m = a.m;
     const float *th = a.theta + (int64_t)b * a.theta_stride;
     const float *dd = a.data ? a.data + (int64_t)b * a.data_stride : nullptr;
+    fill_mzi_table(th, dd, m, a.n_data, lane, sm[w].tab, sm[w].ed);
     float2 x[MMAX];
-    mesh_column<MMAX>(th, dd, m, a.n_data, a.data_col, lane, x);
+    mesh_column<MMAX>(sm[w].tab, sm[w].ed, m, a.n_data, a.data_col, lane, x);
     if (lane < m) {
         float2 *U = a.U + (int64_t)b * m * m;
 #pragma unroll
@@ -114,6 +145,7 @@ __global__ void mesh_fwd_kernel(MeshArgs a) {
 template <int MMAX>
 __global__ void mesh_bwd_kernel(MeshBwdArgs a) {
     extern __shared__ float contrib[];  // [P + n_data][33]
+    __shared__ MeshSmem<MMAX> sm;
     const int lane = threadIdx.x & 31;
     const int b = blockIdx.x;
     if (b >= a.B) return;
@@ -123,7 +155,8 @@ __global__ void mesh_bwd_kernel(MeshBwdArgs a) {
     const float *dd = a.data ? a.data + (int64_t)b * a.data_stride : nullptr;
     float *gth = a.dtheta + (int64_t)b * a.dtheta_stride;
     float2 x[MMAX], mm[MMAX];
-    mesh_column<MMAX>(th, dd, m, a.n_data, a.data_col, lane, x);  // X = U, recomputed
+    fill_mzi_table(th, dd, m, a.n_data, lane, sm.tab, sm.ed);
+    mesh_column<MMAX>(sm.tab, sm.ed, m, a.n_data, a.data_col, lane, x);  // X = U, recomputed
 #pragma unroll
     for (int j = 0; j < MMAX; ++j) {
         mm[j] = make_float2(0.f, 0.f);
@@ -178,9 +211,7 @@ __global__ void mesh_bwd_kernel(MeshBwdArgs a) {
 #pragma unroll
             for (int j = 0; j < MMAX; ++j) {
                 if (j < a.n_data) {
-                    float s, co;
-                    sincosf(dd[j], &s, &co);
-                    const float2 e = make_float2(co, s);
+                    const float2 e = sm.ed[j];
                     // X_before = conj(e) X ; contribution Re(conj(M) Xb (i e))
                     const float2 xb = make_float2(e.x * x[j].x + e.y * x[j].y, e.x * x[j].y - e.y * x[j].x);
                     x[j] = xb;
@@ -211,7 +242,7 @@ __global__ void mesh_reduce_kernel(const float *part, int B, int P, float *out) 
 
 template <int MMAX>
 static cudaError_t launch_fwd(const MeshArgs &a, cudaStream_t s) {
-    const int wpb = 4;
+    const int wpb = mesh_fwd_warps<MMAX>();
     mesh_fwd_kernel<MMAX><<<(a.B + wpb - 1) / wpb, wpb * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
