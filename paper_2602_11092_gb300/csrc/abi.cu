@@ -223,7 +223,9 @@ static slos_status_t build_tables(slos_plan_s *p) {
     const int m = p->m, n = p->n;
     size_t bytes = 0;
     for (int k = 1; k <= n; ++k) {
-        if (p->F[k - 1] >= kMaxTableParent || p->F[k] >= ((int64_t)1 << 31) / m) return SLOS_OK;  // too large
+        // packed parent ranks < 2^26; 32-bit element offsets (state * 32) in the kernels
+        if (p->F[k - 1] >= kMaxTableParent || p->F[k] >= ((int64_t)1 << 27) || p->F[k] >= ((int64_t)1 << 31) / m)
+            return SLOS_OK;  // too large: arithmetic-index kernels
         bytes += 4 * (size_t)(p->F[k] + 1) + 8 * (size_t)m * p->F[k - 1];
     }
     bytes += 8 * (size_t)p->F[n];

@@ -42,13 +42,15 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_tab_kernel(FwdArgs a, TabAr
     }
     __syncthreads();
 
-    const char *prevb[GPW];
+    // 64-bit group bases once; every per-entry offset below is 32-bit
+    // (table plans have F_k * 32 < 2^32)
+    const float2 *prevg[GPW];
     float2 *nextg[GPW];
 #pragma unroll
     for (int q = 0; q < GPW; ++q) {
         const int g = min(grp0 + q, a.NG - 1);  // a missing second group reads group NG-1 and writes nothing
-        prevb[q] = reinterpret_cast<const char *>(a.prev + (int64_t)g * a.Fprev * kLanes + lane);
-        nextg[q] = a.next + (int64_t)g * a.Fk * kLanes + lane;
+        prevg[q] = a.prev + (size_t)g * (size_t)a.Fprev * kLanes + lane;
+        nextg[q] = a.next + (size_t)g * (size_t)a.Fk * kLanes + lane;
     }
     const char *usb = reinterpret_cast<const char *>(&us[0][0][lane]);
     constexpr int kUsGroup = kMaxModes * 32 * 8;  // bytes between the groups' U tables
@@ -91,18 +93,16 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_tab_kernel(FwdArgs a, TabAr
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
                     e[r] = __shfl_sync(0xffffffffu, mine, r0 + r);
-                    const size_t off = (size_t)(e[r] >> 6) << 8;
+                    const uint32_t off = (e[r] >> 6) << 5;  // parent rank * 32 (elements)
 #pragma unroll
                     for (int q = 0; q < GPW; ++q) {
                         v[r][q] = make_float2(0.f, 0.f);
-                        if (e[r] != 0u)
-                            v[r][q] = first_layer ? make_float2(1.f, 0.f)
-                                                  : __ldg(reinterpret_cast<const float2 *>(prevb[q] + off));
+                        if (e[r] != 0u) v[r][q] = first_layer ? make_float2(1.f, 0.f) : __ldg(prevg[q] + off);
                     }
                 }
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    const uint32_t uoff = ((e[r] >> 1) & 31u) << 8;
+                    const uint32_t uoff = (e[r] << 7) & 0x1F00u;  // mode * 256 bytes
 #pragma unroll
                     for (int q = 0; q < GPW; ++q) {
                         const float2 uu = *reinterpret_cast<const float2 *>(usb + q * kUsGroup + uoff);
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_tab_kernel(FwdArgs a, TabAr
 #pragma unroll
                         for (int q = 0; q < GPW; ++q) {
                             if (SAVE || EPI == EPI_STORE) {
-                                if (grp0 + q < a.NG) nextg[q][c * kLanes] = acc[q];
+                                if (grp0 + q < a.NG) nextg[q][(uint32_t)c << 5] = acc[q];
                             }
                             if (EPI == EPI_PROBS) {
                                 tile[(q * 32 + lane) * 33 + ci] = w * (acc[q].x * acc[q].x + acc[q].y * acc[q].y);
