@@ -418,17 +418,12 @@ __global__ void __launch_bounds__(kBwdTabWarps * 32) slos_bwd_tab_kernel(BwdArgs
     float2 dU[MMAX];
 #pragma unroll
     for (int j = 0; j < MMAX; ++j) dU[j] = make_float2(0.f, 0.f);
-    // 64-bit group bases once; per-state offsets are 32-bit (F_k * 32 < 2^32 in table plans)
-    const float2 *aprev_g = a.aprev + (size_t)grp * (size_t)a.Fprev * kLanes + lane;
-    float2 *gprev_g = a.Gprev + (size_t)grp * (size_t)a.Fprev * kLanes + lane;
-    const float2 *gk_g = (SEED == SEED_G ? a.Gk : a.an) + (size_t)grp * (size_t)a.Fk * kLanes + lane;
-    const float2 *seedc_g = reinterpret_cast<const float2 *>(a.seed) + (size_t)grp * (size_t)a.Fk * kLanes + lane;
-    const float *seedf_g = reinterpret_cast<const float *>(a.seed) + (size_t)grp * (size_t)a.Fk * kLanes + lane;
-    const float *dpw = reinterpret_cast<const float *>(a.seed);
-    const uint32_t nwarps = gridDim.x * kBwdTabWarps;
-    for (uint32_t c = blockIdx.x * kBwdTabWarps + warp; c < (uint32_t)a.Fprev; c += nwarps) {
-        const int mine = lane < m ? __ldg(ctab + (size_t)c * m + lane) : 0;
-        const float2 av = (a.k == 1) ? make_float2(1.f, 0.f) : __ldg(aprev_g + (c << 5));
+    const int64_t gofs_prev = (int64_t)grp * a.Fprev * kLanes + lane;
+    const int64_t gofs_k = (int64_t)grp * a.Fk * kLanes + lane;
+    const int64_t nwarps = (int64_t)gridDim.x * kBwdTabWarps;
+    for (int64_t c = (int64_t)blockIdx.x * kBwdTabWarps + warp; c < a.Fprev; c += nwarps) {
+        const int mine = lane < m ? __ldg(ctab + c * m + lane) : 0;
+        const float2 av = (a.k == 1) ? make_float2(1.f, 0.f) : __ldg(a.aprev + gofs_prev + c * kLanes);
         float2 gacc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int h = 0; h < MMAX; h += 8) {
@@ -436,20 +431,9 @@ __global__ void __launch_bounds__(kBwdTabWarps * 32) slos_bwd_tab_kernel(BwdArgs
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 const int j = h + r;
+                const int cidx = __shfl_sync(0xffffffffu, mine, j < 32 ? j : 0);
                 g[r] = make_float2(0.f, 0.f);
-                if (j < MMAX && j < m) {
-                    const uint32_t cidx = (uint32_t)__shfl_sync(0xffffffffu, mine, j);
-                    const uint32_t off = cidx << 5;
-                    if (SEED == SEED_G) {
-                        g[r] = __ldg(gk_g + off);
-                    } else if (SEED == SEED_AMPS_T) {
-                        g[r] = __ldg(seedc_g + off);
-                    } else {
-                        const float2 an = __ldg(gk_g + off);
-                        const float sc = (SEED == SEED_BCAST) ? __ldg(dpw + cidx) : __ldg(seedf_g + off);
-                        g[r] = cscale(an, sc);
-                    }
-                }
+                if (j < m) g[r] = load_child_grad<SEED>(a, gofs_k + (int64_t)cidx * kLanes, cidx);
             }
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
@@ -460,7 +444,7 @@ __global__ void __launch_bounds__(kBwdTabWarps * 32) slos_bwd_tab_kernel(BwdArgs
                 }
             }
         }
-        if (a.k > 1) gprev_g[c << 5] = gacc;
+        if (a.k > 1) a.Gprev[gofs_prev + c * kLanes] = gacc;
     }
     float2 *dst = a.dUpart + (((int64_t)grp * gridDim.x + blockIdx.x) * kLanes) * m;
 #pragma unroll
