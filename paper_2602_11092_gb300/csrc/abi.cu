@@ -164,7 +164,8 @@ static void bars_of(uint64_t z, int m, int L, int *p, int *t) {
 
 static void free_tables(slos_plan_s *p) {
     for (auto &L : p->tab.layer) {
-        if (L.ell) cudaFree(L.ell);
+        if (L.rowptr) cudaFree(L.rowptr);
+        if (L.entries) cudaFree(L.entries);
         if (L.ctab) cudaFree(L.ctab);
         L = LayerTables();
     }
@@ -225,7 +226,7 @@ static slos_status_t build_tables(slos_plan_s *p) {
         // packed parent ranks < 2^26; 32-bit element offsets (state * 32) in the kernels
         if (p->F[k - 1] >= kMaxTableParent || p->F[k] >= ((int64_t)1 << 27) || p->F[k] >= ((int64_t)1 << 31) / m)
             return SLOS_OK;  // too large: arithmetic-index kernels
-        bytes += 4 * (size_t)p->F[k] * (((std::min(m, k) + 3) / 4) * 4) + 4 * (size_t)m * p->F[k - 1];
+        bytes += 4 * (size_t)(p->F[k] + 1) + 8 * (size_t)m * p->F[k - 1];
     }
     bytes += 8 * (size_t)p->F[n];
     if (bytes > kTableBudgetBytes) return SLOS_OK;
@@ -242,21 +243,15 @@ static slos_status_t build_tables(slos_plan_s *p) {
         std::vector<int32_t> rowptr, ctab;
         std::vector<uint32_t> entries;
         build_layer_host(m, k, rowptr, entries, ctab);
-        // fixed-width parent lists for the device
-        const int kw = ((std::min(m, k) + 3) / 4) * 4;
-        std::vector<uint32_t> ell((size_t)p->F[k] * kw, kEllEmpty);
-        for (int64_t c = 0; c < p->F[k]; ++c) {
-            int q = 0;
-            for (int32_t e = rowptr[c]; e < rowptr[c + 1]; ++e, ++q)
-                ell[(size_t)c * kw + q] = ((entries[e] >> 6) << 5) | ((entries[e] >> 1) & 31u);
-        }
         LayerTables &LT = p->tab.layer[k];
-        LT.kw = kw;
-        if (cudaMalloc(&LT.ell, ell.size() * 4) != cudaSuccess || cudaMalloc(&LT.ctab, ctab.size() * 4) != cudaSuccess) {
+        if (cudaMalloc(&LT.rowptr, rowptr.size() * 4) != cudaSuccess ||
+            cudaMalloc(&LT.entries, entries.size() * 4) != cudaSuccess ||
+            cudaMalloc(&LT.ctab, ctab.size() * 4) != cudaSuccess) {
             free_tables(p);
             return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the transition tables");
         }
-        cudaMemcpy(LT.ell, ell.data(), ell.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(LT.rowptr, rowptr.data(), rowptr.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(LT.entries, entries.data(), entries.size() * 4, cudaMemcpyHostToDevice);
         cudaMemcpy(LT.ctab, ctab.data(), ctab.size() * 4, cudaMemcpyHostToDevice);
     }
     // final-layer weights and threshold patterns
@@ -688,11 +683,12 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
     ProfScope ps(name, bytes * batch, s);
     if (p->tab.enabled) {
         TabArgs t;
-        t.ell = p->tab.layer[k].ell;
-        t.kw = p->tab.layer[k].kw;
+        t.rowptr = p->tab.layer[k].rowptr;
+        t.entries = p->tab.layer[k].entries;
         t.w = p->tab.w;
         t.pat = p->tab.pat;
-        SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, NG), s));
+        const int gpw = NG >= 2 ? p->fwd_gpw : 1;
+        SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, (NG + gpw - 1) / gpw), gpw, s));
     } else {
         SLOS_CUDA(launch_fwd(p->m, a, epi, save, bx, s));
     }

@@ -8,13 +8,15 @@
 namespace slos {
 
 struct TabArgs {
-    const uint32_t *ell;      // fixed-width parent lists of layer k [F_k][kw]
-    int kw;                   // slots per state, multiple of 4
+    const int32_t *rowptr;    // [F_k + 1]
+    const uint32_t *entries;  // CSR parent entries of layer k
     const float *w;           // final layer: prod t! / prod s!  [F_n]
     const int32_t *pat;       // final layer, threshold: pattern index [F_n]
 };
 
 cudaError_t slos_tab_init();
-cudaError_t slos_launch_fwd_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, cudaStream_t s);
+// gpw: instance groups served by one warp (1 or 2)
+cudaError_t slos_launch_fwd_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, int gpw,
+                                cudaStream_t s);
 
 }  // namespace slos

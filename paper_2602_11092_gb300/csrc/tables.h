@@ -3,11 +3,10 @@
 // of unitaries; only the U coefficients change per call).
 //
 // For layer k (k photons, built for k = 1..n):
-//   forward:  fixed-width parent lists (ELL).  State c owns slots
-//             ell[c * kw .. c * kw + kw - 1], kw = min(m, k) rounded up to a
-//             multiple of 4; slot = (parent rank << 5) | mode, or 0xFFFFFFFF
-//             when empty.  (The CSR form with rowptr/entries is what
-//             slos_host_transition_table exports; the device keeps the ELL.)
+//   forward:  CSR parent lists.  rowptr[c] .. rowptr[c+1] index the entries of
+//             child state c; entry = (parent rank << 6) | (mode << 1) | last,
+//             where `last` marks the final entry of a child.  Parent ranks are
+//             < 2^26.
 //   backward: dense child table ctab[c'][j] = rank_k(t' + e_j) for every
 //             parent c' of layer k-1 and every mode j.
 // For the final layer n: w[t] = prod t_j! / prod s_i! and, for threshold
@@ -20,12 +19,10 @@
 namespace slos {
 
 struct LayerTables {
-    uint32_t *ell = nullptr;     // [F_k * kw]
-    int kw = 0;
+    int32_t *rowptr = nullptr;   // [F_k + 1]
+    uint32_t *entries = nullptr; // [m * F_{k-1}]
     int32_t *ctab = nullptr;     // [F_{k-1} * m]
 };
-
-constexpr uint32_t kEllEmpty = 0xFFFFFFFFu;
 
 struct PlanTables {
     bool enabled = false;
