@@ -14,7 +14,7 @@ def bf(x):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 200), (129, 257, 1000), (64, 128, 2048),
-                                   (1024, 2048, 288), (256, 12376, 256)])
+                                   (1024, 2048, 288), (256, 12376, 256), (8192, 2048, 2048)])
 def test_tc_gemm_matches_cpu(M, N, K):
     from paper_2602_11092_gb300 import surrogate as S
     rng = np.random.default_rng(M + N + K)
