@@ -1,14 +1,15 @@
 // Tensor-core GEMM for sm_103a: C[M][N] = A[M][K] . B[N][K]^T, BF16 inputs
 // (both K-major), FP32 accumulation in tensor memory (TMEM), fused epilogues.
 //
-// One CTA = 128 threads computes one 128 x 128 output tile.
+// One CTA = 128 threads computes one 128 x 256 output tile.
 //   warp 0, lane 0: TMA producer.  cp.async.bulk.tensor loads 128x64 tiles of
 //                   A and B (128-byte swizzle) into a 4-stage ring; each stage
 //                   has a `full` mbarrier (transaction bytes) and an `empty`
 //                   mbarrier (arrived by tcgen05.commit when the MMAs that
 //                   read the stage are done).
 //   warp 1, lane 0: MMA issuer.  Four tcgen05.mma.kind::f16 (K = 16 each) per
-//                   stage into one 128 x 128 FP32 accumulator in TMEM.
+//                   stage into one 128 x 256 FP32 accumulator in TMEM
+//                   (256 of the SM's 512 TMEM columns).
 //   all 4 warps:    epilogue.  tcgen05.ld 32x32b: warp w reads TMEM lanes
 //                   32w..32w+31 (= output rows), 16 columns per load.
 // Every mbarrier wait has an iteration limit; a wait that runs out sets the
@@ -23,12 +24,12 @@
 namespace slos {
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_TILE = BM * BK * 2;  // bytes
 constexpr int B_TILE = BN * BK * 2;
 constexpr int STAGE_BYTES = A_TILE + B_TILE;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr uint32_t TMEM_COLS = 128;
+constexpr uint32_t TMEM_COLS = BN;
 constexpr long long kWaitLimit = 1ll << 22;  // tries; a few seconds at most
 
 enum TcEpi : int {
@@ -221,32 +222,78 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const int row = m0 + warp * 32 + lane;
     if (ok) {
+        // 16 consecutive outputs per thread per TMEM load: one row segment,
+        // written with 16-byte stores when the row stride allows it
+        const bool vec = (g.ldc % 8) == 0;
 #pragma unroll 1
         for (int c = 0; c < BN; c += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (row < g.M) {
-                const int col0 = n0 + c;
+            const int col0 = n0 + c;
+            if (row < g.M && col0 < g.N) {
+                const int64_t o0 = (int64_t)row * g.ldc + col0;
+                if (EPI == TC_F32_BIAS || EPI == TC_GELU) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int col = col0 + i;
-                    if (col >= g.N) break;
-                    const int64_t o = (int64_t)row * g.ldc + col;
-                    float x = v[i];
-                    if (EPI == TC_F32) {
-                        reinterpret_cast<float *>(g.C)[o] = x;
-                    } else if (EPI == TC_F32_ACCUM) {
-                        reinterpret_cast<float *>(g.C)[o] += x;
-                    } else if (EPI == TC_F32_BIAS) {
-                        reinterpret_cast<float *>(g.C)[o] = x + g.bias[col];
-                    } else if (EPI == TC_GELU) {
-                        const float z = x + g.bias[col];
-                        const __nv_bfloat16 zb = __float2bfloat16(z);
-                        g.aux[o] = zb;
-                        reinterpret_cast<__nv_bfloat16 *>(g.C)[o] = __float2bfloat16(gelu_f(__bfloat162float(zb)));
-                    } else {  // TC_GELU_BWD
-                        const float z = __bfloat162float(g.aux[o]);
-                        reinterpret_cast<__nv_bfloat16 *>(g.C)[o] = __float2bfloat16(x * gelu_grad(z));
+                    for (int i = 0; i < 16; ++i) v[i] += (col0 + i < g.N) ? g.bias[col0 + i] : 0.f;
+                }
+                if (vec && col0 + 16 <= g.N) {
+                    if (EPI == TC_F32 || EPI == TC_F32_BIAS || EPI == TC_F32_ACCUM) {
+                        float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(g.C) + o0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float4 w = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                            if (EPI == TC_F32_ACCUM) {
+                                const float4 old = dst[q];
+                                w.x += old.x;
+                                w.y += old.y;
+                                w.z += old.z;
+                                w.w += old.w;
+                            }
+                            dst[q] = w;
+                        }
+                    } else {
+                        __align__(16) __nv_bfloat16 out[16];
+                        if (EPI == TC_GELU) {
+                            __align__(16) __nv_bfloat16 zb[16];
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                zb[i] = __float2bfloat16(v[i]);
+                                out[i] = __float2bfloat16(gelu_f(__bfloat162float(zb[i])));
+                            }
+                            uint4 *za = reinterpret_cast<uint4 *>(g.aux + o0);
+                            za[0] = reinterpret_cast<const uint4 *>(zb)[0];
+                            za[1] = reinterpret_cast<const uint4 *>(zb)[1];
+                        } else {  // TC_GELU_BWD
+                            __align__(16) __nv_bfloat16 zb[16];
+                            const uint4 *zs = reinterpret_cast<const uint4 *>(g.aux + o0);
+                            reinterpret_cast<uint4 *>(zb)[0] = zs[0];
+                            reinterpret_cast<uint4 *>(zb)[1] = zs[1];
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) out[i] = __float2bfloat16(v[i] * gelu_grad(__bfloat162float(zb[i])));
+                        }
+                        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) + o0);
+                        dst[0] = reinterpret_cast<const uint4 *>(out)[0];
+                        dst[1] = reinterpret_cast<const uint4 *>(out)[1];
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int col = col0 + i;
+                        if (col >= g.N) break;
+                        const int64_t o = o0 + i;
+                        const float x = v[i];
+                        if (EPI == TC_F32 || EPI == TC_F32_BIAS) {
+                            reinterpret_cast<float *>(g.C)[o] = x;
+                        } else if (EPI == TC_F32_ACCUM) {
+                            reinterpret_cast<float *>(g.C)[o] += x;
+                        } else if (EPI == TC_GELU) {
+                            const __nv_bfloat16 zb = __float2bfloat16(x);
+                            g.aux[o] = zb;
+                            reinterpret_cast<__nv_bfloat16 *>(g.C)[o] = __float2bfloat16(gelu_f(__bfloat162float(zb)));
+                        } else {  // TC_GELU_BWD
+                            const float z = __bfloat162float(g.aux[o]);
+                            reinterpret_cast<__nv_bfloat16 *>(g.C)[o] = __float2bfloat16(x * gelu_grad(z));
+                        }
                     }
                 }
             }
