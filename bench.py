@@ -63,7 +63,7 @@ def csrc_hash() -> str:
 def ncu_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it still
     matches the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    path = os.path.join(ROOT, "profiles", "slos_final_layers_train16_dram_traffic.json")
     if not os.path.exists(path):
         return None
     try:
