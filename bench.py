@@ -51,10 +51,16 @@ def peaks():
     return 6800.0, "fallback"
 
 
+SLOS_KERNEL_FILES = ("abi.cu", "common.cuh", "plan.h", "slos_kernels.cuh", "slos_m16.cu", "slos_tab.cu",
+                     "tab_launch.h", "tables.h")
+
+
 def csrc_hash() -> str:
+    """Hash of the sources of the single-shape SLOS kernels (what the DRAM
+    traffic figures under profiles/ were measured on)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2602_11092_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
+    for fn in SLOS_KERNEL_FILES:
         h.update(fn.encode())
         h.update(open(os.path.join(d, fn), "rb").read())
     return h.hexdigest()[:16]
