@@ -2,9 +2,18 @@
 // persistent kernel launch (graph-capturable), with launch shapes picked by
 // an autotuner.
 //
-// Instances with the same shape are packed 32 per "lane group" (lane =
-// instance, as in the single-shape path).  Work item = (lane group, layer k,
-// chunk of consecutive Fock states of layer k).  Items are listed layer by
+// Instances with the same shape are packed 16 per "lane group"; a warp
+// serves one lane group and walks two Fock states at a time (half-warp h
+// takes every other state, lane & 15 is the instance), so the ~14 instances
+// a shape typically has in a 1024-instance batch fill most lanes.  Layer k of
+// a lane group lives in workspace as complex64 [F_k][16].  Each shape's
+// transition graph is built once on the GPU at plan time as fixed-width
+// parent slots: slot = (parent rank << 5) | j for every mode j with t_j > 0,
+// 0xFFFFFFFF when unused (Sec. II-A.3: the transitions depend only on the
+// input state).  The modes in a final state's slots are its occupied-mode
+// pattern (threshold detection); its weight prod t_j! / prod s_i! is a
+// per-state table built with the slots.
+// Work item = (lane group, layer k, chunk of consecutive Fock states).  Items are listed layer by
 // layer (all layer-1 items of every lane group, then all layer-2 items, ...),
 // largest lane groups first inside a layer (longest-processing-time order).
 // Warps pop items in that order with one atomic counter; an item of layer
@@ -34,25 +43,36 @@
 namespace slos {
 slos_status_t fail(slos_status_t st, const std::string &msg);
 
-constexpr int kBMax = 20;  // modes handled by the persistent kernel (m <= 20)
+constexpr int kBMax = 20;   // modes handled by the persistent kernel (m <= 20)
+constexpr int kBLanes = 16; // instances per lane group
+constexpr uint32_t kSlotEmpty = (uint32_t)kBMax;   // parent 0, mode kBMax (a zero row of U)
+constexpr int64_t kBMaxParent = int64_t(1) << 27;  // parent ranks in 27 bits
 
 struct BShape {
     int m, n, det, K;
     int cols[kMaxPhotons];
     int64_t F[kMaxPhotons + 1];
+    int64_t slot_off[kMaxPhotons + 1];  // element offset of layer k's slots in the table buffer
+    int64_t w_off;                      // final-layer weights prod t! / prod s! (float) [F_n]
+    int64_t plist_off;                  // threshold: final states grouped by pattern [F_n]
+    int kw[kMaxPhotons + 1];            // slots per state of layer k (4, 8 or 12)
     float inv_sfact;
-    int pat_off[kMaxPhotons + 2];
+    int nclass;                         // threshold: pattern classes j = 1 .. min(n, m)
+    int pat_off[kMaxPhotons + 2];       // first pattern index with j occupied modes
+    int pat_cnt[kMaxPhotons + 2];       // final states per pattern with j occupied modes: C(n-1, j-1)
+    int64_t pat_base[kMaxPhotons + 2];  // first position of class j in the grouped list
 };
 
 struct BLaneGroup {
     int shape;
-    int inst[kLanes];     // global instance index per lane, -1 = empty lane
-    int64_t buf[2];       // workspace byte offsets of the two layer buffers
+    int inst[kBLanes];    // global instance index per lane, -1 = empty lane
+    int64_t buf[2];       // workspace byte offsets of the two layer buffers; buf[1] also holds
+                          // the final layer's per-state probabilities under threshold detection
 };
 
 struct BDesc {
     int lg;      // lane group
-    int k;       // layer
+    int k;       // layer (n + 1: pattern sums of a threshold shape)
     int dep;     // descriptor of layer k-1 of the same lane group (-1 for k = 1)
     int nchunks;
 };
@@ -62,6 +82,7 @@ struct BArgs {
     const BLaneGroup *lgs;
     const BDesc *desc;
     const int64_t *first_item;  // [ndesc + 1]
+    const uint32_t *slots;      // all shapes' tables
     int ndesc;
     int64_t total_items;
     int chunk;
@@ -76,18 +97,144 @@ struct BArgs {
     long long spin_limit;
 };
 
+// Tables of layer k of one shape, one thread per state, with the index
+// arithmetic of the single-shape kernels (common.cuh):
+//   slots[c][q] = (rank(t - e_j) << 5) | j for the q-th occupied mode j of t;
+// for the final layer also w[c] = prod t_j! / prod s_i! and, under threshold
+// detection, the state's place in the pattern-grouped list: patterns in
+// output order (|b|, then colex), and inside a pattern the states t with
+// support b in descending-lex order of t - 1_b, a composition of n - |b|
+// photons over |b| modes, ranked with the same bar formula.
+template <int MMAX>
+__global__ void build_slots_kernel(const BShape sh, int k, uint32_t *slots, float *w, uint32_t *plist) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= sh.F[k]) return;
+    const int m = sh.m, kw = sh.kw[k];
+    const int L = k + m - 1;
+    int p[MMAX];
+    unrank_bars<MMAX>(c, m, L, p);
+    int64_t S = 0;
+    int q = 0;
+    float fprod = 1.f;
+    uint32_t supp = 0;
+    int tb[MMAX];  // occupations of the occupied modes, in mode order
+    uint32_t *dst = slots + c * kw;
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j) {
+        if (j < m) {
+            const int tj = occupation<MMAX>(j, m, L, p);
+            if (tj > 0) {
+                tb[q] = tj;
+                dst[q++] = ((uint32_t)(c - S) << 5) | (uint32_t)j;
+                fprod *= c_fact.v[tj];
+                supp |= 1u << j;
+            }
+            if (j < m - 1) S += (int64_t)binom_m1(p[j], m - 2 - j);
+        }
+    }
+    const int nb = q;
+    for (; q < kw; ++q) dst[q] = kSlotEmpty;
+    if (w) w[c] = fprod * sh.inv_sfact;
+    if (plist) {
+        const int np = k - nb, Lp = np + nb - 1;
+        int64_t r = 0;
+        int cum = 0;
+        for (int b = 0; b + 1 < nb; ++b) {
+            cum += tb[b] - 1;
+            r += (int64_t)binom(Lp - 1 - b - cum, nb - 1 - b);
+        }
+        const int64_t pos = sh.pat_base[nb] + (int64_t)colex_rank(supp) * sh.pat_cnt[nb] + r;
+        plist[pos] = (uint32_t)c;
+    }
+}
+
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
-template <int MMAX>
+enum BOut { B_NEXT = 0, B_PNR = 1, B_SCRATCH = 2 };
+
+// States c0 + half, c0 + half + 2, ... < c1 of one layer for the 16 instances
+// of a lane group (lane il of each half-warp).  us: this warp's staged column
+// of U, row j = U[j][col] per lane (row kBMax zero); prev: layer k-1 of this
+// lane (rows of 16 complex64).  Parent rows are plain (L1-cached) loads: the
+// wait on layer k-1's completion counter has ordered them after its writes.
+template <int KW>
+__device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int64_t c0, int64_t c1, int half,
+                                           const float2 *us, const char *prev, bool first_layer, int kind,
+                                           float2 *next, float *outp, float *scr, const float *__restrict__ wtab) {
+    for (int64_t c = c0 + half; c < c1; c += 2) {
+        uint32_t e[KW];
+        const uint4 *ep = reinterpret_cast<const uint4 *>(tab + c * KW);
+#pragma unroll
+        for (int q4 = 0; q4 < KW / 4; ++q4) {
+            const uint4 w4 = __ldg(ep + q4);
+            e[4 * q4] = w4.x;
+            e[4 * q4 + 1] = w4.y;
+            e[4 * q4 + 2] = w4.z;
+            e[4 * q4 + 3] = w4.w;
+        }
+        float2 acc;
+        if (first_layer) {
+            acc = us[(e[0] & 31u) * kBLanes];  // one photon: a_1(e_j) = U[j][col]
+        } else {
+            float2 v[KW];
+#pragma unroll
+            for (int q = 0; q < KW; ++q) v[q] = *reinterpret_cast<const float2 *>(prev + (size_t)(e[q] & ~31u) * 4u);
+            acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < KW; ++q) acc = cfma(us[(e[q] & 31u) * kBLanes], v[q], acc);
+        }
+        if (kind == B_NEXT) {
+            next[c * kBLanes] = acc;
+        } else {
+            const float pr = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+            if (kind == B_SCRATCH) scr[c * kBLanes] = pr;
+            else if (outp) outp[c] = pr;
+        }
+    }
+}
+
+// Threshold detection: out[P] = sum of the final-layer probabilities of the
+// states of pattern P, for the patterns whose first list position lies in
+// [s0, s1).  Half-warp `half` takes every other such pattern; the sum runs
+// in list order, so it does not depend on the launch shape.
+__device__ __forceinline__ void pattern_sums(const BShape &sh, const uint32_t *__restrict__ plist, const float *scr,
+                                             float *outp, int64_t s0, int64_t s1, int half) {
+    for (int j = 1; j <= sh.nclass; ++j) {
+        const int64_t cnt = sh.pat_cnt[j];
+        const int64_t b0 = sh.pat_base[j];
+        const int64_t b1 = b0 + (int64_t)(sh.pat_off[j + 1] - sh.pat_off[j]) * cnt;
+        if (b1 <= s0 || b0 >= s1) continue;
+        const int64_t lo = max(s0, b0) - b0, hi = min(s1, b1) - b0;
+        const int64_t q0 = (lo + cnt - 1) / cnt, q1 = (hi + cnt - 1) / cnt;
+        for (int64_t qq = q0 + half; qq < q1; qq += 2) {
+            const uint32_t *lst = plist + b0 + qq * cnt;
+            float sum = 0.f;
+            for (int64_t r = 0; r < cnt; r += 4) {
+                uint32_t id[4];
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) id[u] = r + u < cnt ? __ldg(lst + r + u) : 0xFFFFFFFFu;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = id[u] != 0xFFFFFFFFu ? scr[(size_t)id[u] * kBLanes] : 0.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) sum += v[u];
+            }
+            if (outp) outp[sh.pat_off[j] + qq] = sum;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) slos_batched_kernel(BArgs a) {
-    extern __shared__ float smem_b[];
+    extern __shared__ float2 us_all[];  // [warps][kBMax + 1][16]
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    float *tile = smem_b + warp * (32 * 33);
+    const int half = lane >> 4, il = lane & 15;
+    float2 *us = us_all + warp * ((kBMax + 1) * kBLanes);
+    if (half == 0) us[kBMax * kBLanes + il] = make_float2(0.f, 0.f);
     for (;;) {
         unsigned long long q = 0;
         if (lane == 0) q = atomicAdd(a.head, 1ull);
@@ -104,7 +251,7 @@ __global__ void __launch_bounds__(256) slos_batched_kernel(BArgs a) {
         const int64_t chunk_id = (int64_t)q - a.first_item[lo];
         const BLaneGroup &g = a.lgs[d.lg];
         const BShape &sh = a.shapes[g.shape];
-        const int m = sh.m, n = sh.n, k = d.k;
+        const int n = sh.n, k = d.k;
         if (d.dep >= 0) {
             const int need = a.desc[d.dep].nchunks;
             long long spins = 0;
@@ -124,79 +271,37 @@ __global__ void __launch_bounds__(256) slos_batched_kernel(BArgs a) {
             }
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) return;
+            __syncwarp();
             __threadfence();
         }
-        const int inst = g.inst[lane];
+        const int inst = g.inst[il];
         const bool valid = inst >= 0;
-        const int col = sh.cols[k - 1];
-        float2 u[MMAX];
-#pragma unroll
-        for (int j = 0; j < MMAX; ++j) {
-            u[j] = make_float2(0.f, 0.f);
-            if (j < m && valid) u[j] = a.U[a.u_off[inst] + (int64_t)j * m + col];
-        }
-        const int64_t Fk = sh.F[k], Fp = sh.F[k - 1];
-        const float2 *prev = reinterpret_cast<const float2 *>(a.ws + g.buf[(n - 1 - (k - 1)) & 1]) + lane;
-        float2 *next = reinterpret_cast<float2 *>(a.ws + g.buf[(n - 1 - k) & 1]) + lane;
-        (void)Fp;
-        const int L = k + m - 1;
         const int64_t c0 = chunk_id * a.chunk;
-        const int64_t c1 = min(c0 + (int64_t)a.chunk, Fk);
-        const bool final_layer = k == n;
-        float *outp = (final_layer && valid) ? a.out + a.out_off[inst] : nullptr;
-        int p[MMAX];
-        unrank_bars<MMAX>(c0, m, L, p);
-        int run_pat = -1;
-        float run_val = 0.f;
-        for (int64_t cs = c0; cs < c1; cs += 32) {
-            const int64_t ce = min(cs + 32, c1);
-            for (int64_t c = cs; c < ce; ++c) {
-                float2 acc = make_float2(0.f, 0.f);
-                int64_t S = 0;
-                float fprod = 1.f;
-                uint32_t supp = 0;
-#pragma unroll
-                for (int j = 0; j < MMAX; ++j) {
-                    if (j < m) {
-                        const int tj = occupation<MMAX>(j, m, L, p);
-                        if (tj > 0) {
-                            const float2 v = (k == 1) ? make_float2(1.f, 0.f) : __ldcg(prev + (c - S) * kLanes);
-                            acc = cfma(u[j], v, acc);
-                            fprod *= c_fact.v[tj];
-                            supp |= 1u << j;
-                        }
-                        if (j < m - 1) S += (int64_t)binom_m1(p[j], m - 2 - j);
-                    }
-                }
-                if (!final_layer) {
-                    next[c * kLanes] = acc;
-                } else {
-                    const float pr = fprod * sh.inv_sfact * (acc.x * acc.x + acc.y * acc.y);
-                    if (sh.det == SLOS_DETECT_THRESHOLD) {
-                        const int pat = sh.pat_off[__popc(supp)] + (int)colex_rank(supp);
-                        if (pat != run_pat) {
-                            if (run_pat >= 0 && valid) atomicAdd(outp + run_pat, run_val);
-                            run_pat = pat;
-                            run_val = 0.f;
-                        }
-                        run_val += pr;
-                    } else {
-                        tile[lane * 33 + (int)(c - cs)] = pr;
-                    }
-                }
-                next_bars<MMAX>(m, L, p);
-            }
-            if (final_layer && sh.det == SLOS_DETECT_PNR) {
-                __syncwarp();
-                const int nc = (int)(ce - cs);
-                for (int i = 0; i < kLanes; ++i) {
-                    const int ii = g.inst[i];
-                    if (ii >= 0 && lane < nc) a.out[a.out_off[ii] + cs + lane] = tile[i * 33 + lane];
-                }
-                __syncwarp();
+        float *outp = valid ? a.out + a.out_off[inst] : nullptr;
+        float *scr = reinterpret_cast<float *>(a.ws + g.buf[1]) + il;
+        if (k == n + 1) {
+            const int64_t c1 = min(c0 + (int64_t)a.chunk, sh.F[n]);
+            pattern_sums(sh, a.slots + sh.plist_off, scr, outp, c0, c1, half);
+        } else {
+            const int m = sh.m;
+            const int col = sh.cols[k - 1];
+            __syncwarp();
+            for (int j = half; j < m; j += 2)
+                us[j * kBLanes + il] = valid ? a.U[a.u_off[inst] + (int64_t)j * m + col] : make_float2(0.f, 0.f);
+            __syncwarp();
+            const int64_t c1 = min(c0 + (int64_t)a.chunk, sh.F[k]);
+            const char *prev = a.ws + g.buf[(n - 1 - (k - 1)) & 1] + il * sizeof(float2);
+            float2 *next = reinterpret_cast<float2 *>(a.ws + g.buf[(n - 1 - k) & 1]) + il;
+            const int kind = k < n ? B_NEXT : (sh.det == SLOS_DETECT_THRESHOLD ? B_SCRATCH : B_PNR);
+            const uint32_t *tab = a.slots + sh.slot_off[k];
+            const float *wtab = reinterpret_cast<const float *>(a.slots + sh.w_off);
+            const float2 *usl = us + il;
+            switch (sh.kw[k]) {
+                case 4: fwd_states<4>(tab, c0, c1, half, usl, prev, k == 1, kind, next, outp, scr, wtab); break;
+                case 8: fwd_states<8>(tab, c0, c1, half, usl, prev, k == 1, kind, next, outp, scr, wtab); break;
+                default: fwd_states<12>(tab, c0, c1, half, usl, prev, k == 1, kind, next, outp, scr, wtab); break;
             }
         }
-        if (final_layer && sh.det == SLOS_DETECT_THRESHOLD && run_pat >= 0 && valid) atomicAdd(outp + run_pat, run_val);
         __threadfence();
         __syncwarp();
         if (lane == 0) atomicAdd(a.done + lo, 1);
@@ -218,6 +323,7 @@ struct BatchedPlan {
     BLaneGroup *d_lgs = nullptr;
     BDesc *d_desc = nullptr;
     int64_t *d_first = nullptr, *d_uoff = nullptr, *d_ooff = nullptr;
+    uint32_t *d_slots = nullptr;  // transition tables of every shape
     int ndesc = 0;
     int64_t total_items = 0;
     int built_chunk = -1;
@@ -236,6 +342,7 @@ void batched_destroy(slos_plan_s *p) {
     cudaFree(b->d_first);
     cudaFree(b->d_uoff);
     cudaFree(b->d_ooff);
+    cudaFree(b->d_slots);
     delete b;
     p->batched = nullptr;
 }
@@ -250,24 +357,26 @@ static slos_status_t build_items(BatchedPlan *b, int chunk) {
     int kmax = 0;
     for (auto &sh : b->shapes) kmax = std::max(kmax, sh.n);
     std::vector<BDesc> desc;
-    std::vector<int> idx_of((size_t)b->lgs.size() * (kmax + 1), -1);
-    for (int k = 1; k <= kmax; ++k) {
+    std::vector<int> idx_of((size_t)b->lgs.size() * (kmax + 2), -1);
+    for (int k = 1; k <= kmax + 1; ++k) {
         std::vector<D> layer;
         for (size_t l = 0; l < b->lgs.size(); ++l) {
             const BShape &sh = b->shapes[b->lgs[l].shape];
-            if (k > sh.n) continue;
+            const bool sums = k == sh.n + 1 && sh.det == SLOS_DETECT_THRESHOLD;  // pattern sums
+            if (k > sh.n && !sums) continue;
+            const int64_t states = sums ? sh.F[sh.n] : sh.F[k];
             D x;
             x.d.lg = (int)l;
             x.d.k = k;
             x.d.dep = -1;
-            x.d.nchunks = (int)((sh.F[k] + chunk - 1) / chunk);
-            x.work = sh.F[k] * sh.m;
+            x.d.nchunks = (int)((states + chunk - 1) / chunk);
+            x.work = sums ? states : states * std::min(sh.m, k);
             layer.push_back(x);
         }
         std::stable_sort(layer.begin(), layer.end(), [](const D &a, const D &c) { return a.work > c.work; });
         for (auto &x : layer) {
-            x.d.dep = k > 1 ? idx_of[(size_t)x.d.lg * (kmax + 1) + k - 1] : -1;
-            idx_of[(size_t)x.d.lg * (kmax + 1) + k] = (int)desc.size();
+            x.d.dep = k > 1 ? idx_of[(size_t)x.d.lg * (kmax + 2) + k - 1] : -1;
+            idx_of[(size_t)x.d.lg * (kmax + 2) + k] = (int)desc.size();
             desc.push_back(x.d);
         }
     }
@@ -308,14 +417,12 @@ static slos_status_t batched_launch(slos_plan_s *p, const void *U, float *out, v
     cudaError_t e;
     if ((e = cudaMemsetAsync(w + b->layer_bytes, 0, b->ctrl_bytes, s)) != cudaSuccess)
         return fail(SLOS_ERR_CUDA, std::string("slos_batched_forward: ") + cudaGetErrorString(e));
-    // threshold outputs accumulate: clear the packed output
-    if ((e = cudaMemsetAsync(out, 0, (size_t)b->out_off[b->count] * sizeof(float), s)) != cudaSuccess)
-        return fail(SLOS_ERR_CUDA, std::string("slos_batched_forward: ") + cudaGetErrorString(e));
     BArgs a;
     a.shapes = b->d_shapes;
     a.lgs = b->d_lgs;
     a.desc = b->d_desc;
     a.first_item = b->d_first;
+    a.slots = b->d_slots;
     a.ndesc = b->ndesc;
     a.total_items = b->total_items;
     a.chunk = chunk;
@@ -336,12 +443,12 @@ static slos_status_t batched_launch(slos_plan_s *p, const void *U, float *out, v
         a.spin_limit = 5000;
     }
     const int warps = threads / 32;
-    const size_t smem = (size_t)warps * 32 * 33 * sizeof(float);
+    const size_t smem = (size_t)warps * (kBMax + 1) * kBLanes * sizeof(float2);
     const int grid = std::max(1, p->sm_count * bps);
     double bytes = 0.0;
     for (int i = 0; i < b->count; ++i) bytes += 4.0 * (b->out_off[i + 1] - b->out_off[i]);
     ProfScope ps("slos_batched", bytes, s);
-    slos_batched_kernel<kBMax><<<grid, threads, smem, s>>>(a);
+    slos_batched_kernel<<<grid, threads, smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(SLOS_ERR_CUDA, std::string("slos_batched_forward: ") + cudaGetErrorString(e));
     return SLOS_OK;
@@ -437,11 +544,23 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
                 }
             sh.inv_sfact = (float)(1.0 / sf);
             for (int k = 0; k <= ni; ++k) sh.F[k] = binom_host(mi + k - 1, k);
-            int64_t acc = 0;
-            for (int j = 1; j <= std::min(ni, mi); ++j) {
-                sh.pat_off[j] = (int)acc;
-                acc += binom_host(mi, j);
+            if (sh.F[ni - 1] >= kBMaxParent) {
+                delete b;
+                return fail(SLOS_ERR_UNSUPPORTED, "slos_batched_plan: instance " + std::to_string(i) +
+                                                      " has more than 2^27 parent states");
             }
+            // threshold patterns: classes j = |b| = 1 .. min(n, m), C(m, j) patterns of
+            // C(n-1, j-1) final states each (compositions of n into j positive parts)
+            int64_t acc = 0, pos = 0;
+            sh.nclass = std::min(ni, mi);
+            for (int j = 1; j <= sh.nclass; ++j) {
+                sh.pat_off[j] = (int)acc;
+                sh.pat_cnt[j] = (int)binom_host(ni - 1, j - 1);
+                sh.pat_base[j] = pos;
+                acc += binom_host(mi, j);
+                pos += binom_host(mi, j) * sh.pat_cnt[j];
+            }
+            sh.pat_off[sh.nclass + 1] = (int)acc;
             sh.K = (int)(detection[i] == SLOS_DETECT_PNR ? sh.F[ni] : acc);
             b->shapes.push_back(sh);
             members.emplace_back();
@@ -467,21 +586,38 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
     size_t off = 0;
     for (size_t si = 0; si < members.size(); ++si) {
         const BShape &sh = b->shapes[si];
-        for (size_t q = 0; q < members[si].size(); q += kLanes) {
+        for (size_t q = 0; q < members[si].size(); q += kBLanes) {
             BLaneGroup g;
             g.shape = (int)si;
-            for (int l = 0; l < kLanes; ++l)
+            for (int l = 0; l < kBLanes; ++l)
                 g.inst[l] = q + l < members[si].size() ? members[si][q + l] : -1;
             const int64_t f1 = sh.n >= 2 ? sh.F[sh.n - 1] : 1;
             const int64_t f2 = sh.n >= 3 ? sh.F[sh.n - 2] : 1;
+            // buf[1]: layer n-2, then (threshold) the final layer's probabilities
+            size_t b1 = (size_t)f2 * kBLanes * sizeof(float2);
+            if (sh.det == SLOS_DETECT_THRESHOLD) b1 = std::max(b1, (size_t)sh.F[sh.n] * kBLanes * sizeof(float));
             g.buf[0] = (int64_t)off;
-            off += align_up((size_t)f1 * kLanes * sizeof(float2));
+            off += align_up((size_t)f1 * kBLanes * sizeof(float2));
             g.buf[1] = (int64_t)off;
-            off += align_up((size_t)f2 * kLanes * sizeof(float2));
+            off += align_up(b1);
             b->lgs.push_back(g);
         }
     }
     b->layer_bytes = off;
+    // tables: per shape, layers 1..n of slots, the final weights, the grouped list
+    int64_t tab_elems = 0;
+    for (auto &sh : b->shapes) {
+        for (int k = 1; k <= sh.n; ++k) {
+            sh.kw[k] = (std::min(sh.m, k) + 3) & ~3;
+            sh.slot_off[k] = tab_elems;
+            tab_elems += sh.F[k] * sh.kw[k];
+        }
+        const int64_t fn4 = (sh.F[sh.n] + 3) & ~int64_t(3);
+        sh.w_off = tab_elems;
+        tab_elems += fn4;
+        sh.plist_off = tab_elems;
+        if (sh.det == SLOS_DETECT_THRESHOLD) tab_elems += fn4;
+    }
     b->signature = sig.str();
     slos_plan_s *p = new slos_plan_s();
     p->kind = 1;
@@ -513,6 +649,19 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
     cudaMemcpy(b->d_lgs, b->lgs.data(), b->lgs.size() * sizeof(BLaneGroup), cudaMemcpyHostToDevice);
     cudaMemcpy(b->d_uoff, b->u_off.data(), b->u_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     cudaMemcpy(b->d_ooff, b->out_off.data(), b->out_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (cudaMalloc(&b->d_slots, (size_t)tab_elems * sizeof(uint32_t)) != cudaSuccess)
+        return cleanup("slos_batched_plan: transition tables");
+    for (auto &sh : b->shapes) {
+        for (int k = 1; k <= sh.n; ++k) {
+            const int bs = 256;
+            const unsigned grid = (unsigned)((sh.F[k] + bs - 1) / bs);
+            float *w = k == sh.n ? reinterpret_cast<float *>(b->d_slots + sh.w_off) : nullptr;
+            uint32_t *pl = (k == sh.n && sh.det == SLOS_DETECT_THRESHOLD) ? b->d_slots + sh.plist_off : nullptr;
+            build_slots_kernel<kBMax><<<grid, bs>>>(sh, k, b->d_slots + sh.slot_off[k], w, pl);
+        }
+    }
+    if (cudaStreamSynchronize(0) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return cleanup("slos_batched_plan: building the transition tables failed");
     slos_status_t st = build_items(b, b->chunk);
     if (st != SLOS_OK) {
         batched_destroy(p);
@@ -577,8 +726,8 @@ slos_status_t slos_batched_autotune(slos_plan_t p, const void *U_packed, float *
         for (int th : thread_opts) {
             for (int bps : bps_opts) {
                 int nb = 0;
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, slos_batched_kernel<kBMax>, th,
-                                                              (size_t)(th / 32) * 32 * 33 * sizeof(float));
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, slos_batched_kernel, th,
+                                                              (size_t)(th / 32) * (kBMax + 1) * kBLanes * sizeof(float2));
                 if (nb < bps) continue;  // a persistent grid must be fully resident
                 slos_status_t st = batched_launch(p, U_packed, out_packed, workspace, workspace_bytes, s, ch, th, bps);
                 if (st != SLOS_OK) return st;  // warm-up (also builds the items)
