@@ -162,15 +162,16 @@ enum BOut { B_NEXT = 0, B_PNR = 1, B_SCRATCH = 2 };
 // lane (rows of 16 complex64).  Parent rows are plain (L1-cached) loads: the
 // wait on layer k-1's completion counter has ordered them after its writes.
 template <int KW>
-__device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int64_t c0, int64_t c1, int half,
+__device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int c0, int c1, int half,
                                            const float2 *us, const char *prev, bool first_layer, int kind,
                                            float2 *next, float *outp, float *scr, const float *__restrict__ wtab) {
-    for (int64_t c = c0 + half; c < c1; c += 2) {
+    // states fit in 32 bits (at most C(31, 12) < 2^28 per layer)
+    const uint4 *t4 = reinterpret_cast<const uint4 *>(tab);
+    for (int c = c0 + half; c < c1; c += 2) {
         uint32_t e[KW];
-        const uint4 *ep = reinterpret_cast<const uint4 *>(tab + c * KW);
 #pragma unroll
         for (int q4 = 0; q4 < KW / 4; ++q4) {
-            const uint4 w4 = __ldg(ep + q4);
+            const uint4 w4 = __ldg(t4 + (uint32_t)c * (KW / 4) + q4);
             e[4 * q4] = w4.x;
             e[4 * q4 + 1] = w4.y;
             e[4 * q4 + 2] = w4.z;
@@ -188,10 +189,10 @@ __device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int
             for (int q = 0; q < KW; ++q) acc = cfma(us[(e[q] & 31u) * kBLanes], v[q], acc);
         }
         if (kind == B_NEXT) {
-            next[c * kBLanes] = acc;
+            next[(uint32_t)c * kBLanes] = acc;
         } else {
             const float pr = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
-            if (kind == B_SCRATCH) scr[c * kBLanes] = pr;
+            if (kind == B_SCRATCH) scr[(uint32_t)c * kBLanes] = pr;
             else if (outp) outp[c] = pr;
         }
     }
@@ -228,24 +229,31 @@ __device__ __forceinline__ void pattern_sums(const BShape &sh, const uint32_t *_
     }
 }
 
-__global__ void __launch_bounds__(256) slos_batched_kernel(BArgs a) {
+// MINB: resident 256-thread blocks per SM the register allocation is sized for
+// (a tuning dimension: fewer registers, more warps in flight).
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) slos_batched_kernel(BArgs a) {
     extern __shared__ float2 us_all[];  // [warps][kBMax + 1][16]
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int half = lane >> 4, il = lane & 15;
     float2 *us = us_all + warp * ((kBMax + 1) * kBLanes);
     if (half == 0) us[kBMax * kBLanes + il] = make_float2(0.f, 0.f);
+    int lo = 0;  // descriptor of the previous item: items are handed out in increasing order
     for (;;) {
         unsigned long long q = 0;
         if (lane == 0) q = atomicAdd(a.head, 1ull);
         q = __shfl_sync(0xffffffffu, q, 0);
         if ((int64_t)q >= a.total_items) break;
-        // descriptor of item q: last i with first_item[i] <= q
-        int lo = 0, hi = a.ndesc - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.first_item[mid] <= (int64_t)q) lo = mid;
-            else hi = mid - 1;
+        // descriptor of item q: last i >= lo with first_item[i] <= q
+        if (lo + 1 < a.ndesc && a.first_item[lo + 1] <= (int64_t)q) {
+            int hi = a.ndesc - 1;
+            ++lo;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.first_item[mid] <= (int64_t)q) lo = mid;
+                else hi = mid - 1;
+            }
         }
         const BDesc d = a.desc[lo];
         const int64_t chunk_id = (int64_t)q - a.first_item[lo];
@@ -289,7 +297,7 @@ __global__ void __launch_bounds__(256) slos_batched_kernel(BArgs a) {
             for (int j = half; j < m; j += 2)
                 us[j * kBLanes + il] = valid ? a.U[a.u_off[inst] + (int64_t)j * m + col] : make_float2(0.f, 0.f);
             __syncwarp();
-            const int64_t c1 = min(c0 + (int64_t)a.chunk, sh.F[k]);
+            const int c1 = (int)min(c0 + (int64_t)a.chunk, sh.F[k]);
             const char *prev = a.ws + g.buf[(n - 1 - (k - 1)) & 1] + il * sizeof(float2);
             float2 *next = reinterpret_cast<float2 *>(a.ws + g.buf[(n - 1 - k) & 1]) + il;
             const int kind = k < n ? B_NEXT : (sh.det == SLOS_DETECT_THRESHOLD ? B_SCRATCH : B_PNR);
@@ -297,14 +305,23 @@ __global__ void __launch_bounds__(256) slos_batched_kernel(BArgs a) {
             const float *wtab = reinterpret_cast<const float *>(a.slots + sh.w_off);
             const float2 *usl = us + il;
             switch (sh.kw[k]) {
-                case 4: fwd_states<4>(tab, c0, c1, half, usl, prev, k == 1, kind, next, outp, scr, wtab); break;
-                case 8: fwd_states<8>(tab, c0, c1, half, usl, prev, k == 1, kind, next, outp, scr, wtab); break;
-                default: fwd_states<12>(tab, c0, c1, half, usl, prev, k == 1, kind, next, outp, scr, wtab); break;
+                case 4: fwd_states<4>(tab, (int)c0, c1, half, usl, prev, k == 1, kind, next, outp, scr, wtab); break;
+                case 8: fwd_states<8>(tab, (int)c0, c1, half, usl, prev, k == 1, kind, next, outp, scr, wtab); break;
+                default: fwd_states<12>(tab, (int)c0, c1, half, usl, prev, k == 1, kind, next, outp, scr, wtab); break;
             }
         }
         __threadfence();
         __syncwarp();
         if (lane == 0) atomicAdd(a.done + lo, 1);
+    }
+}
+
+using BKernel = void (*)(BArgs);
+static BKernel batched_kernel(int minb) {
+    switch (minb) {
+        case 4: return slos_batched_kernel<4>;
+        case 5: return slos_batched_kernel<5>;
+        default: return slos_batched_kernel<6>;
     }
 }
 
@@ -317,7 +334,7 @@ struct BatchedPlan {
     std::vector<BLaneGroup> lgs;
     std::string signature;
     // launch configuration (autotuned)
-    int chunk = 128, threads = 256, blocks_per_sm = 2;
+    int chunk = 256, threads = 256, blocks_per_sm = 5, minb = 5;
     // device copies (owned)
     BShape *d_shapes = nullptr;
     BLaneGroup *d_lgs = nullptr;
@@ -405,7 +422,7 @@ static slos_status_t build_items(BatchedPlan *b, int chunk) {
 }
 
 static slos_status_t batched_launch(slos_plan_s *p, const void *U, float *out, void *ws, size_t ws_bytes,
-                                    cudaStream_t s, int chunk, int threads, int bps) {
+                                    cudaStream_t s, int chunk, int threads, int bps, int minb) {
     BatchedPlan *b = p->batched;
     slos_status_t st = build_items(b, chunk);
     if (st != SLOS_OK) return st;
@@ -448,7 +465,7 @@ static slos_status_t batched_launch(slos_plan_s *p, const void *U, float *out, v
     double bytes = 0.0;
     for (int i = 0; i < b->count; ++i) bytes += 4.0 * (b->out_off[i + 1] - b->out_off[i]);
     ProfScope ps("slos_batched", bytes, s);
-    slos_batched_kernel<<<grid, threads, smem, s>>>(a);
+    batched_kernel(minb)<<<grid, threads, smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(SLOS_ERR_CUDA, std::string("slos_batched_forward: ") + cudaGetErrorString(e));
     return SLOS_OK;
@@ -461,12 +478,14 @@ static std::string device_name(int dev) {
     return prop.name;
 }
 
-static bool cache_lookup(const std::string &path, const std::string &key, int *chunk, int *threads, int *bps) {
+static bool cache_lookup(const std::string &path, const std::string &key, int *chunk, int *threads, int *bps,
+                         int *minb) {
     std::ifstream f(path);
     if (!f) return false;
     std::string line;
     while (std::getline(f, line)) {
-        // one JSON object per line: {"key": "...", "chunk": C, "threads": T, "blocks_per_sm": B, "ms": X}
+        // one JSON object per line:
+        // {"key": "...", "chunk": C, "threads": T, "blocks_per_sm": B, "min_blocks": R, "ms": X}
         const std::string kq = "\"key\": \"" + key + "\"";
         if (line.find(kq) == std::string::npos) continue;
         auto num = [&](const char *name, int *dst) {
@@ -476,7 +495,7 @@ static bool cache_lookup(const std::string &path, const std::string &key, int *c
             *dst = atoi(line.c_str() + pos + nq.size());
             return true;
         };
-        return num("chunk", chunk) && num("threads", threads) && num("blocks_per_sm", bps);
+        return num("chunk", chunk) && num("threads", threads) && num("blocks_per_sm", bps) && num("min_blocks", minb);
     }
     return false;
 }
@@ -692,7 +711,7 @@ slos_status_t slos_batched_forward(slos_plan_t p, const void *U_packed, float *o
     if (!U_packed || !out_packed) return fail(SLOS_ERR_INVALID_ARG, "slos_batched_forward: NULL pointer");
     BatchedPlan *b = p->batched;
     return batched_launch(p, U_packed, out_packed, workspace, workspace_bytes, (cudaStream_t)stream, b->chunk,
-                          b->threads, b->blocks_per_sm);
+                          b->threads, b->blocks_per_sm, b->minb);
 }
 
 slos_status_t slos_batched_inject_stall(slos_plan_t p, int enable) {
@@ -707,45 +726,50 @@ slos_status_t slos_batched_autotune(slos_plan_t p, const void *U_packed, float *
     BatchedPlan *b = p->batched;
     cudaStream_t s = (cudaStream_t)stream;
     const std::string key = device_name(p->device) + "|" + std::to_string(std::hash<std::string>()(b->signature));
-    int c = 0, t = 0, bp = 0;
-    if (cache_path && cache_lookup(cache_path, key, &c, &t, &bp)) {
+    int c = 0, t = 0, bp = 0, mb = 0;
+    if (cache_path && cache_lookup(cache_path, key, &c, &t, &bp, &mb)) {
         b->chunk = c;
         b->threads = t;
         b->blocks_per_sm = bp;
+        b->minb = mb;
         return build_items(b, c);
     }
-    const int chunks[] = {64, 128, 256, 512};
+    const int chunks[] = {128, 256, 512};
     const int thread_opts[] = {128, 256};
-    const int bps_opts[] = {1, 2, 3, 4};
+    const int minb_opts[] = {4, 5, 6};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bc = b->chunk, bt = b->threads, bb = b->blocks_per_sm;
-    for (int ch : chunks) {
+    int bc = b->chunk, bt = b->threads, bb = b->blocks_per_sm, bm = b->minb;
+    for (int mbv : minb_opts) {
         for (int th : thread_opts) {
-            for (int bps : bps_opts) {
-                int nb = 0;
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, slos_batched_kernel, th,
-                                                              (size_t)(th / 32) * (kBMax + 1) * kBLanes * sizeof(float2));
-                if (nb < bps) continue;  // a persistent grid must be fully resident
-                slos_status_t st = batched_launch(p, U_packed, out_packed, workspace, workspace_bytes, s, ch, th, bps);
-                if (st != SLOS_OK) return st;  // warm-up (also builds the items)
-                cudaEventRecord(e0, s);
-                for (int r = 0; r < 2; ++r) {
-                    st = batched_launch(p, U_packed, out_packed, workspace, workspace_bytes, s, ch, th, bps);
-                    if (st != SLOS_OK) return st;
-                }
-                cudaEventRecord(e1, s);
-                if (cudaEventSynchronize(e1) != cudaSuccess) return fail(SLOS_ERR_CUDA, "slos_batched_autotune: sync");
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms *= 0.5f;
-                if (ms < best) {
-                    best = ms;
-                    bc = ch;
-                    bt = th;
-                    bb = bps;
+            int nb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_kernel(mbv), th,
+                                                          (size_t)(th / 32) * (kBMax + 1) * kBLanes * sizeof(float2));
+            // a persistent grid must be fully resident: all of it, or one block per SM less
+            for (int bps = std::max(1, nb - 1); bps <= nb; ++bps) {
+                for (int ch : chunks) {
+                    slos_status_t st =
+                        batched_launch(p, U_packed, out_packed, workspace, workspace_bytes, s, ch, th, bps, mbv);
+                    if (st != SLOS_OK) return st;  // warm-up (also builds the items)
+                    cudaEventRecord(e0, s);
+                    for (int r = 0; r < 2; ++r) {
+                        st = batched_launch(p, U_packed, out_packed, workspace, workspace_bytes, s, ch, th, bps, mbv);
+                        if (st != SLOS_OK) return st;
+                    }
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) return fail(SLOS_ERR_CUDA, "slos_batched_autotune: sync");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms *= 0.5f;
+                    if (ms < best) {
+                        best = ms;
+                        bc = ch;
+                        bt = th;
+                        bb = bps;
+                        bm = mbv;
+                    }
                 }
             }
         }
@@ -755,11 +779,12 @@ slos_status_t slos_batched_autotune(slos_plan_t p, const void *U_packed, float *
     b->chunk = bc;
     b->threads = bt;
     b->blocks_per_sm = bb;
+    b->minb = bm;
     if (cache_path) {
         std::ofstream f(cache_path, std::ios::app);
         if (f) {
             f << "{\"key\": \"" << key << "\", \"chunk\": " << bc << ", \"threads\": " << bt
-              << ", \"blocks_per_sm\": " << bb << ", \"ms\": " << best << "}\n";
+              << ", \"blocks_per_sm\": " << bb << ", \"min_blocks\": " << bm << ", \"ms\": " << best << "}\n";
         }
     }
     return build_items(b, bc);
