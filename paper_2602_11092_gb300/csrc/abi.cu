@@ -297,18 +297,19 @@ static slos_status_t build_tables(slos_plan_s *p) {
 // ------------------------------------------------------------------ layouts
 static int groups_for(int batch) { return (batch + kLanes - 1) / kLanes; }
 
-static int blocks_for(const slos_plan_s *p, int64_t states, int chunk, int NG) {
+static int blocks_for(const slos_plan_s *p, int64_t states, int chunk, int NG, int per_sm = 4) {
     const int64_t nchunks = (states + chunk - 1) / chunk;
     const int64_t need = (nchunks + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const int64_t target = std::max<int64_t>(1, (int64_t)p->sm_count * 4 / std::max(1, NG));
+    const int64_t target = std::max<int64_t>(1, (int64_t)p->sm_count * per_sm / std::max(1, NG));
     return (int)std::max<int64_t>(1, std::min(need, std::max<int64_t>(target, 1)));
 }
 
-// Table-mode backward: one parent per warp per step, 4-warp blocks, about
-// 6 resident blocks per SM (80 registers) spread over the groups.
-static int bwd_tab_blocks(const slos_plan_s *p, int64_t parents, int NG) {
+// Table-mode backward: one parent per warp per step, 4-warp blocks, as many
+// blocks as the kernel's register budget keeps resident, spread over the groups.
+static int bwd_tab_blocks(const slos_plan_s *p, int64_t parents, int NG, bool final_layer) {
     const int64_t need = (parents + kBwdTabWarps - 1) / kBwdTabWarps;
-    const int64_t target = std::max<int64_t>(1, (int64_t)p->sm_count * 6 / std::max(1, NG));
+    const int per_sm = bwd_tab_min_blocks(mmax_for(p->m), final_layer);
+    const int64_t target = std::max<int64_t>(1, (int64_t)p->sm_count * per_sm / std::max(1, NG));
     return (int)std::max<int64_t>(1, std::min(need, target));
 }
 
@@ -368,7 +369,7 @@ static Layout make_layout(const slos_plan_s *p, int batch, bool training) {
         L.seedT = take(row * p->F[n]);  // c64-sized: enough for either seed kind
         L.dpw = L.seedT;
         for (int k = 1; k <= n; ++k) {
-            const int bx = p->tab.enabled ? bwd_tab_blocks(p, p->F[k - 1], NG)
+            const int bx = p->tab.enabled ? bwd_tab_blocks(p, p->F[k - 1], NG, k == n)
                                           : blocks_for(p, p->F[k - 1], kChunkBwd, NG);
             L.bwd_blocks[k] = bx;
             L.dupart[k] = take((size_t)NG * bx * kLanes * p->m * sizeof(float2));
@@ -687,8 +688,7 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
         t.entries = p->tab.layer[k].entries;
         t.w = p->tab.w;
         t.pat = p->tab.pat;
-        const int gpw = NG >= 2 ? p->fwd_gpw : 1;
-        SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, (NG + gpw - 1) / gpw), gpw, s));
+        SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, NG, kFwdTabMinBlocks), s));
     } else {
         SLOS_CUDA(launch_fwd(p->m, a, epi, save, bx, s));
     }

@@ -63,6 +63,5 @@ struct slos_plan_s {
     int sm_count;
     int *d_status;          // device status word (owned)
     slos::PlanTables tab;   // transition graph (owned; empty when too large)
-    int fwd_gpw = 1;        // instance groups per warp in the table-driven forward (1 measured fastest)
     slos::BatchedPlan *batched;
 };

@@ -398,12 +398,19 @@ __global__ void slos_seed_bcast_kernel(PrepArgs a) {
 // Backward with the precomputed child table: per parent, lane j < m fetches
 // rank_k(t' + e_j); the warp broadcasts each child index and gathers the child
 // gradients with independent coalesced loads, 8 modes at a time.  U[j, c_k]
-// lives in shared memory and only dU stays in registers, which keeps the
-// kernel near 80 registers (more resident warps, more loads in flight).
+// lives in shared memory and only dU stays in registers.
+//
+// Register budget (resident 4-warp blocks per SM): the final layer, which
+// also forms the child gradient from a_n and the seed, runs fastest at 64
+// registers (8 blocks, a few bytes of spill) for up to 16 modes; the
+// intermediate layers at about 80 (6 blocks).  Measured on the m=16, n=8
+// training step: 8 blocks beat 6, 7 and 9 for the final layer, 6 is best for
+// the others.
 constexpr int kBwdTabWarps = 4;
+constexpr int bwd_tab_min_blocks(int mmax, bool final_layer) { return final_layer && mmax <= 16 ? 8 : 6; }
 
-template <int MMAX, int SEED>
-__global__ void __launch_bounds__(kBwdTabWarps * 32) slos_bwd_tab_kernel(BwdArgs a, const int32_t *ctab) {
+template <int MMAX, int SEED, int MINB>
+__global__ void __launch_bounds__(kBwdTabWarps * 32, MINB) slos_bwd_tab_kernel(BwdArgs a, const int32_t *ctab) {
     __shared__ float2 red[kBwdTabWarps][32];
     __shared__ float2 us[MMAX][32];
     const int lane = threadIdx.x & 31;
@@ -524,10 +531,10 @@ inline size_t fwd_smem_bytes(int epi) {
                                           cudaStream_t s) {                                                  \
         dim3 grid(blocks_x, a.NG);                                                                           \
         switch (seed) {                                                                                      \
-            case SEED_G: slos_bwd_tab_kernel<MM, SEED_G><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;         \
-            case SEED_BCAST: slos_bwd_tab_kernel<MM, SEED_BCAST><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break; \
-            case SEED_T: slos_bwd_tab_kernel<MM, SEED_T><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;         \
-            case SEED_AMPS_T: slos_bwd_tab_kernel<MM, SEED_AMPS_T><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break; \
+            case SEED_G: slos_bwd_tab_kernel<MM, SEED_G, bwd_tab_min_blocks(MM, false)><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;         \
+            case SEED_BCAST: slos_bwd_tab_kernel<MM, SEED_BCAST, bwd_tab_min_blocks(MM, true)><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break; \
+            case SEED_T: slos_bwd_tab_kernel<MM, SEED_T, bwd_tab_min_blocks(MM, true)><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;         \
+            case SEED_AMPS_T: slos_bwd_tab_kernel<MM, SEED_AMPS_T, bwd_tab_min_blocks(MM, true)><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break; \
             default: return cudaErrorInvalidValue;                                                           \
         }                                                                                                    \
         return cudaGetLastError();                                                                           \

@@ -20,7 +20,7 @@
 namespace slos {
 
 template <int EPI, bool SAVE, int GPW>
-__global__ void __launch_bounds__(kThreads) slos_fwd_tab_kernel(FwdArgs a, TabArgs t) {
+__global__ void __launch_bounds__(kThreads, kFwdTabMinBlocks) slos_fwd_tab_kernel(FwdArgs a, TabArgs t) {
     // GPW groups of 32 instances per warp: lane l serves instance l of each
     // group, so the entry stream and its decoding are shared by 32*GPW instances.
     __shared__ float2 us[GPW][kMaxModes][32];
@@ -185,11 +185,7 @@ static cudaError_t tab_attrs() {
     return cudaFuncSetAttribute(slos_fwd_tab_kernel<EPI_AMPS, true, GPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa);
 }
 
-cudaError_t slos_tab_init() {
-    cudaError_t e = tab_attrs<1>();
-    if (e != cudaSuccess) return e;
-    return tab_attrs<2>();
-}
+cudaError_t slos_tab_init() { return tab_attrs<1>(); }
 
 template <int GPW>
 static cudaError_t launch_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, cudaStream_t s) {
@@ -209,9 +205,10 @@ static cudaError_t launch_tab(const FwdArgs &a, const TabArgs &t, int epi, bool 
     return cudaGetLastError();
 }
 
-cudaError_t slos_launch_fwd_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, int gpw,
-                                cudaStream_t s) {
-    if (gpw == 2) return launch_tab<2>(a, t, epi, save, blocks_x, s);
+// One instance group per warp: serving two groups from one entry stream
+// (GPW = 2) halves the entry traffic but measured slower on GB300 (register
+// pressure), so only GPW = 1 is instantiated.
+cudaError_t slos_launch_fwd_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, cudaStream_t s) {
     return launch_tab<1>(a, t, epi, save, blocks_x, s);
 }
 

@@ -14,9 +14,11 @@ struct TabArgs {
     const int32_t *pat;       // final layer, threshold: pattern index [F_n]
 };
 
+// Resident 256-thread blocks per SM the table forward's registers are sized
+// for (48 registers); launch grids are sized to fill them.
+constexpr int kFwdTabMinBlocks = 5;
+
 cudaError_t slos_tab_init();
-// gpw: instance groups served by one warp (1 or 2)
-cudaError_t slos_launch_fwd_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, int gpw,
-                                cudaStream_t s);
+cudaError_t slos_launch_fwd_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, cudaStream_t s);
 
 }  // namespace slos
