@@ -164,8 +164,7 @@ static void bars_of(uint64_t z, int m, int L, int *p, int *t) {
 
 static void free_tables(slos_plan_s *p) {
     for (auto &L : p->tab.layer) {
-        if (L.rowptr) cudaFree(L.rowptr);
-        if (L.entries) cudaFree(L.entries);
+        if (L.slots) cudaFree(L.slots);
         if (L.ctab) cudaFree(L.ctab);
         L = LayerTables();
     }
@@ -226,7 +225,7 @@ static slos_status_t build_tables(slos_plan_s *p) {
         // packed parent ranks < 2^26; 32-bit element offsets (state * 32) in the kernels
         if (p->F[k - 1] >= kMaxTableParent || p->F[k] >= ((int64_t)1 << 27) || p->F[k] >= ((int64_t)1 << 31) / m)
             return SLOS_OK;  // too large: arithmetic-index kernels
-        bytes += 4 * (size_t)(p->F[k] + 1) + 8 * (size_t)m * p->F[k - 1];
+        bytes += 4 * (size_t)p->F[k] * slot_width(m, k) + 4 * (size_t)m * p->F[k - 1];
     }
     bytes += 8 * (size_t)p->F[n];
     if (bytes > kTableBudgetBytes) return SLOS_OK;
@@ -244,14 +243,19 @@ static slos_status_t build_tables(slos_plan_s *p) {
         std::vector<uint32_t> entries;
         build_layer_host(m, k, rowptr, entries, ctab);
         LayerTables &LT = p->tab.layer[k];
-        if (cudaMalloc(&LT.rowptr, rowptr.size() * 4) != cudaSuccess ||
-            cudaMalloc(&LT.entries, entries.size() * 4) != cudaSuccess ||
+        // CSR -> fixed-width slots (parent << 5 | mode), padded with empty slots
+        const int kw = slot_width(m, k);
+        std::vector<uint32_t> slots((size_t)p->F[k] * kw, kSlotEmpty);
+        for (int64_t c = 0; c < p->F[k]; ++c)
+            for (int32_t q = rowptr[c]; q < rowptr[c + 1]; ++q)
+                slots[(size_t)c * kw + (q - rowptr[c])] = ((entries[q] >> 6) << 5) | ((entries[q] >> 1) & 31u);
+        LT.kw = kw;
+        if (cudaMalloc(&LT.slots, slots.size() * 4) != cudaSuccess ||
             cudaMalloc(&LT.ctab, ctab.size() * 4) != cudaSuccess) {
             free_tables(p);
             return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the transition tables");
         }
-        cudaMemcpy(LT.rowptr, rowptr.data(), rowptr.size() * 4, cudaMemcpyHostToDevice);
-        cudaMemcpy(LT.entries, entries.data(), entries.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(LT.slots, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice);
         cudaMemcpy(LT.ctab, ctab.data(), ctab.size() * 4, cudaMemcpyHostToDevice);
     }
     // final-layer weights and threshold patterns
@@ -684,8 +688,8 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
     ProfScope ps(name, bytes * batch, s);
     if (p->tab.enabled) {
         TabArgs t;
-        t.rowptr = p->tab.layer[k].rowptr;
-        t.entries = p->tab.layer[k].entries;
+        t.slots = p->tab.layer[k].slots;
+        t.kw = p->tab.layer[k].kw;
         t.w = p->tab.w;
         t.pat = p->tab.pat;
         SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, NG, kFwdTabMinBlocks), s));

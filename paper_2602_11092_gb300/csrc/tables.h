@@ -3,10 +3,10 @@
 // of unitaries; only the U coefficients change per call).
 //
 // For layer k (k photons, built for k = 1..n):
-//   forward:  CSR parent lists.  rowptr[c] .. rowptr[c+1] index the entries of
-//             child state c; entry = (parent rank << 6) | (mode << 1) | last,
-//             where `last` marks the final entry of a child.  Parent ranks are
-//             < 2^26.
+//   forward:  fixed-width parent slots, kw = min(m, k) rounded up to 4 per
+//             state: slot = (parent rank << 5) | mode for every occupied mode
+//             of the state, then empty slots (parent 0, mode kMaxModes).
+//             Parent ranks are < 2^26.
 //   backward: dense child table ctab[c'][j] = rank_k(t' + e_j) for every
 //             parent c' of layer k-1 and every mode j.
 // For the final layer n: w[t] = prod t_j! / prod s_i! and, for threshold
@@ -19,8 +19,8 @@
 namespace slos {
 
 struct LayerTables {
-    int32_t *rowptr = nullptr;   // [F_k + 1]
-    uint32_t *entries = nullptr; // [m * F_{k-1}]
+    uint32_t *slots = nullptr;   // [F_k][kw]
+    int kw = 0;
     int32_t *ctab = nullptr;     // [F_{k-1} * m]
 };
 
