@@ -407,6 +407,7 @@ __global__ void slos_seed_bcast_kernel(PrepArgs a) {
 // training step: 8 blocks beat 6, 7 and 9 for the final layer, 6 is best for
 // the others.
 constexpr int kBwdTabWarps = 4;
+constexpr int kBwdTabBatch = 8;  // child gathers issued together per parent
 constexpr int bwd_tab_min_blocks(int mmax, bool final_layer) { return final_layer && mmax <= 16 ? 8 : 6; }
 
 template <int MMAX, int SEED, int MINB>
@@ -425,25 +426,37 @@ __global__ void __launch_bounds__(kBwdTabWarps * 32, MINB) slos_bwd_tab_kernel(B
     float2 dU[MMAX];
 #pragma unroll
     for (int j = 0; j < MMAX; ++j) dU[j] = make_float2(0.f, 0.f);
-    const int64_t gofs_prev = (int64_t)grp * a.Fprev * kLanes + lane;
-    const int64_t gofs_k = (int64_t)grp * a.Fk * kLanes + lane;
-    const int64_t nwarps = (int64_t)gridDim.x * kBwdTabWarps;
-    for (int64_t c = (int64_t)blockIdx.x * kBwdTabWarps + warp; c < a.Fprev; c += nwarps) {
-        const int mine = lane < m ? __ldg(ctab + c * m + lane) : 0;
-        const float2 av = (a.k == 1) ? make_float2(1.f, 0.f) : __ldg(a.aprev + gofs_prev + c * kLanes);
+    // 64-bit group bases once; per-state offsets are 32-bit (table plans: F * 32 < 2^32)
+    const size_t gprev = (size_t)grp * (size_t)a.Fprev * kLanes + lane;
+    const size_t gk = (size_t)grp * (size_t)a.Fk * kLanes + lane;
+    const float2 *aprevb = a.aprev + gprev;
+    float2 *Gprevb = a.Gprev + gprev;
+    // child gradient source: G_k, or a_n with a per-instance / shared seed
+    const float2 *srcb = (SEED == SEED_G) ? a.Gk + gk
+                         : (SEED == SEED_AMPS_T) ? reinterpret_cast<const float2 *>(a.seed) + gk : a.an + gk;
+    const float *seedb = (SEED == SEED_T) ? reinterpret_cast<const float *>(a.seed) + gk
+                                          : reinterpret_cast<const float *>(a.seed);
+    const uint32_t nwarps = gridDim.x * kBwdTabWarps;
+    for (uint32_t c = blockIdx.x * kBwdTabWarps + warp; c < (uint32_t)a.Fprev; c += nwarps) {
+        const int mine = lane < m ? __ldg(ctab + (size_t)c * m + lane) : 0;
+        const float2 av = (a.k == 1) ? make_float2(1.f, 0.f) : __ldg(aprevb + (c << 5));
         float2 gacc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int h = 0; h < MMAX; h += 8) {
-            float2 g[8];
+        for (int h = 0; h < MMAX; h += kBwdTabBatch) {
+            float2 g[kBwdTabBatch];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < kBwdTabBatch; ++r) {
                 const int j = h + r;
-                const int cidx = __shfl_sync(0xffffffffu, mine, j < 32 ? j : 0);
+                const uint32_t cidx = (uint32_t)__shfl_sync(0xffffffffu, mine, j < 32 ? j : 0);
                 g[r] = make_float2(0.f, 0.f);
-                if (j < m) g[r] = load_child_grad<SEED>(a, gofs_k + (int64_t)cidx * kLanes, cidx);
+                if (j < m) {
+                    g[r] = __ldg(srcb + (cidx << 5));
+                    if (SEED == SEED_T) g[r] = cscale(g[r], __ldg(seedb + (cidx << 5)));
+                    if (SEED == SEED_BCAST) g[r] = cscale(g[r], __ldg(seedb + cidx));
+                }
             }
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
+            for (int r = 0; r < kBwdTabBatch; ++r) {
                 const int j = h + r;
                 if (j < MMAX && j < m) {
                     gacc = cfma_conj_a(us[j][lane], g[r], gacc);
@@ -451,7 +464,7 @@ __global__ void __launch_bounds__(kBwdTabWarps * 32, MINB) slos_bwd_tab_kernel(B
                 }
             }
         }
-        if (a.k > 1) a.Gprev[gofs_prev + c * kLanes] = gacc;
+        if (a.k > 1) Gprevb[c << 5] = gacc;
     }
     float2 *dst = a.dUpart + (((int64_t)grp * gridDim.x + blockIdx.x) * kLanes) * m;
 #pragma unroll
