@@ -362,6 +362,39 @@ def _timed(fn, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
+def uneven_bench(B, dev, stream, max_fock=None, reps=5):
+    """The 1024-instance uneven workload (m in 8..20, n in 2..min(10, m/2),
+    threshold detection for m >= 16) in one persistent launch, autotuned;
+    max_fock keeps only the instances with at most that many output states
+    (small cases for profiling)."""
+    import torch
+    inst, Us = workloads.uneven()
+    if max_fock is not None:
+        keep = [i for i, it in enumerate(inst) if workloads.fock_dim(it.m, it.n) <= max_fock]
+        inst, Us = [inst[i] for i in keep], [Us[i] for i in keep]
+    bp = B.BatchedPlan([it.m for it in inst], [it.n for it in inst], [it.s for it in inst],
+                       [B.THRESHOLD if it.threshold else B.PNR for it in inst])
+    flat = np.concatenate([np.asarray(U_, dtype=np.complex64).reshape(-1) for U_ in Us])
+    Up = torch.tensor(flat, dtype=torch.complex64, device=dev)
+    wsb = torch.empty(bp.workspace_bytes, dtype=torch.uint8, device=dev)
+    outb = torch.empty((bp.out_offsets[-1],), dtype=torch.float32, device=dev)
+    cache = os.path.join(ROOT, "gpurun_out", "autotune_cache.json") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else None
+    t0 = time.perf_counter()
+    bp.autotune(Up, outb, wsb, cache_path=cache)
+    tune_s = time.perf_counter() - t0
+    bp.forward(Up, outb, wsb)
+    bp.sync_status()
+    msb = _timed(lambda: bp.forward(Up, outb, wsb), reps, stream)
+    bp.sync_status()
+    states = sum(workloads.fock_dim(it.m, it.n) for it in inst)
+    wl = (f"{len(inst)} instances, m in 8..20, n in 2..min(10, m/2), threshold for m>=16, one persistent launch"
+          + ("" if max_fock is None else f" (instances with at most {max_fock} output states)"))
+    return {"workload": wl, "value": len(inst) / (msb * 1e-3), "unit": "instances/s", "ms_per_launch": msb,
+            "final_states_per_s": states / (msb * 1e-3), "autotune_s": tune_s,
+            "workspace_gb": bp.workspace_bytes / 1e9}
+
+
 def run_extras(B, dev, peak_hbm, args):
     """Forward throughput of the m=12 n=6 layer, the 1024-instance uneven
     launch, and the learned surrogate against the exact path."""
@@ -396,28 +429,7 @@ def run_extras(B, dev, peak_hbm, args):
     exact12_rate = 4096 / (ms * 1e-3)
     del ws, probs
     # --- uneven: 1024 instances, one persistent launch, autotuned
-    inst, Us = workloads.uneven()
-    bp = B.BatchedPlan([it.m for it in inst], [it.n for it in inst], [it.s for it in inst],
-                       [B.THRESHOLD if it.threshold else B.PNR for it in inst])
-    flat = np.concatenate([np.asarray(U_, dtype=np.complex64).reshape(-1) for U_ in Us])
-    Up = torch.tensor(flat, dtype=torch.complex64, device=dev)
-    wsb = torch.empty(bp.workspace_bytes, dtype=torch.uint8, device=dev)
-    outb = torch.empty((bp.out_offsets[-1],), dtype=torch.float32, device=dev)
-    cache = os.path.join(ROOT, "gpurun_out", "autotune_cache.json") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else None
-    t0 = time.perf_counter()
-    bp.autotune(Up, outb, wsb, cache_path=cache)
-    tune_s = time.perf_counter() - t0
-    bp.forward(Up, outb, wsb)
-    bp.sync_status()
-    msb = _timed(lambda: bp.forward(Up, outb, wsb), 5, stream)
-    bp.sync_status()
-    states = sum(workloads.fock_dim(it.m, it.n) for it in inst)
-    out["uneven_batched"] = {"workload": "1024 instances, m in 8..20, n in 2..min(10, m/2), threshold for m>=16, "
-                                         "one persistent launch",
-                             "value": 1024 / (msb * 1e-3), "unit": "instances/s", "ms_per_launch": msb,
-                             "final_states_per_s": states / (msb * 1e-3), "autotune_s": tune_s}
-    del wsb, outb, Up
+    out["uneven_batched"] = uneven_bench(B, dev, stream)
     # --- surrogate vs exact on the m=12, n=6 layer
     if not args.no_surrogate:
         from paper_2602_11092_gb300 import surrogate as S
@@ -480,7 +492,18 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads (rank 0, 1 GPU only)")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate among the extras")
     ap.add_argument("--surrogate-samples", type=int, default=2_000_000)
+    ap.add_argument("--uneven-only", type=int, default=None, metavar="MAX_STATES",
+                    help="run only the uneven-batch launch, on the instances with at most MAX_STATES "
+                         "output states (small cases for ncu captures)")
     args = ap.parse_args()
+    if args.uneven_only is not None:
+        import torch
+        import paper_2602_11092_gb300 as pkg
+        B = pkg.load()
+        r = uneven_bench(B, torch.device("cuda", 0), torch.cuda.current_stream(), max_fock=args.uneven_only,
+                         reps=args.steps)
+        print(json.dumps(r))
+        return 0
     global BATCH
     BATCH = args.batch
     if args.impl == "reference":
