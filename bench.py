@@ -170,16 +170,46 @@ def oracle_step_sample(seconds_target: float = 12.0):
     return 1.0 / t_dist, cores, sample
 
 
+def cpu_slos_sample(seconds_target: float = 6.0):
+    """The CPU SLOS recursion (oracle/slos_cpu.c: FP64, OpenMP over instances,
+    every layer kept) on the m=16, n=8 training layer: forward + reverse
+    recursion for a batch of unitaries (U given; the mesh, 4 % of the GPU
+    step, is left out).  Tables are built once beforehand, as a plan is on
+    the GPU.  Returns (distributions/s, cores, sample text)."""
+    import oracle
+    from oracle import cpu_slos
+
+    cores = oracle.default_threads()
+    B = 2 * cores
+    w = workloads.train16(batch=B)
+    mb = w["mesh"]
+    U = np.stack([oracle.mesh_unitary(M, mb.theta, mb.data[b]) for b in range(B)])
+    plan = cpu_slos.Plan(M, w["s"])
+    plan.train(U[:1], w["c"], nthreads=cores)
+    reps, t = 0, 0.0
+    while t < seconds_target and reps < 50:
+        t0 = time.perf_counter()
+        plan.train(U, w["c"], nthreads=cores)
+        t += time.perf_counter() - t0
+        reps += 1
+    v = reps * B / t
+    return v, cores, (f"{reps} x {B} instances of the m=16,n=8 layer: SLOS forward + reverse recursion in FP64 "
+                      f"given U ({t:.1f} s), tables built once beforehand; mesh excluded")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    # each step is a bounded sample of one distribution, sized so that the
+    # whole --steps K --warmup W run takes about 150 s of host time
+    per_step = min(8.0, max(0.3, 150.0 / max(1, args.steps + args.warmup)))
     vals = []
     for _ in range(args.warmup):
-        oracle_step_sample(seconds_target=3.0)
+        oracle_step_sample(seconds_target=per_step)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, cores, sample = oracle_step_sample(seconds_target=8.0)
+        v, cores, sample = oracle_step_sample(seconds_target=per_step)
         vals.append(v)
     wall = time.perf_counter() - t0
     value = float(np.median(vals))
@@ -199,6 +229,25 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------------- ranks
+
+def rank_workload(rank: int, batch: int):
+    """Each rank simulates its own batch (weak scaling, no data-path
+    exchange): the training workload with a per-rank seed."""
+    return workloads.train16(batch=batch, seed=workloads.SEED_BASE + 2 + 1000 * rank)
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """Slowest rank's time (the contract's max over ranks)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------- GPU arm
 
 def run_gpu(args):
@@ -216,7 +265,7 @@ def run_gpu(args):
     import paper_2602_11092_gb300 as pkg
     B = pkg.load()
 
-    w = workloads.train16(batch=BATCH, seed=workloads.SEED_BASE + 2 + 1000 * rank)
+    w = rank_workload(rank, BATCH)
     mb = w["mesh"]
     theta = torch.tensor(mb.theta, dtype=torch.float32, device=dev)
     data = torch.tensor(mb.data, dtype=torch.float32, device=dev)
@@ -244,26 +293,31 @@ def run_gpu(args):
     plan.sync_status()
     barrier()
 
+    # headline: K steps, no per-launch tracing, clocks sampled meanwhile
     clocks = ClockSampler(local)
     clocks.start()
     B.profile_reset()
-    B.profile_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
+    c0 = B.launch_count()
     e0.record(stream)
     for _ in range(args.steps):
         step(theta, data, c)
     e1.record(stream)
     barrier()
-    B.profile_enable(False)
-    launches = B.launch_count()
-    prof = B.profile_collect()
+    launches = B.launch_count() - c0
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    # per-kernel durations: the same K steps again with CUDA events around every
+    # launch of the library, recorded on the launching stream
+    B.profile_reset()
+    B.profile_enable(True)
+    barrier()
+    for _ in range(args.steps):
+        step(theta, data, c)
+    barrier()
+    B.profile_enable(False)
+    prof = B.profile_collect()
 
     # end to end through the public API: inputs from pinned host memory, result back
     theta_h = torch.tensor(mb.theta, dtype=torch.float32).pin_memory()
@@ -291,11 +345,7 @@ def run_gpu(args):
             e2e_step()
         e1.record(stream)
         barrier()
-        ms_e2e = e0.elapsed_time(e1) / args.steps
-        t = torch.tensor([ms_e2e], device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     h2d = (theta_h.numel() + data_h.numel() + c_h.numel()) * 4
     d2h = (dth_h.numel() + dd_h.numel()) * 4
 
@@ -308,10 +358,12 @@ def run_gpu(args):
     kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
                    "gbs": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None} for k, v in prof.items()}
 
-    cpu = None
+    cpu = cpu_slos = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = oracle_step_sample(seconds_target=12.0)
         cpu = {"value": v, "unit": "distributions/s", "cores": cores, "kind": "oracle", "sample": sample}
+        v, cores, sample = cpu_slos_sample(seconds_target=6.0)
+        cpu_slos = {"value": v, "unit": "distributions/s", "cores": cores, "kind": "cpu-slos", "sample": sample}
 
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
@@ -340,6 +392,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "cpu_slos_baseline": cpu_slos,
         "extras": extras,
     }
     if rank == 0:
@@ -362,7 +415,43 @@ def _timed(fn, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
-def uneven_bench(B, dev, stream, max_fock=None, reps=5):
+def oracle_forward_rate(m, s, mb, seconds_target=3.0):
+    """FP64 oracle (Ryser over every output, all host cores) for forward
+    distributions of one mesh workload: distributions/s."""
+    import oracle
+    t0 = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t0 < seconds_target or reps == 0:
+        U = oracle.mesh_unitary(m, mb.theta, mb.data[reps % mb.data.shape[0]])
+        oracle.probabilities(U, s)
+        reps += 1
+    dt = time.perf_counter() - t0
+    return {"value": reps / dt, "unit": "distributions/s", "cores": oracle.default_threads(), "kind": "oracle",
+            "sample": f"{reps} distributions, Ryser over every output"}
+
+
+def uneven_oracle_seconds(inst, Us, sample=20000):
+    """FP64 oracle time for the whole uneven batch, extrapolated: per photon
+    number n, the Ryser cost per output measured on `sample` outputs of the
+    first instance with that n, times every instance's number of outputs
+    (threshold instances need all photon-number outputs)."""
+    import oracle
+    rng = np.random.default_rng(11)
+    per_out = {}
+    for i, it in enumerate(inst):
+        if it.n in per_out:
+            continue
+        K = workloads.fock_dim(it.m, it.n)
+        pos = np.sort(rng.choice(K, size=min(K, sample), replace=False))
+        outs = oracle.enumerate_fock(it.m, it.n, pos)
+        U = np.asarray(Us[i], dtype=np.complex128)
+        t0 = time.perf_counter()
+        oracle.probabilities(U, it.s, outs)
+        per_out[it.n] = (time.perf_counter() - t0) / len(pos)
+    return sum(workloads.fock_dim(it.m, it.n) * per_out[it.n] for it in inst)
+
+
+def uneven_bench(B, dev, stream, max_fock=None, reps=5, with_oracle=False):
     """The 1024-instance uneven workload (m in 8..20, n in 2..min(10, m/2),
     threshold detection for m >= 16) in one persistent launch, autotuned;
     max_fock keeps only the instances with at most that many output states
@@ -388,11 +477,18 @@ def uneven_bench(B, dev, stream, max_fock=None, reps=5):
     msb = _timed(lambda: bp.forward(Up, outb, wsb), reps, stream)
     bp.sync_status()
     states = sum(workloads.fock_dim(it.m, it.n) for it in inst)
+    oracle_s = uneven_oracle_seconds(inst, Us) if with_oracle else None
     wl = (f"{len(inst)} instances, m in 8..20, n in 2..min(10, m/2), threshold for m>=16, one persistent launch"
           + ("" if max_fock is None else f" (instances with at most {max_fock} output states)"))
-    return {"workload": wl, "value": len(inst) / (msb * 1e-3), "unit": "instances/s", "ms_per_launch": msb,
-            "final_states_per_s": states / (msb * 1e-3), "autotune_s": tune_s,
-            "workspace_gb": bp.workspace_bytes / 1e9}
+    r = {"workload": wl, "value": len(inst) / (msb * 1e-3), "unit": "instances/s", "ms_per_launch": msb,
+         "final_states_per_s": states / (msb * 1e-3), "autotune_s": tune_s,
+         "workspace_gb": bp.workspace_bytes / 1e9}
+    if oracle_s is not None:
+        import oracle
+        r["oracle"] = {"value": len(inst) / oracle_s, "unit": "instances/s", "cores": oracle.default_threads(),
+                       "kind": "oracle", "sample": "Ryser cost per output measured per photon number on 20000 "
+                       "outputs, extrapolated to every output of every instance"}
+    return r
 
 
 def run_extras(B, dev, peak_hbm, args):
@@ -427,9 +523,30 @@ def run_extras(B, dev, peak_hbm, args):
                               "final_layer_gbs": tby / (tms * 1e-3) / 1e9,
                               "final_layer_frac": tby / (tms * 1e-3) / 1e9 / peak_hbm}
     exact12_rate = 4096 / (ms * 1e-3)
+    if not args.no_cpu_baseline:
+        out["layer12_forward"]["oracle"] = oracle_forward_rate(12, w["s"], mb, seconds_target=3.0)
     del ws, probs
+    # --- m=6, n=3, one instance: latency of one forward
+    t = workloads.tiny()
+    plan0 = B.Plan(6, t["s"])
+    ws0 = plan0.workspace(1, training=False, device=dev)
+    U0 = torch.tensor(np.asarray(t["U"], dtype=np.complex64), device=dev)
+    p0 = torch.empty((1, plan0.n_outputs), dtype=torch.float32, device=dev)
+    for _ in range(10):
+        plan0.forward(U0, workspace=ws0, out=p0)
+    us0 = _timed(lambda: plan0.forward(U0, workspace=ws0, out=p0), 200, stream) * 1e3
+    out["tiny_forward"] = {"workload": "m=6 n=3 |1,1,1,0,0,0>, one Haar U, forward (56 outputs)",
+                           "us_per_forward": us0, "unit": "us"}
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 0.5:
+            oracle.probabilities(np.asarray(t["U"][0], dtype=np.complex128), t["s"], nthreads=1)
+            reps += 1
+        out["tiny_forward"]["oracle_us"] = (time.perf_counter() - t0) / reps * 1e6
     # --- uneven: 1024 instances, one persistent launch, autotuned
-    out["uneven_batched"] = uneven_bench(B, dev, stream)
+    out["uneven_batched"] = uneven_bench(B, dev, stream, with_oracle=not args.no_cpu_baseline)
     # --- surrogate vs exact on the m=12, n=6 layer
     if not args.no_surrogate:
         from paper_2602_11092_gb300 import surrogate as S
@@ -483,8 +600,8 @@ def run_extras(B, dev, peak_hbm, args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="instances per GPU (small cases for ncu captures)")

@@ -38,7 +38,10 @@ _SO = os.path.join(_HERE, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so with gcc (OpenMP)."""
+    """Compile oracle.c into liboracle.so (and the CPU SLOS baseline,
+    slos_cpu.c) with gcc (OpenMP)."""
+    from . import cpu_slos
+    cpu_slos.build(force)
     src = os.path.join(_HERE, "oracle.c")
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
         tmp = _SO + f".tmp{os.getpid()}"
