@@ -491,6 +491,22 @@ def uneven_bench(B, dev, stream, max_fock=None, reps=5, with_oracle=False):
     return r
 
 
+# m=12, n=6 forward: one complex multiply-add per transition of layers 1..n
+# (sum_k m |F_{k-1}| = 74,256), 8 real flops each
+C1_FLOP_PER_DIST = 594_048
+
+
+def fp32_peak_tflops() -> float:
+    """FP32 FMA peak from the unit counts and the measured maximum SM clock:
+    152 SMs x 128 FP32 lanes x 2 flop per FMA."""
+    d = {}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+    mhz = float(d.get("sm_max_mhz", 2070.0))
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
 def run_extras(B, dev, peak_hbm, args):
     """Forward throughput of the m=12 n=6 layer, the 1024-instance uneven
     launch, and the learned surrogate against the exact path."""
@@ -517,11 +533,20 @@ def run_extras(B, dev, peak_hbm, args):
     ms = _timed(fwd12, 20, stream)
     B.profile_enable(False)
     prof = B.profile_collect()
-    nl, tms, tby = prof["slos_fwd_final"]
+    kname = "slos_fwd_fused" if "slos_fwd_fused" in prof else "slos_fwd_final"
+    nl, tms, tby = prof[kname]
+    kms = tms / nl  # one launch = the whole SLOS forward of the 4096 instances
+    flops = 4096 * C1_FLOP_PER_DIST
     out["layer12_forward"] = {"workload": "m=12 n=6, 4096 Clements meshes (132 shared + 12 data phases), forward",
                               "value": 4096 / (ms * 1e-3), "unit": "distributions/s", "ms_per_batch": ms,
-                              "final_layer_gbs": tby / (tms * 1e-3) / 1e9,
-                              "final_layer_frac": tby / (tms * 1e-3) / 1e9 / peak_hbm}
+                              "kernel": kname, "kernel_ms": kms,
+                              "roofline": {"bound": "alu", "achieved": flops / (kms * 1e-3) / 1e12,
+                                           "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
+                                           "frac": flops / (kms * 1e-3) / 1e12 / fp32_peak_tflops(),
+                                           "peak_kind": "derived: SMs x 128 FP32 lanes x 2 flop x max SM clock"},
+                              "compulsory_hbm": {"achieved": tby / (tms * 1e-3) / 1e9, "peak": peak_hbm,
+                                                 "unit": "GB/s", "frac": tby / (tms * 1e-3) / 1e9 / peak_hbm,
+                                                 "bytes": "U in, probabilities out"}}
     exact12_rate = 4096 / (ms * 1e-3)
     if not args.no_cpu_baseline:
         out["layer12_forward"]["oracle"] = oracle_forward_rate(12, w["s"], mb, seconds_target=3.0)
@@ -535,8 +560,19 @@ def run_extras(B, dev, peak_hbm, args):
     for _ in range(10):
         plan0.forward(U0, workspace=ws0, out=p0)
     us0 = _timed(lambda: plan0.forward(U0, workspace=ws0, out=p0), 200, stream) * 1e3
+    # the same forward captured once in a CUDA graph and replayed
+    gs = torch.cuda.Stream()
+    gs.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(gs):
+        plan0.forward(U0, workspace=ws0, out=p0, stream=gs)
+        with torch.cuda.graph(graph, stream=gs):
+            plan0.forward(U0, workspace=ws0, out=p0, stream=gs)
+    stream.wait_stream(gs)
+    graph.replay()
+    usg = _timed(graph.replay, 200, stream) * 1e3
     out["tiny_forward"] = {"workload": "m=6 n=3 |1,1,1,0,0,0>, one Haar U, forward (56 outputs)",
-                           "us_per_forward": us0, "unit": "us"}
+                           "us_per_forward": us0, "us_per_forward_graph_replay": usg, "unit": "us"}
     if not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()

@@ -17,6 +17,7 @@
 #include "plan.h"
 #include "profile.h"
 #include "slos_kernels.cuh"
+#include "fused.h"
 #include "tab_launch.h"
 
 namespace slos {
@@ -97,6 +98,7 @@ static cudaError_t init_device_once(int dev) {
     if ((e = slos_init_m20()) != cudaSuccess) return e;
     if ((e = slos_init_m24()) != cudaSuccess) return e;
     if ((e = slos_tab_init()) != cudaSuccess) return e;
+    if ((e = slos_fused_init()) != cudaSuccess) return e;
     done[dev] = true;
     return cudaSuccess;
 }
@@ -296,6 +298,31 @@ static slos_status_t build_tables(slos_plan_s *p) {
     p->tab.bytes = bytes;
     p->tab.enabled = true;
     return SLOS_OK;
+}
+
+// On-chip inference forward: PNR table plans whose intermediate layers fit in
+// shared memory for at least one instance.  Small plans (up to 24 KB per
+// instance): as many instances per CTA as fit in half the limit, two
+// 512-thread CTAs per SM.  Larger plans: as many instances as fit in the whole
+// limit, one 1024-thread CTA per SM, so each parent-slot row read from L2
+// serves more instances (measured on m=12, n=6 and m=10, n=5).
+static void choose_fused(slos_plan_s *p) {
+    p->fused_ni = 0;
+    if (!p->tab.enabled || p->det != SLOS_DETECT_PNR) return;
+    int64_t cap[2] = {1, 1};
+    for (int k = 1; k < p->n; ++k) cap[k & 1] = std::max(cap[k & 1], p->F[k]);
+    if (cap[0] + cap[1] > ((int64_t)1 << 24)) return;
+    const int c2[2] = {(int)cap[0], (int)cap[1]};
+    const bool large = slos_fused_smem(1, p->n, c2) > 24 * 1024;
+    const size_t limit = large ? kFusedSmemLimit : kFusedSmemLimit / 2;
+    int ni = 0;
+    for (int q = 1; q <= slos_fused_max_ni(); q *= 2)
+        if (slos_fused_smem(q, p->n, c2) <= limit) ni = q;
+    if (ni == 0) return;
+    p->fused_ni = ni;
+    p->fused_threads = large ? 1024 : 512;
+    p->fused_cap[0] = c2[0];
+    p->fused_cap[1] = c2[1];
 }
 
 // ------------------------------------------------------------------ layouts
@@ -636,6 +663,7 @@ slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t d
         delete p;
         return tst;
     }
+    choose_fused(p);
     *out = p;
     return SLOS_OK;
 }
@@ -717,6 +745,33 @@ slos_status_t slos_forward(slos_plan_t p, const void *U, int batch, slos_output_
     char *ws = reinterpret_cast<char *>(workspace);
     const float2 *Ud = reinterpret_cast<const float2 *>(U);
     const int n = p->n;
+    if (!save && p->fused_ni > 0) {
+        // whole plan on chip: only U in and the outputs out
+        FusedArgs fa;
+        memset(&fa, 0, sizeof(fa));
+        fa.U = Ud;
+        fa.out = out;
+        fa.w = p->tab.w;
+        for (int k = 1; k <= n; ++k) {
+            fa.slots[k] = p->tab.layer[k].slots;
+            fa.kw[k] = p->tab.layer[k].kw;
+            fa.F[k] = (int)p->F[k];
+            fa.cols[k - 1] = p->cols[k - 1];
+        }
+        fa.F[0] = 1;
+        fa.cap[0] = p->fused_cap[0];
+        fa.cap[1] = p->fused_cap[1];
+        fa.m = p->m;
+        fa.n = n;
+        fa.B = batch;
+        fa.K = (int)p->K;
+        fa.NI = p->fused_ni;
+        fa.threads = p->fused_threads;
+        const double bytes = (double)batch * (8.0 * p->m * p->m + (output == SLOS_OUT_AMPS ? 8.0 : 4.0) * p->K);
+        ProfScope ps("slos_fwd_fused", bytes, s);
+        SLOS_CUDA(slos_launch_fused(fa, output == SLOS_OUT_AMPS ? EPI_AMPS : EPI_PROBS, s));
+        return SLOS_OK;
+    }
     if (p->det == SLOS_DETECT_THRESHOLD) SLOS_CUDA(cudaMemsetAsync(out, 0, (size_t)batch * p->K * sizeof(float), s));
     for (int k = 1; k < n; ++k) {
         slos_status_t st = launch_layer_fwd(p, Ly, ws, Ud, batch, k, EPI_STORE, true, nullptr, s);

@@ -63,5 +63,8 @@ struct slos_plan_s {
     int sm_count;
     int *d_status;          // device status word (owned)
     slos::PlanTables tab;   // transition graph (owned; empty when too large)
+    int fused_ni = 0;       // instances per CTA of the on-chip inference forward (0: not eligible)
+    int fused_threads = 512;    // its CTA size
+    int fused_cap[2] = {1, 1};  // its buffer capacities (states per instance, even / odd layers)
     slos::BatchedPlan *batched;
 };

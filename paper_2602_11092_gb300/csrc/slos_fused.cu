@@ -1,0 +1,141 @@
+// Whole-plan forward on chip (inference): one CTA runs every photon-number
+// layer of NI instances in shared memory (Sec. II-A.2/II-A.3), so only U is
+// read and only the output is written to HBM.
+//
+// Used for PNR table plans without activation saving whose two largest
+// intermediate layers fit in shared memory for at least one instance (for
+// example m=12, n=6: 4368 + 1365 states, 46 KB per instance).  Layer k of
+// instance i lives in buffer (k & 1) as complex64 [NI][cap]; the CTA's
+// threads walk the states of a layer (lane = state), read each state's
+// fixed-width parent slots once and form the sums of all NI instances from
+// shared memory.  The U columns of all n photons are staged once, with a zero
+// row (mode kMaxModes) that the padding slots name.  Output writes are
+// coalesced: consecutive threads write consecutive states of one instance.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "fused.h"
+#include "slos_kernels.cuh"
+
+namespace slos {
+
+constexpr int kFusedMaxNI = 4;
+constexpr int kUsRow = kMaxModes + 1;
+
+template <int EPI, int KW, int THREADS>
+__device__ __forceinline__ void fused_layer(const FusedArgs &a, int k, const float2 *us, const float2 *prev,
+                                            int cap_prev, float2 *cur, int cap_cur, int inst0, int ni) {
+    const int Fk = a.F[k];
+    const uint4 *sl = reinterpret_cast<const uint4 *>(a.slots[k]);
+    const bool first = k == 1, final_layer = k == a.n;
+    const size_t us_inst = (size_t)a.n * kUsRow;  // U rows of one instance
+    const float2 *uk = us + (size_t)(k - 1) * kUsRow;
+    for (int c = threadIdx.x; c < Fk; c += THREADS) {
+        uint32_t e[KW];
+#pragma unroll
+        for (int q4 = 0; q4 < KW / 4; ++q4) {
+            const uint4 w4 = __ldg(sl + (size_t)c * (KW / 4) + q4);
+            e[4 * q4] = w4.x;
+            e[4 * q4 + 1] = w4.y;
+            e[4 * q4 + 2] = w4.z;
+            e[4 * q4 + 3] = w4.w;
+        }
+        float wc = 0.f;
+        if (final_layer) wc = __ldg(a.w + c);
+#pragma unroll
+        for (int i = 0; i < kFusedMaxNI; ++i) {
+            if (i < ni) {
+                const float2 *u = uk + i * us_inst;
+                float2 acc;
+                if (first) {
+                    acc = u[e[0] & 31u];  // one photon: a_1(e_j) = U[j, c_1]
+                } else {
+                    const float2 *pv = prev + (size_t)i * cap_prev;
+                    acc = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int q = 0; q < KW; ++q) acc = cfma(u[e[q] & 31u], pv[e[q] >> 5], acc);
+                }
+                if (!final_layer) {
+                    cur[(size_t)i * cap_cur + c] = acc;
+                } else if (EPI == EPI_PROBS) {
+                    reinterpret_cast<float *>(a.out)[(size_t)(inst0 + i) * a.K + c] =
+                        wc * (acc.x * acc.x + acc.y * acc.y);
+                } else {
+                    reinterpret_cast<float2 *>(a.out)[(size_t)(inst0 + i) * a.K + c] = cscale(acc, sqrtf(wc));
+                }
+            }
+        }
+    }
+}
+
+template <int EPI, int THREADS>
+__global__ void __launch_bounds__(THREADS) slos_fwd_fused_kernel(FusedArgs a) {
+    extern __shared__ float2 sm[];
+    const int NI = a.NI;
+    float2 *us = sm;                                  // [NI][n][kUsRow]
+    float2 *buf0 = us + (size_t)NI * a.n * kUsRow;    // [NI][cap0]
+    float2 *buf1 = buf0 + (size_t)NI * a.cap[0];      // [NI][cap1]
+    const int inst0 = blockIdx.x * NI;
+    const int ni = min(NI, a.B - inst0);
+    const int nus = NI * a.n * kUsRow;
+    for (int idx = threadIdx.x; idx < nus; idx += THREADS) {
+        const int j = idx % kUsRow;
+        const int r = idx / kUsRow;
+        const int k = r % a.n, i = r / a.n;
+        float2 v = make_float2(0.f, 0.f);
+        if (i < ni && j < a.m) v = a.U[((size_t)(inst0 + i) * a.m + j) * a.m + a.cols[k]];
+        us[idx] = v;
+    }
+    __syncthreads();
+    for (int k = 1; k <= a.n; ++k) {
+        const float2 *prev = ((k - 1) & 1) ? buf1 : buf0;
+        float2 *cur = (k & 1) ? buf1 : buf0;
+        const int cap_prev = a.cap[(k - 1) & 1], cap_cur = a.cap[k & 1];
+        switch (a.kw[k]) {
+            case 4: fused_layer<EPI, 4, THREADS>(a, k, us, prev, cap_prev, cur, cap_cur, inst0, ni); break;
+            case 8: fused_layer<EPI, 8, THREADS>(a, k, us, prev, cap_prev, cur, cap_cur, inst0, ni); break;
+            default: fused_layer<EPI, 12, THREADS>(a, k, us, prev, cap_prev, cur, cap_cur, inst0, ni); break;
+        }
+        __syncthreads();
+    }
+}
+
+size_t slos_fused_smem(int NI, int n, const int cap[2]) {
+    return sizeof(float2) * ((size_t)NI * n * kUsRow + (size_t)NI * (cap[0] + cap[1]));
+}
+
+int slos_fused_max_ni() { return kFusedMaxNI; }
+
+template <int THREADS>
+static cudaError_t fused_attrs() {
+    cudaError_t e = cudaFuncSetAttribute(slos_fwd_fused_kernel<EPI_PROBS, THREADS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemLimit);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(slos_fwd_fused_kernel<EPI_AMPS, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kFusedSmemLimit);
+}
+
+cudaError_t slos_fused_init() {
+    cudaError_t e = fused_attrs<512>();
+    if (e != cudaSuccess) return e;
+    return fused_attrs<1024>();
+}
+
+template <int THREADS>
+static cudaError_t launch_fused(const FusedArgs &a, int epi, cudaStream_t s) {
+    const unsigned grid = (unsigned)((a.B + a.NI - 1) / a.NI);
+    const size_t sm = slos_fused_smem(a.NI, a.n, a.cap);
+    if (epi == EPI_PROBS) slos_fwd_fused_kernel<EPI_PROBS, THREADS><<<grid, THREADS, sm, s>>>(a);
+    else if (epi == EPI_AMPS) slos_fwd_fused_kernel<EPI_AMPS, THREADS><<<grid, THREADS, sm, s>>>(a);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t slos_launch_fused(const FusedArgs &a, int epi, cudaStream_t s) {
+    if (a.threads == 1024) return launch_fused<1024>(a, epi, s);
+    if (a.threads == 512) return launch_fused<512>(a, epi, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace slos

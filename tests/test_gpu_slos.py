@@ -220,6 +220,26 @@ def test_threshold_matches_oracle(slos, m, n, B):
         check_dist(q[b], ref)
 
 
+@pytest.mark.parametrize("m,s,B", [(6, [1, 1, 1, 0, 0, 0], 1), (12, [1, 0] * 6, 37), (9, [2, 0, 1, 0, 3, 0, 0, 0, 0], 5),
+                                   (4, [0, 2, 0, 0], 3), (12, [1, 0] * 5 + [1, 1], 9), (10, [1, 0] * 5, 70)])
+def test_on_chip_forward_matches_layered_forward(slos, m, s, B):
+    """Inference forwards of small plans run every layer in shared memory;
+    the layered path (taken when activations are kept) computes the same
+    sums in the same order."""
+    rng = np.random.default_rng(m * 7 + B)
+    U = c64(workloads.haar_unitaries(m, B, rng))
+    plan = slos.Plan(m, s)
+    for out_kind in (slos.PROBS, slos.AMPS):
+        fused = plan.forward(U, out_kind)
+        layered = plan.forward(U, out_kind, save_for_backward=True, workspace=plan.workspace(B, training=True))
+        assert torch.allclose(fused, layered, atol=1e-7, rtol=0)
+    Uh = up(U)
+    outs = oracle.enumerate_fock(m, sum(s))
+    p = plan.forward(U).cpu().numpy()
+    for b in range(0, B, max(1, B // 3)):
+        assert np.abs(p[b] - oracle.probabilities(Uh[b], s, outs)).max() <= P_TOL
+
+
 def test_empty_batch_is_noop(slos):
     plan = slos.Plan(4, [1, 1, 0, 0])
     U = torch.empty((0, 4, 4), dtype=torch.complex64, device=dev())
@@ -327,6 +347,49 @@ def test_checkpointing_is_bitwise_equal_to_full_store(slos):
         ws = mid.workspace(B, training=True)
         mid.forward(U, save_for_backward=True, workspace=ws)
         assert torch.equal(mid.backward(U, c, ws), res[0][1])
+
+
+def test_training_step_graph_capture_replays_bitwise(slos):
+    """mesh -> forward (activations kept, checkpoint stride 2) -> backward ->
+    mesh backward, captured once in a CUDA graph: nothing in the calls
+    synchronises, and every replay equals the eager step."""
+    m, s, B = 10, [1, 0] * 5, 40
+    rng = np.random.default_rng(12)
+    mb = workloads.mesh_batch(m, B, 77)
+    theta = torch.tensor(mb.theta, dtype=torch.float32, device=dev())
+    data = torch.tensor(mb.data, dtype=torch.float32, device=dev())
+    plan = slos.Plan(m, s, mem_budget_bytes=7950)
+    assert plan.checkpoint_stride == 2
+    c = torch.tensor(rng.standard_normal(plan.n_outputs), dtype=torch.float32, device=dev())
+    ws = plan.workspace(B, training=True)
+    U = torch.empty((B, m, m), dtype=torch.complex64, device=dev())
+    dU = torch.empty_like(U)
+    probs = torch.empty((B, plan.n_outputs), dtype=torch.float32, device=dev())
+
+    def step(st=None):
+        slos.mesh_unitary(m, theta, data, B, out=U, stream=st)
+        plan.forward(U, save_for_backward=True, workspace=ws, out=probs, stream=st)
+        plan.backward(U, c, ws, dU=dU, stream=st)
+        return slos.mesh_unitary_backward(m, theta, data, B, dU, stream=st)
+
+    dth, dd = step()
+    ref = (probs.clone(), dU.clone(), dth.clone(), dd.clone())
+    gs = torch.cuda.Stream()
+    gs.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(gs):
+        step(gs)
+        with torch.cuda.graph(g, stream=gs):
+            outs = step(gs)
+    torch.cuda.current_stream().wait_stream(gs)
+    for _ in range(3):
+        probs.fill_(float("nan"))
+        dU.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(probs, ref[0]) and torch.equal(dU, ref[1])
+        assert torch.equal(outs[0], ref[2]) and torch.equal(outs[1], ref[3])
+    plan.sync_status()
 
 
 def test_autograd_phase_gradient_against_fd_and_minors(slos):

@@ -28,6 +28,7 @@ def _case(slos, m, s, B, seed, detection):
     (6, [1, 1, 1, 0, 0, 0], 1, 0),
     (12, [1, 0] * 6, 40, 0),
     (8, [1, 0] * 4, 33, 1),
+    (14, [1, 0] * 7, 32, 0),  # too large for the on-chip forward: layers go through the scratch
 ])
 def test_noalloc_forward_matches_workspace_forward_twice(slos, m, s, B, detection):
     plan, U = _case(slos, m, s, B, 7 + m, detection)
