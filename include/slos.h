@@ -60,6 +60,17 @@ typedef enum {
 
 typedef enum { SLOS_DETECT_PNR = 0, SLOS_DETECT_THRESHOLD = 1 } slos_detection_t;
 typedef enum { SLOS_OUT_PROBS = 0, SLOS_OUT_AMPS = 1 } slos_output_t;
+/* Computation space (Sec. II-A.3, QuantumLayer): the Hilbert subspace the
+ * state is represented on.  FOCK: every composition of n photons over m
+ * modes.  UNBUNCHED: only collision-free states (at most one photon per
+ * mode), C(m, n) of them; the recursion then runs over collision-free
+ * intermediate states only, which gives the exact amplitudes of the
+ * collision-free outputs (every path to such an output passes only through
+ * collision-free states).  Unbunched outputs are ordered like the Fock
+ * outputs restricted to them: descending lexicographic order of the
+ * occupation vectors, i.e. ascending lexicographic order of the occupied-mode
+ * tuples. */
+typedef enum { SLOS_SPACE_FOCK = 0, SLOS_SPACE_UNBUNCHED = 1 } slos_space_t;
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char *slos_last_error(void);
@@ -128,8 +139,16 @@ slos_status_t mesh_unitary_backward(const slos_mesh_desc_t *desc, const float *t
 slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t detection,
                         size_t mem_budget_bytes, slos_plan_t *out);
 
+/* slos_plan on a chosen computation space.  SLOS_SPACE_UNBUNCHED needs PNR
+ * detection and n <= m, and a plan small enough for transition tables
+ * (otherwise SLOS_ERR_UNSUPPORTED); the input state may itself be bunched.
+ * slos_plan(...) is slos_plan_space(..., SLOS_SPACE_FOCK, ...). */
+slos_status_t slos_plan_space(int m, int n, const int *input_state, slos_detection_t detection, slos_space_t space,
+                              size_t mem_budget_bytes, slos_plan_t *out);
+
 /* n_outputs: values per instance written by slos_forward (PNR: C(m+n-1, n);
- * threshold: sum_{k=1}^{min(n,m)} C(m, k)).  fock_dim: C(m+n-1, n).
+ * unbunched: C(m, n); threshold: sum_{k=1}^{min(n,m)} C(m, k)).  fock_dim:
+ * number of states of the plan's space, C(m+n-1, n) or C(m, n).
  * checkpoint_stride: the s chosen from the budget (1 = every layer kept). */
 slos_status_t slos_plan_query(slos_plan_t plan, int64_t *n_outputs, int64_t *fock_dim, int *checkpoint_stride);
 
@@ -155,6 +174,35 @@ slos_status_t slos_forward(slos_plan_t plan, const void *U, int batch, slos_outp
  * (columns of modes without input photons are zero). */
 slos_status_t slos_backward(slos_plan_t plan, const void *U, int batch, slos_output_t output, const void *dout,
                             int64_t dout_stride_b, void *dU, void *workspace, size_t workspace_bytes, void *stream);
+
+/* ----------------------------------------------------------------------
+ * Measurement strategies on top of the output distribution (Sec. II-A.3,
+ * QuantumLayer: full distribution, per-mode photon-number expectations) and
+ * renormalisation onto the plan's space.  They read and write caller buffers
+ * only; each has its backward.  Plans built without transition tables (the
+ * largest Fock spaces) return SLOS_ERR_UNSUPPORTED for the expectations.
+ * ---------------------------------------------------------------------- */
+
+/* out[b][j] = sum_t occ_j(t) probs[b][t] over the plan's n_outputs values:
+ * PNR outputs: occ_j(t) = t_j, the mean photon number in mode j; threshold
+ * outcomes: occ_j(b) = [j in b], the click probability of detector j.
+ * probs: float32 [batch][n_outputs]; out: float32 [batch][m].  Each value is
+ * one fixed-order sum (reproducible run to run). */
+slos_status_t slos_expectations(slos_plan_t plan, const float *probs, int batch, float *out, void *stream);
+
+/* dprobs[b][t] = sum_j occ_j(t) dout[b][j]; dout float32 [batch][m],
+ * dprobs float32 [batch][n_outputs] (overwritten). */
+slos_status_t slos_expectations_backward(slos_plan_t plan, const float *dout, int batch, float *dprobs,
+                                         void *stream);
+
+/* Z[b] = sum_t p[b][t], q[b][t] = p[b][t] / Z[b] (the distribution
+ * conditioned on the plan's space, e.g. on collision-free outcomes).  p, q:
+ * float32 [batch][n_outputs] (q may be p); Z: float32 [batch]. */
+slos_status_t slos_renormalise(slos_plan_t plan, const float *p, int batch, float *q, float *Z, void *stream);
+
+/* dp[b][t] = (dq[b][t] - sum_s dq[b][s] q[b][s]) / Z[b]; dp may be dq. */
+slos_status_t slos_renormalise_backward(slos_plan_t plan, const float *q, const float *Z, const float *dq, int batch,
+                                        float *dp, void *stream);
 
 /* Reads the plan's device status word (waits for `stream`), clears it, and
  * returns SLOS_ERR_TIMEOUT / SLOS_ERR_INTERNAL if a kernel reported one. */

@@ -220,6 +220,50 @@ def threshold_prob_of_pattern(U: np.ndarray, s, pattern, nthreads=None) -> float
 
 
 # --------------------------------------------------------------------------
+# Computation spaces and measurement strategies (Sec. II-A.3, QuantumLayer:
+# the Hilbert subspace the state is represented on; full distribution or
+# per-mode photon-number expectations).
+# --------------------------------------------------------------------------
+
+def enumerate_unbunched(m: int, n: int) -> np.ndarray:
+    """Collision-free outputs (every t_j <= 1), one row per output, in the
+    library's order: the Fock order (descending lexicographic over occupation
+    vectors) restricted to them, which lists the occupied-mode tuples in
+    ascending lexicographic order."""
+    rows = []
+    for S in itertools.combinations(range(m), n):
+        t = np.zeros(m, dtype=np.int32)
+        t[list(S)] = 1
+        rows.append(t)
+    return np.array(rows, dtype=np.int32).reshape(-1, m)
+
+
+def mode_expectations(p: np.ndarray, outputs: np.ndarray) -> np.ndarray:
+    """<n_j> = sum_t t_j p(t) over the listed outputs (plain sums, FP64)."""
+    p = np.asarray(p, dtype=np.float64)
+    outputs = np.asarray(outputs)
+    e = np.zeros(outputs.shape[1], dtype=np.float64)
+    for prob, t in zip(p, outputs):
+        e += prob * t
+    return e
+
+
+def click_probabilities(q: np.ndarray, m: int, n: int) -> np.ndarray:
+    """P(detector j clicks) = sum of q(b) over threshold outcomes b with j in b."""
+    e = np.zeros(m, dtype=np.float64)
+    for prob, b in zip(q, threshold_patterns(m, n)):
+        for j in b:
+            e[j] += prob
+    return e
+
+
+def renormalise(p: np.ndarray) -> np.ndarray:
+    """The distribution conditioned on the listed outputs: p / sum p."""
+    p = np.asarray(p, dtype=np.float64)
+    return p / p.sum()
+
+
+# --------------------------------------------------------------------------
 # Interferometer mesh (Sec. II-A.3: trainable parameters are the phases of the
 # physical components; Sec. II-C.1: U(x, theta) = W2(theta2) S(x) W1(theta1)).
 # MZI on modes (k, k+1): T = B diag(e^{i theta}, 1) B diag(e^{i phi}, 1) with

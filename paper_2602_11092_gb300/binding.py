@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libslos.so")
 
 PNR, THRESHOLD = 0, 1
 PROBS, AMPS = 0, 1
+FOCK, UNBUNCHED = 0, 1  # computation spaces (slos_space_t)
 
 _status_names = {0: "SLOS_OK", 1: "SLOS_ERR_INVALID_ARG", 2: "SLOS_ERR_UNSUPPORTED", 3: "SLOS_ERR_OOM",
                  4: "SLOS_ERR_CUDA", 5: "SLOS_ERR_TIMEOUT", 6: "SLOS_ERR_INTERNAL"}
@@ -47,7 +48,12 @@ _SIGNATURES = {
     "mesh_unitary_backward": ([ctypes.POINTER(MeshDesc), _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp, _vp, _sz, _vp],
                               _int),
     "slos_plan": ([_int, _int, ctypes.POINTER(_int), _int, _sz, ctypes.POINTER(_vp)], _int),
+    "slos_plan_space": ([_int, _int, ctypes.POINTER(_int), _int, _int, _sz, ctypes.POINTER(_vp)], _int),
     "slos_plan_query": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_int)], _int),
+    "slos_expectations": ([_vp, _vp, _int, _vp, _vp], _int),
+    "slos_expectations_backward": ([_vp, _vp, _int, _vp, _vp], _int),
+    "slos_renormalise": ([_vp, _vp, _int, _vp, _vp, _vp], _int),
+    "slos_renormalise_backward": ([_vp, _vp, _vp, _vp, _int, _vp, _vp], _int),
     "slos_workspace_bytes": ([_vp, _int, _int, ctypes.POINTER(_sz)], _int),
     "slos_forward": ([_vp, _vp, _int, _int, _vp, _int, _vp, _sz, _vp], _int),
     "slos_backward": ([_vp, _vp, _int, _int, _vp, _i64, _vp, _vp, _sz, _vp], _int),
@@ -163,16 +169,17 @@ def mesh_unitary_backward(m: int, theta, data, batch: int, dU: torch.Tensor, dat
 # ------------------------------------------------------------------ plans
 
 class Plan:
-    """Owns a slos_plan_t for one (m, n, input state, detection)."""
+    """Owns a slos_plan_t for one (m, n, input state, detection, computation
+    space)."""
 
-    def __init__(self, m: int, input_state, detection: int = PNR, mem_budget_bytes: int = 0):
+    def __init__(self, m: int, input_state, detection: int = PNR, mem_budget_bytes: int = 0, space: int = FOCK):
         lib = load()
         s = [int(x) for x in input_state]
         assert len(s) == m
-        self.m, self.n, self.input_state, self.detection = m, sum(s), s, detection
+        self.m, self.n, self.input_state, self.detection, self.space = m, sum(s), s, detection, space
         arr = (ctypes.c_int * m)(*s)
         h = ctypes.c_void_p()
-        _check(lib.slos_plan(m, self.n, arr, detection, mem_budget_bytes, ctypes.byref(h)))
+        _check(lib.slos_plan_space(m, self.n, arr, detection, space, mem_budget_bytes, ctypes.byref(h)))
         self._h = h
         K, F, st = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
         _check(lib.slos_plan_query(h, ctypes.byref(K), ctypes.byref(F), ctypes.byref(st)))
@@ -202,6 +209,43 @@ class Plan:
         _check(load().slos_forward(self._h, _ptr(U), B, output, _ptr(out), 1 if save_for_backward else 0,
                                    _ptr(workspace), workspace.numel(), _stream(stream)))
         return out
+
+    def expectations(self, probs: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Per-mode photon-number expectations (PNR) or click probabilities
+        (threshold) of an output distribution [B, n_outputs] -> [B, m]."""
+        _need(probs, torch.float32, "probs")
+        B = probs.shape[0]
+        if out is None:
+            out = torch.empty((B, self.m), dtype=torch.float32, device=probs.device)
+        _check(load().slos_expectations(self._h, _ptr(probs), B, _ptr(out), _stream(stream)))
+        return out
+
+    def expectations_backward(self, dout: torch.Tensor, dprobs: torch.Tensor | None = None, stream=None):
+        _need(dout, torch.float32, "dout")
+        B = dout.shape[0]
+        if dprobs is None:
+            dprobs = torch.empty((B, self.n_outputs), dtype=torch.float32, device=dout.device)
+        _check(load().slos_expectations_backward(self._h, _ptr(dout), B, _ptr(dprobs), _stream(stream)))
+        return dprobs
+
+    def renormalise(self, p: torch.Tensor, q: torch.Tensor | None = None, Z: torch.Tensor | None = None,
+                    stream=None):
+        """q = p / sum_t p (per instance) and the sums Z."""
+        _need(p, torch.float32, "p")
+        B = p.shape[0]
+        q = torch.empty_like(p) if q is None else q
+        Z = torch.empty(B, dtype=torch.float32, device=p.device) if Z is None else Z
+        _check(load().slos_renormalise(self._h, _ptr(p), B, _ptr(q), _ptr(Z), _stream(stream)))
+        return q, Z
+
+    def renormalise_backward(self, q: torch.Tensor, Z: torch.Tensor, dq: torch.Tensor,
+                             dp: torch.Tensor | None = None, stream=None):
+        for t, nm in ((q, "q"), (Z, "Z"), (dq, "dq")):
+            _need(t, torch.float32, nm)
+        dp = torch.empty_like(dq) if dp is None else dp
+        _check(load().slos_renormalise_backward(self._h, _ptr(q), _ptr(Z), _ptr(dq), q.shape[0], _ptr(dp),
+                                                _stream(stream)))
+        return dp
 
     def forward_noalloc(self, U: torch.Tensor, out: torch.Tensor, output: int = PROBS, stream=None):
         """slos_forward_noalloc: the library's built-in scratch, no workspace."""

@@ -77,13 +77,13 @@ cudaError_t launch_prep(int m, const PrepArgs &a, int bx, bool bcast, cudaStream
         default: return slos_launch_prep_m24(a, bx, bcast, s);
     }
 }
-cudaError_t launch_bwd_tab(int m, const BwdArgs &a, const int32_t *ctab, int seed, int bx, cudaStream_t s) {
+cudaError_t launch_bwd_tab(int m, const BwdArgs &a, const int32_t *ctab, int seed, int bx, bool holes, cudaStream_t s) {
     switch (mmax_for(m)) {
-        case 8: return slos_launch_bwd_tab_m8(a, ctab, seed, bx, s);
-        case 12: return slos_launch_bwd_tab_m12(a, ctab, seed, bx, s);
-        case 16: return slos_launch_bwd_tab_m16(a, ctab, seed, bx, s);
-        case 20: return slos_launch_bwd_tab_m20(a, ctab, seed, bx, s);
-        default: return slos_launch_bwd_tab_m24(a, ctab, seed, bx, s);
+        case 8: return slos_launch_bwd_tab_m8(a, ctab, seed, bx, holes, s);
+        case 12: return slos_launch_bwd_tab_m12(a, ctab, seed, bx, holes, s);
+        case 16: return slos_launch_bwd_tab_m16(a, ctab, seed, bx, holes, s);
+        case 20: return slos_launch_bwd_tab_m20(a, ctab, seed, bx, holes, s);
+        default: return slos_launch_bwd_tab_m24(a, ctab, seed, bx, holes, s);
     }
 }
 
@@ -172,8 +172,10 @@ static void free_tables(slos_plan_s *p) {
     }
     if (p->tab.w) cudaFree(p->tab.w);
     if (p->tab.pat) cudaFree(p->tab.pat);
+    if (p->tab.occ) cudaFree(p->tab.occ);
     p->tab.w = nullptr;
     p->tab.pat = nullptr;
+    p->tab.occ = nullptr;
     p->tab.enabled = false;
 }
 
@@ -220,7 +222,117 @@ static void build_layer_host(int m, int k, std::vector<int32_t> &rowptr, std::ve
     }
 }
 
+// Collision-free lattice (slos_space_t UNBUNCHED): the states of k photons
+// are the k-subsets S of the modes, listed in descending lexicographic order
+// of their occupation vectors (= ascending lexicographic order of the sorted
+// subsets); position of t = sum over empty modes i with r_i > 0 occupied modes
+// at or after i of C(m - i - 1, r_i - 1).  Every parent S \ {j} is in the
+// lattice; a child S + {j} is not when j is in S (child table entry -1).
+static int64_t unbunched_rank(const std::vector<int> &t, int m) {
+    int64_t r = 0;
+    int after = 0;
+    std::vector<int> ones_after(m + 1, 0);
+    for (int i = m - 1; i >= 0; --i) ones_after[i] = ones_after[i + 1] + t[i];
+    for (int i = 0; i < m; ++i) {
+        after = ones_after[i];
+        if (t[i] == 0 && after >= 1) r += binom_host(m - i - 1, after - 1);
+    }
+    return r;
+}
+
+// next k-subset in ascending lexicographic order; false after the last
+static bool next_subset(std::vector<int> &S, int m) {
+    const int k = (int)S.size();
+    int i = k - 1;
+    while (i >= 0 && S[i] == m - k + i) --i;
+    if (i < 0) return false;
+    ++S[i];
+    for (int q = i + 1; q < k; ++q) S[q] = S[q - 1] + 1;
+    return true;
+}
+
+static slos_status_t build_tables_unbunched(slos_plan_s *p) {
+    const int m = p->m, n = p->n;
+    size_t bytes = 0;
+    for (int k = 1; k <= n; ++k) bytes += 4 * (size_t)p->F[k] * slot_width(m, k) + 4 * (size_t)m * p->F[k - 1];
+    bytes += 4 * (size_t)p->F[n] + (size_t)p->K * m;
+    if (bytes > kTableBudgetBytes || p->F[n] >= ((int64_t)1 << 26))
+        return fail(SLOS_ERR_UNSUPPORTED, "slos_plan_space: collision-free space too large for transition tables");
+    p->tab.layer.assign(n + 1, LayerTables());
+    std::vector<int> t(m);
+    for (int k = 1; k <= n; ++k) {
+        const int kw = slot_width(m, k);
+        std::vector<uint32_t> slots((size_t)p->F[k] * kw, kSlotEmpty);
+        std::vector<int32_t> ctab((size_t)p->F[k - 1] * m, -1);
+        // parents' child rows: every (k-1)-subset in order, every mode
+        {
+            std::vector<int> S(k - 1);
+            for (int q = 0; q < k - 1; ++q) S[q] = q;
+            int64_t c = 0;
+            do {
+                std::fill(t.begin(), t.end(), 0);
+                for (int q : S) t[q] = 1;
+                for (int j = 0; j < m; ++j) {
+                    if (t[j]) continue;
+                    t[j] = 1;
+                    ctab[(size_t)c * m + j] = (int32_t)unbunched_rank(t, m);
+                    t[j] = 0;
+                }
+                ++c;
+            } while (k - 1 > 0 && next_subset(S, m));
+        }
+        // states' parent slots
+        {
+            std::vector<int> S(k);
+            for (int q = 0; q < k; ++q) S[q] = q;
+            int64_t c = 0;
+            do {
+                std::fill(t.begin(), t.end(), 0);
+                for (int q : S) t[q] = 1;
+                int q = 0;
+                for (int j : S) {
+                    t[j] = 0;
+                    slots[(size_t)c * kw + q++] = ((uint32_t)unbunched_rank(t, m) << 5) | (uint32_t)j;
+                    t[j] = 1;
+                }
+                ++c;
+            } while (next_subset(S, m));
+        }
+        LayerTables &LT = p->tab.layer[k];
+        LT.kw = kw;
+        if (cudaMalloc(&LT.slots, slots.size() * 4) != cudaSuccess ||
+            cudaMalloc(&LT.ctab, ctab.size() * 4) != cudaSuccess) {
+            free_tables(p);
+            return fail(SLOS_ERR_OOM, "slos_plan_space: cannot allocate the transition tables");
+        }
+        cudaMemcpy(LT.slots, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(LT.ctab, ctab.data(), ctab.size() * 4, cudaMemcpyHostToDevice);
+    }
+    // final layer: prod t! = 1, so every weight is 1 / prod s!
+    std::vector<float> w(p->F[n], p->inv_sfact);
+    std::vector<uint8_t> occ((size_t)p->K * m, 0);
+    {
+        std::vector<int> S(n);
+        for (int q = 0; q < n; ++q) S[q] = q;
+        int64_t c = 0;
+        do {
+            for (int q : S) occ[(size_t)c * m + q] = 1;
+            ++c;
+        } while (next_subset(S, m));
+    }
+    if (cudaMalloc(&p->tab.w, w.size() * 4) != cudaSuccess || cudaMalloc(&p->tab.occ, occ.size()) != cudaSuccess) {
+        free_tables(p);
+        return fail(SLOS_ERR_OOM, "slos_plan_space: cannot allocate the weight tables");
+    }
+    cudaMemcpy(p->tab.w, w.data(), w.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->tab.occ, occ.data(), occ.size(), cudaMemcpyHostToDevice);
+    p->tab.bytes = bytes;
+    p->tab.enabled = true;
+    return SLOS_OK;
+}
+
 static slos_status_t build_tables(slos_plan_s *p) {
+    if (p->space == SLOS_SPACE_UNBUNCHED) return build_tables_unbunched(p);
     const int m = p->m, n = p->n;
     size_t bytes = 0;
     for (int k = 1; k <= n; ++k) {
@@ -229,7 +341,7 @@ static slos_status_t build_tables(slos_plan_s *p) {
             return SLOS_OK;  // too large: arithmetic-index kernels
         bytes += 4 * (size_t)p->F[k] * slot_width(m, k) + 4 * (size_t)m * p->F[k - 1];
     }
-    bytes += 8 * (size_t)p->F[n];
+    bytes += 8 * (size_t)p->F[n] + (size_t)p->K * m;
     if (bytes > kTableBudgetBytes) return SLOS_OK;
     p->tab.layer.assign(n + 1, LayerTables());
     std::vector<int> bar(m + 1), t(m + 1);
@@ -265,9 +377,12 @@ static slos_status_t build_tables(slos_plan_s *p) {
         const int L = n + m - 1;
         std::vector<float> w(p->F[n]);
         std::vector<int32_t> pat(p->F[n]);
+        std::vector<uint8_t> occ((size_t)p->K * m, 0);
         uint64_t z = init_mask(n);
         for (int64_t c = 0; c < p->F[n]; ++c) {
             bars_of(z, m, L, bar.data(), t.data());
+            if (p->det == SLOS_DETECT_PNR)
+                for (int j = 0; j < m; ++j) occ[(size_t)c * m + j] = (uint8_t)t[j];
             double f = 1.0;
             uint32_t supp = 0;
             for (int j = 0; j < m; ++j) {
@@ -280,8 +395,15 @@ static slos_status_t build_tables(slos_plan_s *p) {
             for (int q = 0; q < m; ++q)
                 if ((supp >> q) & 1u) r += binom_host(q, i++);
             pat[c] = p->pat_off[__builtin_popcount(supp)] + (int32_t)r;
+            if (p->det == SLOS_DETECT_THRESHOLD)
+                for (int j = 0; j < m; ++j) occ[(size_t)pat[c] * m + j] = (uint8_t)((supp >> j) & 1u);
             z = next_comb_host(z);
         }
+        if (cudaMalloc(&p->tab.occ, occ.size()) != cudaSuccess) {
+            free_tables(p);
+            return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the occupation table");
+        }
+        cudaMemcpy(p->tab.occ, occ.data(), occ.size(), cudaMemcpyHostToDevice);
         if (cudaMalloc(&p->tab.w, w.size() * 4) != cudaSuccess) {
             free_tables(p);
             return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the weight table");
@@ -577,6 +699,11 @@ slos_status_t mesh_unitary_backward(const slos_mesh_desc_t *desc, const float *t
 
 slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t detection, size_t mem_budget_bytes,
                         slos_plan_t *out) {
+    return slos_plan_space(m, n, input_state, detection, SLOS_SPACE_FOCK, mem_budget_bytes, out);
+}
+
+slos_status_t slos_plan_space(int m, int n, const int *input_state, slos_detection_t detection, slos_space_t space,
+                              size_t mem_budget_bytes, slos_plan_t *out) {
     if (!out) return fail(SLOS_ERR_INVALID_ARG, "slos_plan: NULL out");
     *out = nullptr;
     if (!input_state) return fail(SLOS_ERR_INVALID_ARG, "slos_plan: NULL input_state");
@@ -590,7 +717,14 @@ slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t d
         tot += input_state[i];
     }
     if (tot != n) return fail(SLOS_ERR_INVALID_ARG, "slos_plan: input_state does not hold n photons");
-    if (binom_host(m + n - 1, n) >= (int64_t)1 << 31)
+    if (space != SLOS_SPACE_FOCK && space != SLOS_SPACE_UNBUNCHED)
+        return fail(SLOS_ERR_INVALID_ARG, "slos_plan_space: unknown computation space");
+    const bool unb = space == SLOS_SPACE_UNBUNCHED;
+    if (unb && detection != SLOS_DETECT_PNR)
+        return fail(SLOS_ERR_UNSUPPORTED, "slos_plan_space: the collision-free space takes PNR detection");
+    if (unb && n > m)
+        return fail(SLOS_ERR_INVALID_ARG, "slos_plan_space: no collision-free state holds more photons than modes");
+    if (!unb && binom_host(m + n - 1, n) >= (int64_t)1 << 31)
         return fail(SLOS_ERR_UNSUPPORTED, "slos_plan: Fock space too large (>= 2^31 states)");
     slos_plan_s *p = new (std::nothrow) slos_plan_s();
     if (!p) return fail(SLOS_ERR_OOM, "slos_plan: host allocation failed");
@@ -601,8 +735,9 @@ slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t d
     for (int i = 0; i < m; ++i)
         for (int q = 0; q < input_state[i]; ++q) p->cols.push_back(i);
     p->det = detection;
+    p->space = (int)space;
     p->F.resize(n + 1);
-    for (int k = 0; k <= n; ++k) p->F[k] = binom_host(m + k - 1, k);
+    for (int k = 0; k <= n; ++k) p->F[k] = unb ? binom_host(m, k) : binom_host(m + k - 1, k);
     double sf = 1.0;
     for (int i = 0; i < m; ++i)
         for (int q = 2; q <= input_state[i]; ++q) sf *= q;
@@ -681,6 +816,44 @@ slos_status_t slos_workspace_bytes(slos_plan_t p, int batch, int training, size_
         return fail(SLOS_ERR_INVALID_ARG, "slos_workspace_bytes: bad argument");
     *bytes = batch == 0 ? 0 : make_layout(p, batch, training != 0).total;
     return SLOS_OK;
+}
+
+// Backward seed from the plan's weight table (plans whose outputs are not
+// enumerated by the Fock index arithmetic, i.e. the collision-free space):
+// shared seed: dpw[t] = 2 w_t dout[t]; per instance: seedT[g][t][lane] =
+// 2 w_t dout[b][t] (probabilities) or sqrt(w_t) dout[b][t] (amplitudes).
+struct SeedTabArgs {
+    const void *dout;
+    int64_t stride;
+    void *outT;
+    const float *w;
+    int64_t Fn;
+    int B, kind, bcast;  // kind: 0 probabilities, 1 amplitudes
+};
+
+__global__ void seed_table_kernel(SeedTabArgs a) {
+    if (a.bcast) {
+        const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (c < a.Fn) reinterpret_cast<float *>(a.outT)[c] = 2.f * a.w[c] * reinterpret_cast<const float *>(a.dout)[c];
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int grp = blockIdx.y;
+    const int b = grp * kLanes + lane;
+    const bool valid = b < a.B;
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < a.Fn; c += (int64_t)gridDim.x * wpb) {
+        const size_t o = ((size_t)grp * a.Fn + c) * kLanes + lane;
+        const float wc = __ldg(a.w + c);
+        if (a.kind == 0) {
+            const float v = valid ? reinterpret_cast<const float *>(a.dout)[(int64_t)b * a.stride + c] : 0.f;
+            reinterpret_cast<float *>(a.outT)[o] = 2.f * wc * v;
+        } else {
+            const float2 v = valid ? reinterpret_cast<const float2 *>(a.dout)[(int64_t)b * a.stride + c]
+                                   : make_float2(0.f, 0.f);
+            reinterpret_cast<float2 *>(a.outT)[o] = cscale(v, sqrtf(wc));
+        }
+    }
 }
 
 static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws, const float2 *U, int batch, int k,
@@ -820,7 +993,26 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
         pa.outT = ws + (bcast ? Ly.dpw : Ly.seedT);
         ProfScope ps("slos_seed_prep", bcast ? 8.0 * p->F[n]
                                             : (double)batch * ((pa.kind == 1 ? 16.0 : 8.0) * p->F[n]), s);
-        SLOS_CUDA(launch_prep(m, pa, blocks_for(p, pa.Fn, pa.chunk, NG), bcast, s));
+        if (p->space == SLOS_SPACE_UNBUNCHED) {
+            SeedTabArgs sa;
+            sa.dout = dout;
+            sa.stride = dout_stride_b;
+            sa.outT = pa.outT;
+            sa.w = p->tab.w;
+            sa.Fn = p->F[n];
+            sa.B = batch;
+            sa.kind = pa.kind;
+            sa.bcast = bcast ? 1 : 0;
+            if (bcast) {
+                seed_table_kernel<<<(unsigned)((p->F[n] + 255) / 256), 256, 0, s>>>(sa);
+            } else {
+                dim3 grid((unsigned)std::min<int64_t>((p->F[n] + 7) / 8, (int64_t)p->sm_count * 8), NG);
+                seed_table_kernel<<<grid, 256, 0, s>>>(sa);
+            }
+            SLOS_CUDA(cudaGetLastError());
+        } else {
+            SLOS_CUDA(launch_prep(m, pa, blocks_for(p, pa.Fn, pa.chunk, NG), bcast, s));
+        }
         seed = bcast ? SEED_BCAST : (pa.kind == 1 ? SEED_AMPS_T : SEED_T);
         seed_ptr = pa.outT;
     }
@@ -866,7 +1058,8 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
             double bytes = (kp >= 1 ? 16.0 * a.Fprev : 0.0) + (k == n ? 12.0 : 8.0) * a.Fk;
             ProfScope ps(k == n ? "slos_bwd_final" : "slos_bwd_layer", bytes * batch, s);
             if (p->tab.enabled)
-                SLOS_CUDA(launch_bwd_tab(m, a, p->tab.layer[k].ctab, k == n ? seed : SEED_G, Ly.bwd_blocks[k], s));
+                SLOS_CUDA(launch_bwd_tab(m, a, p->tab.layer[k].ctab, k == n ? seed : SEED_G, Ly.bwd_blocks[k],
+                                         p->space == SLOS_SPACE_UNBUNCHED, s));
             else
                 SLOS_CUDA(launch_bwd(m, a, k == n ? seed : SEED_G, Ly.bwd_blocks[k], s));
         }

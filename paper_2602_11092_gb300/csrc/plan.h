@@ -53,6 +53,7 @@ struct slos_plan_s {
     std::vector<int> s;     // input occupations
     std::vector<int> cols;  // c_1 <= ... <= c_n
     slos_detection_t det;
+    int space = 0;          // slos_space_t: 0 Fock, 1 collision-free states only
     int64_t K;              // outputs per instance
     std::vector<int64_t> F; // |F(m, k)| for k = 0..n
     float inv_sfact;

@@ -410,7 +410,9 @@ constexpr int kBwdTabWarps = 4;
 constexpr int kBwdTabBatch = 8;  // child gathers issued together per parent
 constexpr int bwd_tab_min_blocks(int mmax, bool final_layer) { return final_layer && mmax <= 16 ? 8 : 6; }
 
-template <int MMAX, int SEED, int MINB>
+// HOLES: the child table may name no child (-1), for lattices where t' + e_j
+// leaves the space (collision-free states); such children contribute nothing.
+template <int MMAX, int SEED, int MINB, bool HOLES>
 __global__ void __launch_bounds__(kBwdTabWarps * 32, MINB) slos_bwd_tab_kernel(BwdArgs a, const int32_t *ctab) {
     __shared__ float2 red[kBwdTabWarps][32];
     __shared__ float2 us[MMAX][32];
@@ -449,7 +451,7 @@ __global__ void __launch_bounds__(kBwdTabWarps * 32, MINB) slos_bwd_tab_kernel(B
                 const int j = h + r;
                 const uint32_t cidx = (uint32_t)__shfl_sync(0xffffffffu, mine, j < 32 ? j : 0);
                 g[r] = make_float2(0.f, 0.f);
-                if (j < m) {
+                if (j < m && (!HOLES || (int)cidx >= 0)) {
                     g[r] = __ldg(srcb + (cidx << 5));
                     if (SEED == SEED_T) g[r] = cscale(g[r], __ldg(seedb + (cidx << 5)));
                     if (SEED == SEED_BCAST) g[r] = cscale(g[r], __ldg(seedb + cidx));
@@ -491,6 +493,20 @@ inline size_t fwd_smem_bytes(int epi) {
     if (epi == EPI_PROBS) return (size_t)kWarpsPerBlock * 32 * 33 * sizeof(float);
     if (epi == EPI_AMPS) return (size_t)kWarpsPerBlock * 32 * 33 * sizeof(float2);
     return 0;
+}
+
+template <int MM, bool HOLES>
+cudaError_t launch_bwd_tab_t(const BwdArgs &a, const int32_t *ctab, int seed, int blocks_x, cudaStream_t s) {
+    dim3 grid(blocks_x, a.NG);
+    constexpr int mg = bwd_tab_min_blocks(MM, false), mf = bwd_tab_min_blocks(MM, true);
+    switch (seed) {
+        case SEED_G: slos_bwd_tab_kernel<MM, SEED_G, mg, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;
+        case SEED_BCAST: slos_bwd_tab_kernel<MM, SEED_BCAST, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;
+        case SEED_T: slos_bwd_tab_kernel<MM, SEED_T, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;
+        case SEED_AMPS_T: slos_bwd_tab_kernel<MM, SEED_AMPS_T, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // Defines the host launchers of one MMAX instantiation (one per .cu file so
@@ -541,16 +557,9 @@ inline size_t fwd_smem_bytes(int epi) {
         return cudaGetLastError();                                                                           \
     }                                                                                                        \
     cudaError_t slos_launch_bwd_tab_m##MM(const BwdArgs &a, const int32_t *ctab, int seed, int blocks_x,    \
-                                          cudaStream_t s) {                                                  \
-        dim3 grid(blocks_x, a.NG);                                                                           \
-        switch (seed) {                                                                                      \
-            case SEED_G: slos_bwd_tab_kernel<MM, SEED_G, bwd_tab_min_blocks(MM, false)><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;         \
-            case SEED_BCAST: slos_bwd_tab_kernel<MM, SEED_BCAST, bwd_tab_min_blocks(MM, true)><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break; \
-            case SEED_T: slos_bwd_tab_kernel<MM, SEED_T, bwd_tab_min_blocks(MM, true)><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;         \
-            case SEED_AMPS_T: slos_bwd_tab_kernel<MM, SEED_AMPS_T, bwd_tab_min_blocks(MM, true)><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break; \
-            default: return cudaErrorInvalidValue;                                                           \
-        }                                                                                                    \
-        return cudaGetLastError();                                                                           \
+                                          bool holes, cudaStream_t s) {                                      \
+        return holes ? launch_bwd_tab_t<MM, true>(a, ctab, seed, blocks_x, s)                                \
+                     : launch_bwd_tab_t<MM, false>(a, ctab, seed, blocks_x, s);                              \
     }
 
 #define SLOS_DECLARE_LAUNCHERS(MM)                                                                  \
@@ -559,6 +568,6 @@ inline size_t fwd_smem_bytes(int epi) {
     cudaError_t slos_launch_bwd_m##MM(const BwdArgs &a, int seed, int blocks_x, cudaStream_t s);  \
     cudaError_t slos_launch_prep_m##MM(const PrepArgs &a, int blocks_x, bool bcast, cudaStream_t s);      \
     cudaError_t slos_launch_bwd_tab_m##MM(const BwdArgs &a, const int32_t *ctab, int seed, int blocks_x,  \
-                                          cudaStream_t s);
+                                          bool holes, cudaStream_t s);
 
 }  // namespace slos

@@ -29,6 +29,8 @@ struct PlanTables {
     std::vector<LayerTables> layer;  // [0..n], layer[0] unused
     float *w = nullptr;              // [F_n]
     int32_t *pat = nullptr;          // [F_n] (threshold only)
+    uint8_t *occ = nullptr;          // [K][m]: occupation of mode j in output k (photon counts for PNR
+                                     // outputs, 0/1 for threshold outcomes)
     size_t bytes = 0;
 };
 

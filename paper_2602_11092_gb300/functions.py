@@ -54,6 +54,35 @@ class SlosFn(torch.autograd.Function):
         return dU, None, None
 
 
+class ExpectationFn(torch.autograd.Function):
+    """probabilities [B, K] -> per-mode expectations [B, m]."""
+
+    @staticmethod
+    def forward(ctx, probs, plan: B.Plan):
+        ctx.plan = plan
+        return plan.expectations(probs.contiguous())
+
+    @staticmethod
+    def backward(ctx, dout):
+        return ctx.plan.expectations_backward(dout.contiguous()), None
+
+
+class RenormaliseFn(torch.autograd.Function):
+    """p [B, K] -> p / sum_t p: the distribution conditioned on the plan's space."""
+
+    @staticmethod
+    def forward(ctx, p, plan: B.Plan):
+        q, Z = plan.renormalise(p.contiguous())
+        ctx.save_for_backward(q, Z)
+        ctx.plan = plan
+        return q
+
+    @staticmethod
+    def backward(ctx, dq):
+        q, Z = ctx.saved_tensors
+        return ctx.plan.renormalise_backward(q, Z, dq.contiguous()), None
+
+
 def mesh_unitary(theta, data, m: int, batch: int, data_col: int | None = None):
     return MeshFn.apply(theta, data, m, batch, m // 2 if data_col is None else data_col)
 
@@ -64,15 +93,27 @@ def slos(U, plan: B.Plan, output: int = B.PROBS):
 
 class QuantumLayer(torch.nn.Module):
     """U(x, theta) = W2(theta2) S(x) W1(theta1) followed by the SLOS output
-    distribution of a fixed Fock input (Sec. II-B, Sec. II-C.1)."""
+    of a fixed Fock input (Sec. II-B, Sec. II-C.1).
+
+    space: FOCK or UNBUNCHED (collision-free outputs only); renormalise:
+    condition the distribution on the space (divide by its total);
+    measurement: "probs" (the distribution), "expectations" (per-mode photon
+    numbers, or click probabilities under threshold detection) or "amps"."""
 
     def __init__(self, m: int, input_state, detection: int = B.PNR, output: int = B.PROBS,
                  mem_budget_bytes: int = 0, theta: torch.Tensor | None = None, w: torch.Tensor | None = None,
-                 device="cuda"):
+                 device="cuda", space: int = B.FOCK, renormalise: bool = False, measurement: str | None = None):
         super().__init__()
         self.m = m
-        self.plan = B.Plan(m, input_state, detection, mem_budget_bytes)
-        self.output = output
+        self.plan = B.Plan(m, input_state, detection, mem_budget_bytes, space)
+        if measurement is None:
+            measurement = "amps" if output == B.AMPS else "probs"
+        if measurement not in ("probs", "expectations", "amps"):
+            raise ValueError("measurement must be 'probs', 'expectations' or 'amps'")
+        if measurement == "amps" and renormalise:
+            raise ValueError("renormalisation applies to distributions")
+        self.measurement, self.renormalise = measurement, renormalise
+        self.output = B.AMPS if measurement == "amps" else B.PROBS
         P = m * (m - 1)
         if theta is None:
             theta = torch.rand(P, device=device) * 2 * torch.pi
@@ -84,4 +125,9 @@ class QuantumLayer(torch.nn.Module):
     def forward(self, x: torch.Tensor) -> torch.Tensor:
         data = (x * self.w[None, : x.shape[-1]]).to(torch.float32)
         U = mesh_unitary(self.theta, data, self.m, x.shape[0])
-        return slos(U, self.plan, self.output)
+        y = slos(U, self.plan, self.output)
+        if self.renormalise:
+            y = RenormaliseFn.apply(y, self.plan)
+        if self.measurement == "expectations":
+            y = ExpectationFn.apply(y, self.plan)
+        return y

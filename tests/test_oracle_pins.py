@@ -369,3 +369,56 @@ def test_mlp_reference_invariants():
     params = [(np.zeros((4, 2)), np.log(p[0]))]
     loss, _, _ = mlp.loss_and_grads(params, np.zeros((1, 1)), p[:1], bf=False)
     assert abs(loss) < 1e-12
+
+
+# ---------------------------------------------------------------- spaces and measurements
+
+@pytest.mark.parametrize("m,n", [(2, 2), (4, 2), (6, 3), (7, 7), (5, 1)])
+def test_unbunched_outputs_are_the_fock_outputs_without_collisions(m, n):
+    full = oracle.enumerate_fock(m, n)
+    restricted = full[full.max(axis=1) <= 1]
+    assert np.array_equal(oracle.enumerate_unbunched(m, n), restricted)
+    assert len(restricted) == math.comb(m, n)
+
+
+def test_unbunched_hong_ou_mandel_and_permutation():
+    # |1,1> through a 50:50 beam splitter never leaves one photon per mode
+    bs = np.array([[1, 1j], [1j, 1]]) / np.sqrt(2)
+    assert oracle.probabilities(bs, [1, 1], oracle.enumerate_unbunched(2, 2))[0] <= 1e-15
+    # a permutation sends |1,0,1,0> to one collision-free state with certainty
+    perm = [2, 0, 3, 1]
+    U = np.zeros((4, 4), dtype=np.complex128)
+    for i, j in enumerate(perm):
+        U[j, i] = 1.0
+    outs = oracle.enumerate_unbunched(4, 2)
+    p = oracle.probabilities(U, [1, 0, 1, 0], outs)
+    target = np.zeros(4, dtype=np.int32)
+    target[[perm[0], perm[2]]] = 1
+    assert np.allclose(p, [1.0 if np.array_equal(t, target) else 0.0 for t in outs], atol=1e-15)
+
+
+def test_mode_expectations_match_the_linear_closed_form():
+    rng = np.random.default_rng(19)
+    m, s = 6, [2, 0, 1, 0, 1, 0]
+    U = workloads.haar_unitaries(m, 1, rng)[0]
+    outs = oracle.enumerate_fock(m, 4)
+    e = oracle.mode_expectations(oracle.probabilities(U, s, outs), outs)
+    assert np.allclose(e, (np.abs(U) ** 2) @ np.array(s, dtype=float), atol=1e-13)
+
+
+def test_click_probabilities_are_one_minus_no_photon():
+    rng = np.random.default_rng(23)
+    m, n, s = 5, 3, [1, 1, 0, 1, 0]
+    U = workloads.haar_unitaries(m, 1, rng)[0]
+    outs = oracle.enumerate_fock(m, n)
+    p = oracle.probabilities(U, s, outs)
+    clicks = oracle.click_probabilities(oracle.threshold_probs(p, outs, m, n), m, n)
+    dark = np.array([p[outs[:, j] == 0].sum() for j in range(m)])
+    assert np.allclose(clicks, 1.0 - dark, atol=1e-13)
+
+
+def test_renormalise_sums_to_one_and_keeps_ratios():
+    p = np.array([0.1, 0.0, 0.3, 0.05])
+    q = oracle.renormalise(p)
+    assert abs(q.sum() - 1.0) < 1e-15
+    assert abs(q[2] / q[0] - 3.0) < 1e-12 and q[1] == 0.0
