@@ -204,6 +204,29 @@ slos_status_t slos_renormalise(slos_plan_t plan, const float *p, int batch, floa
 slos_status_t slos_renormalise_backward(slos_plan_t plan, const float *q, const float *Z, const float *dq, int batch,
                                         float *dp, void *stream);
 
+/* ----------------------------------------------------------------------
+ * Shot sampling (the hardware-aware design section: a photonic processor
+ * returns a finite number of shots, MerlinProcessor's nsample).  Each shot
+ * turns one caller-supplied uniform draw u in [0, 1) into an outcome index by
+ * inverting the cumulative distribution in exact integer arithmetic: weights
+ * P(t) = floor(p(t) 2^32), C(t) = P(0) + ... + P(t), T = C(n_outputs - 1);
+ * the outcome is the first t with C(t) > floor(floor(u 2^32) T / 2^32).
+ * Draws outside [0, 1) are clamped into it (NaN counts as 0); NaN or negative
+ * weights count as 0; outcomes whose weight rounds to zero are never drawn; a
+ * distribution with no weight gives -1.  The result depends on nothing but p
+ * and u, bit for bit.
+ * ---------------------------------------------------------------------- */
+
+/* Device scratch bytes slos_sample needs for `batch` distributions. */
+slos_status_t slos_sample_workspace_bytes(slos_plan_t plan, int batch, size_t *bytes);
+
+/* probs: float32 [batch][n_outputs] (any non-negative weights: the
+ * distribution is T-normalised); uniforms: float32 [batch][shots];
+ * samples: int32 [batch][shots] outcome indices; counts: NULL or int32
+ * [batch][n_outputs], overwritten with the number of shots per outcome. */
+slos_status_t slos_sample(slos_plan_t plan, const float *probs, int batch, int shots, const float *uniforms,
+                          int32_t *samples, int32_t *counts, void *workspace, size_t workspace_bytes, void *stream);
+
 /* Reads the plan's device status word (waits for `stream`), clears it, and
  * returns SLOS_ERR_TIMEOUT / SLOS_ERR_INTERNAL if a kernel reported one. */
 slos_status_t slos_sync_status(slos_plan_t plan, void *stream);

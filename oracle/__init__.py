@@ -24,6 +24,7 @@ against physics or mathematics that does not use the function itself.
 """
 from __future__ import annotations
 
+import bisect
 import ctypes
 import itertools
 import math
@@ -261,6 +262,37 @@ def renormalise(p: np.ndarray) -> np.ndarray:
     """The distribution conditioned on the listed outputs: p / sum p."""
     p = np.asarray(p, dtype=np.float64)
     return p / p.sum()
+
+
+# --------------------------------------------------------------------------
+# Shot sampling (hardware-aware design section, MerlinProcessor: outputs as
+# they come from a photonic processor, a finite number of shots).  A shot maps
+# one uniform draw u in [0, 1) to an outcome by inverting the cumulative
+# distribution.  To make the decision exact (the same on any machine and in
+# any summation order) the weights are fixed-point integers:
+# P(t) = floor(p(t) 2^32), C(t) = P(0) + ... + P(t) (exact integers),
+# T = C(K-1); the shot's target is floor(floor(u 2^32) T / 2^32) and its
+# outcome is the first t with C(t) > target.  Outcomes whose weight rounds to
+# zero are never drawn.
+# --------------------------------------------------------------------------
+
+def sample_outcomes(p: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Outcome index of every draw in u (1-D) for the distribution p (1-D,
+    float32 values as given); plain Python integers for the arithmetic.
+    NaN or negative weights weigh nothing; draws outside [0, 1) are clamped
+    into it (NaN counts as 0); a distribution with no weight gives -1."""
+    P = [int(math.floor(float(x) * 2.0 ** 32)) if float(x) > 0.0 else 0 for x in np.asarray(p, dtype=np.float32)]
+    C = list(itertools.accumulate(P))
+    T = C[-1]
+    out = np.empty(len(u), dtype=np.int64)
+    for i, x in enumerate(np.asarray(u, dtype=np.float32)):
+        U32 = 0 if not float(x) > 0.0 else min(int(math.floor(float(x) * 2.0 ** 32)), 2 ** 32 - 1)
+        if T == 0:
+            out[i] = -1
+            continue
+        target = (U32 * T) >> 32
+        out[i] = bisect.bisect_right(C, target)
+    return out
 
 
 # --------------------------------------------------------------------------

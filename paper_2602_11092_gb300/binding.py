@@ -54,6 +54,8 @@ _SIGNATURES = {
     "slos_expectations_backward": ([_vp, _vp, _int, _vp, _vp], _int),
     "slos_renormalise": ([_vp, _vp, _int, _vp, _vp, _vp], _int),
     "slos_renormalise_backward": ([_vp, _vp, _vp, _vp, _int, _vp, _vp], _int),
+    "slos_sample_workspace_bytes": ([_vp, _int, ctypes.POINTER(_sz)], _int),
+    "slos_sample": ([_vp, _vp, _int, _int, _vp, _vp, _vp, _vp, _sz, _vp], _int),
     "slos_workspace_bytes": ([_vp, _int, _int, ctypes.POINTER(_sz)], _int),
     "slos_forward": ([_vp, _vp, _int, _int, _vp, _int, _vp, _sz, _vp], _int),
     "slos_backward": ([_vp, _vp, _int, _int, _vp, _i64, _vp, _vp, _sz, _vp], _int),
@@ -246,6 +248,24 @@ class Plan:
         _check(load().slos_renormalise_backward(self._h, _ptr(q), _ptr(Z), _ptr(dq), q.shape[0], _ptr(dp),
                                                 _stream(stream)))
         return dp
+
+    def sample(self, probs: torch.Tensor, uniforms: torch.Tensor, counts: bool = False, stream=None):
+        """Shots from distributions [B, n_outputs] driven by draws [B, shots]
+        in [0, 1): returns int32 outcome indices [B, shots] (and int32
+        counts [B, n_outputs] when counts=True)."""
+        _need(probs, torch.float32, "probs")
+        _need(uniforms, torch.float32, "uniforms")
+        B, S = uniforms.shape
+        if probs.shape[0] != B:
+            raise ValueError("probs and uniforms need the same batch")
+        nb = ctypes.c_size_t()
+        _check(load().slos_sample_workspace_bytes(self._h, B, ctypes.byref(nb)))
+        ws = torch.empty(max(1, nb.value), dtype=torch.uint8, device=probs.device)
+        samples = torch.empty((B, S), dtype=torch.int32, device=probs.device)
+        cnt = torch.empty((B, self.n_outputs), dtype=torch.int32, device=probs.device) if counts else None
+        _check(load().slos_sample(self._h, _ptr(probs), B, S, _ptr(uniforms), _ptr(samples), _ptr(cnt), _ptr(ws),
+                                  ws.numel(), _stream(stream)))
+        return (samples, cnt) if counts else samples
 
     def forward_noalloc(self, U: torch.Tensor, out: torch.Tensor, output: int = PROBS, stream=None):
         """slos_forward_noalloc: the library's built-in scratch, no workspace."""

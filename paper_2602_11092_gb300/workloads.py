@@ -128,3 +128,21 @@ def surrogate_phases(count: int, seed: int):
     rng = np.random.default_rng(seed)
     x = rng.standard_normal((count, 12))
     return mb.theta, x * mb.w[None, :]
+
+
+def random_distributions(batch: int, K: int, seed: int, zero_fraction: float = 0.1) -> np.ndarray:
+    """float32 [batch, K] rows of non-negative weights summing to about one
+    (exponential draws, a seeded fraction set to zero), for sampling tests."""
+    rng = np.random.default_rng(seed)
+    w = rng.exponential(size=(batch, K))
+    w[rng.random((batch, K)) < zero_fraction] = 0.0
+    w /= np.maximum(w.sum(axis=1, keepdims=True), 1e-300)
+    return w.astype(np.float32)
+
+
+def uniforms(batch: int, shots: int, seed: int) -> np.ndarray:
+    """float32 [batch, shots] draws in [0, 1): the random numbers shot
+    sampling consumes, passed in so that every side sees the same ones."""
+    rng = np.random.default_rng(seed)
+    u = rng.random((batch, shots)).astype(np.float32)
+    return np.minimum(u, np.float32(np.nextafter(np.float32(1.0), np.float32(0.0))))

@@ -422,3 +422,34 @@ def test_renormalise_sums_to_one_and_keeps_ratios():
     q = oracle.renormalise(p)
     assert abs(q.sum() - 1.0) < 1e-15
     assert abs(q[2] / q[0] - 3.0) < 1e-12 and q[1] == 0.0
+
+
+# ---------------------------------------------------------------- shot sampling
+
+def test_sampling_dyadic_boundaries_are_exact():
+    # p = (1/4, 3/4): draws below 1/4 give outcome 0, from 1/4 on outcome 1
+    p = np.array([0.25, 0.75], dtype=np.float32)
+    just_below = np.float32(np.nextafter(np.float32(0.25), np.float32(0.0)))
+    u = np.array([0.0, just_below, 0.25, 0.5, np.nextafter(np.float32(1.0), np.float32(0.0))], dtype=np.float32)
+    assert list(oracle.sample_outcomes(p, u)) == [0, 0, 1, 1, 1]
+
+
+def test_sampling_never_draws_zero_weight_outcomes_and_follows_p():
+    p = workloads.random_distributions(1, 40, seed=3, zero_fraction=0.3)[0]
+    u = workloads.uniforms(1, 40000, seed=4)[0]
+    s = oracle.sample_outcomes(p, u)
+    counts = np.bincount(s, minlength=40)
+    assert np.all(counts[p == 0] == 0)
+    # every frequency within 5 standard deviations of its probability
+    sd = np.sqrt(p * (1 - p) / len(u))
+    assert np.all(np.abs(counts / len(u) - p) <= 5 * sd + 1e-9)
+
+
+def test_sampling_one_hot_monotone_and_empty():
+    p = np.zeros(7, dtype=np.float32)
+    p[4] = 1.0
+    assert set(oracle.sample_outcomes(p, workloads.uniforms(1, 200, seed=5)[0])) == {4}
+    q = workloads.random_distributions(1, 30, seed=6)[0]
+    u = np.sort(workloads.uniforms(1, 500, seed=7)[0])
+    assert np.all(np.diff(oracle.sample_outcomes(q, u)) >= 0)
+    assert set(oracle.sample_outcomes(np.zeros(5, np.float32), u[:10])) == {-1}
