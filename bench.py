@@ -551,6 +551,24 @@ def run_extras(B, dev, peak_hbm, args):
     if not args.no_cpu_baseline:
         out["layer12_forward"]["oracle"] = oracle_forward_rate(12, w["s"], mb, seconds_target=3.0)
     del ws, probs
+    # --- fidelity kernel: Gram matrix of 1024 data points on the m=12, n=6 layer
+    Ng = 1024
+    Ug = torch.empty((Ng, 12, 12), dtype=torch.complex64, device=dev)
+    B.mesh_unitary(12, theta, data[:Ng].contiguous(), Ng, out=Ug)
+    Kg = torch.empty((Ng, Ng), dtype=torch.float32, device=dev)
+    B.fidelity_kernel(w["s"], Ug, Ug, out=Kg)
+    msg = _timed(lambda: B.fidelity_kernel(w["s"], Ug, Ug, out=Kg), 5, stream)
+    out["fidelity_gram"] = {"workload": "Gram matrix of 1024 points, m=12 n=6 layer (132 shared + 12 data phases)",
+                            "value": Ng * Ng / (msg * 1e-3), "unit": "kernel entries/s", "ms_per_matrix": msg}
+    if not args.no_cpu_baseline:
+        import oracle
+        Uh = Ug[:8].cpu().numpy().astype(np.complex128)
+        t0 = time.perf_counter()
+        oracle.fidelity_kernel(Uh, Uh, w["s"])
+        dt = time.perf_counter() - t0
+        out["fidelity_gram"]["oracle"] = {"value": 64 / dt, "unit": "kernel entries/s", "cores": 1,
+                                          "kind": "oracle", "sample": "8 x 8 entries, Ryser in FP64"}
+    del Ug, Kg
     # --- m=6, n=3, one instance: latency of one forward
     t = workloads.tiny()
     plan0 = B.Plan(6, t["s"])

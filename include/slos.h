@@ -227,6 +227,18 @@ slos_status_t slos_sample_workspace_bytes(slos_plan_t plan, int batch, size_t *b
 slos_status_t slos_sample(slos_plan_t plan, const float *probs, int batch, int shots, const float *uniforms,
                           int32_t *samples, int32_t *counts, void *workspace, size_t workspace_bytes, void *stream);
 
+/* ----------------------------------------------------------------------
+ * Fidelity kernel (kernel-methods section): the embedding |phi(x)> =
+ * U(x)|s> of a Fock input s gives K[i][j] = |<phi_a(i)|phi_b(j)>|^2 =
+ * |<s|Ua[i]^dag Ub[j]|s>|^2 = |Per(W_ij)|^2 / (prod s_i!)^2, W_ij the n x n
+ * block of Ua[i]^dag Ub[j] on the photon columns.  Ua: complex64 [Na][m][m],
+ * Ub: complex64 [Nb][m][m] (e.g. from mesh_unitary); K: float32 [Na][Nb].
+ * W in FP32, the permanent (Glynn, Gray-code order) in FP64.  1 <= n <= 8
+ * photons, m <= 24; otherwise SLOS_ERR_UNSUPPORTED.
+ * ---------------------------------------------------------------------- */
+slos_status_t slos_fidelity_kernel(int m, const int *input_state, const void *Ua, int Na, const void *Ub, int Nb,
+                                   float *K, void *stream);
+
 /* Reads the plan's device status word (waits for `stream`), clears it, and
  * returns SLOS_ERR_TIMEOUT / SLOS_ERR_INTERNAL if a kernel reported one. */
 slos_status_t slos_sync_status(slos_plan_t plan, void *stream);

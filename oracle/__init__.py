@@ -296,6 +296,27 @@ def sample_outcomes(p: np.ndarray, u: np.ndarray) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Fidelity kernel (kernel-methods section): |phi(x)> = U(x)|s>,
+# k(x1, x2) = |<phi(x1)|phi(x2)>|^2 = |<s|U(x1)^dag U(x2)|s>|^2, and for a
+# Fock state <s|V|s> = Per(V[cols(s), cols(s)]) / prod_i s_i!.
+# --------------------------------------------------------------------------
+
+def fidelity_kernel(Ua, Ub, s) -> np.ndarray:
+    """k[i][j] = |<s|Ua[i]^dag Ub[j]|s>|^2 (FP64, Ryser permanents)."""
+    s = [int(x) for x in s]
+    cols = [i for i in range(len(s)) for _ in range(s[i])]
+    sf = float(np.prod([math.factorial(x) for x in s]))
+    Ua = np.asarray(Ua, dtype=np.complex128)
+    Ub = np.asarray(Ub, dtype=np.complex128)
+    K = np.empty((len(Ua), len(Ub)), dtype=np.float64)
+    for i in range(len(Ua)):
+        for j in range(len(Ub)):
+            V = Ua[i].conj().T @ Ub[j]
+            K[i, j] = abs(permanent(V[np.ix_(cols, cols)]) / sf) ** 2
+    return K
+
+
+# --------------------------------------------------------------------------
 # Interferometer mesh (Sec. II-A.3: trainable parameters are the phases of the
 # physical components; Sec. II-C.1: U(x, theta) = W2(theta2) S(x) W1(theta1)).
 # MZI on modes (k, k+1): T = B diag(e^{i theta}, 1) B diag(e^{i phi}, 1) with

@@ -56,6 +56,7 @@ _SIGNATURES = {
     "slos_renormalise_backward": ([_vp, _vp, _vp, _vp, _int, _vp, _vp], _int),
     "slos_sample_workspace_bytes": ([_vp, _int, ctypes.POINTER(_sz)], _int),
     "slos_sample": ([_vp, _vp, _int, _int, _vp, _vp, _vp, _vp, _sz, _vp], _int),
+    "slos_fidelity_kernel": ([_int, ctypes.POINTER(_int), _vp, _int, _vp, _int, _vp, _vp], _int),
     "slos_workspace_bytes": ([_vp, _int, _int, ctypes.POINTER(_sz)], _int),
     "slos_forward": ([_vp, _vp, _int, _int, _vp, _int, _vp, _sz, _vp], _int),
     "slos_backward": ([_vp, _vp, _int, _int, _vp, _i64, _vp, _vp, _sz, _vp], _int),
@@ -166,6 +167,23 @@ def mesh_unitary_backward(m: int, theta, data, batch: int, dU: torch.Tensor, dat
     _check(lib.mesh_unitary_backward(ctypes.byref(desc), _ptr(theta), ts, _ptr(data), ds, batch, _ptr(dU),
                                      _ptr(dtheta), _ptr(ddata), _ptr(ws), nbytes.value, _stream(stream)))
     return dtheta, ddata
+
+
+def fidelity_kernel(input_state, Ua: torch.Tensor, Ub: torch.Tensor | None = None, out=None, stream=None):
+    """K[i][j] = |<s|Ua[i]^dag Ub[j]|s>|^2 for unitaries [Na, m, m] and
+    [Nb, m, m] (Ub = Ua: the Gram matrix)."""
+    _need(Ua, torch.complex64, "Ua")
+    Ub = Ua if Ub is None else Ub
+    _need(Ub, torch.complex64, "Ub")
+    m = Ua.shape[-1]
+    s = [int(x) for x in input_state]
+    if len(s) != m:
+        raise ValueError("input_state needs one occupation per mode")
+    K = torch.empty((Ua.shape[0], Ub.shape[0]), dtype=torch.float32, device=Ua.device) if out is None else out
+    arr = (ctypes.c_int * m)(*s)
+    _check(load().slos_fidelity_kernel(m, arr, _ptr(Ua), Ua.shape[0], _ptr(Ub), Ub.shape[0], _ptr(K),
+                                       _stream(stream)))
+    return K
 
 
 # ------------------------------------------------------------------ plans

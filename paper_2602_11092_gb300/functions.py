@@ -131,3 +131,31 @@ class QuantumLayer(torch.nn.Module):
         if self.measurement == "expectations":
             y = ExpectationFn.apply(y, self.plan)
         return y
+
+
+class FidelityKernel(torch.nn.Module):
+    """k(x1, x2) = |<s|U(x1)^dag U(x2)|s>|^2 with U(x) = W2(theta) S(x w)
+    W1(theta) (the angle-encoding circuit): kernel(X) gives the Gram matrix,
+    kernel(X1, X2) the cross kernel (kernel-methods section)."""
+
+    def __init__(self, m: int, input_state, theta: torch.Tensor | None = None, w: torch.Tensor | None = None,
+                 device="cuda"):
+        super().__init__()
+        self.m, self.input_state = m, [int(x) for x in input_state]
+        P = m * (m - 1)
+        if theta is None:
+            theta = torch.rand(P, device=device) * 2 * torch.pi
+        self.register_buffer("theta", theta.to(device=device, dtype=torch.float32))
+        if w is None:
+            w = torch.ones(m, device=device)
+        self.register_buffer("w", w.to(device=device, dtype=torch.float32))
+
+    def unitaries(self, x: torch.Tensor) -> torch.Tensor:
+        data = (x * self.w[None, : x.shape[-1]]).to(torch.float32).contiguous()
+        return B.mesh_unitary(self.m, self.theta, data, x.shape[0])
+
+    @torch.no_grad()
+    def forward(self, x1: torch.Tensor, x2: torch.Tensor | None = None) -> torch.Tensor:
+        U1 = self.unitaries(x1)
+        U2 = U1 if x2 is None else self.unitaries(x2)
+        return B.fidelity_kernel(self.input_state, U1, U2)

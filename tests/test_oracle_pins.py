@@ -453,3 +453,35 @@ def test_sampling_one_hot_monotone_and_empty():
     u = np.sort(workloads.uniforms(1, 500, seed=7)[0])
     assert np.all(np.diff(oracle.sample_outcomes(q, u)) >= 0)
     assert set(oracle.sample_outcomes(np.zeros(5, np.float32), u[:10])) == {-1}
+
+
+# ---------------------------------------------------------------- fidelity kernel
+
+def test_fidelity_kernel_identity_symmetry_and_transition_probability():
+    rng = np.random.default_rng(31)
+    m, s = 5, [1, 0, 2, 0, 1]
+    A = workloads.haar_unitaries(m, 3, rng)
+    Bm = workloads.haar_unitaries(m, 4, rng)
+    K = oracle.fidelity_kernel(A, Bm, s)
+    assert np.allclose(np.diag(oracle.fidelity_kernel(A, A, s)), 1.0, atol=1e-13)
+    assert np.allclose(K, oracle.fidelity_kernel(Bm, A, s).T, atol=1e-14)
+    # the same number is the probability of output s for input s through Ua^dag Ub
+    V = A[1].conj().T @ Bm[2]
+    p = oracle.probabilities(V, s, np.array([s], dtype=np.int32))[0]
+    assert abs(K[1, 2] - p) < 1e-13
+    assert np.all((K >= 0) & (K <= 1 + 1e-12))
+
+
+def test_fidelity_kernel_closed_forms():
+    rng = np.random.default_rng(37)
+    m = 4
+    A = workloads.haar_unitaries(m, 2, rng)
+    Bm = workloads.haar_unitaries(m, 3, rng)
+    # one photon in mode 2: the squared overlap of the two columns
+    K1 = oracle.fidelity_kernel(A, Bm, [0, 0, 1, 0])
+    ref1 = np.abs(np.einsum("ij,kj->ik", A[:, :, 2].conj(), Bm[:, :, 2])) ** 2
+    assert np.allclose(K1, ref1, atol=1e-14)
+    # two photons in mode 1: <s|V|s> = V_11^2
+    K2 = oracle.fidelity_kernel(A, Bm, [0, 2, 0, 0])
+    v = np.einsum("ij,kj->ik", A[:, :, 1].conj(), Bm[:, :, 1])
+    assert np.allclose(K2, np.abs(v) ** 4, atol=1e-14)
