@@ -569,6 +569,23 @@ def run_extras(B, dev, peak_hbm, args):
         out["fidelity_gram"]["oracle"] = {"value": 64 / dt, "unit": "kernel entries/s", "cores": 1,
                                           "kind": "oracle", "sample": "8 x 8 entries, Ryser in FP64"}
     del Ug, Kg
+    # --- amplitude encoding: 4096 state vectors over the m=10, n=5 Fock basis through one U
+    pe = B.Plan(10, [1, 0] * 5)
+    Ke = pe.n_outputs
+    rng_e = np.random.default_rng(1006)
+    Xe = rng_e.standard_normal((4096, Ke)) + 1j * rng_e.standard_normal((4096, Ke))
+    Xe = torch.tensor((Xe / np.linalg.norm(Xe, axis=1, keepdims=True)).astype(np.complex64), device=dev)
+    Ue = torch.tensor(workloads.haar_unitaries(10, 1, rng_e)[0].astype(np.complex64), device=dev)
+    nb = pe.encoded_workspace_bytes()
+    wse = torch.empty(nb, dtype=torch.uint8, device=dev)
+    oute = torch.empty((4096, Ke), dtype=torch.float32, device=dev)
+    pe.encoded_forward(Ue, Xe, B.PROBS, out=oute, workspace=wse)
+    mse = _timed(lambda: pe.encoded_forward(Ue, Xe, B.PROBS, out=oute, workspace=wse), 5, stream)
+    out["amplitude_encoding"] = {"workload": "4096 amplitude-encoded states over the m=10 n=5 Fock basis (2002 states), "
+                                             "one U: transfer matrix + complex GEMM",
+                                 "value": 4096 / (mse * 1e-3), "unit": "distributions/s", "ms_per_batch": mse,
+                                 "gemm_tflops": 8.0 * 4096 * Ke * Ke / (mse * 1e-3) / 1e12}
+    del Xe, wse, oute
     # --- m=6, n=3, one instance: latency of one forward
     t = workloads.tiny()
     plan0 = B.Plan(6, t["s"])

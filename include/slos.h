@@ -239,6 +239,26 @@ slos_status_t slos_sample(slos_plan_t plan, const float *probs, int batch, int s
 slos_status_t slos_fidelity_kernel(int m, const int *input_state, const void *Ua, int Na, const void *Ub, int Nb,
                                    float *K, void *stream);
 
+/* ----------------------------------------------------------------------
+ * Amplitude-encoded input (Sec. II-C, amplitude encoding): the input is a
+ * state vector |x> = sum_s x_s |s> over the plan's output basis (same order,
+ * n photons; Fock or collision-free space) and the output is U|x>:
+ *     psi(t) = sum_s <t|U|s> x_s.
+ * The call builds the n-photon transfer matrix of U (K x K) layer by layer
+ * with the photon-by-photon recursion, in the workspace, then applies it to
+ * the batch's vectors with one complex GEMM.  One U for the whole batch.
+ * PNR plans with K <= 32768 outputs (tables built at plan time); forward only.
+ * ---------------------------------------------------------------------- */
+
+/* Device scratch bytes slos_encoded_forward needs (K^2 + F_{n-1}^2 complex64). */
+slos_status_t slos_encoded_workspace_bytes(slos_plan_t plan, size_t *bytes);
+
+/* U: complex64 [m][m]; X: complex64 [batch][n_outputs] input amplitudes;
+ * out: complex64 [batch][n_outputs] amplitudes (SLOS_OUT_AMPS) or float32
+ * probabilities |psi(t)|^2 (SLOS_OUT_PROBS). */
+slos_status_t slos_encoded_forward(slos_plan_t plan, const void *U, const void *X, int batch, slos_output_t output,
+                                   void *out, void *workspace, size_t workspace_bytes, void *stream);
+
 /* Reads the plan's device status word (waits for `stream`), clears it, and
  * returns SLOS_ERR_TIMEOUT / SLOS_ERR_INTERNAL if a kernel reported one. */
 slos_status_t slos_sync_status(slos_plan_t plan, void *stream);

@@ -317,6 +317,23 @@ def fidelity_kernel(Ua, Ub, s) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Amplitude encoding (Sec. II-C): |x> = sum_s x_s |s> over a basis of n-photon
+# Fock states; output amplitudes psi(t) = sum_s <t|U|s> x_s.
+# --------------------------------------------------------------------------
+
+def transfer_matrix(U: np.ndarray, basis: np.ndarray) -> np.ndarray:
+    """Phi[t][s] = <t|U|s> for t, s in the basis (rows of occupations)."""
+    basis = np.asarray(basis, dtype=np.int32)
+    return np.stack([amplitudes(U, list(s), basis) for s in basis], axis=1)
+
+
+def encoded_amplitudes(U: np.ndarray, X: np.ndarray, basis: np.ndarray) -> np.ndarray:
+    """psi[b][t] = sum_s <t|U|s> X[b][s]."""
+    Phi = transfer_matrix(U, basis)
+    return np.asarray(X, dtype=np.complex128) @ Phi.T
+
+
+# --------------------------------------------------------------------------
 # Interferometer mesh (Sec. II-A.3: trainable parameters are the phases of the
 # physical components; Sec. II-C.1: U(x, theta) = W2(theta2) S(x) W1(theta1)).
 # MZI on modes (k, k+1): T = B diag(e^{i theta}, 1) B diag(e^{i phi}, 1) with

@@ -57,6 +57,8 @@ _SIGNATURES = {
     "slos_sample_workspace_bytes": ([_vp, _int, ctypes.POINTER(_sz)], _int),
     "slos_sample": ([_vp, _vp, _int, _int, _vp, _vp, _vp, _vp, _sz, _vp], _int),
     "slos_fidelity_kernel": ([_int, ctypes.POINTER(_int), _vp, _int, _vp, _int, _vp, _vp], _int),
+    "slos_encoded_workspace_bytes": ([_vp, ctypes.POINTER(_sz)], _int),
+    "slos_encoded_forward": ([_vp, _vp, _vp, _int, _int, _vp, _vp, _sz, _vp], _int),
     "slos_workspace_bytes": ([_vp, _int, _int, ctypes.POINTER(_sz)], _int),
     "slos_forward": ([_vp, _vp, _int, _int, _vp, _int, _vp, _sz, _vp], _int),
     "slos_backward": ([_vp, _vp, _int, _int, _vp, _i64, _vp, _vp, _sz, _vp], _int),
@@ -284,6 +286,29 @@ class Plan:
         _check(load().slos_sample(self._h, _ptr(probs), B, S, _ptr(uniforms), _ptr(samples), _ptr(cnt), _ptr(ws),
                                   ws.numel(), _stream(stream)))
         return (samples, cnt) if counts else samples
+
+    def encoded_workspace_bytes(self) -> int:
+        nb = ctypes.c_size_t()
+        _check(load().slos_encoded_workspace_bytes(self._h, ctypes.byref(nb)))
+        return nb.value
+
+    def encoded_forward(self, U: torch.Tensor, X: torch.Tensor, output: int = PROBS, out=None, workspace=None,
+                        stream=None):
+        """Amplitude-encoded inputs X [B, n_outputs] (complex64 state vectors
+        over this plan's basis) through one unitary U [m, m]."""
+        _need(U, torch.complex64, "U")
+        _need(X, torch.complex64, "X")
+        Bn = X.shape[0]
+        if workspace is None:
+            nb = ctypes.c_size_t()
+            _check(load().slos_encoded_workspace_bytes(self._h, ctypes.byref(nb)))
+            workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=X.device)
+        if out is None:
+            dt = torch.complex64 if output == AMPS else torch.float32
+            out = torch.empty((Bn, self.n_outputs), dtype=dt, device=X.device)
+        _check(load().slos_encoded_forward(self._h, _ptr(U), _ptr(X), Bn, output, _ptr(out), _ptr(workspace),
+                                           workspace.numel(), _stream(stream)))
+        return out
 
     def forward_noalloc(self, U: torch.Tensor, out: torch.Tensor, output: int = PROBS, stream=None):
         """slos_forward_noalloc: the library's built-in scratch, no workspace."""

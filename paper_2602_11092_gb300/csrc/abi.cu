@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <new>
 #include <string>
@@ -168,11 +169,14 @@ static void free_tables(slos_plan_s *p) {
     for (auto &L : p->tab.layer) {
         if (L.slots) cudaFree(L.slots);
         if (L.ctab) cudaFree(L.ctab);
+        if (L.colinfo) cudaFree(L.colinfo);
         L = LayerTables();
     }
     if (p->tab.w) cudaFree(p->tab.w);
     if (p->tab.pat) cudaFree(p->tab.pat);
     if (p->tab.occ) cudaFree(p->tab.occ);
+    if (p->tab.gfact) cudaFree(p->tab.gfact);
+    p->tab.gfact = nullptr;
     p->tab.w = nullptr;
     p->tab.pat = nullptr;
     p->tab.occ = nullptr;
@@ -420,6 +424,63 @@ static slos_status_t build_tables(slos_plan_s *p) {
     p->tab.bytes = bytes;
     p->tab.enabled = true;
     return SLOS_OK;
+}
+
+// Amplitude encoding (slos_encoded_forward): for every state s of every
+// layer k, its highest occupied mode c and the rank of s - e_c in layer k-1
+// (the column recursion of the transfer matrix), and sqrt(prod t!) of the
+// final states.  Built for PNR table plans of at most kMaxEncodeStates
+// outputs; an allocation failure just leaves the feature off.
+static void build_encode_tables(slos_plan_s *p) {
+    if (!p->tab.enabled || p->det != SLOS_DETECT_PNR || p->K > kMaxEncodeStates) return;
+    const int m = p->m, n = p->n;
+    const bool unb = p->space == SLOS_SPACE_UNBUNCHED;
+    std::vector<float> g(p->F[n], 1.f);
+    for (int k = 1; k <= n; ++k) {
+        std::vector<uint32_t> info(p->F[k]);
+        std::vector<int> t(m + 1), bar(m + 1);
+        auto emit = [&](int64_t c) {
+            int hi = m - 1;
+            while (t[hi] == 0) --hi;
+            t[hi] -= 1;
+            const int64_t r = unb ? unbunched_rank(std::vector<int>(t.begin(), t.begin() + m), m) : host_rank(m, t.data());
+            t[hi] += 1;
+            info[c] = ((uint32_t)r << 5) | (uint32_t)hi;
+            if (k == n) {
+                double f = 1.0;
+                for (int j = 0; j < m; ++j)
+                    for (int q = 2; q <= t[j]; ++q) f *= q;
+                g[c] = (float)std::sqrt(f);
+            }
+        };
+        if (unb) {
+            std::vector<int> S(k);
+            for (int q = 0; q < k; ++q) S[q] = q;
+            int64_t c = 0;
+            do {
+                std::fill(t.begin(), t.end(), 0);
+                for (int q : S) t[q] = 1;
+                emit(c++);
+            } while (next_subset(S, m));
+        } else {
+            uint64_t z = 0;
+            for (int b = 0; b < m - 1; ++b) z |= 1ull << b;
+            for (int64_t c = 0; c < p->F[k]; ++c) {
+                bars_of(z, m, k + m - 1, bar.data(), t.data());
+                emit(c);
+                z = next_comb_host(z);
+            }
+        }
+        uint32_t *d = nullptr;
+        if (cudaMalloc(&d, info.size() * 4) != cudaSuccess) return;
+        cudaMemcpy(d, info.data(), info.size() * 4, cudaMemcpyHostToDevice);
+        p->tab.layer[k].colinfo = d;
+    }
+    if (cudaMalloc(&p->tab.gfact, g.size() * 4) != cudaSuccess) {
+        p->tab.gfact = nullptr;
+        return;
+    }
+    cudaMemcpy(p->tab.gfact, g.data(), g.size() * 4, cudaMemcpyHostToDevice);
 }
 
 // On-chip inference forward: PNR table plans whose intermediate layers fit in
@@ -799,6 +860,7 @@ slos_status_t slos_plan_space(int m, int n, const int *input_state, slos_detecti
         return tst;
     }
     choose_fused(p);
+    build_encode_tables(p);
     *out = p;
     return SLOS_OK;
 }

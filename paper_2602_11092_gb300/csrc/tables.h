@@ -20,6 +20,7 @@ namespace slos {
 
 struct LayerTables {
     uint32_t *slots = nullptr;   // [F_k][kw]
+    uint32_t *colinfo = nullptr; // [F_k]: (rank of s - e_c in layer k-1) << 5 | c, c = highest occupied mode of s
     int kw = 0;
     int32_t *ctab = nullptr;     // [F_{k-1} * m]
 };
@@ -29,6 +30,7 @@ struct PlanTables {
     std::vector<LayerTables> layer;  // [0..n], layer[0] unused
     float *w = nullptr;              // [F_n]
     int32_t *pat = nullptr;          // [F_n] (threshold only)
+    float *gfact = nullptr;          // [F_n]: sqrt(prod t_j!) of the final states (amplitude encoding)
     uint8_t *occ = nullptr;          // [K][m]: occupation of mode j in output k (photon counts for PNR
                                      // outputs, 0/1 for threshold outcomes)
     size_t bytes = 0;
@@ -36,5 +38,6 @@ struct PlanTables {
 
 constexpr size_t kTableBudgetBytes = size_t(1) << 30;  // per plan
 constexpr int64_t kMaxTableParent = int64_t(1) << 26;
+constexpr int64_t kMaxEncodeStates = 32768;  // amplitude encoding: the transfer matrix is K x K
 
 }  // namespace slos

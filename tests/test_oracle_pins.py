@@ -485,3 +485,37 @@ def test_fidelity_kernel_closed_forms():
     K2 = oracle.fidelity_kernel(A, Bm, [0, 2, 0, 0])
     v = np.einsum("ij,kj->ik", A[:, :, 1].conj(), Bm[:, :, 1])
     assert np.allclose(K2, np.abs(v) ** 4, atol=1e-14)
+
+
+# ---------------------------------------------------------------- amplitude encoding
+
+def test_transfer_matrix_is_a_unitary_representation():
+    rng = np.random.default_rng(43)
+    m, n = 4, 3
+    basis = oracle.enumerate_fock(m, n)
+    U1, U2 = workloads.haar_unitaries(m, 2, rng)
+    P1, P2 = oracle.transfer_matrix(U1, basis), oracle.transfer_matrix(U2, basis)
+    # a representation: Phi(U1 U2) = Phi(U1) Phi(U2), and unitary on the full Fock basis
+    assert np.allclose(oracle.transfer_matrix(U1 @ U2, basis), P1 @ P2, atol=1e-12)
+    assert np.allclose(P1.conj().T @ P1, np.eye(len(basis)), atol=1e-12)
+    x = rng.standard_normal((3, len(basis))) + 1j * rng.standard_normal((3, len(basis)))
+    x /= np.linalg.norm(x, axis=1, keepdims=True)
+    assert np.allclose(np.linalg.norm(oracle.encoded_amplitudes(U1, x, basis), axis=1), 1.0, atol=1e-12)
+
+
+def test_transfer_matrix_of_a_permutation_permutes_the_basis():
+    m, n = 3, 2
+    basis = oracle.enumerate_fock(m, n)
+    perm = [2, 0, 1]  # input mode i -> output mode perm[i]
+    U = np.zeros((m, m), dtype=np.complex128)
+    for i, j in enumerate(perm):
+        U[j, i] = 1.0
+    P = oracle.transfer_matrix(U, basis)
+    index = {tuple(t): i for i, t in enumerate(basis)}
+    for si, s in enumerate(basis):
+        t = [0] * m
+        for i in range(m):
+            t[perm[i]] = s[i]
+        col = np.zeros(len(basis))
+        col[index[tuple(t)]] = 1.0
+        assert np.allclose(P[:, si], col, atol=1e-15)
