@@ -171,7 +171,7 @@ __global__ void mesh_bwd_kernel(MeshBwdArgs a) {
             for (int k = 0; k < MMAX - 1; ++k) {
                 if ((k & 1) == par && k + 1 < m) {
                     const int idx = base + (k - par) / 2;
-                    const Mzi z = make_mzi(th[2 * idx], th[2 * idx + 1]);
+                    const MziTab z = sm.tab[idx];  // precomputed by fill_mzi_table
                     // X_before = T^H X
                     const float2 xk = x[k], xk1 = x[k + 1];
                     const float2 bk = cfma_conj_a(z.t10, xk1, make_float2(z.t00.x * xk.x + z.t00.y * xk.y,
