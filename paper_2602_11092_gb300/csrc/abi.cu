@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -89,8 +90,10 @@ cudaError_t launch_bwd_tab(int m, const BwdArgs &a, const int32_t *ctab, int see
 }
 
 static cudaError_t init_device_once(int dev) {
+    static std::mutex mu;
     static bool done[64] = {false};
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
     if (done[dev]) return cudaSuccess;
     cudaError_t e;
     if ((e = slos_init_m8()) != cudaSuccess) return e;

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "mesh.h"
 #include "profile.h"
@@ -250,12 +252,20 @@ static cudaError_t launch_fwd(const MeshArgs &a, cudaStream_t s) {
 template <int MMAX>
 static cudaError_t launch_bwd(const MeshBwdArgs &a, cudaStream_t s) {
     const size_t smem = (size_t)(a.m * (a.m - 1) + a.n_data) * 33 * sizeof(float);
-    static bool attr_set = false;  // largest case: m = 24 needs 76 KB
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(mesh_bwd_kernel<MMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)((24 * 23 + 24) * 33 * sizeof(float)));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    // the attribute belongs to the current device's context: set it once per device
+    // (largest case: m = 24 needs 76 KB)
+    static std::mutex mu;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!attr_set[dev]) {
+            cudaError_t e = cudaFuncSetAttribute(mesh_bwd_kernel<MMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)((24 * 23 + 24) * 33 * sizeof(float)));
+            if (e != cudaSuccess) return e;
+            attr_set[dev] = true;
+        }
     }
     mesh_bwd_kernel<MMAX><<<a.B, 32, smem, s>>>(a);
     return cudaGetLastError();
