@@ -70,6 +70,14 @@ slos_status_t surr_get_param(surr_model_t model, int layer, float *w_host, float
 slos_status_t surr_set_param(surr_model_t model, int layer, const float *w_host, const float *b_host);
 slos_status_t surr_get_grad(surr_model_t model, int layer, float *gw_host, float *gb_host);
 
+/* Training checkpoint and resume: writes the FP32 weights, the Adam moments
+ * and step count, and a caller's data-stream position (stream_index) to the
+ * file `path`; surr_load restores them into a model of the same dimensions
+ * (SLOS_ERR_INVALID_ARG otherwise), so that training resumed from the file
+ * repeats, bit for bit, the training that continued in memory.  Synchronous. */
+slos_status_t surr_save(surr_model_t model, const char *path, int64_t stream_index);
+slos_status_t surr_load(surr_model_t model, const char *path, int64_t *stream_index);
+
 /* ---- checks used by the inference driver (exact path as judge) ---- */
 
 /* tv[i] = 1/2 sum_t |q[rows[i]][t] - p[i][t]| : total variation of checked

@@ -14,6 +14,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cstdio>
+#include <cstring>
 #include <cudaTypedefs.h>
 #include <stdint.h>
 #include <string.h>
@@ -623,6 +625,81 @@ slos_status_t surr_set_param(surr_model_t M, int layer, const float *w_host, con
         cudaMemcpy(M->wbt[layer], hbt.data(), nw * 2, cudaMemcpyHostToDevice);
     }
     if (b_host) cudaMemcpy(M->b[layer], b_host, fo * 4, cudaMemcpyHostToDevice);
+    return SLOS_OK;
+}
+
+// Training checkpoint: a little-endian binary file
+//   "SURRCKP1", int32 n_phases, hidden, n_layers, K, int32 step, float lr,
+//   int64 stream_index, then per layer l = 0..n_layers: W, b, m_W, v_W, m_b, v_b (float32)
+// (FP32 master weights and Adam moments; the BF16 copies are rebuilt on load).
+slos_status_t surr_save(surr_model_t M, const char *path, int64_t stream_index) {
+    if (!M || !path) return fail(SLOS_ERR_INVALID_ARG, "surr_save: NULL argument");
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(SLOS_ERR_CUDA, "surr_save: device error");
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(SLOS_ERR_INVALID_ARG, std::string("surr_save: cannot open ") + path);
+    bool ok = fwrite("SURRCKP1", 1, 8, f) == 8;
+    const int32_t hdr[5] = {M->n_phases, M->hidden, M->n_layers, M->K, M->step};
+    ok = ok && fwrite(hdr, 4, 5, f) == 5 && fwrite(&M->lr, 4, 1, f) == 1 && fwrite(&stream_index, 8, 1, f) == 1;
+    std::vector<float> h;
+    for (int l = 0; ok && l <= M->n_layers; ++l) {
+        const size_t nw = (size_t)M->fan_in[l] * M->fan_out[l], nb = (size_t)M->fan_out[l];
+        const float *arrs[6] = {M->w[l], M->b[l], M->mw[l], M->vw[l], M->mb[l], M->vb[l]};
+        const size_t lens[6] = {nw, nb, nw, nw, nb, nb};
+        for (int q = 0; ok && q < 6; ++q) {
+            h.resize(lens[q]);
+            ok = cudaMemcpy(h.data(), arrs[q], lens[q] * 4, cudaMemcpyDeviceToHost) == cudaSuccess &&
+                 fwrite(h.data(), 4, lens[q], f) == lens[q];
+        }
+    }
+    ok = (fclose(f) == 0) && ok;
+    return ok ? SLOS_OK : fail(SLOS_ERR_INTERNAL, std::string("surr_save: writing ") + path + " failed");
+}
+
+slos_status_t surr_load(surr_model_t M, const char *path, int64_t *stream_index) {
+    if (!M || !path) return fail(SLOS_ERR_INVALID_ARG, "surr_load: NULL argument");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(SLOS_ERR_INVALID_ARG, std::string("surr_load: cannot open ") + path);
+    char magic[8];
+    int32_t hdr[5];
+    float lr = 0.f;
+    int64_t idx = 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "SURRCKP1", 8) == 0 && fread(hdr, 4, 5, f) == 5 &&
+              fread(&lr, 4, 1, f) == 1 && fread(&idx, 8, 1, f) == 1;
+    if (!ok) {
+        fclose(f);
+        return fail(SLOS_ERR_INVALID_ARG, std::string("surr_load: ") + path + " is not a surrogate checkpoint");
+    }
+    if (hdr[0] != M->n_phases || hdr[1] != M->hidden || hdr[2] != M->n_layers || hdr[3] != M->K) {
+        fclose(f);
+        return fail(SLOS_ERR_INVALID_ARG, "surr_load: the checkpoint's model dimensions differ from this model's");
+    }
+    std::vector<float> h;
+    for (int l = 0; ok && l <= M->n_layers; ++l) {
+        const size_t nw = (size_t)M->fan_in[l] * M->fan_out[l], nb = (size_t)M->fan_out[l];
+        float *arrs[6] = {M->w[l], M->b[l], M->mw[l], M->vw[l], M->mb[l], M->vb[l]};
+        const size_t lens[6] = {nw, nb, nw, nw, nb, nb};
+        for (int q = 0; ok && q < 6; ++q) {
+            h.resize(lens[q]);
+            ok = fread(h.data(), 4, lens[q], f) == lens[q] &&
+                 cudaMemcpy(arrs[q], h.data(), lens[q] * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+            if (ok && q == 0) {
+                // BF16 copies of W and W^T, as the Adam kernel writes them
+                const int fi = M->fan_in[l], fo = M->fan_out[l];
+                std::vector<__nv_bfloat16> hb(nw), hbt(nw);
+                for (size_t i = 0; i < nw; ++i) {
+                    hb[i] = __float2bfloat16(h[i]);
+                    hbt[(i % fi) * fo + i / fi] = hb[i];
+                }
+                ok = cudaMemcpy(M->wb[l], hb.data(), nw * 2, cudaMemcpyHostToDevice) == cudaSuccess &&
+                     cudaMemcpy(M->wbt[l], hbt.data(), nw * 2, cudaMemcpyHostToDevice) == cudaSuccess;
+            }
+        }
+    }
+    fclose(f);
+    if (!ok) return fail(SLOS_ERR_INVALID_ARG, std::string("surr_load: ") + path + " is truncated");
+    M->step = hdr[4];
+    M->lr = lr;
+    if (stream_index) *stream_index = idx;
     return SLOS_OK;
 }
 

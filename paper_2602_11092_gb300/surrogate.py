@@ -21,6 +21,8 @@ _SIG = {
     "surr_get_param": ([_vp, _int, _vp, _vp], _int),
     "surr_set_param": ([_vp, _int, _vp, _vp], _int),
     "surr_get_grad": ([_vp, _int, _vp, _vp], _int),
+    "surr_save": ([_vp, ctypes.c_char_p, _i64], _int),
+    "surr_load": ([_vp, ctypes.c_char_p, ctypes.POINTER(_i64)], _int),
     "surr_tv_rows": ([_vp, _vp, _vp, _int, _int, _vp, _vp], _int),
     "surr_screen": ([_vp, _int, _int, _vp, _int, _vp, ctypes.POINTER(_int), _f, _vp, _vp, _vp], _int),
     "surr_scatter_rows": ([_vp, _vp, _int, _int, _vp, _vp], _int),
@@ -103,6 +105,16 @@ class Surrogate:
         w = np.ascontiguousarray(w, dtype=np.float32)
         b = np.ascontiguousarray(b, dtype=np.float32)
         B._check(lib().surr_set_param(self._h, layer, w.ctypes.data, b.ctypes.data))
+
+    def save(self, path: str, stream_index: int = 0):
+        """Checkpoint weights, Adam state and the caller's data-stream position."""
+        B._check(lib().surr_save(self._h, str(path).encode(), int(stream_index)))
+
+    def load(self, path: str) -> int:
+        """Restore a checkpoint; returns the data-stream position saved with it."""
+        idx = ctypes.c_int64()
+        B._check(lib().surr_load(self._h, str(path).encode(), ctypes.byref(idx)))
+        return idx.value
 
     def get_grad(self, layer):
         import numpy as np

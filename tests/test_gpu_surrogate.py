@@ -94,3 +94,48 @@ def test_surrogate_learns_a_small_map():
         model.train_step(phases, target, 1e-3, losses)
     S.sync_status()
     assert losses.mean().item() < 0.5 * first
+
+
+def test_training_checkpoint_resume_is_bitwise(tmp_path):
+    """Save weights, Adam state and the data-stream position mid-training;
+    a fresh model loaded from the file continues with exactly the same losses
+    and ends with exactly the same weights."""
+    from paper_2602_11092_gb300.surrogate import Surrogate
+    n_ph, K, Bn = 8, 64, 64
+
+    def batch(i):
+        rng = np.random.default_rng(5000 + i)
+        ph = torch.tensor(rng.uniform(0, 2 * np.pi, (Bn, n_ph)), dtype=torch.float32, device="cuda")
+        z = rng.standard_normal((Bn, K))
+        t = np.exp(z) / np.exp(z).sum(axis=1, keepdims=True)
+        return ph, torch.tensor(t, dtype=torch.float32, device="cuda")
+
+    def run(model, start, stop):
+        out = []
+        for i in range(start, stop):
+            ph, tg = batch(i)
+            loss = torch.empty(Bn, dtype=torch.float32, device="cuda")
+            model.train_step(ph, tg, 2e-3, loss_rows=loss)
+            out.append(loss.clone())
+        torch.cuda.synchronize()
+        return out
+
+    a = Surrogate(n_phases=n_ph, hidden=64, n_hidden_layers=2, n_outputs=K, max_batch=Bn, seed=5)
+    run(a, 0, 6)
+    path = tmp_path / "surrogate.ckpt"
+    a.save(path, stream_index=6)
+    ref = run(a, 6, 10)
+    b = Surrogate(n_phases=n_ph, hidden=64, n_hidden_layers=2, n_outputs=K, max_batch=Bn, seed=99)
+    start = b.load(path)
+    assert start == 6
+    got = run(b, start, 10)
+    for x, y in zip(ref, got):
+        assert torch.equal(x, y)
+    for layer in range(3):
+        wa, ba = a.get_param(layer)
+        wb, bb = b.get_param(layer)
+        assert np.array_equal(wa, wb) and np.array_equal(ba, bb)
+    # a model of other dimensions refuses the file
+    c = Surrogate(n_phases=n_ph, hidden=128, n_hidden_layers=2, n_outputs=K, max_batch=Bn, seed=1)
+    with pytest.raises(Exception):
+        c.load(path)
