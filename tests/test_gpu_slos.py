@@ -455,3 +455,32 @@ def test_train16_gradients_against_fd_on_8_samples(slos):
             assert np.linalg.norm(gt - gt_an) / np.linalg.norm(gt_an) < 1e-6
     g = theta.grad.cpu().double().numpy()
     assert np.linalg.norm(g - gt_sum) / np.linalg.norm(gt_sum) <= G_TOL
+
+
+def test_repeated_runs_are_bitwise_identical(slos):
+    """Every path without float atomics (PNR probabilities and amplitudes, the
+    on-chip and layered forwards, the backward and its dU reduction, the mesh
+    kernels, the collision-free space) gives the same bits run after run."""
+    m, s, B = 10, [1, 0] * 5, 37
+    mb = workloads.mesh_batch(m, B, seed=4242)
+    theta = torch.tensor(mb.theta, dtype=torch.float32, device=dev())
+    data = torch.tensor(mb.data, dtype=torch.float32, device=dev())
+    rng = np.random.default_rng(3)
+    runs = []
+    for _ in range(2):
+        res = []
+        for space in (slos.FOCK, slos.UNBUNCHED):
+            plan = slos.Plan(m, s, space=space, mem_budget_bytes=1)
+            c = torch.tensor(np.random.default_rng(4).standard_normal(plan.n_outputs), dtype=torch.float32,
+                             device=dev())
+            U = slos.mesh_unitary(m, theta, data, B)
+            ws = plan.workspace(B, training=True)
+            res.append(plan.forward(U))                      # on-chip forward
+            res.append(plan.forward(U, slos.AMPS))
+            res.append(plan.forward(U, save_for_backward=True, workspace=ws))  # layered forward
+            dU = plan.backward(U, c, ws)
+            res.append(dU)
+            res.extend(slos.mesh_unitary_backward(m, theta, data, B, dU))
+        runs.append(res)
+    for x, y in zip(*runs):
+        assert torch.equal(x, y)
