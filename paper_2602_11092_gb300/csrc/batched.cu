@@ -7,12 +7,18 @@
 // takes every other state, lane & 15 is the instance), so the ~14 instances
 // a shape typically has in a 1024-instance batch fill most lanes.  Layer k of
 // a lane group lives in workspace as complex64 [F_k][16].  Each shape's
-// transition graph is built once on the GPU at plan time as fixed-width
-// parent slots: slot = (parent rank << 5) | j for every mode j with t_j > 0,
-// 0xFFFFFFFF when unused (Sec. II-A.3: the transitions depend only on the
-// input state).  The modes in a final state's slots are its occupied-mode
-// pattern (threshold detection); its weight prod t_j! / prod s_i! is a
-// per-state table built with the slots.
+// transition graph is built once on the GPU at plan time as parent slots:
+// slot = (parent position << 5) | j for every mode j with t_j > 0, padded
+// with a slot that reads a zero row of U (Sec. II-A.3: the transitions
+// depend only on the input state).  A state with q occupied modes has q
+// parents, so each layer (but a PNR output layer, kept in Fock order for
+// the output) is stored with its states sorted, stably, by q rounded up to
+// even: a section of rows 2, 4, ..., 12 slots wide, so that no state pays
+// for the widest one.  A layer's "position" of a state is its place in that
+// order; the next layer's slots and the pattern lists use positions.  The
+// modes in a final state's slots are its occupied-mode pattern (threshold
+// detection); its weight prod t_j! / prod s_i! is a per-position table
+// built with the slots.
 // Work item = (lane group, layer k, chunk of consecutive Fock states).  Items are listed layer by
 // layer (all layer-1 items of every lane group, then all layer-2 items, ...),
 // largest lane groups first inside a layer (longest-processing-time order).
@@ -47,6 +53,7 @@ constexpr int kBMax = 20;   // modes handled by the persistent kernel (m <= 20)
 constexpr int kBLanes = 16; // instances per lane group
 constexpr uint32_t kSlotEmpty = (uint32_t)kBMax;   // parent 0, mode kBMax (a zero row of U)
 constexpr int64_t kBMaxParent = int64_t(1) << 27;  // parent ranks in 27 bits
+constexpr int kBSec = 6;    // slot-row widths 2, 4, ..., 12 (at most 12 occupied modes)
 
 struct BShape {
     int m, n, det, K;
@@ -55,7 +62,13 @@ struct BShape {
     int64_t slot_off[kMaxPhotons + 1];  // element offset of layer k's slots in the table buffer
     int64_t w_off;                      // final-layer weights prod t! / prod s! (float) [F_n]
     int64_t plist_off;                  // threshold: final states grouped by pattern [F_n]
-    int kw[kMaxPhotons + 1];            // slots per state of layer k (4, 8 or 12)
+    int kw[kMaxPhotons + 1];            // widest slot row of layer k (even, <= 12)
+    // Layer k is stored in sections of states with 2s+1 or 2s+2 occupied
+    // modes (s = 0 .. kBSec-1), each section with rows of 2s+2 slots;
+    // positions sec_pos[k][s] .. sec_pos[k][s+1]-1, rows from element
+    // sec_off[k][s] of the layer's table.  An unsorted layer is one section.
+    int sec_pos[kMaxPhotons + 1][kBSec + 1];
+    int64_t sec_off[kMaxPhotons + 1][kBSec];
     float inv_sfact;
     int nclass;                         // threshold: pattern classes j = 1 .. min(n, m)
     int pat_off[kMaxPhotons + 2];       // first pattern index with j occupied modes
@@ -97,19 +110,71 @@ struct BArgs {
     long long spin_limit;
 };
 
-// Tables of layer k of one shape, one thread per state, with the index
-// arithmetic of the single-shape kernels (common.cuh):
-//   slots[c][q] = (rank(t - e_j) << 5) | j for the q-th occupied mode j of t;
-// for the final layer also w[c] = prod t_j! / prod s_i! and, under threshold
-// detection, the state's place in the pattern-grouped list: patterns in
-// output order (|b|, then colex), and inside a pattern the states t with
-// support b in descending-lex order of t - 1_b, a composition of n - |b|
-// photons over |b| modes, ranked with the same bar formula.
+// Occupied modes of state c of layer k (descending-lex rank, bar unranking
+// of common.cuh) and the section it goes to: (q + 1) / 2 - 1.
 template <int MMAX>
-__global__ void build_slots_kernel(const BShape sh, int k, uint32_t *slots, float *w, uint32_t *plist) {
+__device__ __forceinline__ int state_section(const BShape &sh, int k, int64_t c) {
+    const int m = sh.m, L = k + m - 1;
+    int p[MMAX];
+    unrank_bars<MMAX>(c, m, L, p);
+    int q = 0;
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j)
+        if (j < m && occupation<MMAX>(j, m, L, p) > 0) ++q;
+    return (q + 1) / 2 - 1;
+}
+
+// Stable partition of layer k by section, in two passes over blocks of 256
+// consecutive states: (1) cnt[blk][s] = states of block blk in section s;
+// (2) pos[c] = base[blk][s] + rank of c among the block's states of its
+// section, base being the section start plus the counts of earlier blocks
+// (an exclusive scan the host does between the passes).
+template <int MMAX>
+__global__ void __launch_bounds__(256) section_pass_kernel(const BShape sh, int k, int *cnt, const int *base,
+                                                            int *pos) {
+    __shared__ int wcnt[8][kBSec];
+    const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int sec = c < sh.F[k] ? state_section<MMAX>(sh, k, c) : -1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int wrank = 0;
+#pragma unroll
+    for (int q = 0; q < kBSec; ++q) {
+        const unsigned bal = __ballot_sync(0xffffffffu, sec == q);
+        if (sec == q) wrank = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) wcnt[warp][q] = __popc(bal);
+    }
+    __syncthreads();
+    if (!pos) {
+        if (threadIdx.x < kBSec) {
+            int t = 0;
+            for (int w = 0; w < 8; ++w) t += wcnt[w][threadIdx.x];
+            cnt[(size_t)blockIdx.x * kBSec + threadIdx.x] = t;
+        }
+        return;
+    }
+    if (sec < 0) return;
+    int r = wrank;
+    for (int w = 0; w < warp; ++w) r += wcnt[w][sec];
+    pos[c] = base[(size_t)blockIdx.x * kBSec + sec] + r;
+}
+
+// Tables of layer k of one shape, one thread per state, with the index
+// arithmetic of the single-shape kernels (common.cuh): the row of state c
+// (at position cpos[c], or c in an unsorted layer) holds
+//   (position of t - e_j in layer k-1 << 5) | j
+// for the occupied modes j of t in mode order, then padding; ppos maps the
+// parent layer's ranks to positions (null: unsorted).  For the final layer
+// also w[position] = prod t_j! / prod s_i! and, under threshold detection,
+// the state's place in the pattern-grouped list: patterns in output order
+// (|b|, then colex), and inside a pattern the states t with support b in
+// descending-lex order of t - 1_b, a composition of n - |b| photons over
+// |b| modes, ranked with the same bar formula.
+template <int MMAX>
+__global__ void build_slots_kernel(const BShape sh, int k, uint32_t *tab, const int *ppos, const int *cpos,
+                                   float *w, uint32_t *plist) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= sh.F[k]) return;
-    const int m = sh.m, kw = sh.kw[k];
+    const int m = sh.m;
     const int L = k + m - 1;
     int p[MMAX];
     unrank_bars<MMAX>(c, m, L, p);
@@ -118,14 +183,16 @@ __global__ void build_slots_kernel(const BShape sh, int k, uint32_t *slots, floa
     float fprod = 1.f;
     uint32_t supp = 0;
     int tb[MMAX];  // occupations of the occupied modes, in mode order
-    uint32_t *dst = slots + c * kw;
+    uint32_t e[MMAX];
 #pragma unroll
     for (int j = 0; j < MMAX; ++j) {
         if (j < m) {
             const int tj = occupation<MMAX>(j, m, L, p);
             if (tj > 0) {
                 tb[q] = tj;
-                dst[q++] = ((uint32_t)(c - S) << 5) | (uint32_t)j;
+                int64_t r = c - S;
+                if (ppos) r = ppos[r];
+                e[q++] = ((uint32_t)r << 5) | (uint32_t)j;
                 fprod *= c_fact.v[tj];
                 supp |= 1u << j;
             }
@@ -133,8 +200,21 @@ __global__ void build_slots_kernel(const BShape sh, int k, uint32_t *slots, floa
         }
     }
     const int nb = q;
-    for (; q < kw; ++q) dst[q] = kSlotEmpty;
-    if (w) w[c] = fprod * sh.inv_sfact;
+    int64_t at = c;
+    uint32_t *dst;
+    int width;
+    if (cpos) {
+        const int sec = (nb + 1) / 2 - 1;
+        at = cpos[c];
+        width = 2 * sec + 2;
+        dst = tab + sh.sec_off[k][sec] + (at - sh.sec_pos[k][sec]) * width;
+    } else {
+        width = sh.kw[k];
+        dst = tab + c * width;
+    }
+    for (int i = 0; i < nb; ++i) dst[i] = e[i];
+    for (int i = nb; i < width; ++i) dst[i] = kSlotEmpty;
+    if (w) w[at] = fprod * sh.inv_sfact;
     if (plist) {
         const int np = k - nb, Lp = np + nb - 1;
         int64_t r = 0;
@@ -143,8 +223,8 @@ __global__ void build_slots_kernel(const BShape sh, int k, uint32_t *slots, floa
             cum += tb[b] - 1;
             r += (int64_t)binom(Lp - 1 - b - cum, nb - 1 - b);
         }
-        const int64_t pos = sh.pat_base[nb] + (int64_t)colex_rank(supp) * sh.pat_cnt[nb] + r;
-        plist[pos] = (uint32_t)c;
+        const int64_t pl = sh.pat_base[nb] + (int64_t)colex_rank(supp) * sh.pat_cnt[nb] + r;
+        plist[pl] = (uint32_t)at;
     }
 }
 
@@ -156,26 +236,39 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 
 enum BOut { B_NEXT = 0, B_PNR = 1, B_SCRATCH = 2 };
 
-// States c0 + half, c0 + half + 2, ... < c1 of one layer for the 16 instances
-// of a lane group (lane il of each half-warp).  us: this warp's staged column
-// of U, row j = U[j][col] per lane (row kBMax zero); prev: layer k-1 of this
-// lane (rows of 16 complex64).  Parent rows are plain (L1-cached) loads: the
-// wait on layer k-1's completion counter has ordered them after its writes.
+// Positions c0 + half, c0 + half + 2, ... < c1 of one section of a layer
+// (rows of KW slots from tab, the first row being position pos0) for the 16
+// instances of a lane group (lane il of each half-warp).  us: this warp's
+// staged column of U, row j = U[j][col] per lane (row kBMax zero); prev:
+// layer k-1 of this lane (rows of 16 complex64).  Parent rows are plain
+// (L1-cached) loads: the wait on layer k-1's completion counter has ordered
+// them after its writes.
 template <int KW>
-__device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int c0, int c1, int half,
+__device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int pos0, int c0, int c1, int half,
                                            const float2 *us, const char *prev, bool first_layer, int kind,
                                            float2 *next, float *outp, float *scr, const float *__restrict__ wtab) {
-    // states fit in 32 bits (at most C(31, 12) < 2^28 per layer)
-    const uint4 *t4 = reinterpret_cast<const uint4 *>(tab);
+    // positions fit in 32 bits (at most C(31, 12) < 2^28 per layer)
     for (int c = c0 + half; c < c1; c += 2) {
         uint32_t e[KW];
+        const uint32_t row = (uint32_t)(c - pos0) * KW;
+        if (KW % 4 == 0) {
+            const uint4 *t4 = reinterpret_cast<const uint4 *>(tab + row);
 #pragma unroll
-        for (int q4 = 0; q4 < KW / 4; ++q4) {
-            const uint4 w4 = __ldg(t4 + (uint32_t)c * (KW / 4) + q4);
-            e[4 * q4] = w4.x;
-            e[4 * q4 + 1] = w4.y;
-            e[4 * q4 + 2] = w4.z;
-            e[4 * q4 + 3] = w4.w;
+            for (int q4 = 0; q4 < KW / 4; ++q4) {
+                const uint4 w4 = __ldg(t4 + q4);
+                e[4 * q4] = w4.x;
+                e[4 * q4 + 1] = w4.y;
+                e[4 * q4 + 2] = w4.z;
+                e[4 * q4 + 3] = w4.w;
+            }
+        } else {
+            const uint2 *t2 = reinterpret_cast<const uint2 *>(tab + row);
+#pragma unroll
+            for (int q2 = 0; q2 < KW / 2; ++q2) {
+                const uint2 w2 = __ldg(t2 + q2);
+                e[2 * q2] = w2.x;
+                e[2 * q2 + 1] = w2.y;
+            }
         }
         float2 acc;
         if (first_layer) {
@@ -304,10 +397,21 @@ __global__ void __launch_bounds__(256, MINB) slos_batched_kernel(BArgs a) {
             const uint32_t *tab = a.slots + sh.slot_off[k];
             const float *wtab = reinterpret_cast<const float *>(a.slots + sh.w_off);
             const float2 *usl = us + il;
-            switch (sh.kw[k]) {
-                case 4: fwd_states<4>(tab, (int)c0, c1, half, usl, prev, k == 1, kind, next, outp, scr, wtab); break;
-                case 8: fwd_states<8>(tab, (int)c0, c1, half, usl, prev, k == 1, kind, next, outp, scr, wtab); break;
-                default: fwd_states<12>(tab, (int)c0, c1, half, usl, prev, k == 1, kind, next, outp, scr, wtab); break;
+            for (int sec = 0; sec < kBSec; ++sec) {
+                const int p0 = sh.sec_pos[k][sec];
+                const int lo = max((int)c0, p0), hi = min(c1, sh.sec_pos[k][sec + 1]);
+                if (lo >= hi) continue;
+                const uint32_t *st = tab + sh.sec_off[k][sec];
+#define SLOS_B_SEC(W) fwd_states<W>(st, p0, lo, hi, half, usl, prev, k == 1, kind, next, outp, scr, wtab)
+                switch (sec) {
+                    case 0: SLOS_B_SEC(2); break;
+                    case 1: SLOS_B_SEC(4); break;
+                    case 2: SLOS_B_SEC(6); break;
+                    case 3: SLOS_B_SEC(8); break;
+                    case 4: SLOS_B_SEC(10); break;
+                    default: SLOS_B_SEC(12); break;
+                }
+#undef SLOS_B_SEC
             }
         }
         __threadfence();
@@ -315,6 +419,10 @@ __global__ void __launch_bounds__(256, MINB) slos_batched_kernel(BArgs a) {
         if (lane == 0) atomicAdd(a.done + lo, 1);
     }
 }
+
+// Layers stored sorted by occupied modes: all but layer 1 (one section
+// anyway) and a PNR output layer (written in Fock order).
+static bool layer_sorted(const BShape &sh, int k) { return k >= 2 && !(k == sh.n && sh.det == SLOS_DETECT_PNR); }
 
 using BKernel = void (*)(BArgs);
 static BKernel batched_kernel(int minb) {
@@ -625,11 +733,31 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
     b->layer_bytes = off;
     // tables: per shape, layers 1..n of slots, the final weights, the grouped list
     int64_t tab_elems = 0;
+    int64_t max_sorted = 0;  // largest sorted layer (plan-time scratch)
     for (auto &sh : b->shapes) {
         for (int k = 1; k <= sh.n; ++k) {
-            sh.kw[k] = (std::min(sh.m, k) + 3) & ~3;
+            sh.kw[k] = (std::min(sh.m, k) + 1) & ~1;
             sh.slot_off[k] = tab_elems;
-            tab_elems += sh.F[k] * sh.kw[k];
+            int64_t off = 0;
+            if (layer_sorted(sh, k)) {
+                // states of layer k with q occupied modes: C(m, q) C(k-1, q-1)
+                max_sorted = std::max(max_sorted, sh.F[k]);
+                sh.sec_pos[k][0] = 0;
+                for (int sec = 0; sec < kBSec; ++sec) {
+                    int64_t cnt = 0;
+                    for (int q = 2 * sec + 1; q <= 2 * sec + 2 && q <= std::min(sh.m, k); ++q)
+                        cnt += binom_host(sh.m, q) * binom_host(k - 1, q - 1);
+                    sh.sec_pos[k][sec + 1] = sh.sec_pos[k][sec] + (int)cnt;
+                    off = (off + 3) & ~int64_t(3);  // 16-byte aligned rows for the uint4 reads
+                    sh.sec_off[k][sec] = off;
+                    off += cnt * (2 * sec + 2);
+                }
+            } else {
+                const int su = sh.kw[k] / 2 - 1;
+                for (int sec = 0; sec <= kBSec; ++sec) sh.sec_pos[k][sec] = sec <= su ? 0 : (int)sh.F[k];
+                off = sh.F[k] * sh.kw[k];
+            }
+            tab_elems += (off + 3) & ~int64_t(3);
         }
         const int64_t fn4 = (sh.F[sh.n] + 3) & ~int64_t(3);
         sh.w_off = tab_elems;
@@ -670,17 +798,65 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
     cudaMemcpy(b->d_ooff, b->out_off.data(), b->out_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (cudaMalloc(&b->d_slots, (size_t)tab_elems * sizeof(uint32_t)) != cudaSuccess)
         return cleanup("slos_batched_plan: transition tables");
+    // plan-time scratch: positions of two consecutive layers, per-block section counts
+    const int64_t max_blk = (max_sorted + 255) / 256;
+    int *d_pos[2] = {nullptr, nullptr};
+    int *d_cnt = nullptr, *d_base = nullptr;
+    auto free_scratch = [&]() {
+        cudaFree(d_pos[0]);
+        cudaFree(d_pos[1]);
+        cudaFree(d_cnt);
+        cudaFree(d_base);
+    };
+    if (max_sorted > 0 &&
+        (cudaMalloc(&d_pos[0], (size_t)max_sorted * sizeof(int)) != cudaSuccess ||
+         cudaMalloc(&d_pos[1], (size_t)max_sorted * sizeof(int)) != cudaSuccess ||
+         cudaMalloc(&d_cnt, (size_t)max_blk * kBSec * sizeof(int)) != cudaSuccess ||
+         cudaMalloc(&d_base, (size_t)max_blk * kBSec * sizeof(int)) != cudaSuccess)) {
+        free_scratch();
+        return cleanup("slos_batched_plan: plan-time scratch");
+    }
+    std::vector<int> hcnt, hbase;
     for (auto &sh : b->shapes) {
+        const int *ppos = nullptr;
         for (int k = 1; k <= sh.n; ++k) {
             const int bs = 256;
             const unsigned grid = (unsigned)((sh.F[k] + bs - 1) / bs);
+            int *cpos = nullptr;
+            if (layer_sorted(sh, k)) {
+                cpos = d_pos[k & 1];
+                section_pass_kernel<kBMax><<<grid, bs>>>(sh, k, d_cnt, nullptr, nullptr);
+                hcnt.resize((size_t)grid * kBSec);
+                hbase.resize((size_t)grid * kBSec);
+                if (cudaMemcpy(hcnt.data(), d_cnt, hcnt.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                    free_scratch();
+                    return cleanup("slos_batched_plan: sorting a layer by occupied modes failed");
+                }
+                bool ok = true;
+                for (int sec = 0; sec < kBSec; ++sec) {
+                    int64_t run = sh.sec_pos[k][sec];
+                    for (unsigned blk = 0; blk < grid; ++blk) {
+                        hbase[(size_t)blk * kBSec + sec] = (int)run;
+                        run += hcnt[(size_t)blk * kBSec + sec];
+                    }
+                    ok = ok && run == sh.sec_pos[k][sec + 1];  // the closed-form section sizes
+                }
+                if (!ok) {
+                    free_scratch();
+                    return cleanup("slos_batched_plan: section sizes disagree with C(m, q) C(k-1, q-1)");
+                }
+                cudaMemcpy(d_base, hbase.data(), hbase.size() * sizeof(int), cudaMemcpyHostToDevice);
+                section_pass_kernel<kBMax><<<grid, bs>>>(sh, k, nullptr, d_base, cpos);
+            }
             float *w = k == sh.n ? reinterpret_cast<float *>(b->d_slots + sh.w_off) : nullptr;
             uint32_t *pl = (k == sh.n && sh.det == SLOS_DETECT_THRESHOLD) ? b->d_slots + sh.plist_off : nullptr;
-            build_slots_kernel<kBMax><<<grid, bs>>>(sh, k, b->d_slots + sh.slot_off[k], w, pl);
+            build_slots_kernel<kBMax><<<grid, bs>>>(sh, k, b->d_slots + sh.slot_off[k], ppos, cpos, w, pl);
+            ppos = cpos;
         }
     }
-    if (cudaStreamSynchronize(0) != cudaSuccess || cudaGetLastError() != cudaSuccess)
-        return cleanup("slos_batched_plan: building the transition tables failed");
+    const bool built = cudaStreamSynchronize(0) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    free_scratch();
+    if (!built) return cleanup("slos_batched_plan: building the transition tables failed");
     slos_status_t st = build_items(b, b->chunk);
     if (st != SLOS_OK) {
         batched_destroy(p);
