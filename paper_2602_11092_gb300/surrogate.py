@@ -151,8 +151,9 @@ class SurrogateLayer:
         self.wdata = mb.w
         self.plan = B.Plan(self.m, self.s)
         self.K = self.plan.n_outputs
-        self.model = Surrogate(n_phases=self.theta.numel() + self.m, hidden=hidden, n_hidden_layers=n_hidden_layers,
-                               n_outputs=self.K, max_batch=max_batch, seed=seed)
+        self.harmonics = torch.arange(1, 13, dtype=torch.float32, device=self.device)
+        self.model = Surrogate(n_phases=self.harmonics.numel() * self.m, hidden=hidden,
+                               n_hidden_layers=n_hidden_layers, n_outputs=self.K, max_batch=max_batch, seed=seed)
         self.max_batch = max_batch
         occ, _ = B.device_index_table(self.m, self.n, 0, self.K, device=self.device)
         self.occ = occ
@@ -164,7 +165,15 @@ class SurrogateLayer:
         return torch.tensor(x * self.wdata[None, :], dtype=torch.float32, device=self.device)
 
     def phases(self, data: torch.Tensor) -> torch.Tensor:
-        return torch.cat([self.theta.expand(data.shape[0], -1), data], dim=1).contiguous()
+        """The model's 144 phase inputs: h * x_j for harmonics h = 1..12 of the
+        12 data phases (the model takes sin and cos of each).  The 132
+        trainable phases are the same for every sample and carry nothing; the
+        data phases sit in one column between the two halves of the mesh, so
+        every amplitude is a homogeneous polynomial of degree n = 6 in the
+        e^{i x_j} and each probability a trigonometric polynomial of degree
+        <= 6 in every x_j: its harmonics are the natural inputs."""
+        Bn = data.shape[0]
+        return (data[:, None, :] * self.harmonics[None, :, None]).reshape(Bn, -1).contiguous()
 
     def exact(self, data: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         U = B.mesh_unitary(self.m, self.theta, data.contiguous(), data.shape[0])
