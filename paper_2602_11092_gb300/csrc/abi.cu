@@ -958,7 +958,7 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
         t.kw = p->tab.layer[k].kw;
         t.w = p->tab.w;
         t.pat = p->tab.pat;
-        SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, NG, kFwdTabMinBlocks), s));
+        SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, NG, fwd_tab_min_blocks(epi)), s));
     } else {
         SLOS_CUDA(launch_fwd(p->m, a, epi, save, bx, s));
     }

@@ -10,8 +10,9 @@
 // its KW parent rows (coalesced 256-byte loads) are issued together, and the
 // sum runs over all KW slots without branches.  U[j, c_k] for the 32
 // instances sits in shared memory, one row per mode plus the zero row.  The
-// register budget (kFwdTabMinBlocks resident blocks) keeps enough warps in
-// flight to cover the gather latency.
+// register budget (fwd_tab_min_blocks resident blocks) keeps enough warps in
+// flight to cover the gather latency: the walk is bound by the latency of each
+// warp's chain (slot row, gathers, sums), so resident warps are what count.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,7 +23,7 @@
 namespace slos {
 
 template <int EPI, bool SAVE, int KW>
-__global__ void __launch_bounds__(kThreads, kFwdTabMinBlocks) slos_fwd_tab_kernel(FwdArgs a, TabArgs t) {
+__global__ void __launch_bounds__(kThreads, fwd_tab_min_blocks(EPI)) slos_fwd_tab_kernel(FwdArgs a, TabArgs t) {
     __shared__ float2 us[kMaxModes + 1][32];
     extern __shared__ float4 smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -40,7 +41,8 @@ __global__ void __launch_bounds__(kThreads, kFwdTabMinBlocks) slos_fwd_tab_kerne
     float2 *nextg = a.next + (size_t)grp * (size_t)a.Fk * kLanes + lane;
     const float2 *usl = &us[0][lane];
     const uint4 *slots = reinterpret_cast<const uint4 *>(t.slots);
-    float *tile = reinterpret_cast<float *>(smem_raw) + warp * (32 * 33 * (EPI == EPI_AMPS ? 2 : 1));
+    constexpr int TS = kFwdTabTile;  // states per output tile
+    float *tile = reinterpret_cast<float *>(smem_raw) + warp * (32 * (TS + 1) * (EPI == EPI_AMPS ? 2 : 1));
     const int64_t nchunks = (a.Fk + 31) / 32;
     const int64_t wstride = (int64_t)gridDim.x * kWarpsPerBlock;
     const bool first_layer = a.k == 1;
@@ -82,9 +84,9 @@ __global__ void __launch_bounds__(kThreads, kFwdTabMinBlocks) slos_fwd_tab_kerne
             if (EPI != EPI_STORE) {
                 const float w = __shfl_sync(0xffffffffu, wl, ci);
                 if (EPI == EPI_PROBS) {
-                    tile[lane * 33 + ci] = w * (acc.x * acc.x + acc.y * acc.y);
+                    tile[lane * (TS + 1) + (ci & (TS - 1))] = w * (acc.x * acc.x + acc.y * acc.y);
                 } else if (EPI == EPI_AMPS) {
-                    reinterpret_cast<float2 *>(tile)[lane * 33 + ci] = cscale(acc, sqrtf(w));
+                    reinterpret_cast<float2 *>(tile)[lane * (TS + 1) + (ci & (TS - 1))] = cscale(acc, sqrtf(w));
                 } else if (EPI == EPI_THRESH) {
                     const int pat = __shfl_sync(0xffffffffu, patl, ci);
                     const float pr = w * (acc.x * acc.x + acc.y * acc.y);
@@ -97,31 +99,35 @@ __global__ void __launch_bounds__(kThreads, kFwdTabMinBlocks) slos_fwd_tab_kerne
                     run_val += pr;
                 }
             }
+            // a full tile (or the chunk's last states) goes out: 32 / TS
+            // instances per pass, TS consecutive outputs each
+            if ((EPI == EPI_PROBS || EPI == EPI_AMPS) && ((ci & (TS - 1)) == TS - 1 || ci == nc - 1)) {
+                __syncwarp();
+                const int cb = ci & ~(TS - 1), cnt = ci - cb + 1;
+                const int il = lane & (TS - 1);
+                for (int i = lane / TS; i < kLanes; i += 32 / TS) {
+                    const int ii = grp * kLanes + i;
+                    if (ii < a.B && il < cnt) {
+                        const int64_t o = (int64_t)ii * a.K + c0 + cb + il;
+                        if (EPI == EPI_PROBS) {
+                            reinterpret_cast<float *>(a.out)[o] = tile[i * (TS + 1) + il];
+                        } else {
+                            reinterpret_cast<float2 *>(a.out)[o] = reinterpret_cast<const float2 *>(tile)[i * (TS + 1) + il];
+                        }
+                    }
+                }
+                __syncwarp();
+            }
         }
         if (EPI == EPI_THRESH && run_pat >= 0 && valid)
             atomicAdd(reinterpret_cast<float *>(a.out) + (int64_t)inst * a.K + run_pat, run_val);
-        if (EPI == EPI_PROBS || EPI == EPI_AMPS) {
-            __syncwarp();
-            for (int i = 0; i < kLanes; ++i) {
-                const int ii = grp * kLanes + i;
-                if (ii < a.B && lane < nc) {
-                    if (EPI == EPI_PROBS) {
-                        reinterpret_cast<float *>(a.out)[(int64_t)ii * a.K + c0 + lane] = tile[i * 33 + lane];
-                    } else {
-                        reinterpret_cast<float2 *>(a.out)[(int64_t)ii * a.K + c0 + lane] =
-                            reinterpret_cast<const float2 *>(tile)[i * 33 + lane];
-                    }
-                }
-            }
-            __syncwarp();
-        }
     }
 }
 
 template <int KW>
 static cudaError_t tab_attrs() {
     cudaError_t e;
-    const int sp = (int)fwd_smem_bytes(EPI_PROBS), sa = (int)fwd_smem_bytes(EPI_AMPS);
+    const int sp = (int)fwd_tab_smem_bytes(EPI_PROBS), sa = (int)fwd_tab_smem_bytes(EPI_AMPS);
     if ((e = cudaFuncSetAttribute(slos_fwd_tab_kernel<EPI_PROBS, false, KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sp)))
         return e;
     if ((e = cudaFuncSetAttribute(slos_fwd_tab_kernel<EPI_PROBS, true, KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sp)))
@@ -141,7 +147,7 @@ cudaError_t slos_tab_init() {
 template <int KW>
 static cudaError_t launch_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, cudaStream_t s) {
     dim3 grid(blocks_x, a.NG);
-    const size_t sm = fwd_smem_bytes(epi);
+    const size_t sm = fwd_tab_smem_bytes(epi);
     switch (epi * 2 + (save ? 1 : 0)) {
         case 0:
         case 1: slos_fwd_tab_kernel<EPI_STORE, true, KW><<<grid, kThreads, 0, s>>>(a, t); break;

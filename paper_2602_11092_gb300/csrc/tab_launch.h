@@ -19,8 +19,20 @@ constexpr uint32_t kSlotEmpty = (uint32_t)kMaxModes;
 constexpr int slot_width(int m, int k) { return ((m < k ? m : k) + 3) & ~3; }
 
 // Resident 256-thread blocks per SM the table forward's registers are sized
-// for (48 registers); launch grids are sized to fill them.
-constexpr int kFwdTabMinBlocks = 5;
+// for; launch grids are sized to fill them.  Measured on the m=16, n=8
+// training step: the final layer runs fastest at 8 blocks (32 registers, 64
+// warps per SM, which its output tile of kFwdTabTile states per warp leaves
+// room for), the intermediate layers at 5 (48 registers: at 32 they lose more
+// to the smaller register budget than they gain from the warps).
+constexpr int kFwdTabMinBlocksStore = 5;
+constexpr int kFwdTabMinBlocksFinal = 8;
+constexpr int kFwdTabTile = 16;
+constexpr int fwd_tab_min_blocks(int epi) { return epi == 0 ? kFwdTabMinBlocksStore : kFwdTabMinBlocksFinal; }
+// dynamic shared memory of a table-forward block: per warp a [32][kFwdTabTile + 1] tile
+inline size_t fwd_tab_smem_bytes(int epi) {
+    const size_t cells = (size_t)kWarpsPerBlock * 32 * (kFwdTabTile + 1);
+    return epi == 1 ? cells * sizeof(float) : (epi == 2 ? cells * sizeof(float2) : 0);
+}
 
 cudaError_t slos_tab_init();
 cudaError_t slos_launch_fwd_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, cudaStream_t s);
