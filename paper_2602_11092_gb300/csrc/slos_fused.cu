@@ -9,7 +9,13 @@
 // threads walk the states of a layer (lane = state), read each state's
 // fixed-width parent slots once and form the sums of all NI instances from
 // shared memory.  The U columns of all n photons are staged once, with a zero
-// row (mode kMaxModes) that the padding slots name.  Output writes are
+// row (mode kMaxModes) that the padding slots name.  With lane = state the
+// padding slots differ from lane to lane, so they are skipped by predicate:
+// a predicated-off lane sends no shared-memory request, and the shared-memory
+// pipe is this kernel's limit (the last layers of m=12, n=6 have 8-slot rows
+// for 3.8 and 4.2 occupied modes on average; m=12: 0.299 -> 0.275 ms per
+// 4096 instances).  Plans with only 4-slot rows run the plain sum (m=8, n=4
+// measured slower with the predicated kernel).  Output writes are
 // coalesced: consecutive threads write consecutive states of one instance.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -17,13 +23,14 @@
 #include "common.cuh"
 #include "fused.h"
 #include "slos_kernels.cuh"
+#include "tab_launch.h"
 
 namespace slos {
 
 constexpr int kFusedMaxNI = 4;
 constexpr int kUsRow = kMaxModes + 1;
 
-template <int EPI, int KW, int THREADS>
+template <int EPI, int KW, int THREADS, bool PRED>
 __device__ __forceinline__ void fused_layer(const FusedArgs &a, int k, const float2 *us, const float2 *prev,
                                             int cap_prev, float2 *cur, int cap_cur, int inst0, int ni) {
     const int Fk = a.F[k];
@@ -54,7 +61,9 @@ __device__ __forceinline__ void fused_layer(const FusedArgs &a, int k, const flo
                     const float2 *pv = prev + (size_t)i * cap_prev;
                     acc = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int q = 0; q < KW; ++q) acc = cfma(u[e[q] & 31u], pv[e[q] >> 5], acc);
+                    for (int q = 0; q < KW; ++q)
+                        if (!PRED || KW == 4 || q == 0 || e[q] != kSlotEmpty)
+                            acc = cfma(u[e[q] & 31u], pv[e[q] >> 5], acc);
                 }
                 if (!final_layer) {
                     cur[(size_t)i * cap_cur + c] = acc;
@@ -69,7 +78,7 @@ __device__ __forceinline__ void fused_layer(const FusedArgs &a, int k, const flo
     }
 }
 
-template <int EPI, int THREADS>
+template <int EPI, int THREADS, bool PRED>
 __global__ void __launch_bounds__(THREADS) slos_fwd_fused_kernel(FusedArgs a) {
     extern __shared__ float2 sm[];
     const int NI = a.NI;
@@ -93,9 +102,9 @@ __global__ void __launch_bounds__(THREADS) slos_fwd_fused_kernel(FusedArgs a) {
         float2 *cur = (k & 1) ? buf1 : buf0;
         const int cap_prev = a.cap[(k - 1) & 1], cap_cur = a.cap[k & 1];
         switch (a.kw[k]) {
-            case 4: fused_layer<EPI, 4, THREADS>(a, k, us, prev, cap_prev, cur, cap_cur, inst0, ni); break;
-            case 8: fused_layer<EPI, 8, THREADS>(a, k, us, prev, cap_prev, cur, cap_cur, inst0, ni); break;
-            default: fused_layer<EPI, 12, THREADS>(a, k, us, prev, cap_prev, cur, cap_cur, inst0, ni); break;
+            case 4: fused_layer<EPI, 4, THREADS, PRED>(a, k, us, prev, cap_prev, cur, cap_cur, inst0, ni); break;
+            case 8: fused_layer<EPI, 8, THREADS, PRED>(a, k, us, prev, cap_prev, cur, cap_cur, inst0, ni); break;
+            default: fused_layer<EPI, 12, THREADS, PRED>(a, k, us, prev, cap_prev, cur, cap_cur, inst0, ni); break;
         }
         __syncthreads();
     }
@@ -107,34 +116,44 @@ size_t slos_fused_smem(int NI, int n, const int cap[2]) {
 
 int slos_fused_max_ni() { return kFusedMaxNI; }
 
-template <int THREADS>
+template <int THREADS, bool PRED>
 static cudaError_t fused_attrs() {
-    cudaError_t e = cudaFuncSetAttribute(slos_fwd_fused_kernel<EPI_PROBS, THREADS>,
+    cudaError_t e = cudaFuncSetAttribute(slos_fwd_fused_kernel<EPI_PROBS, THREADS, PRED>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemLimit);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(slos_fwd_fused_kernel<EPI_AMPS, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kFusedSmemLimit);
+    return cudaFuncSetAttribute(slos_fwd_fused_kernel<EPI_AMPS, THREADS, PRED>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemLimit);
 }
 
 cudaError_t slos_fused_init() {
-    cudaError_t e = fused_attrs<512>();
-    if (e != cudaSuccess) return e;
-    return fused_attrs<1024>();
+    cudaError_t e;
+    if ((e = fused_attrs<512, false>()) != cudaSuccess) return e;
+    if ((e = fused_attrs<512, true>()) != cudaSuccess) return e;
+    if ((e = fused_attrs<1024, false>()) != cudaSuccess) return e;
+    return fused_attrs<1024, true>();
 }
 
-template <int THREADS>
+template <int THREADS, bool PRED>
 static cudaError_t launch_fused(const FusedArgs &a, int epi, cudaStream_t s) {
     const unsigned grid = (unsigned)((a.B + a.NI - 1) / a.NI);
     const size_t sm = slos_fused_smem(a.NI, a.n, a.cap);
-    if (epi == EPI_PROBS) slos_fwd_fused_kernel<EPI_PROBS, THREADS><<<grid, THREADS, sm, s>>>(a);
-    else if (epi == EPI_AMPS) slos_fwd_fused_kernel<EPI_AMPS, THREADS><<<grid, THREADS, sm, s>>>(a);
+    if (epi == EPI_PROBS) slos_fwd_fused_kernel<EPI_PROBS, THREADS, PRED><<<grid, THREADS, sm, s>>>(a);
+    else if (epi == EPI_AMPS) slos_fwd_fused_kernel<EPI_AMPS, THREADS, PRED><<<grid, THREADS, sm, s>>>(a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
+template <int THREADS>
+static cudaError_t launch_fused_t(const FusedArgs &a, int epi, cudaStream_t s) {
+    // the predicated walk only where some layer has rows wider than 4 slots
+    bool wide = false;
+    for (int k = 1; k <= a.n; ++k) wide = wide || a.kw[k] > 4;
+    return wide ? launch_fused<THREADS, true>(a, epi, s) : launch_fused<THREADS, false>(a, epi, s);
+}
+
 cudaError_t slos_launch_fused(const FusedArgs &a, int epi, cudaStream_t s) {
-    if (a.threads == 1024) return launch_fused<1024>(a, epi, s);
-    if (a.threads == 512) return launch_fused<512>(a, epi, s);
+    if (a.threads == 1024) return launch_fused_t<1024>(a, epi, s);
+    if (a.threads == 512) return launch_fused_t<512>(a, epi, s);
     return cudaErrorInvalidValue;
 }
 
