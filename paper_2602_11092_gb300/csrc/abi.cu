@@ -168,7 +168,20 @@ static void bars_of(uint64_t z, int m, int L, int *p, int *t) {
     }
 }
 
+static void free_fused_tables(slos_plan_s *p) {
+    for (auto &L : p->tab.fused) {
+        if (L.rows) cudaFree(L.rows);
+        if (L.blk) cudaFree(L.blk);
+    }
+    p->tab.fused.clear();
+    if (p->tab.fused_id) cudaFree(p->tab.fused_id);
+    if (p->tab.fused_w) cudaFree(p->tab.fused_w);
+    p->tab.fused_id = nullptr;
+    p->tab.fused_w = nullptr;
+}
+
 static void free_tables(slos_plan_s *p) {
+    free_fused_tables(p);
     for (auto &L : p->tab.layer) {
         if (L.slots) cudaFree(L.slots);
         if (L.ctab) cudaFree(L.ctab);
@@ -486,14 +499,101 @@ static void build_encode_tables(slos_plan_s *p) {
     cudaMemcpy(p->tab.gfact, g.data(), g.size() * 4, cudaMemcpyHostToDevice);
 }
 
+// Sorted on-chip layout (tables.h, FusedLayer) from the plan's slot tables.
+// Returns false (nothing kept) on an allocation failure.
+static bool build_fused_tables(slos_plan_s *p) {
+    const int n = p->n;
+    std::vector<std::vector<int32_t>> pos(n + 1);
+    pos[0].assign(1, 0);
+    std::vector<float> wnat(p->F[n]);
+    if (cudaMemcpy(wnat.data(), p->tab.w, wnat.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    p->tab.fused.assign(n + 1, FusedLayer());
+    for (int k = 1; k <= n; ++k) {
+        const int64_t Fk = p->F[k];
+        const int kw = p->tab.layer[k].kw;
+        std::vector<uint32_t> nat((size_t)Fk * kw);
+        if (cudaMemcpy(nat.data(), p->tab.layer[k].slots, nat.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return false;
+        std::vector<int> occ(Fk, 0);
+        int qmax = 0;
+        for (int64_t c = 0; c < Fk; ++c) {
+            while (occ[c] < kw && nat[(size_t)c * kw + occ[c]] != kSlotEmpty) ++occ[c];
+            qmax = std::max(qmax, occ[c]);
+        }
+        std::vector<std::vector<int64_t>> by_q(qmax + 1);
+        for (int64_t c = 0; c < Fk; ++c) by_q[occ[c]].push_back(c);
+        pos[k].assign(Fk, -1);
+        std::vector<uint32_t> rows, blk;
+        std::vector<int32_t> id;
+        std::vector<float> wf;
+        int fpad = 0;
+        for (int q = 1; q <= qmax; ++q) {
+            const auto &list = by_q[q];
+            for (size_t b0 = 0; b0 < list.size(); b0 += 32) {
+                const size_t off = rows.size();
+                blk.push_back((uint32_t)(off << 4) | (uint32_t)q);
+                rows.resize(off + (size_t)q * 32, kSlotEmpty);
+                for (int l = 0; l < 32; ++l) {
+                    const int position = fpad + l;
+                    int32_t out_id = -1;
+                    float wv = 0.f;
+                    if (b0 + l < list.size()) {
+                        const int64_t c = list[b0 + l];
+                        pos[k][c] = position;
+                        for (int i = 0; i < q; ++i) {
+                            const uint32_t e = nat[(size_t)c * kw + i];
+                            const uint32_t pp = (uint32_t)pos[k - 1][e >> 5];
+                            rows[off + (size_t)i * 32 + l] = (pp << 5) | (e & 31u);
+                        }
+                        out_id = (int32_t)c;
+                        if (k == n) wv = wnat[c];
+                    }
+                    if (k == n) {
+                        id.push_back(out_id);
+                        wf.push_back(wv);
+                    }
+                }
+                fpad += 32;
+            }
+        }
+        FusedLayer &FL = p->tab.fused[k];
+        FL.nblk = (int)blk.size();
+        FL.fpad = fpad;
+        if (cudaMalloc(&FL.rows, rows.size() * 4) != cudaSuccess || cudaMalloc(&FL.blk, blk.size() * 4) != cudaSuccess)
+            return false;
+        cudaMemcpy(FL.rows, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(FL.blk, blk.data(), blk.size() * 4, cudaMemcpyHostToDevice);
+        if (k == n) {
+            if (cudaMalloc(&p->tab.fused_id, id.size() * 4) != cudaSuccess ||
+                cudaMalloc(&p->tab.fused_w, wf.size() * 4) != cudaSuccess)
+                return false;
+            cudaMemcpy(p->tab.fused_id, id.data(), id.size() * 4, cudaMemcpyHostToDevice);
+            cudaMemcpy(p->tab.fused_w, wf.data(), wf.size() * 4, cudaMemcpyHostToDevice);
+        }
+        if (k > 1) pos[k - 1].clear();
+    }
+    return true;
+}
+
 // On-chip inference forward: PNR table plans whose intermediate layers fit in
 // shared memory for at least one instance.  Small plans (up to 24 KB per
 // instance): as many instances per CTA as fit in half the limit, two
 // 512-thread CTAs per SM.  Larger plans: as many instances as fit in the whole
 // limit, one 1024-thread CTA per SM, so each parent-slot row read from L2
 // serves more instances (measured on m=12, n=6 and m=10, n=5).
+//
+// Large plans walk the sorted layout (build_fused_tables) when it still fits
+// one instance; small plans walk Fock order (slos_fused.cu gives the timings).
+static int fused_ni_for(const int c2[2], int n, size_t limit) {
+    int ni = 0;
+    for (int q = 1; q <= slos_fused_max_ni(); q *= 2)
+        if (slos_fused_smem(q, n, c2) <= limit) ni = q;
+    return ni;
+}
+
 static void choose_fused(slos_plan_s *p) {
     p->fused_ni = 0;
+    p->fused_sorted = false;
     if (!p->tab.enabled || p->det != SLOS_DETECT_PNR) return;
     int64_t cap[2] = {1, 1};
     for (int k = 1; k < p->n; ++k) cap[k & 1] = std::max(cap[k & 1], p->F[k]);
@@ -501,14 +601,29 @@ static void choose_fused(slos_plan_s *p) {
     const int c2[2] = {(int)cap[0], (int)cap[1]};
     const bool large = slos_fused_smem(1, p->n, c2) > 24 * 1024;
     const size_t limit = large ? kFusedSmemLimit : kFusedSmemLimit / 2;
-    int ni = 0;
-    for (int q = 1; q <= slos_fused_max_ni(); q *= 2)
-        if (slos_fused_smem(q, p->n, c2) <= limit) ni = q;
+    const int ni = fused_ni_for(c2, p->n, limit);
     if (ni == 0) return;
     p->fused_ni = ni;
     p->fused_threads = large ? 1024 : 512;
     p->fused_cap[0] = c2[0];
     p->fused_cap[1] = c2[1];
+    if (!large) return;
+    if (!build_fused_tables(p)) {
+        free_fused_tables(p);
+        return;
+    }
+    int64_t sc[2] = {32, 32};
+    for (int k = 1; k < p->n; ++k) sc[k & 1] = std::max<int64_t>(sc[k & 1], p->tab.fused[k].fpad);
+    const int s2[2] = {(int)sc[0], (int)sc[1]};
+    const int sni = fused_ni_for(s2, p->n, kFusedSmemLimit);
+    if (sni == 0) {
+        free_fused_tables(p);
+        return;
+    }
+    p->fused_sorted = true;
+    p->fused_ni = sni;
+    p->fused_cap[0] = s2[0];
+    p->fused_cap[1] = s2[1];
 }
 
 // ------------------------------------------------------------------ layouts
@@ -989,11 +1104,19 @@ slos_status_t slos_forward(slos_plan_t p, const void *U, int batch, slos_output_
         memset(&fa, 0, sizeof(fa));
         fa.U = Ud;
         fa.out = out;
+        fa.sorted = p->fused_sorted ? 1 : 0;
         fa.w = p->tab.w;
+        fa.ws = p->tab.fused_w;
+        fa.id = p->tab.fused_id;
         for (int k = 1; k <= n; ++k) {
             fa.slots[k] = p->tab.layer[k].slots;
             fa.kw[k] = p->tab.layer[k].kw;
             fa.F[k] = (int)p->F[k];
+            if (p->fused_sorted) {
+                fa.rows[k] = p->tab.fused[k].rows;
+                fa.blk[k] = p->tab.fused[k].blk;
+                fa.nblk[k] = p->tab.fused[k].nblk;
+            }
             fa.cols[k - 1] = p->cols[k - 1];
         }
         fa.F[0] = 1;

@@ -67,5 +67,6 @@ struct slos_plan_s {
     int fused_ni = 0;       // instances per CTA of the on-chip inference forward (0: not eligible)
     int fused_threads = 512;    // its CTA size
     int fused_cap[2] = {1, 1};  // its buffer capacities (states per instance, even / odd layers)
+    bool fused_sorted = false;  // walks the sorted layout (tab.fused) instead of Fock order
     slos::BatchedPlan *batched;
 };

@@ -5,18 +5,26 @@
 // Used for PNR table plans without activation saving whose two largest
 // intermediate layers fit in shared memory for at least one instance (for
 // example m=12, n=6: 4368 + 1365 states, 46 KB per instance).  Layer k of
-// instance i lives in buffer (k & 1) as complex64 [NI][cap]; the CTA's
-// threads walk the states of a layer (lane = state), read each state's
-// fixed-width parent slots once and form the sums of all NI instances from
-// shared memory.  The U columns of all n photons are staged once, with a zero
-// row (mode kMaxModes) that the padding slots name.  With lane = state the
-// padding slots differ from lane to lane, so they are skipped by predicate:
-// a predicated-off lane sends no shared-memory request, and the shared-memory
-// pipe is this kernel's limit (the last layers of m=12, n=6 have 8-slot rows
-// for 3.8 and 4.2 occupied modes on average; m=12: 0.299 -> 0.275 ms per
-// 4096 instances).  Plans with only 4-slot rows run the plain sum (m=8, n=4
-// measured slower with the predicated kernel).  Output writes are
-// coalesced: consecutive threads write consecutive states of one instance.
+// instance i lives in buffer (k & 1) as complex64 [NI][cap].  The U columns of
+// all n photons are staged once, with a zero row (mode kMaxModes) that the
+// padding slots name.  Two walks of the layers:
+//
+// * Fock order (slos_fwd_fused_kernel, small plans): lane = state, each state
+//   reads its fixed-width parent slots once and forms the sums of all NI
+//   instances; output writes are coalesced.  Padding slots differ from lane to
+//   lane, so for plans with 8- or 12-slot rows they are predicated off (a
+//   predicated-off lane sends no shared-memory request, and the shared-memory
+//   pipe limits this walk).
+// * Sorted order (slos_fwd_fused_sorted_kernel, plans that need 1024-thread
+//   CTAs): the states of a layer sorted by their number q of occupied modes,
+//   runs of equal q padded to 32 (tables.h, FusedLayer).  A warp takes a
+//   block of 32 positions whose states all have q parents: one loop of q
+//   slots, no padding slots, no predicates, slot rows read slot-major
+//   (coalesced).  The final layer writes each output to its Fock index.
+//   Measured per 4096 instances: m=12, n=6 0.275 -> 0.246 ms; the small plans
+//   are slower this way (m=10, n=5 0.043 -> 0.045 ms, m=8, n=4 0.013 ->
+//   0.017 ms: padding runs to 32 and scattered writes cost more than the
+//   shorter walk saves).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -110,6 +118,99 @@ __global__ void __launch_bounds__(THREADS) slos_fwd_fused_kernel(FusedArgs a) {
     }
 }
 
+// one block of 32 positions of layer k, all with Q parents
+template <int EPI, int Q>
+__device__ __forceinline__ void fused_block(const FusedArgs &a, int k, const float2 *uk, const float2 *prev,
+                                            int cap_prev, float2 *cur, int cap_cur, int inst0, int ni,
+                                            const uint32_t *row, int p) {
+    const int lane = threadIdx.x & 31;
+    const size_t us_inst = (size_t)a.n * kUsRow;  // U rows of one instance
+    uint32_t e[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) e[q] = __ldg(row + q * 32 + lane);
+    const bool final_layer = k == a.n;
+    int oc = -1;
+    float wc = 0.f;
+    if (final_layer) {
+        oc = __ldg(a.id + p);
+        wc = __ldg(a.ws + p);
+    }
+#pragma unroll
+    for (int i = 0; i < kFusedMaxNI; ++i) {
+        if (i < ni) {
+            const float2 *u = uk + i * us_inst;
+            float2 acc;
+            if (k == 1) {
+                acc = u[e[0] & 31u];  // one photon: a_1(e_j) = U[j, c_1]
+            } else {
+                const float2 *pv = prev + (size_t)i * cap_prev;
+                acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < Q; ++q) acc = cfma(u[e[q] & 31u], pv[e[q] >> 5], acc);
+            }
+            if (!final_layer) {
+                cur[(size_t)i * cap_cur + p] = acc;
+            } else if (oc >= 0) {
+                if (EPI == EPI_PROBS)
+                    reinterpret_cast<float *>(a.out)[(size_t)(inst0 + i) * a.K + oc] = wc * (acc.x * acc.x + acc.y * acc.y);
+                else
+                    reinterpret_cast<float2 *>(a.out)[(size_t)(inst0 + i) * a.K + oc] = cscale(acc, sqrtf(wc));
+            }
+        }
+    }
+}
+
+template <int EPI, int THREADS>
+__global__ void __launch_bounds__(THREADS) slos_fwd_fused_sorted_kernel(FusedArgs a) {
+    extern __shared__ float2 sm[];
+    const int NI = a.NI;
+    float2 *us = sm;                                  // [NI][n][kUsRow]
+    float2 *buf0 = us + (size_t)NI * a.n * kUsRow;    // [NI][cap0]
+    float2 *buf1 = buf0 + (size_t)NI * a.cap[0];      // [NI][cap1]
+    const int inst0 = blockIdx.x * NI;
+    const int ni = min(NI, a.B - inst0);
+    const int nus = NI * a.n * kUsRow;
+    for (int idx = threadIdx.x; idx < nus; idx += THREADS) {
+        const int j = idx % kUsRow;
+        const int r = idx / kUsRow;
+        const int k = r % a.n, i = r / a.n;
+        float2 v = make_float2(0.f, 0.f);
+        if (i < ni && j < a.m) v = a.U[((size_t)(inst0 + i) * a.m + j) * a.m + a.cols[k]];
+        us[idx] = v;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = 1; k <= a.n; ++k) {
+        const float2 *prev = ((k - 1) & 1) ? buf1 : buf0;
+        float2 *cur = (k & 1) ? buf1 : buf0;
+        const int cap_prev = a.cap[(k - 1) & 1], cap_cur = a.cap[k & 1];
+        const float2 *uk = us + (size_t)(k - 1) * kUsRow;
+        for (int b = warp; b < a.nblk[k]; b += THREADS / 32) {
+            const uint32_t info = __ldg(a.blk[k] + b);
+            const uint32_t *row = a.rows[k] + (info >> 4);
+            const int p = b * 32 + lane;
+#define SLOS_FUSED_Q(Q) \
+    case Q: fused_block<EPI, Q>(a, k, uk, prev, cap_prev, cur, cap_cur, inst0, ni, row, p); break;
+            switch (info & 15u) {
+                SLOS_FUSED_Q(1)
+                SLOS_FUSED_Q(2)
+                SLOS_FUSED_Q(3)
+                SLOS_FUSED_Q(4)
+                SLOS_FUSED_Q(5)
+                SLOS_FUSED_Q(6)
+                SLOS_FUSED_Q(7)
+                SLOS_FUSED_Q(8)
+                SLOS_FUSED_Q(9)
+                SLOS_FUSED_Q(10)
+                SLOS_FUSED_Q(11)
+                default: fused_block<EPI, 12>(a, k, uk, prev, cap_prev, cur, cap_cur, inst0, ni, row, p); break;
+            }
+#undef SLOS_FUSED_Q
+        }
+        __syncthreads();
+    }
+}
+
 size_t slos_fused_smem(int NI, int n, const int cap[2]) {
     return sizeof(float2) * ((size_t)NI * n * kUsRow + (size_t)NI * (cap[0] + cap[1]));
 }
@@ -130,7 +231,12 @@ cudaError_t slos_fused_init() {
     if ((e = fused_attrs<512, false>()) != cudaSuccess) return e;
     if ((e = fused_attrs<512, true>()) != cudaSuccess) return e;
     if ((e = fused_attrs<1024, false>()) != cudaSuccess) return e;
-    return fused_attrs<1024, true>();
+    if ((e = fused_attrs<1024, true>()) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(slos_fwd_fused_sorted_kernel<EPI_PROBS, 1024>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemLimit)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(slos_fwd_fused_sorted_kernel<EPI_AMPS, 1024>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemLimit);
 }
 
 template <int THREADS, bool PRED>
@@ -152,6 +258,15 @@ static cudaError_t launch_fused_t(const FusedArgs &a, int epi, cudaStream_t s) {
 }
 
 cudaError_t slos_launch_fused(const FusedArgs &a, int epi, cudaStream_t s) {
+    if (a.sorted) {
+        if (a.threads != 1024) return cudaErrorInvalidValue;
+        const unsigned grid = (unsigned)((a.B + a.NI - 1) / a.NI);
+        const size_t sm = slos_fused_smem(a.NI, a.n, a.cap);
+        if (epi == EPI_PROBS) slos_fwd_fused_sorted_kernel<EPI_PROBS, 1024><<<grid, 1024, sm, s>>>(a);
+        else if (epi == EPI_AMPS) slos_fwd_fused_sorted_kernel<EPI_AMPS, 1024><<<grid, 1024, sm, s>>>(a);
+        else return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
     if (a.threads == 1024) return launch_fused_t<1024>(a, epi, s);
     if (a.threads == 512) return launch_fused_t<512>(a, epi, s);
     return cudaErrorInvalidValue;

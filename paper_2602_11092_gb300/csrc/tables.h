@@ -25,9 +25,25 @@ struct LayerTables {
     int32_t *ctab = nullptr;     // [F_{k-1} * m]
 };
 
+// On-chip forward layout of layer k: the states sorted, stably, by their
+// number q of occupied modes, each run of equal q padded to a multiple of 32
+// ("positions"); one warp walks a block of 32 positions, all with q parents.
+// Block b's rows are slot-major, rows[off + i * 32 + lane] = (parent position
+// << 5) | mode of slot i, with blk[b] = off << 4 | q.  Padding positions name
+// parent 0 and the zero row of U.
+struct FusedLayer {
+    uint32_t *rows = nullptr;
+    uint32_t *blk = nullptr;
+    int nblk = 0;
+    int fpad = 0;   // positions (a multiple of 32)
+};
+
 struct PlanTables {
     bool enabled = false;
     std::vector<LayerTables> layer;  // [0..n], layer[0] unused
+    std::vector<FusedLayer> fused;   // [0..n] when the on-chip forward is used
+    int32_t *fused_id = nullptr;     // final layer: output index of each position, -1 for padding
+    float *fused_w = nullptr;        // final layer: weight of each position
     float *w = nullptr;              // [F_n]
     int32_t *pat = nullptr;          // [F_n] (threshold only)
     float *gfact = nullptr;          // [F_n]: sqrt(prod t_j!) of the final states (amplitude encoding)
