@@ -390,29 +390,35 @@ __global__ void __launch_bounds__(256, MINB) slos_batched_kernel(BArgs a) {
             for (int j = half; j < m; j += 2)
                 us[j * kBLanes + il] = valid ? a.U[a.u_off[inst] + (int64_t)j * m + col] : make_float2(0.f, 0.f);
             __syncwarp();
-            const int c1 = (int)min(c0 + (int64_t)a.chunk, sh.F[k]);
+            // the item's section: chunks are counted section by section, so no
+            // item straddles two widths
+            int sec = 0;
+            int64_t rem = chunk_id;
+            for (; sec < kBSec - 1; ++sec) {
+                const int64_t nch = (sh.sec_pos[k][sec + 1] - sh.sec_pos[k][sec] + a.chunk - 1) / a.chunk;
+                if (rem < nch) break;
+                rem -= nch;
+            }
+            const int p0 = sh.sec_pos[k][sec];
+            const int lo = p0 + (int)rem * a.chunk;
+            const int hi = min(lo + a.chunk, sh.sec_pos[k][sec + 1]);
             const char *prev = a.ws + g.buf[(n - 1 - (k - 1)) & 1] + il * sizeof(float2);
             float2 *next = reinterpret_cast<float2 *>(a.ws + g.buf[(n - 1 - k) & 1]) + il;
             const int kind = k < n ? B_NEXT : (sh.det == SLOS_DETECT_THRESHOLD ? B_SCRATCH : B_PNR);
             const uint32_t *tab = a.slots + sh.slot_off[k];
             const float *wtab = reinterpret_cast<const float *>(a.slots + sh.w_off);
             const float2 *usl = us + il;
-            for (int sec = 0; sec < kBSec; ++sec) {
-                const int p0 = sh.sec_pos[k][sec];
-                const int lo = max((int)c0, p0), hi = min(c1, sh.sec_pos[k][sec + 1]);
-                if (lo >= hi) continue;
-                const uint32_t *st = tab + sh.sec_off[k][sec];
+            const uint32_t *st = tab + sh.sec_off[k][sec];
 #define SLOS_B_SEC(W) fwd_states<W>(st, p0, lo, hi, half, usl, prev, k == 1, kind, next, outp, scr, wtab)
-                switch (sec) {
-                    case 0: SLOS_B_SEC(2); break;
-                    case 1: SLOS_B_SEC(4); break;
-                    case 2: SLOS_B_SEC(6); break;
-                    case 3: SLOS_B_SEC(8); break;
-                    case 4: SLOS_B_SEC(10); break;
-                    default: SLOS_B_SEC(12); break;
-                }
-#undef SLOS_B_SEC
+            switch (sec) {
+                case 0: SLOS_B_SEC(2); break;
+                case 1: SLOS_B_SEC(4); break;
+                case 2: SLOS_B_SEC(6); break;
+                case 3: SLOS_B_SEC(8); break;
+                case 4: SLOS_B_SEC(10); break;
+                default: SLOS_B_SEC(12); break;
             }
+#undef SLOS_B_SEC
         }
         __threadfence();
         __syncwarp();
@@ -495,6 +501,12 @@ static slos_status_t build_items(BatchedPlan *b, int chunk) {
             x.d.k = k;
             x.d.dep = -1;
             x.d.nchunks = (int)((states + chunk - 1) / chunk);
+            if (!sums) {  // layer items never straddle a section (slot width)
+                int64_t nch = 0;
+                for (int sec = 0; sec < kBSec; ++sec)
+                    nch += (sh.sec_pos[k][sec + 1] - sh.sec_pos[k][sec] + chunk - 1) / chunk;
+                x.d.nchunks = (int)nch;
+            }
             x.work = sums ? states : states * std::min(sh.m, k);
             layer.push_back(x);
         }
