@@ -223,9 +223,11 @@ def test_threshold_matches_oracle(slos, m, n, B):
 @pytest.mark.parametrize("m,s,B", [(6, [1, 1, 1, 0, 0, 0], 1), (12, [1, 0] * 6, 37), (9, [2, 0, 1, 0, 3, 0, 0, 0, 0], 5),
                                    (4, [0, 2, 0, 0], 3), (12, [1, 0] * 5 + [1, 1], 9), (10, [1, 0] * 5, 70)])
 def test_on_chip_forward_matches_layered_forward(slos, m, s, B):
-    """Inference forwards of small plans run every layer in shared memory;
-    the layered path (taken when activations are kept) computes the same
-    sums in the same order."""
+    """Inference forwards of small plans run every layer in shared memory,
+    in Fock order (m <= 10 here) or sorted by occupied-mode count (the m=12
+    plans, which need 1024-thread CTAs; B=37 leaves the last CTA one
+    instance); the layered path (taken when activations are kept) computes
+    the same sums in the same order."""
     rng = np.random.default_rng(m * 7 + B)
     U = c64(workloads.haar_unitaries(m, B, rng))
     plan = slos.Plan(m, s)
