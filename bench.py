@@ -293,7 +293,7 @@ def run_gpu(args):
     plan.sync_status()
     barrier()
 
-    # headline: K steps, no per-launch tracing, clocks sampled meanwhile
+    # timed steps: K steps, no per-launch tracing, clocks sampled meanwhile
     clocks = ClockSampler(local)
     clocks.start()
     B.profile_reset()
@@ -467,8 +467,8 @@ def uneven_bench(B, dev, stream, max_fock=None, reps=5, with_oracle=False):
     Up = torch.tensor(flat, dtype=torch.complex64, device=dev)
     wsb = torch.empty(bp.workspace_bytes, dtype=torch.uint8, device=dev)
     outb = torch.empty((bp.out_offsets[-1],), dtype=torch.float32, device=dev)
-    cache = os.path.join(ROOT, "gpurun_out", "autotune_cache.json") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else None
+    # launch shapes the autotuner picked, reused by later runs on the same machine
+    cache = os.environ.get("SLOS_AUTOTUNE_CACHE", os.path.join(ROOT, ".autotune_cache.json"))
     t0 = time.perf_counter()
     bp.autotune(Up, outb, wsb, cache_path=cache)
     tune_s = time.perf_counter() - t0

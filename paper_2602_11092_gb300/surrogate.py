@@ -1,6 +1,6 @@
 """ctypes binding of include/surrogate.h (argument marshalling only) and the
 surrogate driver: tensor-core MLP inference with an exact SLOS spot check and
-exact fallback (the exact path judges the surrogate's total variation)."""
+exact fallback (the exact path checks the surrogate's total variation)."""
 from __future__ import annotations
 
 import ctypes
@@ -215,7 +215,7 @@ class SurrogateLayer:
                 "frac_gt_0.02": float((tv > 0.02).mean()), "count": int(tv.size)}
 
     def infer(self, data: torch.Tensor, rho: float = 1 / 64, tv_tol: float = 0.02, seed: int = 0):
-        """Surrogate outputs with the exact path as judge: a mean-photon-number
+        """Surrogate outputs with the exact path as arbiter: a mean-photon-number
         screen on every sample (a difference above 2 n tv_tol proves TV >
         tv_tol), an exact spot check of a seeded fraction rho, exact fallback
         for every sample that failed either."""
