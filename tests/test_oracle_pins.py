@@ -519,3 +519,17 @@ def test_transfer_matrix_of_a_permutation_permutes_the_basis():
         col = np.zeros(len(basis))
         col[index[tuple(t)]] = 1.0
         assert np.allclose(P[:, si], col, atol=1e-15)
+
+
+@pytest.mark.parametrize("m,k", [(3, 5), (8, 4), (12, 6), (16, 7), (20, 3)])
+def test_occupied_mode_counts_of_a_layer(m, k):
+    """The uneven-batch planner sizes the sections of a layer (states with q
+    occupied modes) in closed form: choose the q modes, then split k photons
+    into q positive parts, C(m, q) C(k-1, q-1); the sizes sum to the layer,
+    C(m+k-1, k) (Vandermonde).  Checked by counting the enumerated states."""
+    states = oracle.enumerate_fock(m, k)
+    counts = np.bincount((states > 0).sum(axis=1), minlength=min(m, k) + 1)
+    assert counts[0] == 0
+    for q in range(1, min(m, k) + 1):
+        assert counts[q] == math.comb(m, q) * math.comb(k - 1, q - 1)
+    assert counts.sum() == math.comb(m + k - 1, k) == oracle.fock_dim(m, k)
