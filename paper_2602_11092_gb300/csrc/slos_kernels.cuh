@@ -404,15 +404,19 @@ __global__ void slos_seed_bcast_kernel(PrepArgs a) {
 // also forms the child gradient from a_n and the seed, runs fastest at 64
 // registers (8 blocks, a few bytes of spill) for up to 16 modes; the
 // intermediate layers at about 80 (6 blocks).  Measured on the m=16, n=8
-// training step: 8 blocks beat 6, 7 and 9 for the final layer, 6 is best for
-// the others.
+// training step: 8 blocks beat 6, 7 and 9 for the final layer.  The 16-mode
+// intermediate layers issue all 16 child gathers of a parent at once (one
+// round trip instead of two) at 90 registers, 5 blocks: 0.478 -> 0.472 ms per
+// step (4 blocks: 0.556 ms); the other mode counts keep batches of 8 at 6.
 constexpr int kBwdTabWarps = 4;
 constexpr int kBwdTabBatch = 8;  // child gathers issued together per parent
-constexpr int bwd_tab_min_blocks(int mmax, bool final_layer) { return final_layer && mmax <= 16 ? 8 : 6; }
+constexpr int bwd_tab_min_blocks(int mmax, bool final_layer) { return final_layer && mmax <= 16 ? 8 : (mmax == 16 ? 5 : 6); }
+// child gathers issued together by the intermediate layers
+constexpr int bwd_layer_batch(int mmax) { return mmax == 16 ? 16 : kBwdTabBatch; }
 
 // HOLES: the child table may name no child (-1), for lattices where t' + e_j
 // leaves the space (collision-free states); such children contribute nothing.
-template <int MMAX, int SEED, int MINB, bool HOLES>
+template <int MMAX, int SEED, int MINB, bool HOLES, int BATCH = kBwdTabBatch>
 __global__ void __launch_bounds__(kBwdTabWarps * 32, MINB) slos_bwd_tab_kernel(BwdArgs a, const int32_t *ctab) {
     __shared__ float2 red[kBwdTabWarps][32];
     __shared__ float2 us[MMAX][32];
@@ -444,10 +448,10 @@ __global__ void __launch_bounds__(kBwdTabWarps * 32, MINB) slos_bwd_tab_kernel(B
         const float2 av = (a.k == 1) ? make_float2(1.f, 0.f) : __ldg(aprevb + (c << 5));
         float2 gacc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int h = 0; h < MMAX; h += kBwdTabBatch) {
-            float2 g[kBwdTabBatch];
+        for (int h = 0; h < MMAX; h += BATCH) {
+            float2 g[BATCH];
 #pragma unroll
-            for (int r = 0; r < kBwdTabBatch; ++r) {
+            for (int r = 0; r < BATCH; ++r) {
                 const int j = h + r;
                 const uint32_t cidx = (uint32_t)__shfl_sync(0xffffffffu, mine, j < 32 ? j : 0);
                 g[r] = make_float2(0.f, 0.f);
@@ -458,7 +462,7 @@ __global__ void __launch_bounds__(kBwdTabWarps * 32, MINB) slos_bwd_tab_kernel(B
                 }
             }
 #pragma unroll
-            for (int r = 0; r < kBwdTabBatch; ++r) {
+            for (int r = 0; r < BATCH; ++r) {
                 const int j = h + r;
                 if (j < MMAX && j < m) {
                     gacc = cfma_conj_a(us[j][lane], g[r], gacc);
@@ -500,7 +504,9 @@ cudaError_t launch_bwd_tab_t(const BwdArgs &a, const int32_t *ctab, int seed, in
     dim3 grid(blocks_x, a.NG);
     constexpr int mg = bwd_tab_min_blocks(MM, false), mf = bwd_tab_min_blocks(MM, true);
     switch (seed) {
-        case SEED_G: slos_bwd_tab_kernel<MM, SEED_G, mg, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;
+        case SEED_G:
+            slos_bwd_tab_kernel<MM, SEED_G, mg, HOLES, bwd_layer_batch(MM)><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab);
+            break;
         case SEED_BCAST: slos_bwd_tab_kernel<MM, SEED_BCAST, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;
         case SEED_T: slos_bwd_tab_kernel<MM, SEED_T, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;
         case SEED_AMPS_T: slos_bwd_tab_kernel<MM, SEED_AMPS_T, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;
