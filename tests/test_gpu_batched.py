@@ -205,3 +205,38 @@ def test_bounded_wait_reports_timeout_and_context_survives(slos):
     ref = torch.empty_like(out)
     bp.forward(U, ref, ws)
     assert torch.equal(out, ref)
+
+
+def test_batched_widest_slot_rows(slos):
+    """States with 11 or 12 occupied modes (m=12, n=11 and n=12) take the
+    launcher's widest slot rows (12 slots; layers are sorted by occupied-mode
+    count): against single-shape plans on every output and the oracle on
+    sampled outputs and patterns."""
+    rng = np.random.default_rng(57)
+    specs = [(12, [1] * 11 + [0], False, 2), (12, [1] * 12, True, 1), (12, [2] + [1] * 10 + [0], False, 1)]
+    inst = []
+    for m, s, thr, cnt in specs:
+        inst += [workloads.UnevenInstance(m=m, n=sum(s), s=list(s), threshold=thr)] * cnt
+    Us = [workloads.haar_unitaries(it.m, 1, rng)[0] for it in inst]
+    bp = make_plan(slos, inst)
+    ws = torch.empty(bp.workspace_bytes, dtype=torch.uint8, device="cuda")
+    out = torch.full((bp.out_offsets[-1],), float("nan"), dtype=torch.float32, device="cuda")
+    bp.forward(pack(Us), out, ws)
+    bp.sync_status()
+    out = out.cpu().numpy()
+    for i, it in enumerate(inst):
+        got = out[bp.out_offsets[i]:bp.out_offsets[i + 1]]
+        plan = slos.Plan(it.m, it.s, slos.THRESHOLD if it.threshold else slos.PNR)
+        ref = plan.forward(torch.tensor(Us[i][None], dtype=torch.complex64, device="cuda")).cpu().numpy()[0]
+        assert got.shape == ref.shape
+        assert np.abs(got - ref).max() <= P_TOL
+        Uq = np.asarray(Us[i], dtype=np.complex64).astype(np.complex128)
+        if it.threshold:
+            pats = oracle.threshold_patterns(it.m, it.n)
+            for idx in list(rng.choice(len(pats), size=10, replace=False)) + [len(pats) - 1]:
+                assert abs(got[idx] - oracle.threshold_prob_of_pattern(Uq, it.s, pats[idx])) <= P_TOL
+        else:
+            K = workloads.fock_dim(it.m, it.n)
+            pos = np.sort(rng.choice(K, size=150, replace=False))
+            refo = oracle.probabilities(Uq, it.s, oracle.enumerate_fock(it.m, it.n, pos))
+            assert np.abs(got[pos] - refo).max() <= P_TOL
