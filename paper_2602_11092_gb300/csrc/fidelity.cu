@@ -11,10 +11,12 @@
 // uses Glynn's formula
 //     Per(W) = 2^(1-n) sum_{delta in {+-1}^n, delta_1 = 1} (prod_a delta_a)
 //              prod_b (sum_a delta_a W[a][b])
-// walked in Gray-code order (one row sum update per term) with the row sums
-// and products in FP64: the terms reach about n^n / 2^(n-1) while the
+// walked in Gray-code order (one row sum update per term) with the row sums,
+// products and the signed total in double-float arithmetic (dfloat.cuh, about
+// 44 bits on the FP32 pipe): the terms reach about n^n / 2^(n-1) while the
 // permanent of a block of a unitary is at most 1, so FP32 sums would lose the
-// result.  n <= 8 keeps W in registers.
+// result.  The updates add +-2 W[r][c], exact in float.  n <= 8 keeps W in
+// registers.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,6 +24,7 @@
 
 #include "../../include/slos.h"
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "profile.h"
 
 namespace slos {
@@ -35,7 +38,7 @@ struct FidArgs {
     float *K;
     int m, Na, Nb;
     int cols[kFidMaxPhotons];
-    double inv_sf2;  // 1 / (prod s_i!)^2
+    float inv_sf2;   // 1 / (prod s_i!)^2
 };
 
 template <int N>
@@ -71,58 +74,44 @@ __global__ void __launch_bounds__(kFidTile *kFidTile) fidelity_kernel(FidArgs a)
         }
     }
     // Glynn, Gray-code order over delta_2..delta_N (bit q-1 of d: delta_{q+1} = -1)
-    double Sr[N], Si[N];
+    cdfl S[N];
 #pragma unroll
     for (int c = 0; c < N; ++c) {
-        Sr[c] = 0.0;
-        Si[c] = 0.0;
+        S[c] = {df_zero(), df_zero()};
 #pragma unroll
         for (int r = 0; r < N; ++r) {
-            Sr[c] += (double)W[r][c].x;
-            Si[c] += (double)W[r][c].y;
+            S[c].re = df_add_f(S[c].re, W[r][c].x);
+            S[c].im = df_add_f(S[c].im, W[r][c].y);
         }
     }
-    auto product = [&](double &pr, double &pi) {
-        pr = Sr[0];
-        pi = Si[0];
+    auto product = [&]() {
+        cdfl pr = S[0];
 #pragma unroll
-        for (int c = 1; c < N; ++c) {
-            const double xr = pr * Sr[c] - pi * Si[c];
-            pi = pr * Si[c] + pi * Sr[c];
-            pr = xr;
-        }
+        for (int c = 1; c < N; ++c) pr = cdf_mul(pr, S[c]);
+        return pr;
     };
-    double tr, ti;
-    product(tr, ti);
+    cdfl t = product();
     uint32_t d = 0;
     for (uint32_t g = 1; g < (1u << (N - 1)); ++g) {
         const int q = __ffs(g);  // flips delta_{q+1}, row q of W (1-based bit index q)
         d ^= 1u << (q - 1);
-        const double sgn = ((d >> (q - 1)) & 1u) ? -2.0 : 2.0;
+        const float sgn = ((d >> (q - 1)) & 1u) ? -2.f : 2.f;
 #pragma unroll
         for (int r = 1; r < N; ++r) {
             if (r == q) {
 #pragma unroll
                 for (int c = 0; c < N; ++c) {
-                    Sr[c] += sgn * (double)W[r][c].x;
-                    Si[c] += sgn * (double)W[r][c].y;
+                    S[c].re = df_add_f(S[c].re, sgn * W[r][c].x);
+                    S[c].im = df_add_f(S[c].im, sgn * W[r][c].y);
                 }
             }
         }
-        double pr, pi;
-        product(pr, pi);
-        if (__popc(d) & 1) {
-            tr -= pr;
-            ti -= pi;
-        } else {
-            tr += pr;
-            ti += pi;
-        }
+        const cdfl pr = product();
+        t = (__popc(d) & 1) ? cdf_sub(t, pr) : cdf_add(t, pr);
     }
-    const double scale = 1.0 / (double)(1u << (N - 1));
-    tr *= scale;
-    ti *= scale;
-    a.K[(size_t)i * a.Nb + j] = (float)((tr * tr + ti * ti) * a.inv_sf2);
+    const float scale = 1.f / (float)(1u << (N - 1));
+    const float tr = df_float(t.re) * scale, ti = df_float(t.im) * scale;
+    a.K[(size_t)i * a.Nb + j] = (tr * tr + ti * ti) * a.inv_sf2;
 }
 
 template <int N>

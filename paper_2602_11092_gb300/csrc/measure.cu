@@ -10,6 +10,7 @@
 
 #include "../../include/slos.h"
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "plan.h"
 #include "profile.h"
 
@@ -65,41 +66,44 @@ __global__ void __launch_bounds__(kMeasThreads) expect_bwd_kernel(const float *d
     dp[(size_t)b * K + c] = v;
 }
 
-// block sum of one double per thread, fixed order; every thread gets it
-__device__ double block_sum(double v, double *red) {
+// block sum of one double-float per thread, fixed order; every thread gets it
+__device__ dfl block_sum(dfl v, dfl *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        const dfl w = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, w);
+    }
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < kMeasWarps; ++w) s += red[w];
+    dfl s = df_zero();
+    for (int w = 0; w < kMeasWarps; ++w) s = df_add(s, red[w]);
     __syncthreads();
     return s;
 }
 
-// Z = sum_t p[t]; q[t] = p[t] / Z
+// Z = sum_t p[t]; q[t] = p[t] / Z  (sums in double-float, dfloat.cuh)
 __global__ void __launch_bounds__(kMeasThreads) renorm_fwd_kernel(const float *p, int64_t K, float *q, float *Z) {
-    __shared__ double red[kMeasWarps];
+    __shared__ dfl red[kMeasWarps];
     const int b = blockIdx.x;
     const float *pb = p + (size_t)b * K;
-    double acc = 0.0;
-    for (int64_t c = threadIdx.x; c < K; c += kMeasThreads) acc += (double)pb[c];
-    const double z = block_sum(acc, red);
-    const float inv = z > 0.0 ? (float)(1.0 / z) : 0.f;
+    dfl acc = df_zero();
+    for (int64_t c = threadIdx.x; c < K; c += kMeasThreads) acc = df_add_f(acc, pb[c]);
+    const float z = df_float(block_sum(acc, red));
+    const float inv = z > 0.f ? 1.f / z : 0.f;
     float *qb = q + (size_t)b * K;
     for (int64_t c = threadIdx.x; c < K; c += kMeasThreads) qb[c] = pb[c] * inv;
-    if (threadIdx.x == 0) Z[b] = (float)z;
+    if (threadIdx.x == 0) Z[b] = z;
 }
 
 // dp[t] = (dq[t] - sum_s dq[s] q[s]) / Z
 __global__ void __launch_bounds__(kMeasThreads) renorm_bwd_kernel(const float *q, const float *Z, const float *dq,
                                                                   int64_t K, float *dp) {
-    __shared__ double red[kMeasWarps];
+    __shared__ dfl red[kMeasWarps];
     const int b = blockIdx.x;
     const float *qb = q + (size_t)b * K, *dqb = dq + (size_t)b * K;
-    double acc = 0.0;
-    for (int64_t c = threadIdx.x; c < K; c += kMeasThreads) acc += (double)dqb[c] * (double)qb[c];
-    const float sdot = (float)block_sum(acc, red);
+    dfl acc = df_zero();
+    for (int64_t c = threadIdx.x; c < K; c += kMeasThreads) acc = df_add(acc, two_prod(dqb[c], qb[c]));
+    const float sdot = df_float(block_sum(acc, red));
     const float z = Z[b];
     const float inv = z > 0.f ? 1.f / z : 0.f;
     float *dpb = dp + (size_t)b * K;
