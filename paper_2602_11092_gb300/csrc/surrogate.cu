@@ -20,6 +20,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <random>
@@ -76,10 +77,25 @@ int *err_ptr() {
 }
 
 bool g_attr_done[64] = {false};
+int g_sm_count[64] = {0};
+
+int sm_count() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 148;
+    if (g_sm_count[dev] <= 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        g_sm_count[dev] = n > 0 ? n : 148;
+    }
+    return g_sm_count[dev];
+}
 
 template <int EPI>
 cudaError_t set_attr() {
-    return cudaFuncSetAttribute(tc_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(tc_gemm_persist_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
 }
 
 cudaError_t init_attrs() {
@@ -118,14 +134,17 @@ slos_status_t gemm(int epi, int M, int N, int K, const __nv_bfloat16 *A, int64_t
     g.bias = bias;
     g.aux = aux;
     g.err = err_ptr();
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    // persistent CTAs, one per SM (the shared-memory ring allows no second)
+    const int64_t tiles = (int64_t)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, sm_count());
     ProfScope ps("tc_gemm", 2.0 * M * N * K, s);  // flops, not bytes
+    constexpr int T = kPersistThreads;
     switch (epi) {
-        case TC_F32: tc_gemm_kernel<TC_F32><<<grid, 128, SMEM_BYTES, s>>>(ta, tb, g); break;
-        case TC_F32_BIAS: tc_gemm_kernel<TC_F32_BIAS><<<grid, 128, SMEM_BYTES, s>>>(ta, tb, g); break;
-        case TC_GELU: tc_gemm_kernel<TC_GELU><<<grid, 128, SMEM_BYTES, s>>>(ta, tb, g); break;
-        case TC_GELU_BWD: tc_gemm_kernel<TC_GELU_BWD><<<grid, 128, SMEM_BYTES, s>>>(ta, tb, g); break;
-        case TC_F32_ACCUM: tc_gemm_kernel<TC_F32_ACCUM><<<grid, 128, SMEM_BYTES, s>>>(ta, tb, g); break;
+        case TC_F32: tc_gemm_persist_kernel<TC_F32><<<grid, T, SMEM_BYTES, s>>>(ta, tb, g); break;
+        case TC_F32_BIAS: tc_gemm_persist_kernel<TC_F32_BIAS><<<grid, T, SMEM_BYTES, s>>>(ta, tb, g); break;
+        case TC_GELU: tc_gemm_persist_kernel<TC_GELU><<<grid, T, SMEM_BYTES, s>>>(ta, tb, g); break;
+        case TC_GELU_BWD: tc_gemm_persist_kernel<TC_GELU_BWD><<<grid, T, SMEM_BYTES, s>>>(ta, tb, g); break;
+        case TC_F32_ACCUM: tc_gemm_persist_kernel<TC_F32_ACCUM><<<grid, T, SMEM_BYTES, s>>>(ta, tb, g); break;
         default: return fail(SLOS_ERR_INVALID_ARG, "GEMM epilogue");
     }
     e = cudaGetLastError();

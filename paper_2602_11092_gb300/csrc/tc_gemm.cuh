@@ -1,5 +1,9 @@
 // Tensor-core GEMM for sm_103a: C[M][N] = A[M][K] . B[N][K]^T, BF16 inputs
 // (both K-major), FP32 accumulation in tensor memory (TMEM), fused epilogues.
+// Two kernels share the pipeline below: tc_gemm_kernel (one tile per CTA) and
+// tc_gemm_persist_kernel (one CTA per SM over many tiles, two accumulators,
+// the epilogue of one tile overlapping the next tile's MMAs), which the
+// library launches.
 //
 // One CTA = 128 threads computes one 128 x 256 output tile.
 //   warp 0, lane 0: TMA producer.  cp.async.bulk.tensor loads 128x64 tiles of
@@ -70,6 +74,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 // Bounded wait: true if the phase completed, false if the limit ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     for (long long i = 0; i < kWaitLimit; ++i)
@@ -138,6 +145,79 @@ __device__ __forceinline__ float gelu_grad(float z) {
     const float u = c * (z + 0.044715f * z * z * z);
     const float t = tanhf(u);
     return 0.5f * (1.f + t) + 0.5f * z * (1.f - t * t) * c * (1.f + 3.f * 0.044715f * z * z);
+}
+
+// Epilogue of one 16-column segment of an output row: v holds the
+// accumulator values of row `row`, columns col0 .. col0 + 15.
+template <int EPI>
+__device__ __forceinline__ void tc_store16(const TcArgs &g, int row, int col0, float (&v)[16], bool vec) {
+    if (row < g.M && col0 < g.N) {
+        const int64_t o0 = (int64_t)row * g.ldc + col0;
+        if (EPI == TC_F32_BIAS || EPI == TC_GELU) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] += (col0 + i < g.N) ? g.bias[col0 + i] : 0.f;
+        }
+        if (vec && col0 + 16 <= g.N) {
+            if (EPI == TC_F32 || EPI == TC_F32_BIAS || EPI == TC_F32_ACCUM) {
+                float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(g.C) + o0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float4 w = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    if (EPI == TC_F32_ACCUM) {
+                        const float4 old = dst[q];
+                        w.x += old.x;
+                        w.y += old.y;
+                        w.z += old.z;
+                        w.w += old.w;
+                    }
+                    dst[q] = w;
+                }
+            } else {
+                __align__(16) __nv_bfloat16 out[16];
+                if (EPI == TC_GELU) {
+                    __align__(16) __nv_bfloat16 zb[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        zb[i] = __float2bfloat16(v[i]);
+                        out[i] = __float2bfloat16(gelu_f(__bfloat162float(zb[i])));
+                    }
+                    uint4 *za = reinterpret_cast<uint4 *>(g.aux + o0);
+                    za[0] = reinterpret_cast<const uint4 *>(zb)[0];
+                    za[1] = reinterpret_cast<const uint4 *>(zb)[1];
+                } else {  // TC_GELU_BWD
+                    __align__(16) __nv_bfloat16 zb[16];
+                    const uint4 *zs = reinterpret_cast<const uint4 *>(g.aux + o0);
+                    reinterpret_cast<uint4 *>(zb)[0] = zs[0];
+                    reinterpret_cast<uint4 *>(zb)[1] = zs[1];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) out[i] = __float2bfloat16(v[i] * gelu_grad(__bfloat162float(zb[i])));
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) + o0);
+                dst[0] = reinterpret_cast<const uint4 *>(out)[0];
+                dst[1] = reinterpret_cast<const uint4 *>(out)[1];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int col = col0 + i;
+                if (col >= g.N) break;
+                const int64_t o = o0 + i;
+                const float x = v[i];
+                if (EPI == TC_F32 || EPI == TC_F32_BIAS) {
+                    reinterpret_cast<float *>(g.C)[o] = x;
+                } else if (EPI == TC_F32_ACCUM) {
+                    reinterpret_cast<float *>(g.C)[o] += x;
+                } else if (EPI == TC_GELU) {
+                    const __nv_bfloat16 zb = __float2bfloat16(x);
+                    g.aux[o] = zb;
+                    reinterpret_cast<__nv_bfloat16 *>(g.C)[o] = __float2bfloat16(gelu_f(__bfloat162float(zb)));
+                } else {  // TC_GELU_BWD
+                    const float z = __bfloat162float(g.aux[o]);
+                    reinterpret_cast<__nv_bfloat16 *>(g.C)[o] = __float2bfloat16(x * gelu_grad(z));
+                }
+            }
+        }
+    }
 }
 
 template <int EPI>
@@ -229,74 +309,7 @@ __global__ void __launch_bounds__(128, 1)
         for (int c = 0; c < BN; c += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            const int col0 = n0 + c;
-            if (row < g.M && col0 < g.N) {
-                const int64_t o0 = (int64_t)row * g.ldc + col0;
-                if (EPI == TC_F32_BIAS || EPI == TC_GELU) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] += (col0 + i < g.N) ? g.bias[col0 + i] : 0.f;
-                }
-                if (vec && col0 + 16 <= g.N) {
-                    if (EPI == TC_F32 || EPI == TC_F32_BIAS || EPI == TC_F32_ACCUM) {
-                        float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(g.C) + o0);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            float4 w = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                            if (EPI == TC_F32_ACCUM) {
-                                const float4 old = dst[q];
-                                w.x += old.x;
-                                w.y += old.y;
-                                w.z += old.z;
-                                w.w += old.w;
-                            }
-                            dst[q] = w;
-                        }
-                    } else {
-                        __align__(16) __nv_bfloat16 out[16];
-                        if (EPI == TC_GELU) {
-                            __align__(16) __nv_bfloat16 zb[16];
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                zb[i] = __float2bfloat16(v[i]);
-                                out[i] = __float2bfloat16(gelu_f(__bfloat162float(zb[i])));
-                            }
-                            uint4 *za = reinterpret_cast<uint4 *>(g.aux + o0);
-                            za[0] = reinterpret_cast<const uint4 *>(zb)[0];
-                            za[1] = reinterpret_cast<const uint4 *>(zb)[1];
-                        } else {  // TC_GELU_BWD
-                            __align__(16) __nv_bfloat16 zb[16];
-                            const uint4 *zs = reinterpret_cast<const uint4 *>(g.aux + o0);
-                            reinterpret_cast<uint4 *>(zb)[0] = zs[0];
-                            reinterpret_cast<uint4 *>(zb)[1] = zs[1];
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) out[i] = __float2bfloat16(v[i] * gelu_grad(__bfloat162float(zb[i])));
-                        }
-                        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) + o0);
-                        dst[0] = reinterpret_cast<const uint4 *>(out)[0];
-                        dst[1] = reinterpret_cast<const uint4 *>(out)[1];
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int col = col0 + i;
-                        if (col >= g.N) break;
-                        const int64_t o = o0 + i;
-                        const float x = v[i];
-                        if (EPI == TC_F32 || EPI == TC_F32_BIAS) {
-                            reinterpret_cast<float *>(g.C)[o] = x;
-                        } else if (EPI == TC_F32_ACCUM) {
-                            reinterpret_cast<float *>(g.C)[o] += x;
-                        } else if (EPI == TC_GELU) {
-                            const __nv_bfloat16 zb = __float2bfloat16(x);
-                            g.aux[o] = zb;
-                            reinterpret_cast<__nv_bfloat16 *>(g.C)[o] = __float2bfloat16(gelu_f(__bfloat162float(zb)));
-                        } else {  // TC_GELU_BWD
-                            const float z = __bfloat162float(g.aux[o]);
-                            reinterpret_cast<__nv_bfloat16 *>(g.C)[o] = __float2bfloat16(x * gelu_grad(z));
-                        }
-                    }
-                }
-            }
+            tc_store16<EPI>(g, row, n0 + c, v, vec);
         }
     }
     tc_fence_before();
@@ -304,6 +317,163 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+
+// Persistent variant: one CTA per SM walks the output tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (row-major over 128 x 256 tiles, so the CTAs
+// running together share A rows in L2).  Six warps:
+//   warp 0, lane 0: TMA producer over one stage ring that runs on across tiles;
+//   warp 1, lane 0: MMA issuer, alternating between two 128 x 256 FP32
+//                   accumulators in TMEM (all 512 columns): tile j uses
+//                   accumulator j & 1, after the epilogue has released it
+//                   (`tempty`, one arrival per epilogue warp), and commits
+//                   `tfull` when its last MMA has completed;
+//   warps 2-5:      epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31, the
+//                   quarter its position in the warpgroup gives access to.
+// So a tile's epilogue runs while the next tile's loads and MMAs proceed, and
+// the ring's fill is paid once per CTA.  Waits are bounded as above; a wait
+// that runs out sets the error word and the abort flag, and every role leaves
+// its loop.
+constexpr int kPersistThreads = 192;
+constexpr uint32_t kPersistTmemCols = 2 * BN;
+
+template <int EPI>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+    tc_gemm_persist_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, TcArgs g) {
+    extern __shared__ uint8_t smem_tc[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_tc) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = base;
+    uint8_t *sB = base + STAGES * A_TILE;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + STAGES * B_TILE);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;  // [2]
+    uint64_t *tempty = tfull + 2;      // [2]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (g.K + BK - 1) / BK;
+    const int ntn = (g.N + BN - 1) / BN;
+    const int ntiles = ((g.M + BM - 1) / BM) * ntn;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull + a, 1);
+            mbar_init(tempty + a, 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kPersistTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer
+            uint32_t it = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                const int m0 = (t / ntn) * BM, n0 = (t % ntn) * BN;
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (it >= STAGES && !mbar_wait(empty + s, ph ^ 1)) {
+                        atomicExch(g.err, 1);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    mbar_expect_tx(full + s, STAGE_BYTES);
+                    tma_load_2d(sA + s * A_TILE, &ta, kt * BK, m0, full + s);
+                    tma_load_2d(sB + s * B_TILE, &tb, kt * BK, n0, full + s);
+                }
+            }
+            // never leave with copies in flight: wait (bounded) for the last loads
+            for (uint32_t q = (it > (uint32_t)STAGES ? it - STAGES : 0); q < it; ++q)
+                mbar_wait(full + (q % STAGES), (q / STAGES) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            uint32_t it = 0;
+            int j = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++j) {
+                const int acc = j & 1;
+                const int use = j >> 1;  // this accumulator's use count
+                if (use > 0 && !mbar_wait(tempty + acc, (use - 1) & 1)) {
+                    atomicExch(g.err, 4);
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * BN);
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (*abort_flag || !mbar_wait(full + s, ph)) {
+                        atomicExch(g.err, 2);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + s * A_TILE), b0 = smem_u32(sB + s * B_TILE);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        mma_bf16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kt > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(empty + s);
+                }
+                if (*abort_flag) break;
+                mma_commit(tfull + acc);  // arrives once this tile's MMAs have completed
+            }
+        }
+    } else {
+        // epilogue warps
+        const int q = warp & 3;
+        const bool vec = (g.ldc % 8) == 0;
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+            const int acc = j & 1;
+            const bool ok = __all_sync(0xffffffffu, !*abort_flag && mbar_wait(tfull + acc, (j >> 1) & 1));
+            if (!ok) {
+                if (lane == 0) {
+                    atomicExch(g.err, 3);
+                    *abort_flag = 1;
+                }
+                break;
+            }
+            tc_fence_after();
+            const int m0 = (t / ntn) * BM, n0 = (t % ntn) * BN;
+            const int row = m0 + q * 32 + lane;
+            const uint32_t src = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 16) {
+                float v[16];
+                tmem_ld16(src + (uint32_t)c, v);
+                tc_store16<EPI>(g, row, n0 + c, v, vec);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty + acc);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kPersistTmemCols)
+                     : "memory");
     }
 }
 
