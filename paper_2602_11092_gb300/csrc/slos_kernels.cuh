@@ -410,7 +410,13 @@ __global__ void slos_seed_bcast_kernel(PrepArgs a) {
 // step (4 blocks: 0.556 ms); the other mode counts keep batches of 8 at 6.
 constexpr int kBwdTabWarps = 4;
 constexpr int kBwdTabBatch = 8;  // child gathers issued together per parent
-constexpr int bwd_tab_min_blocks(int mmax, bool final_layer) { return final_layer && mmax <= 16 ? 8 : (mmax == 16 ? 5 : 6); }
+// final layer of 16-mode plans, dU in tensor memory: 9 blocks (56 registers,
+// no spill) measured 0.890 ms per step against 1.077 ms with the register
+// accumulators at 8; 8 blocks the same, 10 (spills) 0.960 ms
+constexpr int kBwdTmemMinBlocks = 9;
+constexpr int bwd_tab_min_blocks(int mmax, bool final_layer) {
+    return final_layer ? (mmax == 16 ? kBwdTmemMinBlocks : (mmax < 16 ? 8 : 6)) : (mmax == 16 ? 5 : 6);
+}
 // child gathers issued together by the intermediate layers
 constexpr int bwd_layer_batch(int mmax) { return mmax == 16 ? 16 : kBwdTabBatch; }
 
@@ -492,6 +498,149 @@ __global__ void __launch_bounds__(kBwdTabWarps * 32, MINB) slos_bwd_tab_kernel(B
     }
 }
 
+// Tensor-memory accumulators.  Each warp of a CTA owns one 32-lane quarter
+// of the CTA's tensor memory (warp w: lanes 32 w .. 32 w + 31); 32x32b
+// loads and stores move 16 consecutive 32-bit columns of that quarter
+// between TMEM and 16 registers per lane.
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tm_st16(uint32_t taddr, const float (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Final backward layer of 16-mode plans with the dU accumulators in tensor
+// memory instead of registers: per batch of 8 modes a warp loads its 8
+// accumulators (16 columns), adds conj(a_{k-1}) G_k for the batch's children
+// and stores them back, so only 8 of the 16 live in registers at a time and
+// the register budget admits more resident warps.  TMEM traffic has its own
+// datapath, not the L1 / shared-memory pipe the gathers use.  32 columns per
+// CTA (the minimum allocation); the CTA frees them before it exits.
+constexpr int kBwdTmemCols = 32;
+template <int MMAX, int SEED, int MINB, bool HOLES>
+__global__ void __launch_bounds__(kBwdTabWarps * 32, MINB) slos_bwd_tmem_kernel(BwdArgs a, const int32_t *ctab) {
+    static_assert(MMAX == 16 && kBwdTabBatch == 8, "two batches of 8 modes, 32 TMEM columns");
+    __shared__ float2 red[kBwdTabWarps][32];
+    __shared__ float2 us[MMAX][32];
+    __shared__ uint32_t tmem_slot;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int grp = blockIdx.y;
+    const int inst = grp * kLanes + lane;
+    const bool valid = inst < a.B;
+    const int m = a.m;
+    for (int j = warp; j < m; j += kBwdTabWarps)
+        us[j][lane] = valid ? a.U[((int64_t)inst * m + j) * m + a.col] : make_float2(0.f, 0.f);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         static_cast<uint32_t>(__cvta_generic_to_shared(&tmem_slot))),
+                     "r"(kBwdTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tq = tmem_slot + ((uint32_t)(warp * 32) << 16);  // this warp's lane quarter
+    {
+        float z[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) z[i] = 0.f;
+        tm_st16(tq, z);
+        tm_st16(tq + 16, z);
+    }
+    const size_t gprev = (size_t)grp * (size_t)a.Fprev * kLanes + lane;
+    const size_t gk = (size_t)grp * (size_t)a.Fk * kLanes + lane;
+    const float2 *aprevb = a.aprev + gprev;
+    float2 *Gprevb = a.Gprev + gprev;
+    const float2 *srcb = (SEED == SEED_AMPS_T) ? reinterpret_cast<const float2 *>(a.seed) + gk : a.an + gk;
+    const float *seedb = (SEED == SEED_T) ? reinterpret_cast<const float *>(a.seed) + gk
+                                          : reinterpret_cast<const float *>(a.seed);
+    const uint32_t nwarps = gridDim.x * kBwdTabWarps;
+    for (uint32_t c = blockIdx.x * kBwdTabWarps + warp; c < (uint32_t)a.Fprev; c += nwarps) {
+        const int mine = lane < m ? __ldg(ctab + (size_t)c * m + lane) : 0;
+        const float2 av = (a.k == 1) ? make_float2(1.f, 0.f) : __ldg(aprevb + (c << 5));
+        float2 gacc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int h = 0; h < MMAX; h += 8) {
+            float2 g[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int j = h + r;
+                const uint32_t cidx = (uint32_t)__shfl_sync(0xffffffffu, mine, j);
+                g[r] = make_float2(0.f, 0.f);
+                if (j < m && (!HOLES || (int)cidx >= 0)) {
+                    g[r] = __ldg(srcb + (cidx << 5));
+                    if (SEED == SEED_T) g[r] = cscale(g[r], __ldg(seedb + (cidx << 5)));
+                    if (SEED == SEED_BCAST) g[r] = cscale(g[r], __ldg(seedb + cidx));
+                }
+            }
+            float du[16];
+            tm_ld16(tq + 2 * h, du);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int j = h + r;
+                if (j < m) {
+                    gacc = cfma_conj_a(us[j][lane], g[r], gacc);
+                    const float2 d = cfma_conj_a(av, g[r], make_float2(du[2 * r], du[2 * r + 1]));
+                    du[2 * r] = d.x;
+                    du[2 * r + 1] = d.y;
+                }
+            }
+            tm_st16(tq + 2 * h, du);
+        }
+        if (a.k > 1) Gprevb[c << 5] = gacc;
+    }
+    float2 *dst = a.dUpart + (((int64_t)grp * gridDim.x + blockIdx.x) * kLanes) * m;
+#pragma unroll
+    for (int h = 0; h < MMAX; h += 8) {
+        float du[16];
+        tm_ld16(tq + 2 * h, du);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int j = h + r;
+            if (j < m) {
+                red[warp][lane] = make_float2(du[2 * r], du[2 * r + 1]);
+                __syncthreads();
+                if (warp == 0) {
+                    float2 sacc = red[0][lane];
+#pragma unroll
+                    for (int w = 1; w < kBwdTabWarps; ++w) {
+                        sacc.x += red[w][lane].x;
+                        sacc.y += red[w][lane].y;
+                    }
+                    dst[lane * m + j] = sacc;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(kBwdTmemCols)
+                     : "memory");
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 inline size_t fwd_smem_bytes(int epi) {
     if (epi == EPI_PROBS) return (size_t)kWarpsPerBlock * 32 * 33 * sizeof(float);
@@ -507,9 +656,18 @@ cudaError_t launch_bwd_tab_t(const BwdArgs &a, const int32_t *ctab, int seed, in
         case SEED_G:
             slos_bwd_tab_kernel<MM, SEED_G, mg, HOLES, bwd_layer_batch(MM)><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab);
             break;
-        case SEED_BCAST: slos_bwd_tab_kernel<MM, SEED_BCAST, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;
-        case SEED_T: slos_bwd_tab_kernel<MM, SEED_T, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;
-        case SEED_AMPS_T: slos_bwd_tab_kernel<MM, SEED_AMPS_T, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab); break;
+        case SEED_BCAST:
+            if constexpr (MM == 16) slos_bwd_tmem_kernel<16, SEED_BCAST, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab);
+            else slos_bwd_tab_kernel<MM, SEED_BCAST, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab);
+            break;
+        case SEED_T:
+            if constexpr (MM == 16) slos_bwd_tmem_kernel<16, SEED_T, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab);
+            else slos_bwd_tab_kernel<MM, SEED_T, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab);
+            break;
+        case SEED_AMPS_T:
+            if constexpr (MM == 16) slos_bwd_tmem_kernel<16, SEED_AMPS_T, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab);
+            else slos_bwd_tab_kernel<MM, SEED_AMPS_T, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
