@@ -403,22 +403,20 @@ __global__ void slos_seed_bcast_kernel(PrepArgs a) {
 // Register budget (resident 4-warp blocks per SM): the final layer, which
 // also forms the child gradient from a_n and the seed, runs fastest at 64
 // registers (8 blocks, a few bytes of spill) for up to 16 modes; the
-// intermediate layers at about 80 (6 blocks).  Measured on the m=16, n=8
-// training step: 8 blocks beat 6, 7 and 9 for the final layer.  The 16-mode
-// intermediate layers issue all 16 child gathers of a parent at once (one
-// round trip instead of two) at 90 registers, 5 blocks: 0.478 -> 0.472 ms per
-// step (4 blocks: 0.556 ms); the other mode counts keep batches of 8 at 6.
+// intermediate layers at about 80 (6 blocks).  Plans of 13-16 modes use
+// slos_bwd_tmem_kernel below instead, whose dU accumulators live in tensor
+// memory.
 constexpr int kBwdTabWarps = 4;
 constexpr int kBwdTabBatch = 8;  // child gathers issued together per parent
 // final layer of 16-mode plans, dU in tensor memory: 9 blocks (56 registers,
 // no spill) measured 0.890 ms per step against 1.077 ms with the register
 // accumulators at 8; 8 blocks the same, 10 (spills) 0.960 ms
 constexpr int kBwdTmemMinBlocks = 9;
+constexpr int kBwdTmemLayerMinBlocks = 8;  // the other layers of 16-mode plans: 0.472 -> 0.430 ms (9 blocks 0.435)
 constexpr int bwd_tab_min_blocks(int mmax, bool final_layer) {
-    return final_layer ? (mmax == 16 ? kBwdTmemMinBlocks : (mmax < 16 ? 8 : 6)) : (mmax == 16 ? 5 : 6);
+    return final_layer ? (mmax == 16 ? kBwdTmemMinBlocks : (mmax < 16 ? 8 : 6)) : (mmax == 16 ? kBwdTmemLayerMinBlocks : 6);
 }
-// child gathers issued together by the intermediate layers
-constexpr int bwd_layer_batch(int mmax) { return mmax == 16 ? 16 : kBwdTabBatch; }
+
 
 // HOLES: the child table may name no child (-1), for lattices where t' + e_j
 // leaves the space (collision-free states); such children contribute nothing.
@@ -570,7 +568,8 @@ __global__ void __launch_bounds__(kBwdTabWarps * 32, MINB) slos_bwd_tmem_kernel(
     const size_t gk = (size_t)grp * (size_t)a.Fk * kLanes + lane;
     const float2 *aprevb = a.aprev + gprev;
     float2 *Gprevb = a.Gprev + gprev;
-    const float2 *srcb = (SEED == SEED_AMPS_T) ? reinterpret_cast<const float2 *>(a.seed) + gk : a.an + gk;
+    const float2 *srcb = (SEED == SEED_G) ? a.Gk + gk
+                         : (SEED == SEED_AMPS_T) ? reinterpret_cast<const float2 *>(a.seed) + gk : a.an + gk;
     const float *seedb = (SEED == SEED_T) ? reinterpret_cast<const float *>(a.seed) + gk
                                           : reinterpret_cast<const float *>(a.seed);
     const uint32_t nwarps = gridDim.x * kBwdTabWarps;
@@ -654,7 +653,8 @@ cudaError_t launch_bwd_tab_t(const BwdArgs &a, const int32_t *ctab, int seed, in
     constexpr int mg = bwd_tab_min_blocks(MM, false), mf = bwd_tab_min_blocks(MM, true);
     switch (seed) {
         case SEED_G:
-            slos_bwd_tab_kernel<MM, SEED_G, mg, HOLES, bwd_layer_batch(MM)><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab);
+            if constexpr (MM == 16) slos_bwd_tmem_kernel<16, SEED_G, mg, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab);
+            else slos_bwd_tab_kernel<MM, SEED_G, mg, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab);
             break;
         case SEED_BCAST:
             if constexpr (MM == 16) slos_bwd_tmem_kernel<16, SEED_BCAST, mf, HOLES><<<grid, kBwdTabWarps * 32, 0, s>>>(a, ctab);
