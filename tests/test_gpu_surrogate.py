@@ -14,7 +14,8 @@ def bf(x):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 200), (129, 257, 1000), (64, 128, 2048),
-                                   (1024, 2048, 288), (256, 12376, 256), (8192, 2048, 2048)])
+                                   (1024, 2048, 288), (256, 12376, 256), (8192, 2048, 2048),
+                                   (2000, 3000, 96)])  # 192 ragged tiles: CTAs alternate accumulators
 def test_tc_gemm_matches_cpu(M, N, K):
     from paper_2602_11092_gb300 import surrogate as S
     rng = np.random.default_rng(M + N + K)
@@ -46,6 +47,30 @@ def test_tc_gemm_epilogues():
     D = S.gemm(A.cuda(), Bm.cuda(), S.GEMM_GELU_BWD, aux=Z)
     dref = mlp.bf16(acc * mlp.gelu_grad(Z.double().cpu().numpy()))
     assert np.abs(D.double().cpu().numpy() - dref).max() <= 1e-2 * np.abs(dref).max()
+    C0 = torch.tensor(rng.standard_normal((M, N)), dtype=torch.float32, device="cuda")
+    C1 = C0.clone()
+    S.gemm(A.cuda(), Bm.cuda(), S.GEMM_F32_ACCUM, C=C1)
+    assert np.abs(C1.cpu().numpy() - (C0.cpu().numpy() + acc)).max() < 1e-4
+    S.sync_status()
+
+
+def test_tc_gemm_epilogues_many_tiles():
+    """More tiles than SMs (200 here), ragged on both edges, so the persistent
+    CTAs walk several tiles and alternate their two TMEM accumulators while the
+    fused epilogues (bias + GELU with the pre-activation, accumulate) run."""
+    from paper_2602_11092_gb300 import surrogate as S
+    rng = np.random.default_rng(4)
+    M, N, K = 5000, 1100, 320
+    A = bf(rng.standard_normal((M, K)) * 0.2)
+    Bm = bf(rng.standard_normal((N, K)) * 0.2)
+    bias = torch.tensor(rng.standard_normal(N), dtype=torch.float32)
+    acc = A.double().numpy() @ Bm.double().numpy().T
+    Z = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+    H = S.gemm(A.cuda(), Bm.cuda(), S.GEMM_GELU, bias=bias.cuda(), aux=Z)
+    zref = mlp.bf16(acc + bias.numpy())
+    assert np.abs(Z.float().cpu().numpy() - zref).max() <= 1e-2 * np.abs(zref).max()
+    href = mlp.bf16(mlp.gelu(Z.double().cpu().numpy()))
+    assert np.abs(H.double().cpu().numpy() - href).max() <= 1e-2 * np.abs(href).max()
     C0 = torch.tensor(rng.standard_normal((M, N)), dtype=torch.float32, device="cuda")
     C1 = C0.clone()
     S.gemm(A.cuda(), Bm.cuda(), S.GEMM_F32_ACCUM, C=C1)
