@@ -260,6 +260,8 @@ def _grad_U_ref(Uh, s, c, outs):
     (5, [2, 0, 1, 0, 0], 2, False),
     (8, [1, 0, 1, 0, 1, 0, 1, 0], 33, True),
     (4, [1, 0, 0, 0], 2, False),
+    (14, [1, 0, 1, 0, 1] + [0] * 9, 5, False),   # 13-16 modes: dU in tensor memory, per-instance seed
+    (16, [0, 2] + [0] * 14, 4, True),            # 16 modes, bunched input, shared seed
 ])
 def test_backward_dU_matches_permanent_minors(slos, m, s, B, shared):
     rng = np.random.default_rng(5 + m + B)
@@ -279,9 +281,9 @@ def test_backward_dU_matches_permanent_minors(slos, m, s, B, shared):
         assert rel <= G_TOL, f"instance {b}: rel err {rel:.2e}"
 
 
-def test_backward_amplitudes(slos):
-    m, s, B = 5, [1, 1, 0, 1, 0], 3
-    rng = np.random.default_rng(12)
+@pytest.mark.parametrize("m,s,B", [(5, [1, 1, 0, 1, 0], 3), (13, [0, 1, 0, 0, 1] + [0] * 8, 2)])
+def test_backward_amplitudes(slos, m, s, B):
+    rng = np.random.default_rng(12 + m)
     U = c64(workloads.haar_unitaries(m, B, rng))
     plan = slos.Plan(m, s)
     K = plan.n_outputs
@@ -290,7 +292,7 @@ def test_backward_amplitudes(slos):
     plan.forward(U, output=slos.AMPS, save_for_backward=True, workspace=ws)
     dU = plan.backward(U, torch.tensor(g, device=dev()), ws, output=slos.AMPS).cpu().numpy()
     # L = Re sum conj(g) a  => dL/dU via FD on the oracle amplitudes
-    outs = oracle.enumerate_fock(m, 3)
+    outs = oracle.enumerate_fock(m, sum(s))
     Uh = up(U)
     h = 1e-6
     for b in range(B):
@@ -305,10 +307,10 @@ def test_backward_amplitudes(slos):
         assert np.linalg.norm(dU[b] - ref) / np.linalg.norm(ref) <= G_TOL
 
 
-def test_backward_threshold(slos):
-    m, n, B = 8, 4, 3
+@pytest.mark.parametrize("m,n,B", [(8, 4, 3), (15, 3, 2)])
+def test_backward_threshold(slos, m, n, B):
     s = workloads.even_mode_input(m, n)
-    rng = np.random.default_rng(21)
+    rng = np.random.default_rng(21 + m)
     U = c64(workloads.haar_unitaries(m, B, rng))
     plan = slos.Plan(m, s, slos.THRESHOLD)
     Kq = plan.n_outputs

@@ -79,6 +79,7 @@ def test_unbunched_rejects_bad_plans(slos):
     (8, [2, 0, 1, 0, 1, 0, 0, 0], 7, False),
     (12, [1, 0] * 6, 9, True),
     (5, [1, 1, 1, 1, 1], 3, False),
+    (16, [1, 0] * 3 + [0] * 10, 3, False),  # 16 modes: dU in tensor memory, holes in the child table
 ])
 def test_unbunched_backward_matches_permanent_minors(slos, m, s, B, shared):
     rng = np.random.default_rng(200 + m)
