@@ -7,7 +7,7 @@
  * (here the m=12, n=6 layer): features [sin phi, cos phi] -> n_hidden GELU
  * layers of width `hidden` -> logits over the n_outputs Fock states ->
  * softmax.  It is trained with the KL divergence KL(p_exact || q); the exact
- * path (slos_forward) stays the judge of its total-variation error and the
+ * path (slos_forward) stays the arbiter of its total-variation error and the
  * fallback for samples that fail the check.
  *
  * Conventions: all pointers are device pointers owned by the caller unless
@@ -78,7 +78,7 @@ slos_status_t surr_get_grad(surr_model_t model, int layer, float *gw_host, float
 slos_status_t surr_save(surr_model_t model, const char *path, int64_t stream_index);
 slos_status_t surr_load(surr_model_t model, const char *path, int64_t *stream_index);
 
-/* ---- checks used by the inference driver (exact path as judge) ---- */
+/* ---- checks used by the inference driver (exact path as arbiter) ---- */
 
 /* tv[i] = 1/2 sum_t |q[rows[i]][t] - p[i][t]| : total variation of checked
  * rows.  q float [*][K], rows int [n], p float [n][K] (exact), tv float [n]. */
