@@ -122,3 +122,18 @@ def test_transition_graph_matches_enumeration(lib, m, k):
         for j in range(m):
             tt = parent[cp].copy(); tt[j] += 1
             assert ctab[cp, j] == ckey[tuple(tt)]
+
+
+def test_dram_traffic_profile_matches_the_kernel_sources():
+    """bench.py reports the dominant kernel's DRAM bytes from the committed ncu
+    capture only while it was taken on the current single-shape kernel
+    sources (a hash of them); a kernel change must come with a new capture."""
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+
+    for kernel in ("slos_bwd_final", "slos_fwd_final"):
+        traffic = bench.ncu_traffic(kernel)
+        assert traffic is not None and traffic > 0, kernel
