@@ -52,7 +52,7 @@ def peaks():
 
 
 SLOS_KERNEL_FILES = ("abi.cu", "common.cuh", "plan.h", "slos_kernels.cuh", "slos_m16.cu", "slos_tab.cu",
-                     "tab_launch.h", "tables.h")
+                     "tab_launch.h", "tables.h", "slos_split.cu", "split.h")
 
 
 def csrc_hash() -> str:

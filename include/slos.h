@@ -315,6 +315,37 @@ slos_status_t slos_host_unrank(int m, int k, int64_t rank, int *t);
  * be NULL.  SLOS_ERR_UNSUPPORTED when parent ranks do not fit 26 bits. */
 slos_status_t slos_host_transition_table(int m, int k, int32_t *rowptr, uint32_t *entries, int32_t *ctab);
 
+/* Host: the split-lattice tables that plans of 8..16 modes build once
+ * (Sec. II-A.3's transition graph regrouped by head blocks).  The m modes are
+ * split into head modes 0..h-1 and tail modes h..m-1; the states of layer k
+ * with the same head occupations form one block of consecutive ranks.
+ * Layer k (2 <= k <= n):
+ *   counts   int64 [4]: forward blocks, backward blocks, forward chunks,
+ *            backward chunks (always written).
+ *   fdesc    int32 [blocks][4]: base rank, size, base rank of the same head in
+ *            layer k-1, tail photons | occupied head modes << 8.
+ *   fhead    uint32 [blocks][8]: (base rank of head t_H - e_j in layer k-1)
+ *            << 5 | j for the occupied head modes j, ascending, then 0.
+ *   fchunk   int32 [chunks]: block holding state 4 * chunk of layer k.
+ *   bdesc    int32 [blocks][4]: the blocks of layer k-1: base rank, size, base
+ *            rank of the same head in layer k, tail photons.
+ *   bhead    int32 [blocks][8]: base rank in layer k of head t_H + e_j, j < h.
+ *   bchunk   int32 [chunks]: block holding state 4 * chunk of layer k-1.
+ * Any array may be NULL.  h: head modes (written).  SLOS_ERR_UNSUPPORTED
+ * when the plan shape takes no split tables. */
+slos_status_t slos_host_split_layer(int m, int n, int k, int *h, int64_t *counts, int32_t *fdesc, uint32_t *fhead,
+                                    int32_t *fchunk, int32_t *bdesc, int32_t *bhead, int32_t *bchunk);
+
+/* Host: the tail tables of the split lattice over the m - h tail modes, for
+ * tail photon numbers rho = 0..n.  offsets int32 [3][n+1]: start of rho's
+ * slot rows (uint32 units), slot-row width, start of rho's child rows (rows
+ * of 8).  counts int64 [2]: slot entries, child entries (always written).
+ * slots: (local parent position << 5) | (h + tail mode) per occupied tail
+ * mode, padded with 24 (parent 0, the zero U row); ctab: uint16 local
+ * position of t_L + e_j for j < m - h, then 0.  Any array may be NULL. */
+slos_status_t slos_host_split_tail(int m, int n, int *h, int32_t *offsets, int64_t *counts, uint32_t *slots,
+                                   uint16_t *ctab);
+
 /* Device: for ranks [first, first + count) of layer k (k photons, m modes)
  * write the composition (uint8 [count][m]) and the parent index
  * rank_{k-1}(t - e_j) for every mode j (int32 [count][m], -1 where t_j = 0),

@@ -20,6 +20,7 @@
 #include "profile.h"
 #include "slos_kernels.cuh"
 #include "fused.h"
+#include "split.h"
 #include "tab_launch.h"
 
 namespace slos {
@@ -103,6 +104,7 @@ static cudaError_t init_device_once(int dev) {
     if ((e = slos_init_m24()) != cudaSuccess) return e;
     if ((e = slos_tab_init()) != cudaSuccess) return e;
     if ((e = slos_fused_init()) != cudaSuccess) return e;
+    if ((e = slos_split_init()) != cudaSuccess) return e;
     done[dev] = true;
     return cudaSuccess;
 }
@@ -180,7 +182,25 @@ static void free_fused_tables(slos_plan_s *p) {
     p->tab.fused_w = nullptr;
 }
 
+static void free_split_tables(slos_plan_s *p) {
+    SplitTables *st = p->split;
+    if (!st) return;
+    for (auto &L : st->layer) {
+        cudaFree(L.fdesc);
+        cudaFree(L.fhead);
+        cudaFree(L.fchunk);
+        cudaFree(L.bdesc);
+        cudaFree(L.bhead);
+        cudaFree(L.bchunk);
+    }
+    cudaFree(st->tslots);
+    cudaFree(st->tctab);
+    delete st;
+    p->split = nullptr;
+}
+
 static void free_tables(slos_plan_s *p) {
+    free_split_tables(p);
     free_fused_tables(p);
     for (auto &L : p->tab.layer) {
         if (L.slots) cudaFree(L.slots);
@@ -499,6 +519,59 @@ static void build_encode_tables(slos_plan_s *p) {
     cudaMemcpy(p->tab.gfact, g.data(), g.size() * 4, cudaMemcpyHostToDevice);
 }
 
+// Split-lattice tables (split.h) for Fock table plans of 8..16 modes: head
+// block descriptors of every layer k >= 2 and the shared tail tables.
+template <typename T>
+static bool upload(T **dst, const std::vector<T> &v) {
+    *dst = nullptr;
+    if (v.empty()) return true;
+    if (cudaMalloc(dst, v.size() * sizeof(T)) != cudaSuccess) {
+        *dst = nullptr;
+        return false;
+    }
+    return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+static slos_status_t build_split_tables(slos_plan_s *p) {
+    int h = 0;
+    if (!p->tab.enabled || p->space != SLOS_SPACE_FOCK || !split_eligible(p->m, p->n, &h)) return SLOS_OK;
+    SplitTables *st = new (std::nothrow) SplitTables();
+    if (!st) return fail(SLOS_ERR_OOM, "slos_plan: host allocation failed (split tables)");
+    p->split = st;
+    st->h = h;
+    st->layer.assign(p->n + 1, SplitLayer());
+    SplitTailHost tail;
+    split_build_tail_host(p->m, h, p->n, tail);
+    memcpy(st->soff, tail.soff, sizeof(st->soff));
+    memcpy(st->tw, tail.tw, sizeof(st->tw));
+    memcpy(st->coff, tail.coff, sizeof(st->coff));
+    bool ok = upload(&st->tslots, tail.slots) && upload(&st->tctab, tail.ctab);
+    st->bytes = tail.slots.size() * 4 + tail.ctab.size() * 2;
+    for (int k = 2; ok && k <= p->n; ++k) {
+        SplitLayerHost L;
+        split_build_layer_host(p->m, h, k, L);
+        // the blocks must tile both layers in rank order
+        int64_t next = 0;
+        for (size_t b = 0; b < L.fdesc.size() / 4; ++b) {
+            if (L.fdesc[4 * b] != next) return fail(SLOS_ERR_INTERNAL, "slos_plan: split blocks out of order");
+            next += L.fdesc[4 * b + 1];
+        }
+        if (next != p->F[k]) return fail(SLOS_ERR_INTERNAL, "slos_plan: split blocks do not cover the layer");
+        SplitLayer &D = st->layer[k];
+        D.nfblk = (int)(L.fdesc.size() / 4);
+        D.nbblk = (int)(L.bdesc.size() / 4);
+        std::vector<int4> fd(D.nfblk), bd(D.nbblk);
+        memcpy(fd.data(), L.fdesc.data(), L.fdesc.size() * 4);
+        memcpy(bd.data(), L.bdesc.data(), L.bdesc.size() * 4);
+        ok = upload(&D.fdesc, fd) && upload(&D.fhead, L.fhead) && upload(&D.fchunk, L.fchunk) &&
+             upload(&D.bdesc, bd) && upload(&D.bhead, L.bhead) && upload(&D.bchunk, L.bchunk);
+        st->bytes += (L.fdesc.size() + L.fhead.size() + L.fchunk.size() + L.bdesc.size() + L.bhead.size() +
+                      L.bchunk.size()) * 4;
+    }
+    if (!ok) return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate or upload the split-lattice tables");
+    return SLOS_OK;
+}
+
 // Sorted on-chip layout (tables.h, FusedLayer) from the plan's slot tables.
 // Returns false (nothing kept) on an allocation failure.
 static bool build_fused_tables(slos_plan_s *p) {
@@ -645,6 +718,17 @@ static int bwd_tab_blocks(const slos_plan_s *p, int64_t parents, int NG, bool fi
     return (int)std::max<int64_t>(1, std::min(need, target));
 }
 
+// Split-lattice kernels: the forward walks CTA tiles of kSplitTile states,
+// the backward warp runs of kSplitRun parents; grids fill the resident blocks
+// their register budgets allow.
+static int split_blocks(const slos_plan_s *p, int64_t items, int items_per_block, int NG, int per_sm) {
+    const int64_t need = (items + items_per_block - 1) / items_per_block;
+    const int64_t target = std::max<int64_t>(1, (int64_t)p->sm_count * per_sm / std::max(1, NG));
+    return (int)std::max<int64_t>(1, std::min(need, target));
+}
+static int64_t split_runs(int64_t states) { return (states + kSplitRun - 1) / kSplitRun; }
+static int64_t split_tiles(int64_t states) { return (states + kSplitTile - 1) / kSplitTile; }
+
 constexpr int kChunkStore = 64;
 constexpr int kChunkFinal = 32;
 constexpr int kChunkBwd = 64;
@@ -701,8 +785,9 @@ static Layout make_layout(const slos_plan_s *p, int batch, bool training) {
         L.seedT = take(row * p->F[n]);  // c64-sized: enough for either seed kind
         L.dpw = L.seedT;
         for (int k = 1; k <= n; ++k) {
-            const int bx = p->tab.enabled ? bwd_tab_blocks(p, p->F[k - 1], NG, k == n)
-                                          : blocks_for(p, p->F[k - 1], kChunkBwd, NG);
+            const int bx = (p->split && k >= 2) ? split_blocks(p, split_runs(p->F[k - 1]), kSplitBwdWarps, NG, kSplitBwdMinBlocks)
+                           : p->tab.enabled ? bwd_tab_blocks(p, p->F[k - 1], NG, k == n)
+                                            : blocks_for(p, p->F[k - 1], kChunkBwd, NG);
             L.bwd_blocks[k] = bx;
             L.dupart[k] = take((size_t)NG * bx * kLanes * p->m * sizeof(float2));
         }
@@ -977,6 +1062,13 @@ slos_status_t slos_plan_space(int m, int n, const int *input_state, slos_detecti
         delete p;
         return tst;
     }
+    tst = build_split_tables(p);
+    if (tst != SLOS_OK) {
+        free_tables(p);
+        cudaFree(p->d_status);
+        delete p;
+        return tst;
+    }
     choose_fused(p);
     build_encode_tables(p);
     *out = p;
@@ -1067,13 +1159,40 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
         bytes += (epi == EPI_AMPS ? 8.0 : 4.0) * p->K + (save ? 8.0 * a.Fk : 0.0);
     }
     ProfScope ps(name, bytes * batch, s);
+    if (kSplitForward && p->split && k >= 2) {
+        const SplitTables &st = *p->split;
+        const SplitLayer &L = st.layer[k];
+        SplitFwdArgs sa;
+        memset(&sa, 0, sizeof(sa));
+        sa.prev = a.prev;
+        sa.next = a.next;
+        sa.U = U;
+        sa.out = out;
+        sa.w = p->tab.w;
+        sa.pat = p->tab.pat;
+        sa.desc = L.fdesc;
+        sa.head = L.fhead;
+        sa.chunk = L.fchunk;
+        sa.tslots = st.tslots;
+        memcpy(sa.soff, st.soff, sizeof(sa.soff));
+        memcpy(sa.tw, st.tw, sizeof(sa.tw));
+        sa.Fk = (int)p->F[k];
+        sa.Fprev = (int)p->F[k - 1];
+        sa.ntiles = (int)split_tiles(p->F[k]);
+        sa.K = p->K;
+        sa.m = p->m;
+        sa.col = a.col;
+        sa.B = batch;
+        SLOS_CUDA(slos_launch_fwd_split(sa, NG, epi, save, split_blocks(p, sa.ntiles, 1, NG, kSplitFwdMinBlocks), s));
+        return SLOS_OK;
+    }
     if (p->tab.enabled) {
         TabArgs t;
         t.slots = p->tab.layer[k].slots;
         t.kw = p->tab.layer[k].kw;
         t.w = p->tab.w;
         t.pat = p->tab.pat;
-        SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, NG, fwd_tab_min_blocks(epi)), s));
+        SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, NG, fwd_tab_resident_blocks(epi)), s));
     } else {
         SLOS_CUDA(launch_fwd(p->m, a, epi, save, bx, s));
     }
@@ -1245,7 +1364,31 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
             // layered-model bytes: read a_{k-1} and G_k (or a_n and dL/dout), write G_{k-1}
             double bytes = (kp >= 1 ? 16.0 * a.Fprev : 0.0) + (k == n ? 12.0 : 8.0) * a.Fk;
             ProfScope ps(k == n ? "slos_bwd_final" : "slos_bwd_layer", bytes * batch, s);
-            if (p->tab.enabled)
+            if (p->split && k >= 2) {
+                const SplitTables &st = *p->split;
+                const SplitLayer &L = st.layer[k];
+                SplitBwdArgs sa;
+                memset(&sa, 0, sizeof(sa));
+                sa.aprev = a.aprev;
+                sa.Gk = a.Gk;
+                sa.Gprev = a.Gprev;
+                sa.an = a.an;
+                sa.seed = a.seed;
+                sa.U = Ud;
+                sa.dUpart = a.dUpart;
+                sa.desc = L.bdesc;
+                sa.head = L.bhead;
+                sa.chunk = L.bchunk;
+                sa.tctab = st.tctab;
+                memcpy(sa.coff, st.coff, sizeof(sa.coff));
+                sa.Fk = (int)p->F[k];
+                sa.Fprev = (int)p->F[kp];
+                sa.nruns = (int)split_runs(p->F[kp]);
+                sa.m = m;
+                sa.col = a.col;
+                sa.B = batch;
+                SLOS_CUDA(slos_launch_bwd_split(sa, NG, k == n ? seed : SEED_G, st.h, Ly.bwd_blocks[k], s));
+            } else if (p->tab.enabled)
                 SLOS_CUDA(launch_bwd_tab(m, a, p->tab.layer[k].ctab, k == n ? seed : SEED_G, Ly.bwd_blocks[k],
                                          p->space == SLOS_SPACE_UNBUNCHED, s));
             else
@@ -1325,6 +1468,52 @@ slos_status_t slos_host_transition_table(int m, int k, int32_t *rowptr, uint32_t
     if (rowptr) memcpy(rowptr, rp.data(), rp.size() * 4);
     if (entries) memcpy(entries, en.data(), en.size() * 4);
     if (ctab) memcpy(ctab, ct.data(), ct.size() * 4);
+    return SLOS_OK;
+}
+
+slos_status_t slos_host_split_layer(int m, int n, int k, int *h, int64_t *counts, int32_t *fdesc, uint32_t *fhead,
+                                    int32_t *fchunk, int32_t *bdesc, int32_t *bhead, int32_t *bchunk) {
+    int hh = 0;
+    if (m < 2 || m > kMaxModes || n < 2 || n > kMaxPhotons || k < 2 || k > n || !split_eligible(m, n, &hh))
+        return fail(SLOS_ERR_UNSUPPORTED, "slos_host_split_layer: no split tables for this shape");
+    SplitLayerHost L;
+    split_build_layer_host(m, hh, k, L);
+    if (h) *h = hh;
+    if (counts) {
+        counts[0] = (int64_t)L.fdesc.size() / 4;
+        counts[1] = (int64_t)L.bdesc.size() / 4;
+        counts[2] = (int64_t)L.fchunk.size();
+        counts[3] = (int64_t)L.bchunk.size();
+    }
+    if (fdesc) memcpy(fdesc, L.fdesc.data(), L.fdesc.size() * 4);
+    if (fhead) memcpy(fhead, L.fhead.data(), L.fhead.size() * 4);
+    if (fchunk) memcpy(fchunk, L.fchunk.data(), L.fchunk.size() * 4);
+    if (bdesc) memcpy(bdesc, L.bdesc.data(), L.bdesc.size() * 4);
+    if (bhead) memcpy(bhead, L.bhead.data(), L.bhead.size() * 4);
+    if (bchunk) memcpy(bchunk, L.bchunk.data(), L.bchunk.size() * 4);
+    return SLOS_OK;
+}
+
+slos_status_t slos_host_split_tail(int m, int n, int *h, int32_t *offsets, int64_t *counts, uint32_t *slots,
+                                   uint16_t *ctab) {
+    int hh = 0;
+    if (m < 2 || m > kMaxModes || n < 2 || n > kMaxPhotons || !split_eligible(m, n, &hh))
+        return fail(SLOS_ERR_UNSUPPORTED, "slos_host_split_tail: no split tables for this shape");
+    SplitTailHost T;
+    split_build_tail_host(m, hh, n, T);
+    if (h) *h = hh;
+    if (offsets)
+        for (int r = 0; r <= n; ++r) {
+            offsets[r] = T.soff[r];
+            offsets[(n + 1) + r] = T.tw[r];
+            offsets[2 * (n + 1) + r] = T.coff[r];
+        }
+    if (counts) {
+        counts[0] = (int64_t)T.slots.size();
+        counts[1] = (int64_t)T.ctab.size();
+    }
+    if (slots) memcpy(slots, T.slots.data(), T.slots.size() * 4);
+    if (ctab) memcpy(ctab, T.ctab.data(), T.ctab.size() * 2);
     return SLOS_OK;
 }
 

@@ -25,6 +25,7 @@ int64_t host_rank(int m, const int *t);
 void host_unrank(int m, int k, int64_t r, int *t);
 
 struct BatchedPlan;  // uneven batches (batched.cu)
+struct SplitTables;  // head/tail split of the lattice (split.h)
 
 struct Layout {
     // byte offsets into the workspace (SIZE_MAX = absent)
@@ -69,4 +70,5 @@ struct slos_plan_s {
     int fused_cap[2] = {1, 1};  // its buffer capacities (states per instance, even / odd layers)
     bool fused_sorted = false;  // walks the sorted layout (tab.fused) instead of Fock order
     slos::BatchedPlan *batched;
+    slos::SplitTables *split = nullptr;  // split-lattice tables (null: slot-table kernels only)
 };

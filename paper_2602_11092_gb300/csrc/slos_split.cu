@@ -1,0 +1,616 @@
+// SLOS layers on the head/tail split of the Fock lattice (split.h).
+//
+// Forward, layer k:  a_k(t) = sum_{j: t_j > 0} U[j, c_k] a_{k-1}(t - e_j)
+// (Sec. II-A.2/II-A.3).  Each warp owns a group of 32 instances (lane =
+// instance, layout [F_k][32] complex64, one coalesced 256-byte row per state)
+// and walks a chunk of 32 consecutive states.  Within a head block the
+// head-mode parents of state c are rows c + (parent block base - block base),
+// and their U factors are loaded into registers once per block; the tail
+// parents come from the block's tail slot row (one 16- or 32-byte broadcast
+// load per state) and take U from shared memory.  A per-block switch on the
+// number of occupied head modes selects a body whose head loop is fully
+// unrolled, so the head slots need neither padding nor per-state decoding.
+//
+// Backward, layer k:  for every parent t' of layer k-1
+//      G_{k-1}(t') = sum_j conj(U[j, c_k]) G_k(t' + e_j)
+//      dU[j, c_k] += conj(a_{k-1}(t')) G_k(t' + e_j)
+// with all m children present: head children at fixed offsets per block,
+// tail children from the tail child row.  The mode of every child is a
+// compile-time index, so U[j, c_k] and the dU accumulators sit in tensor
+// memory (one 32-lane quarter per warp, 16 columns per batch of 8 modes) and
+// move with one tcgen05.ld / tcgen05.st per batch instead of per-child
+// shared-memory loads.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "slos_kernels.cuh"
+#include "split.h"
+#include "tab_launch.h"
+
+namespace slos {
+
+// ============================================================ host tables
+int64_t binom_host(int a, int e);
+int64_t host_rank(int m, const int *t);
+
+// Successor in descending lexicographic order among compositions with the
+// same sum; false after the last one, (0, ..., 0, sum).
+static bool next_comp_desc(std::vector<int> &t) {
+    const int P = (int)t.size();
+    int i = P - 2;
+    while (i >= 0 && t[i] == 0) --i;
+    if (i < 0) return false;
+    int rest = 0;
+    for (int q = i + 1; q < P; ++q) {
+        rest += t[q];
+        t[q] = 0;
+    }
+    t[i] -= 1;
+    t[i + 1] = rest + 1;
+    return true;
+}
+
+bool split_eligible(int m, int n, int *h_out) {
+    if (m < 8 || m > 16 || n < 2) return false;
+    const int h = m >= 13 ? 8 : 6;
+    const int mL = m - h;
+    if (mL < 1 || mL > kSplitMaxTail || h > kSplitMaxHead) return false;
+    if (binom_host(n + mL - 1, n) > kSplitMaxTailStates) return false;
+    if (h_out) *h_out = h;
+    return true;
+}
+
+void split_build_layer_host(int m, int h, int k, SplitLayerHost &out) {
+    const int mL = m - h;
+    std::vector<int> full(m, 0);
+    // forward: head compositions of at most k photons, as (h+1)-compositions
+    // of k whose last part is the tail photon count
+    {
+        out.fdesc.clear();
+        out.fhead.clear();
+        std::vector<int> tc(h + 1, 0);
+        tc[0] = k;
+        do {
+            const int rho = tc[h];
+            std::fill(full.begin(), full.end(), 0);
+            for (int j = 0; j < h; ++j) full[j] = tc[j];
+            full[h] = rho;
+            const int64_t base = host_rank(m, full.data());
+            const int64_t size = binom_host(rho + mL - 1, mL - 1);
+            int64_t zbase = 0;
+            if (rho >= 1) {
+                full[h] = rho - 1;
+                zbase = host_rank(m, full.data());
+                full[h] = rho;
+            }
+            uint32_t heads[kSplitMaxHead] = {0};
+            int qh = 0;
+            for (int j = 0; j < h; ++j) {
+                if (tc[j] == 0) continue;
+                full[j] -= 1;
+                heads[qh++] = ((uint32_t)host_rank(m, full.data()) << 5) | (uint32_t)j;
+                full[j] += 1;
+            }
+            out.fdesc.push_back((int32_t)base);
+            out.fdesc.push_back((int32_t)size);
+            out.fdesc.push_back((int32_t)zbase);
+            out.fdesc.push_back(rho | (qh << 8));
+            for (int q = 0; q < kSplitMaxHead; ++q) out.fhead.push_back(heads[q]);
+        } while (next_comp_desc(tc));
+        const int64_t Fk = binom_host(m + k - 1, k);
+        out.fchunk.assign((size_t)((Fk + kSplitRun - 1) / kSplitRun), 0);
+        const size_t nb = out.fdesc.size() / 4;
+        for (size_t b = 0; b < nb; ++b) {
+            const int64_t lo = out.fdesc[4 * b], hi = lo + out.fdesc[4 * b + 1];
+            for (int64_t c0 = (lo + kSplitRun - 1) / kSplitRun * kSplitRun; c0 < hi; c0 += kSplitRun)
+                out.fchunk[(size_t)(c0 / kSplitRun)] = (int32_t)b;
+        }
+    }
+    // backward: head compositions of at most k-1 photons (the parents)
+    {
+        out.bdesc.clear();
+        out.bhead.clear();
+        std::vector<int> tc(h + 1, 0);
+        tc[0] = k - 1;
+        do {
+            const int rho = tc[h];
+            std::fill(full.begin(), full.end(), 0);
+            for (int j = 0; j < h; ++j) full[j] = tc[j];
+            full[h] = rho;
+            const int64_t base = host_rank(m, full.data());
+            const int64_t size = binom_host(rho + mL - 1, mL - 1);
+            full[h] = rho + 1;
+            const int64_t lcb = host_rank(m, full.data());
+            full[h] = rho;
+            out.bdesc.push_back((int32_t)base);
+            out.bdesc.push_back((int32_t)size);
+            out.bdesc.push_back((int32_t)lcb);
+            out.bdesc.push_back(rho);
+            for (int j = 0; j < kSplitMaxHead; ++j) {
+                if (j < h) {
+                    full[j] += 1;
+                    out.bhead.push_back((int32_t)host_rank(m, full.data()));
+                    full[j] -= 1;
+                } else {
+                    out.bhead.push_back(0);
+                }
+            }
+        } while (next_comp_desc(tc));
+        const int64_t Fp = binom_host(m + k - 2, k - 1);
+        out.bchunk.assign((size_t)((Fp + kSplitRun - 1) / kSplitRun), 0);
+        const size_t nb = out.bdesc.size() / 4;
+        for (size_t b = 0; b < nb; ++b) {
+            const int64_t lo = out.bdesc[4 * b], hi = lo + out.bdesc[4 * b + 1];
+            for (int64_t c0 = (lo + kSplitRun - 1) / kSplitRun * kSplitRun; c0 < hi; c0 += kSplitRun)
+                out.bchunk[(size_t)(c0 / kSplitRun)] = (int32_t)b;
+        }
+    }
+}
+
+void split_build_tail_host(int m, int h, int n, SplitTailHost &out) {
+    const int mL = m - h;
+    out.slots.clear();
+    out.ctab.clear();
+    std::vector<int> t(mL, 0);
+    for (int rho = 0; rho <= n; ++rho) {
+        const int tw = rho == 0 ? 0 : ((std::min(mL, rho) + 3) & ~3);
+        out.tw[rho] = tw;
+        out.soff[rho] = (int)out.slots.size();
+        out.coff[rho] = (int)(out.ctab.size() / 8);
+        std::fill(t.begin(), t.end(), 0);
+        t[0] = rho;
+        do {
+            if (tw > 0) {
+                int q = 0;
+                for (int j = 0; j < mL; ++j) {
+                    if (t[j] == 0) continue;
+                    t[j] -= 1;
+                    out.slots.push_back(((uint32_t)host_rank(mL, t.data()) << 5) | (uint32_t)(h + j));
+                    t[j] += 1;
+                    ++q;
+                }
+                for (; q < tw; ++q) out.slots.push_back(kSlotEmpty);
+            }
+            if (rho < n) {
+                for (int j = 0; j < 8; ++j) {
+                    uint16_t v = 0;
+                    if (j < mL) {
+                        t[j] += 1;
+                        v = (uint16_t)host_rank(mL, t.data());
+                        t[j] -= 1;
+                    }
+                    out.ctab.push_back(v);
+                }
+            }
+        } while (mL > 1 && next_comp_desc(t));
+    }
+}
+
+// ============================================================ forward kernel
+size_t split_fwd_smem_bytes(int epi) {
+    const size_t cells = (size_t)32 * (kSplitTile + 1);
+    return epi == EPI_PROBS ? cells * sizeof(float) : (epi == EPI_AMPS ? cells * sizeof(float2) : 0);
+}
+
+struct SplitFwdCtx {
+    const float2 *prevg;  // a_{k-1} of the warp's group, lane offset included
+    float2 *nextg;        // a_k of the group (or null)
+    const float2 *usl;    // this lane's column of the staged U rows
+    float *tile;          // the CTA's [32 instances][kSplitTile + 1] output tile
+    int t0;               // first state of the CTA tile
+    int c0;               // first state of the warp's run
+    float wl;             // final weight of state c0 + lane (lanes < kSplitRun)
+    int patl;             // threshold pattern of state c0 + lane
+    int run_pat;
+    float run_val;
+    int64_t orow;         // this lane's output row offset (inst * K)
+    bool valid;
+};
+
+// Sum over the first N tail slots: parent rows issued together, then the
+// products with the staged U rows.
+template <int N, int KW>
+__device__ __forceinline__ float2 split_tail_sum(const uint32_t (&e)[KW], const float2 *lprev, const float2 *usl,
+                                                 float2 acc) {
+    float2 v[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = __ldg(lprev + ((e[q] >> 5) << 5));
+#pragma unroll
+    for (int q = 0; q < N; ++q) acc = cfma(usl[(e[q] & 31u) * 32u], v[q], acc);
+    return acc;
+}
+
+template <int EPI, bool SAVE>
+__device__ __forceinline__ void split_emit(const SplitFwdArgs &a, SplitFwdCtx &x, int c, float2 acc) {
+    if (SAVE || EPI == EPI_STORE) x.nextg[(uint32_t)c << 5] = acc;
+    if (EPI == EPI_STORE) return;
+    const int lane = threadIdx.x & 31;
+    const int ci = c - x.t0;
+    const float w = __shfl_sync(0xffffffffu, x.wl, c - x.c0);
+    if (EPI == EPI_PROBS) {
+        x.tile[lane * (kSplitTile + 1) + ci] = w * (acc.x * acc.x + acc.y * acc.y);
+    } else if (EPI == EPI_AMPS) {
+        reinterpret_cast<float2 *>(x.tile)[lane * (kSplitTile + 1) + ci] = cscale(acc, sqrtf(w));
+    } else if (EPI == EPI_THRESH) {
+        const int pat = __shfl_sync(0xffffffffu, x.patl, c - x.c0);
+        const float pr = w * (acc.x * acc.x + acc.y * acc.y);
+        if (pat != x.run_pat) {
+            if (x.run_pat >= 0 && x.valid) atomicAdd(reinterpret_cast<float *>(a.out) + x.orow + x.run_pat, x.run_val);
+            x.run_pat = pat;
+            x.run_val = 0.f;
+        }
+        x.run_val += pr;
+    }
+}
+
+// States [c, stop) of head block b (descriptor d) with QH occupied head modes.
+template <int QH, int EPI, bool SAVE>
+__device__ __forceinline__ void split_walk(const SplitFwdArgs &a, SplitFwdCtx &x, const int4 d, int b, int c,
+                                           int stop) {
+    int hoff[QH > 0 ? QH : 1];
+    float2 uh[QH > 0 ? QH : 1];
+#pragma unroll
+    for (int q = 0; q < QH; ++q) {
+        const uint32_t e = __ldg(a.head + (size_t)b * kSplitMaxHead + q);
+        hoff[q] = (int)(e >> 5) - d.x;  // head parent of state c: row c + hoff[q]
+        uh[q] = x.usl[(e & 31u) * 32u];
+    }
+    const int rho = d.w & 255;
+    const int W = a.tw[rho];
+    const uint4 *trow = reinterpret_cast<const uint4 *>(a.tslots + a.soff[rho] + (size_t)(c - d.x) * W);
+    const float2 *lprev = x.prevg + ((uint32_t)d.z << 5);
+    for (; c < stop; ++c) {
+        float2 v[QH > 0 ? QH : 1];
+#pragma unroll
+        for (int q = 0; q < QH; ++q) v[q] = __ldg(x.prevg + ((uint32_t)(c + hoff[q]) << 5));
+        float2 acc = make_float2(0.f, 0.f);
+        if (W == 4) {
+            const uint4 r = __ldg(trow);
+            const uint32_t e[4] = {r.x, r.y, r.z, r.w};
+            acc = split_tail_sum<4, 4>(e, lprev, x.usl, acc);
+            trow += 1;
+        } else if (W == 8) {
+            const uint4 r0 = __ldg(trow), r1 = __ldg(trow + 1);
+            const uint32_t e[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            // the state is the warp's (lane = instance): a uniform branch skips padding
+            if (e[4] == kSlotEmpty) acc = split_tail_sum<4, 8>(e, lprev, x.usl, acc);
+            else if (e[6] == kSlotEmpty) acc = split_tail_sum<6, 8>(e, lprev, x.usl, acc);
+            else acc = split_tail_sum<8, 8>(e, lprev, x.usl, acc);
+            trow += 2;
+        }
+#pragma unroll
+        for (int q = 0; q < QH; ++q) acc = cfma(uh[q], v[q], acc);
+        split_emit<EPI, SAVE>(a, x, c, acc);
+    }
+}
+
+template <int EPI, bool SAVE>
+__global__ void __launch_bounds__(kSplitFwdWarps * 32, kSplitFwdMinBlocks) slos_fwd_split_kernel(SplitFwdArgs a) {
+    __shared__ float2 us[kMaxModes + 1][32];
+    extern __shared__ float4 smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int grp = blockIdx.y;
+    const int inst = grp * kLanes + lane;
+    const bool valid = inst < a.B;
+    for (int j = warp; j < a.m; j += kSplitFwdWarps)
+        us[j][lane] = valid ? a.U[((int64_t)inst * a.m + j) * a.m + a.col] : make_float2(0.f, 0.f);
+    if (warp == 0) us[kMaxModes][lane] = make_float2(0.f, 0.f);
+    __syncthreads();
+
+    SplitFwdCtx x;
+    x.prevg = a.prev + (size_t)grp * (size_t)a.Fprev * kLanes + lane;
+    x.nextg = (SAVE || EPI == EPI_STORE) ? a.next + (size_t)grp * (size_t)a.Fk * kLanes + lane : nullptr;
+    x.usl = &us[0][lane];
+    x.tile = reinterpret_cast<float *>(smem_raw);
+    x.valid = valid;
+    x.orow = (int64_t)inst * a.K;
+    x.run_pat = -1;
+    x.run_val = 0.f;
+    x.wl = 0.f;
+    x.patl = 0;
+    // the CTA walks tiles of kSplitTile consecutive states, warp w the run of
+    // kSplitRun states at w * kSplitRun, so the states in flight across the
+    // grid stay a compact rank window (their parents share L2 lines)
+    for (int tl = blockIdx.x; tl < a.ntiles; tl += gridDim.x) {
+        const int t0 = tl * kSplitTile;
+        const int c0 = t0 + warp * kSplitRun;
+        const int cend = min(c0 + kSplitRun, a.Fk);
+        x.t0 = t0;
+        x.c0 = c0;
+        if (c0 < cend) {
+            if (EPI != EPI_STORE) {
+                x.wl = c0 + lane < cend ? __ldg(a.w + c0 + lane) : 0.f;
+                if (EPI == EPI_THRESH) x.patl = c0 + lane < cend ? __ldg(a.pat + c0 + lane) : 0;
+            }
+            int b = __ldg(a.chunk + c0 / kSplitRun);
+            for (int c = c0; c < cend; ++b) {
+                const int4 d = __ldg(reinterpret_cast<const int4 *>(a.desc) + b);
+                const int stop = min(d.x + d.y, cend);
+                switch ((d.w >> 8) & 15) {
+                    case 0: split_walk<0, EPI, SAVE>(a, x, d, b, c, stop); break;
+                    case 1: split_walk<1, EPI, SAVE>(a, x, d, b, c, stop); break;
+                    case 2: split_walk<2, EPI, SAVE>(a, x, d, b, c, stop); break;
+                    case 3: split_walk<3, EPI, SAVE>(a, x, d, b, c, stop); break;
+                    case 4: split_walk<4, EPI, SAVE>(a, x, d, b, c, stop); break;
+                    case 5: split_walk<5, EPI, SAVE>(a, x, d, b, c, stop); break;
+                    case 6: split_walk<6, EPI, SAVE>(a, x, d, b, c, stop); break;
+                    case 7: split_walk<7, EPI, SAVE>(a, x, d, b, c, stop); break;
+                    default: split_walk<8, EPI, SAVE>(a, x, d, b, c, stop); break;
+                }
+                c = stop;
+            }
+        }
+        if (EPI == EPI_PROBS || EPI == EPI_AMPS) {
+            // the tile: instance i's kSplitTile consecutive outputs in one 128/256-byte store
+            __syncthreads();
+            const int nc = min(kSplitTile, a.Fk - t0);
+            for (int i = warp; i < kLanes; i += kSplitFwdWarps) {
+                const int ii = grp * kLanes + i;
+                if (ii < a.B && lane < nc) {
+                    const int64_t o = (int64_t)ii * a.K + t0 + lane;
+                    if (EPI == EPI_PROBS)
+                        reinterpret_cast<float *>(a.out)[o] = x.tile[i * (kSplitTile + 1) + lane];
+                    else
+                        reinterpret_cast<float2 *>(a.out)[o] =
+                            reinterpret_cast<const float2 *>(x.tile)[i * (kSplitTile + 1) + lane];
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (EPI == EPI_THRESH && x.run_pat >= 0 && valid)
+        atomicAdd(reinterpret_cast<float *>(a.out) + x.orow + x.run_pat, x.run_val);
+}
+
+// ============================================================ backward kernel
+// 8-column tensor-memory moves (4 complex values per lane).  The wait on the
+// loads names the loaded registers, so no use of them can be scheduled
+// before it; none of these statements is a compiler memory barrier, so the
+// global loads of the children stay free to move around them.
+__device__ __forceinline__ void tm_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tm_wait_ld8(uint32_t (&r)[8], uint32_t (&q)[8]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(q[0]), "+r"(q[1]), "+r"(q[2]), "+r"(q[3]), "+r"(q[4]), "+r"(q[5]), "+r"(q[6]), "+r"(q[7]));
+}
+__device__ __forceinline__ void tm_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]));
+    asm volatile("tcgen05.wait::st.sync.aligned;");
+}
+
+// 16-bit local child position J of a tail child row
+template <int J>
+__device__ __forceinline__ uint32_t crow16(const uint4 &r) {
+    const uint32_t w = J < 2 ? r.x : (J < 4 ? r.y : (J < 6 ? r.z : r.w));
+    return (J & 1) ? (w >> 16) : (w & 0xffffu);
+}
+
+template <int SEED>
+__device__ __forceinline__ float2 split_child(const float2 *srcb, const float *seedb, uint32_t x) {
+    float2 g = __ldg(srcb + (x << 5));
+    if (SEED == SEED_T) g = cscale(g, __ldg(seedb + (x << 5)));
+    if (SEED == SEED_BCAST) g = cscale(g, __ldg(seedb + x));
+    return g;
+}
+
+// One batch of (up to) 4 children of a parent: G_{k-1} += conj(U_j) g_j and
+// dU_j += conj(a_{k-1}) g_j, with dU_j and U_j in tensor-memory columns
+// [cd, cd + 8) and [cu, cu + 8) of the warp's lane quarter.  Modes past the
+// plan's last one hold U = 0 and g = 0.
+template <int N>
+__device__ __forceinline__ void split_bwd_batch(uint32_t tq, uint32_t cd, uint32_t cu, const float2 (&g)[4], float2 av,
+                                                float2 &gacc) {
+    uint32_t du[8], uu[8];
+    tm_ld8(tq + cd, du);
+    tm_ld8(tq + cu, uu);
+    tm_wait_ld8(du, uu);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const float2 u = make_float2(__uint_as_float(uu[2 * j]), __uint_as_float(uu[2 * j + 1]));
+        gacc = cfma_conj_a(u, g[j], gacc);
+        const float2 d = cfma_conj_a(av, g[j], make_float2(__uint_as_float(du[2 * j]), __uint_as_float(du[2 * j + 1])));
+        du[2 * j] = __float_as_uint(d.x);
+        du[2 * j + 1] = __float_as_uint(d.y);
+    }
+    tm_st8(tq + cd, du);
+}
+
+// TMEM columns of a warp's lane quarter: dU of the head modes [0, 16), of the
+// tail modes [16, 32); U[j, c_k] of the head modes [32, 48), tail [48, 64).
+constexpr int kSplitTmemCols = 64;
+
+template <int H, int SEED>
+__global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_bwd_split_kernel(SplitBwdArgs a) {
+    constexpr int T = kSplitMaxTail;
+    __shared__ float2 red[kSplitBwdWarps][32];
+    __shared__ uint32_t tmem_slot;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int grp = blockIdx.y;
+    const int inst = grp * kLanes + lane;
+    const bool valid = inst < a.B;
+    const int m = a.m;
+    const int mL = m - H;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         static_cast<uint32_t>(__cvta_generic_to_shared(&tmem_slot))),
+                     "r"(kSplitTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tq = tmem_slot + ((uint32_t)(warp * 32) << 16);
+    {
+        float z[16], uh[16], ut[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) z[i] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float2 u = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+            if (valid && j < H) u = a.U[((int64_t)inst * m + j) * m + a.col];
+            if (valid && j < mL) v = a.U[((int64_t)inst * m + H + j) * m + a.col];
+            uh[2 * j] = u.x;
+            uh[2 * j + 1] = u.y;
+            ut[2 * j] = v.x;
+            ut[2 * j + 1] = v.y;
+        }
+        tm_st16(tq, z);
+        tm_st16(tq + 16, z);
+        tm_st16(tq + 32, uh);
+        tm_st16(tq + 48, ut);
+    }
+    const size_t gprev = (size_t)grp * (size_t)a.Fprev * kLanes + lane;
+    const size_t gk = (size_t)grp * (size_t)a.Fk * kLanes + lane;
+    const float2 *aprevb = a.aprev + gprev;
+    float2 *Gprevb = a.Gprev + gprev;
+    const float2 *srcb = (SEED == SEED_G) ? a.Gk + gk
+                         : (SEED == SEED_AMPS_T) ? reinterpret_cast<const float2 *>(a.seed) + gk : a.an + gk;
+    const float *seedb = (SEED == SEED_T) ? reinterpret_cast<const float *>(a.seed) + gk
+                                          : reinterpret_cast<const float *>(a.seed);
+    const int wstride = gridDim.x * kSplitBwdWarps;
+    for (int ch = blockIdx.x * kSplitBwdWarps + warp; ch < a.nruns; ch += wstride) {
+        const int c0 = ch * kSplitRun;
+        const int cend = min(c0 + kSplitRun, a.Fprev);
+        int b = __ldg(a.chunk + ch);
+        for (int c = c0; c < cend; ++b) {
+            const int4 d = __ldg(reinterpret_cast<const int4 *>(a.desc) + b);
+            const int stop = min(d.x + d.y, cend);
+            int hoff[8];
+            {
+                const int4 h0 = __ldg(reinterpret_cast<const int4 *>(a.head) + 2 * b);
+                const int4 h1 = __ldg(reinterpret_cast<const int4 *>(a.head) + 2 * b + 1);
+                const int hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+#pragma unroll
+                for (int j = 0; j < 8; ++j) hoff[j] = hv[j] - d.x;  // head child of parent c: c + hoff[j]
+            }
+            const uint4 *crow = reinterpret_cast<const uint4 *>(a.tctab) + a.coff[d.w] + (c - d.x);
+            const uint32_t lc = (uint32_t)d.z;
+            for (; c < stop; ++c, ++crow) {
+                const float2 av = __ldg(aprevb + ((uint32_t)c << 5));
+                const uint4 cr = __ldg(crow);
+                float2 gacc = make_float2(0.f, 0.f);
+                float2 g[4];
+                // head modes 0..3, 4..H-1
+#pragma unroll
+                for (int j = 0; j < 4; ++j) g[j] = split_child<SEED>(srcb, seedb, (uint32_t)(c + hoff[j]));
+                split_bwd_batch<4>(tq, 0, 32, g, av, gacc);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    g[j] = (4 + j < H) ? split_child<SEED>(srcb, seedb, (uint32_t)(c + hoff[4 + j])) : make_float2(0.f, 0.f);
+                split_bwd_batch<H - 4>(tq, 8, 40, g, av, gacc);
+                // tail modes 0..3, 4..7 (positions from the tail child row)
+                g[0] = mL > 0 ? split_child<SEED>(srcb, seedb, lc + crow16<0>(cr)) : make_float2(0.f, 0.f);
+                g[1] = mL > 1 ? split_child<SEED>(srcb, seedb, lc + crow16<1>(cr)) : make_float2(0.f, 0.f);
+                g[2] = mL > 2 ? split_child<SEED>(srcb, seedb, lc + crow16<2>(cr)) : make_float2(0.f, 0.f);
+                g[3] = mL > 3 ? split_child<SEED>(srcb, seedb, lc + crow16<3>(cr)) : make_float2(0.f, 0.f);
+                split_bwd_batch<4>(tq, 16, 48, g, av, gacc);
+                g[0] = mL > 4 ? split_child<SEED>(srcb, seedb, lc + crow16<4>(cr)) : make_float2(0.f, 0.f);
+                g[1] = mL > 5 ? split_child<SEED>(srcb, seedb, lc + crow16<5>(cr)) : make_float2(0.f, 0.f);
+                g[2] = mL > 6 ? split_child<SEED>(srcb, seedb, lc + crow16<6>(cr)) : make_float2(0.f, 0.f);
+                g[3] = mL > 7 ? split_child<SEED>(srcb, seedb, lc + crow16<7>(cr)) : make_float2(0.f, 0.f);
+                split_bwd_batch<4>(tq, 24, 56, g, av, gacc);
+                Gprevb[(uint32_t)c << 5] = gacc;
+            }
+        }
+    }
+    static_assert(T == 8, "two tail batches of 4 modes");
+    // reduce dU over the CTA's warps, one mode at a time
+    float2 *dst = a.dUpart + (((int64_t)grp * gridDim.x + blockIdx.x) * kLanes) * m;
+    {
+        float dh[16], dt[16];
+        tm_ld16(tq, dh);
+        tm_ld16(tq + 16, dt);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j < m) {
+                red[warp][lane] = j < H ? make_float2(dh[2 * j], dh[2 * j + 1])
+                                        : make_float2(dt[2 * (j - H)], dt[2 * (j - H) + 1]);
+                __syncthreads();
+                if (warp == 0) {
+                    float2 s = red[0][lane];
+#pragma unroll
+                    for (int w = 1; w < kSplitBwdWarps; ++w) {
+                        s.x += red[w][lane].x;
+                        s.y += red[w][lane].y;
+                    }
+                    dst[lane * m + j] = s;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(kSplitTmemCols)
+                     : "memory");
+    }
+}
+
+// ============================================================ launchers
+cudaError_t slos_split_init() {
+    cudaError_t e;
+    const int sp = (int)split_fwd_smem_bytes(EPI_PROBS), sa = (int)split_fwd_smem_bytes(EPI_AMPS);
+    if ((e = cudaFuncSetAttribute(slos_fwd_split_kernel<EPI_PROBS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sp)))
+        return e;
+    if ((e = cudaFuncSetAttribute(slos_fwd_split_kernel<EPI_PROBS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sp)))
+        return e;
+    if ((e = cudaFuncSetAttribute(slos_fwd_split_kernel<EPI_AMPS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa)))
+        return e;
+    return cudaFuncSetAttribute(slos_fwd_split_kernel<EPI_AMPS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa);
+}
+
+cudaError_t slos_launch_fwd_split(const SplitFwdArgs &a, int NG, int epi, bool save, int blocks_x, cudaStream_t s) {
+    const dim3 grid(blocks_x, NG);
+    const int th = kSplitFwdWarps * 32;
+    const size_t sm = split_fwd_smem_bytes(epi);
+    switch (epi * 2 + (save ? 1 : 0)) {
+        case 0:
+        case 1: slos_fwd_split_kernel<EPI_STORE, true><<<grid, th, 0, s>>>(a); break;
+        case 2: slos_fwd_split_kernel<EPI_PROBS, false><<<grid, th, sm, s>>>(a); break;
+        case 3: slos_fwd_split_kernel<EPI_PROBS, true><<<grid, th, sm, s>>>(a); break;
+        case 4: slos_fwd_split_kernel<EPI_AMPS, false><<<grid, th, sm, s>>>(a); break;
+        case 5: slos_fwd_split_kernel<EPI_AMPS, true><<<grid, th, sm, s>>>(a); break;
+        case 6: slos_fwd_split_kernel<EPI_THRESH, false><<<grid, th, 0, s>>>(a); break;
+        case 7: slos_fwd_split_kernel<EPI_THRESH, true><<<grid, th, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int H>
+static cudaError_t launch_bwd_split_h(const SplitBwdArgs &a, int NG, int seed, int blocks_x, cudaStream_t s) {
+    const dim3 grid(blocks_x, NG);
+    const int th = kSplitBwdWarps * 32;
+    switch (seed) {
+        case SEED_G: slos_bwd_split_kernel<H, SEED_G><<<grid, th, 0, s>>>(a); break;
+        case SEED_BCAST: slos_bwd_split_kernel<H, SEED_BCAST><<<grid, th, 0, s>>>(a); break;
+        case SEED_T: slos_bwd_split_kernel<H, SEED_T><<<grid, th, 0, s>>>(a); break;
+        case SEED_AMPS_T: slos_bwd_split_kernel<H, SEED_AMPS_T><<<grid, th, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t slos_launch_bwd_split(const SplitBwdArgs &a, int NG, int seed, int h, int blocks_x, cudaStream_t s) {
+    switch (h) {
+        case 6: return launch_bwd_split_h<6>(a, NG, seed, blocks_x, s);
+        case 8: return launch_bwd_split_h<8>(a, NG, seed, blocks_x, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace slos

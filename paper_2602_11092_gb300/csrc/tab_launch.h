@@ -28,6 +28,20 @@ constexpr int kFwdTabMinBlocksStore = 5;
 constexpr int kFwdTabMinBlocksFinal = 8;
 constexpr int kFwdTabTile = 16;
 constexpr int fwd_tab_min_blocks(int epi) { return epi == 0 ? kFwdTabMinBlocksStore : kFwdTabMinBlocksFinal; }
+// The same walk with U in tensor memory (slos_fwd_tabu_kernel): one 64-column
+// allocation per CTA, so at most 8 resident CTAs per SM.
+#ifndef SLOS_FWD_TMEM_U
+#define SLOS_FWD_TMEM_U 1
+#endif
+#ifndef SLOS_FWD_TABU_MINB_STORE
+#define SLOS_FWD_TABU_MINB_STORE 6
+#endif
+#ifndef SLOS_FWD_TABU_MINB_FINAL
+#define SLOS_FWD_TABU_MINB_FINAL 6
+#endif
+constexpr bool kFwdTabTmemU = SLOS_FWD_TMEM_U != 0;
+constexpr int fwd_tabu_min_blocks(int epi) { return epi == 0 ? SLOS_FWD_TABU_MINB_STORE : SLOS_FWD_TABU_MINB_FINAL; }
+inline int fwd_tab_resident_blocks(int epi) { return kFwdTabTmemU ? fwd_tabu_min_blocks(epi) : fwd_tab_min_blocks(epi); }
 // dynamic shared memory of a table-forward block: per warp a [32][kFwdTabTile + 1] tile
 inline size_t fwd_tab_smem_bytes(int epi) {
     const size_t cells = (size_t)kWarpsPerBlock * 32 * (kFwdTabTile + 1);
