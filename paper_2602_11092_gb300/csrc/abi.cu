@@ -105,6 +105,7 @@ static cudaError_t init_device_once(int dev) {
     if ((e = slos_tab_init()) != cudaSuccess) return e;
     if ((e = slos_fused_init()) != cudaSuccess) return e;
     if ((e = slos_split_init()) != cudaSuccess) return e;
+    if ((e = slos_pair_init()) != cudaSuccess) return e;
     done[dev] = true;
     return cudaSuccess;
 }
@@ -751,6 +752,7 @@ static Layout make_layout(const slos_plan_s *p, int batch, bool training) {
         off += align_up(bytes);
         return o;
     };
+    L.counters = take(kCounters * sizeof(int));
     if (!training) {
         // ping-pong: layer k in buffer (n-1-k) % 2
         size_t b0 = n >= 2 ? take(row * p->F[n - 1]) : SIZE_MAX;
@@ -1130,6 +1132,7 @@ __global__ void seed_table_kernel(SeedTabArgs a) {
 
 static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws, const float2 *U, int batch, int k,
                                       int epi, bool save, void *out, cudaStream_t s, bool recompute = false) {
+    int *counter = reinterpret_cast<int *>(ws + Ly.counters) + (recompute ? kCtrRecompute + k : k);
     const int NG = groups_for(batch);
     FwdArgs a;
     memset(&a, 0, sizeof(a));
@@ -1192,7 +1195,20 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
         t.kw = p->tab.layer[k].kw;
         t.w = p->tab.w;
         t.pat = p->tab.pat;
-        SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, blocks_for(p, a.Fk, 32, NG, fwd_tab_resident_blocks(epi)), s));
+        t.work = counter;
+        t.items_per_group = (int)((a.Fk + 32 * kWarpsPerBlock - 1) / (32 * kWarpsPerBlock));
+        if (kFwdPair) {
+            // warp items: one 32-state chunk of a group pair
+            const int64_t items = ((a.Fk + 31) / 32) * ((NG + 1) / 2);
+            const int64_t blocks = (items + slos_pair_warps() - 1) / slos_pair_warps();
+            const int grid = (int)std::max<int64_t>(
+                1, std::min<int64_t>(blocks, (int64_t)p->sm_count * slos_pair_resident_blocks(p->m)));
+            SLOS_CUDA(slos_launch_fwd_pair(a, t, epi, save, grid, s));
+        } else {
+            const int64_t items = (int64_t)t.items_per_group * NG;
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)p->sm_count * fwd_tab_resident_blocks(epi)));
+            SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, grid, s));
+        }
     } else {
         SLOS_CUDA(launch_fwd(p->m, a, epi, save, bx, s));
     }
@@ -1253,6 +1269,7 @@ slos_status_t slos_forward(slos_plan_t p, const void *U, int batch, slos_output_
         return SLOS_OK;
     }
     if (p->det == SLOS_DETECT_THRESHOLD) SLOS_CUDA(cudaMemsetAsync(out, 0, (size_t)batch * p->K * sizeof(float), s));
+    SLOS_CUDA(cudaMemsetAsync(ws + Ly.counters, 0, kCounters * sizeof(int), s));
     for (int k = 1; k < n; ++k) {
         slos_status_t st = launch_layer_fwd(p, Ly, ws, Ud, batch, k, EPI_STORE, true, nullptr, s);
         if (st != SLOS_OK) return st;
@@ -1278,6 +1295,7 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
     const float2 *Ud = reinterpret_cast<const float2 *>(U);
     const int n = p->n, m = p->m;
     const int NG = groups_for(batch);
+    SLOS_CUDA(cudaMemsetAsync(ws + Ly.counters, 0, kCounters * sizeof(int), s));
 
     // seed: the factorial weights are folded in here (see Seed)
     int seed;

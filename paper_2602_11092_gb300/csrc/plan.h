@@ -15,6 +15,12 @@
 namespace slos {
 
 constexpr size_t kAlign = 256;
+// Work-queue counters in the workspace: forward layer k uses counter k, a
+// recomputed layer q counter kCtrRecompute + q, backward layer k counter
+// kCtrBackward + k.
+constexpr int kCounters = 64;
+constexpr int kCtrRecompute = 16;
+constexpr int kCtrBackward = 32;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -36,6 +42,7 @@ struct Layout {
     std::vector<int> bwd_blocks;  // [1..n]: blocks_x of the backward launch of layer k
     size_t dpw;                   // shared seed [F_n] floats (aliases seedT)
     size_t dulayer;               // per-layer dU sums [n][NG][32][m] c64
+    size_t counters;              // kCounters work-queue counters (zeroed by each forward / backward call)
     size_t total;
 };
 
