@@ -1198,8 +1198,8 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
         t.work = counter;
         t.items_per_group = (int)((a.Fk + 32 * kWarpsPerBlock - 1) / (32 * kWarpsPerBlock));
         if (kFwdPair) {
-            // warp items: one 32-state chunk of a group pair
-            const int64_t items = ((a.Fk + 31) / 32) * ((NG + 1) / 2);
+            // warp items: one chunk of consecutive states of a group pair
+            const int64_t items = ((a.Fk + slos_pair_chunk() - 1) / slos_pair_chunk()) * ((NG + 1) / 2);
             const int64_t blocks = (items + slos_pair_warps() - 1) / slos_pair_warps();
             const int grid = (int)std::max<int64_t>(
                 1, std::min<int64_t>(blocks, (int64_t)p->sm_count * slos_pair_resident_blocks(p->m)));

@@ -40,6 +40,13 @@ constexpr int kPairMinBlocks = SLOS_PAIR_MINB;
 #define SLOS_PAIR_TS 16
 #endif
 constexpr int pair_tile_states(int epi) { return epi == EPI_AMPS ? 16 : SLOS_PAIR_TS; }
+// states per warp item; the chunk's slot rows are fetched once, one state per
+// lane, and handed to the walk by shuffles
+#ifndef SLOS_PAIR_CHUNK
+#define SLOS_PAIR_CHUNK 16
+#endif
+constexpr int kPairChunk = SLOS_PAIR_CHUNK;
+static_assert(kPairChunk == 16 || kPairChunk == 32, "chunk of 16 or 32 states");
 size_t pair_smem_bytes(int epi) {
     if (epi != EPI_PROBS && epi != EPI_AMPS) return 0;
     const size_t cells = (size_t)kPairWarps * (64 * (pair_tile_states(epi) + 1) + 1);
@@ -156,7 +163,7 @@ __global__ void __launch_bounds__(kPairThreads, kPairMinBlocks) slos_fwd_pair_ke
     constexpr int TS = pair_tile_states(EPI);
     constexpr int TW = 64 * (TS + 1) + 1;  // tile words per warp
     float *tile = reinterpret_cast<float *>(smem_raw) + warp * (TW * (EPI == EPI_AMPS ? 2 : 1));
-    const int nchunks = (int)((a.Fk + 31) / 32);
+    const int nchunks = (int)((a.Fk + kPairChunk - 1) / kPairChunk);
     const int npairs = (a.NG + 1) / 2;
     const int total = nchunks * npairs;
     const bool first_layer = a.k == 1;
@@ -203,13 +210,27 @@ __global__ void __launch_bounds__(kPairThreads, kPairMinBlocks) slos_fwd_pair_ke
             nexth = reinterpret_cast<float4 *>(a.next + (size_t)gl * (size_t)a.Fk * kLanes) + sl;
         }
         const int ch = item - pair * nchunks;
-        const uint32_t c0 = (uint32_t)ch * 32u;
-        const int nc = (int)min((int64_t)32, a.Fk - (int64_t)c0);
+        const uint32_t c0 = (uint32_t)ch * (uint32_t)kPairChunk;
+        const int nc = (int)min((int64_t)kPairChunk, a.Fk - (int64_t)c0);
         float wl = 0.f;
         int patl = 0;
-        if (EPI != EPI_STORE && lane < nc) {
-            wl = __ldg(t.w + c0 + lane);
-            if (EPI == EPI_THRESH) patl = __ldg(t.pat + c0 + lane);
+        // slot row of state c0 + lane (lanes < nc), handed out by shuffles below
+        uint32_t sr[KW];
+#pragma unroll
+        for (int q = 0; q < KW; ++q) sr[q] = kSlotEmpty;
+        if (lane < nc) {
+#pragma unroll
+            for (int q4 = 0; q4 < KW / 4; ++q4) {
+                const uint4 w4 = __ldg(slots + (c0 + lane) * (KW / 4) + q4);
+                sr[4 * q4] = w4.x;
+                sr[4 * q4 + 1] = w4.y;
+                sr[4 * q4 + 2] = w4.z;
+                sr[4 * q4 + 3] = w4.w;
+            }
+            if (EPI != EPI_STORE) {
+                wl = __ldg(t.w + c0 + lane);
+                if (EPI == EPI_THRESH) patl = __ldg(t.pat + c0 + lane);
+            }
         }
         int run_pat = -1;
         float run0 = 0.f, run1 = 0.f;
@@ -217,13 +238,7 @@ __global__ void __launch_bounds__(kPairThreads, kPairMinBlocks) slos_fwd_pair_ke
             const uint32_t c = c0 + (uint32_t)ci;
             uint32_t e[KW];
 #pragma unroll
-            for (int q4 = 0; q4 < KW / 4; ++q4) {
-                const uint4 w4 = __ldg(slots + c * (KW / 4) + q4);
-                e[4 * q4] = w4.x;
-                e[4 * q4 + 1] = w4.y;
-                e[4 * q4 + 2] = w4.z;
-                e[4 * q4 + 3] = w4.w;
-            }
+            for (int q = 0; q < KW; ++q) e[q] = __shfl_sync(0xffffffffu, sr[q], ci);
             float2 acc0, acc1;
             if (first_layer) {
                 uint32_t u[4][4];
@@ -349,6 +364,7 @@ static cudaError_t launch_pair(const FwdArgs &a, const TabArgs &t, int epi, bool
 // memory (512 columns) holds.
 int slos_pair_resident_blocks(int m) { return std::min(kPairMinBlocks, 512 / pair_tmem_cols(m)); }
 int slos_pair_warps() { return kPairWarps; }
+int slos_pair_chunk() { return kPairChunk; }
 
 cudaError_t slos_launch_fwd_pair(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks, cudaStream_t s) {
     const bool wide = pair_tmem_cols(a.m) == 128;

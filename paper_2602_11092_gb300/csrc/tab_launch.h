@@ -57,6 +57,7 @@ constexpr bool kFwdPair = SLOS_FWD_PAIR != 0;
 cudaError_t slos_pair_init();
 int slos_pair_resident_blocks(int m);
 int slos_pair_warps();
+int slos_pair_chunk();
 cudaError_t slos_launch_fwd_pair(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks, cudaStream_t s);
 cudaError_t slos_launch_fwd_tab(const FwdArgs &a, const TabArgs &t, int epi, bool save, int blocks_x, cudaStream_t s);
 
