@@ -787,7 +787,8 @@ static Layout make_layout(const slos_plan_s *p, int batch, bool training) {
         L.seedT = take(row * p->F[n]);  // c64-sized: enough for either seed kind
         L.dpw = L.seedT;
         for (int k = 1; k <= n; ++k) {
-            const int bx = (p->split && k >= 2) ? split_blocks(p, split_runs(p->F[k - 1]), kSplitBwdWarps, NG, kSplitBwdMinBlocks)
+            const int bx = (p->split && k >= 2)
+                               ? split_blocks(p, split_runs(p->F[k - 1]), kSplitBwdWarps, NG, kSplitBwdMinBlocks)
                            : p->tab.enabled ? bwd_tab_blocks(p, p->F[k - 1], NG, k == n)
                                             : blocks_for(p, p->F[k - 1], kChunkBwd, NG);
             L.bwd_blocks[k] = bx;
@@ -816,19 +817,34 @@ struct ReduceArgs {
     float2 *dU;
 };
 
+// grid (layer, group, 32-entry column of [32][m]); warp w sums the partials
+// of blocks w, w + 8, ... for its 32 entries, then the 8 warps' sums are added
+// in a fixed order
 __global__ void dU_layer_sum_kernel(ReduceArgs a) {
+    __shared__ float2 part[8][32];
     const int k = blockIdx.x + 1, grp = blockIdx.y;
     const int per = kLanes * a.m;
+    const int e = blockIdx.z * 32 + (threadIdx.x & 31);
+    const int w = threadIdx.x >> 5;
     const int bx = a.blocks[k];
     const float2 *base = a.part[k] + (int64_t)grp * bx * per;
-    for (int e = threadIdx.x; e < per; e += blockDim.x) {
-        float2 s = make_float2(0.f, 0.f);
-        for (int blk = 0; blk < bx; ++blk) {
+    float2 s = make_float2(0.f, 0.f);
+    if (e < per) {
+        for (int blk = w; blk < bx; blk += 8) {
             const float2 v = base[(int64_t)blk * per + e];
             s.x += v.x;
             s.y += v.y;
         }
-        a.layer[((int64_t)k * a.NG + grp) * per + e] = s;
+    }
+    part[w][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (w == 0 && e < per) {
+        float2 t = part[0][threadIdx.x];
+        for (int q = 1; q < 8; ++q) {
+            t.x += part[q][threadIdx.x].x;
+            t.y += part[q][threadIdx.x].y;
+        }
+        a.layer[((int64_t)k * a.NG + grp) * per + e] = t;
     }
 }
 
@@ -1427,7 +1443,7 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
         double bytes = 0.0;
         for (int k = 1; k <= n; ++k) bytes += 8.0 * NG * Ly.bwd_blocks[k] * kLanes * m;
         ProfScope ps("slos_dU_reduce", bytes + 8.0 * tot, s);
-        dU_layer_sum_kernel<<<dim3(n, NG), 256, 0, s>>>(ra);
+        dU_layer_sum_kernel<<<dim3(n, NG, (kLanes * m + 31) / 32), 256, 0, s>>>(ra);
         SLOS_CUDA(cudaGetLastError());
         count_launch();
         dU_assemble_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ra);

@@ -593,8 +593,8 @@ cudaError_t slos_launch_fwd_split(const SplitFwdArgs &a, int NG, int epi, bool s
 
 template <int H>
 static cudaError_t launch_bwd_split_h(const SplitBwdArgs &a, int NG, int seed, int blocks_x, cudaStream_t s) {
-    const dim3 grid(blocks_x, NG);
     const int th = kSplitBwdWarps * 32;
+    const dim3 grid(blocks_x, NG);
     switch (seed) {
         case SEED_G: slos_bwd_split_kernel<H, SEED_G><<<grid, th, 0, s>>>(a); break;
         case SEED_BCAST: slos_bwd_split_kernel<H, SEED_BCAST><<<grid, th, 0, s>>>(a); break;

@@ -134,6 +134,7 @@ constexpr int kSplitBwdWarps = 4;
 #endif
 constexpr int kSplitBwdMinBlocks = SLOS_SPLIT_BWD_MINB;
 
+
 size_t split_fwd_smem_bytes(int epi);
 // The forward layers take the split walk only when this is set (the backward
 // layers always do for plans with split tables).
