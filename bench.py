@@ -197,6 +197,102 @@ def cpu_slos_sample(seconds_target: float = 6.0):
                       f"given U ({t:.1f} s), tables built once beforehand; mesh excluded")
 
 
+def _dist_err(p_gpu, p_ref):
+    d = np.abs(np.asarray(p_gpu, dtype=np.float64) - p_ref)
+    return float(d.max()), float(0.5 * d.sum())
+
+
+def accuracy_vs_oracle(B, dev, plan, U, probs, dU, dd, w, theta_f32, data_f32):
+    """Measured errors of the GPU path per workload, against the oracle on the
+    complex64 unitaries the GPU used (upcast; the device arithmetic alone) and
+    against the oracle on the FP64 unitary built from the unrounded phases
+    (the whole path: phases, mesh, SLOS).  Part of the CPU-baseline leg: the
+    oracle is timed and consulted only here."""
+    import torch
+
+    import oracle
+
+    acc = {}
+    s16 = w["s"]
+    outs16 = oracle.enumerate_fock(M, N)
+    c = np.asarray(w["c"], dtype=np.float64)
+    mb = w["mesh"]
+    Uh = U.detach().cpu().numpy().astype(np.complex128)
+    ph = probs.detach().cpu().numpy()
+    dUh = dU.detach().cpu().numpy().astype(np.complex128)
+    ddh = dd.detach().cpu().numpy().astype(np.float64)
+    rows = []
+    for b in (0, BATCH - 1):
+        ref = oracle.probabilities(Uh[b], s16, outs16)
+        mx, tv = _dist_err(ph[b], ref)
+        gref = oracle.grad_U_minors(Uh[b], s16, c, outs16)
+        g_rel = float(np.linalg.norm(dUh[b] - gref) / np.linalg.norm(gref))
+        _, dref = oracle.phase_grad_from_dU(M, theta_f32.astype(np.float64), data_f32[b].astype(np.float64), gref)
+        d_rel = float(np.linalg.norm(ddh[b] - dref) / np.linalg.norm(dref))
+        U64 = oracle.mesh_unitary(M, mb.theta, mb.data[b])
+        mx64, tv64 = _dist_err(ph[b], oracle.probabilities(U64, s16, outs16))
+        rows.append((mx, tv, g_rel, d_rel, mx64, tv64))
+    r = np.max(np.array(rows), axis=0)
+    acc["train16"] = {"instances": [0, BATCH - 1], "outputs": int(outs16.shape[0]), "max_abs_dp": r[0], "tv": r[1],
+                      "grad_dU_rel_err": r[2], "grad_data_phase_rel_err": r[3],
+                      "vs_fp64_unitary": {"max_abs_dp": r[4], "tv": r[5]}}
+    # m=12, n=6 layer (on-chip inference forward), 4 instances
+    w12 = workloads.layer12(batch=64)
+    m12 = w12["mesh"]
+    plan12 = B.Plan(12, w12["s"])
+    th12 = torch.tensor(m12.theta, dtype=torch.float32, device=dev)
+    d12 = torch.tensor(m12.data, dtype=torch.float32, device=dev)
+    U12 = B.mesh_unitary(12, th12, d12, 64)
+    p12 = plan12.forward(U12).cpu().numpy()
+    U12h = U12.cpu().numpy().astype(np.complex128)
+    outs12 = oracle.enumerate_fock(12, 6)
+    e = []
+    for b in range(4):
+        e.append(_dist_err(p12[b], oracle.probabilities(U12h[b], w12["s"], outs12)) +
+                 _dist_err(p12[b], oracle.probabilities(oracle.mesh_unitary(12, m12.theta, m12.data[b]), w12["s"],
+                                                        outs12)))
+    e = np.max(np.array(e), axis=0)
+    acc["layer12"] = {"instances": 4, "max_abs_dp": e[0], "tv": e[1],
+                      "vs_fp64_unitary": {"max_abs_dp": e[2], "tv": e[3]}}
+    # tiny m=6, n=3: one Haar unitary (complex128 drawn, complex64 on the GPU)
+    t = workloads.tiny()
+    U0 = torch.tensor(np.asarray(t["U"]), dtype=torch.complex64, device=dev)
+    p0 = B.Plan(6, t["s"]).forward(U0).cpu().numpy()[0]
+    outs0 = oracle.enumerate_fock(6, 3)
+    mx, tv = _dist_err(p0, oracle.probabilities(U0.cpu().numpy().astype(np.complex128)[0], t["s"], outs0))
+    mx64, tv64 = _dist_err(p0, oracle.probabilities(np.asarray(t["U"])[0], t["s"], outs0))
+    acc["tiny"] = {"max_abs_dp": mx, "tv": tv, "vs_fp64_unitary": {"max_abs_dp": mx64, "tv": tv64}}
+    # uneven batch: the largest PNR shape and the largest threshold shape whose
+    # Fock space the oracle enumerates, plus the smallest shape, in one launch
+    inst, Us = workloads.uneven()
+    pnr = [i for i, it in enumerate(inst) if not it.threshold]
+    thr = [i for i, it in enumerate(inst) if it.threshold and workloads.fock_dim(it.m, it.n) <= 200_000]
+    key = lambda i: workloads.fock_dim(inst[i].m, inst[i].n)
+    pick = [max(pnr, key=key), max(thr, key=key), min(range(len(inst)), key=key)]
+    sub = [inst[i] for i in pick]
+    bp = B.BatchedPlan([it.m for it in sub], [it.n for it in sub], [it.s for it in sub],
+                       [B.THRESHOLD if it.threshold else B.PNR for it in sub])
+    Up = torch.cat([torch.tensor(np.asarray(Us[i]), dtype=torch.complex64).reshape(-1) for i in pick]).to(dev)
+    wsb = torch.empty(bp.workspace_bytes, dtype=torch.uint8, device=dev)
+    outb = torch.empty((bp.out_offsets[-1],), dtype=torch.float32, device=dev)
+    bp.forward(Up, outb, wsb)
+    bp.sync_status()
+    outb = outb.cpu().numpy()
+    e = []
+    for q, i in enumerate(pick):
+        it = inst[i]
+        Uq = np.asarray(Us[i], dtype=np.complex64).astype(np.complex128)
+        outs = oracle.enumerate_fock(it.m, it.n)
+        pr = oracle.probabilities(Uq, it.s, outs)
+        ref = oracle.threshold_probs(pr, outs, it.m, it.n) if it.threshold else pr
+        e.append(_dist_err(outb[bp.out_offsets[q]:bp.out_offsets[q + 1]], ref))
+    e = np.max(np.array(e), axis=0)
+    acc["uneven"] = {"shapes": [[inst[i].m, inst[i].n, "threshold" if inst[i].threshold else "pnr"] for i in pick],
+                     "max_abs_dp": e[0], "tv": e[1]}
+    acc["bounds"] = {"max_abs_dp": 1e-5, "tv": 1e-5, "grad_rel_err": 1e-3}
+    return acc
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -283,6 +379,8 @@ def run_gpu(args):
         plan.backward(U, c, ws, B.PROBS, dU=dU)
         return B.mesh_unitary_backward(M, theta, data, BATCH, dU)
 
+    last = {}
+
     def barrier():
         if world > 1:
             dist.barrier()
@@ -314,7 +412,7 @@ def run_gpu(args):
     B.profile_enable(True)
     barrier()
     for _ in range(args.steps):
-        step(theta, data, c)
+        last["grads"] = step(theta, data, c)
     barrier()
     B.profile_enable(False)
     prof = B.profile_collect()
@@ -358,8 +456,10 @@ def run_gpu(args):
     kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
                    "gbs": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None} for k, v in prof.items()}
 
-    cpu = cpu_slos = None
+    cpu = cpu_slos = accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        accuracy = accuracy_vs_oracle(B, dev, plan, U, probs, dU, last["grads"][1], w, mb.theta.astype(np.float32),
+                                      mb.data.astype(np.float32))
         v, cores, sample = oracle_step_sample(seconds_target=12.0)
         cpu = {"value": v, "unit": "distributions/s", "cores": cores, "kind": "oracle", "sample": sample}
         v, cores, sample = cpu_slos_sample(seconds_target=6.0)
@@ -393,6 +493,7 @@ def run_gpu(args):
         "clocks": clk,
         "cpu_baseline": cpu,
         "cpu_slos_baseline": cpu_slos,
+        "accuracy": accuracy,
         "extras": extras,
     }
     if rank == 0:

@@ -136,6 +136,24 @@ slos_status_t mesh_unitary_backward(const slos_mesh_desc_t *desc, const float *t
  * segment) and the others are recomputed in the backward pass; the final
  * layer a_n is always kept.  Allocates a 64-byte device status word on the
  * current device. */
+/* The same mesh with data phases formed from features and weights (the
+ * angle encoding of Sec. II-C.1, phi_j = x_j * w_j): x float32 device
+ * [batch][n_data] with row stride x_stride_b, w float32 device [n_data]
+ * (shared by the batch).  Otherwise as mesh_unitary. */
+slos_status_t mesh_unitary_weighted(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
+                                    const float *x, int64_t x_stride_b, const float *w, int batch, void *U,
+                                    void *stream);
+
+/* Reverse sweep of mesh_unitary_weighted: dtheta as in mesh_unitary_backward;
+ * dx float32 device [batch][n_data] = dL/dphi_j * w_j; dw float32 device
+ * [batch][n_data] (per instance, the caller sums over the batch) =
+ * dL/dphi_j * x_j, or NULL when not needed.  Same workspace as
+ * mesh_unitary_backward. */
+slos_status_t mesh_unitary_weighted_backward(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
+                                             const float *x, int64_t x_stride_b, const float *w, int batch,
+                                             const void *dU, float *dtheta, float *dx, float *dw, void *workspace,
+                                             size_t workspace_bytes, void *stream);
+
 slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t detection,
                         size_t mem_budget_bytes, slos_plan_t *out);
 
@@ -233,7 +251,9 @@ slos_status_t slos_sample(slos_plan_t plan, const float *probs, int batch, int s
  * |<s|Ua[i]^dag Ub[j]|s>|^2 = |Per(W_ij)|^2 / (prod s_i!)^2, W_ij the n x n
  * block of Ua[i]^dag Ub[j] on the photon columns.  Ua: complex64 [Na][m][m],
  * Ub: complex64 [Nb][m][m] (e.g. from mesh_unitary); K: float32 [Na][Nb].
- * W in FP32, the permanent (Glynn, Gray-code order) in FP64.  1 <= n <= 8
+ * W in FP32; the permanent (Glynn, Gray-code order) in double-float
+ * arithmetic on the FP32 pipe (pairs of floats, about 44 bits), no FP64
+ * instruction.  1 <= n <= 8
  * photons, m <= 24; otherwise SLOS_ERR_UNSUPPORTED.
  * ---------------------------------------------------------------------- */
 slos_status_t slos_fidelity_kernel(int m, const int *input_state, const void *Ua, int Na, const void *Ub, int Nb,
@@ -394,7 +414,11 @@ slos_status_t slos_profile_entry(int i, char *name, size_t name_len, int64_t *la
  *   device current; make that first call before any stream capture.
  * - Every call uses the same array: calls that overlap on the GPU (different
  *   streams, or several host threads) race and must be serialised by the
- *   caller.  No state carries over between calls.
+ *   caller.  No state carries over between calls (the call zeroes the few
+ *   counters it needs).
+ * - The plan, U and out must belong to the current device; otherwise
+ *   SLOS_ERR_INVALID_ARG.  The looked-up address is kept for the process: do
+ *   not call this entry point again on a device after cudaDeviceReset.
  * ---------------------------------------------------------------------- */
 size_t slos_noalloc_scratch_bytes(void);
 slos_status_t slos_forward_noalloc(slos_plan_t plan, const void *U, int batch, slos_output_t output, void *out,

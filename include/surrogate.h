@@ -53,6 +53,15 @@ slos_status_t surr_create(int n_phases, int hidden, int n_hidden_layers, int n_o
                           unsigned long long seed, surr_model_t *out);
 slos_status_t surr_destroy(surr_model_t model);
 
+/* Input harmonics (0 = off, the default): with H > 0 the `phases` argument
+ * of surr_forward / surr_train_step holds n_phases / H values x_j per row and
+ * the model's phases are h * x_j for h = 1..H (phase index (h - 1) * n_x + j),
+ * formed in the feature kernel.  H must divide n_phases.  (The data phases of
+ * an angle-encoded layer enter every amplitude through e^{i x_j}, so the
+ * output distribution is a trigonometric polynomial in them, Sec. II-C.1;
+ * its harmonics are the natural features.) */
+slos_status_t surr_set_input_harmonics(surr_model_t model, int harmonics);
+
 /* phases: float [B][n_phases]; probs: float [B][n_outputs] = softmax(logits).
  * B a multiple of 8, <= max_batch. */
 slos_status_t surr_forward(surr_model_t model, const float *phases, int B, float *probs, void *stream);

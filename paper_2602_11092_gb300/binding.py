@@ -47,6 +47,9 @@ _SIGNATURES = {
     "mesh_unitary_backward_workspace": ([ctypes.POINTER(MeshDesc), _int, _i64, ctypes.POINTER(_sz)], _int),
     "mesh_unitary_backward": ([ctypes.POINTER(MeshDesc), _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp, _vp, _sz, _vp],
                               _int),
+    "mesh_unitary_weighted": ([ctypes.POINTER(MeshDesc), _vp, _i64, _vp, _i64, _vp, _int, _vp, _vp], _int),
+    "mesh_unitary_weighted_backward": ([ctypes.POINTER(MeshDesc), _vp, _i64, _vp, _i64, _vp, _int, _vp, _vp, _vp,
+                                        _vp, _vp, _sz, _vp], _int),
     "slos_plan": ([_int, _int, ctypes.POINTER(_int), _int, _sz, ctypes.POINTER(_vp)], _int),
     "slos_plan_space": ([_int, _int, ctypes.POINTER(_int), _int, _int, _sz, ctypes.POINTER(_vp)], _int),
     "slos_plan_query": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_int)], _int),
@@ -138,23 +141,36 @@ def _need(t: torch.Tensor, dtype, name: str):
 # ------------------------------------------------------------------ mesh
 
 def mesh_unitary(m: int, theta: torch.Tensor, data: torch.Tensor | None, batch: int, data_col: int | None = None,
-                 out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """theta: float32 [P] (shared) or [B, P]; data: float32 [B, n_data] or None."""
+                 out: torch.Tensor | None = None, stream=None, w: torch.Tensor | None = None) -> torch.Tensor:
+    """theta: float32 [P] (shared) or [B, P]; data: float32 [B, n_data] or
+    None.  With w (float32 [n_data]) the data phases are data * w, formed in
+    the kernel (mesh_unitary_weighted)."""
     lib = load()
     _need(theta, torch.float32, "theta")
     n_data = 0 if data is None else data.shape[-1]
     if data is not None:
         _need(data, torch.float32, "data")
+    if w is not None:
+        _need(w, torch.float32, "w")
+        if data is None or w.numel() < n_data:
+            raise ValueError("w needs one weight per data phase")
     desc = MeshDesc(m, n_data, m // 2 if data_col is None else data_col)
     if out is None:
         out = torch.empty((batch, m, m), dtype=torch.complex64, device=theta.device)
     ts = 0 if theta.dim() == 1 else theta.shape[-1]
     ds = 0 if data is None else data.shape[-1]
-    _check(lib.mesh_unitary(ctypes.byref(desc), _ptr(theta), ts, _ptr(data), ds, batch, _ptr(out), _stream(stream)))
+    if w is None:
+        _check(lib.mesh_unitary(ctypes.byref(desc), _ptr(theta), ts, _ptr(data), ds, batch, _ptr(out),
+                                _stream(stream)))
+    else:
+        _check(lib.mesh_unitary_weighted(ctypes.byref(desc), _ptr(theta), ts, _ptr(data), ds, _ptr(w), batch,
+                                         _ptr(out), _stream(stream)))
     return out
 
 
-def mesh_unitary_backward(m: int, theta, data, batch: int, dU: torch.Tensor, data_col=None, stream=None):
+def mesh_unitary_backward(m: int, theta, data, batch: int, dU: torch.Tensor, data_col=None, stream=None,
+                          w: torch.Tensor | None = None, need_dw: bool = False):
+    """(dtheta, ddata) or, with need_dw, (dtheta, ddata, dw per instance)."""
     lib = load()
     _need(dU, torch.complex64, "dU")
     n_data = 0 if data is None else data.shape[-1]
@@ -164,13 +180,19 @@ def mesh_unitary_backward(m: int, theta, data, batch: int, dU: torch.Tensor, dat
     P = m * (m - 1)
     dtheta = torch.empty((P,) if shared else (batch, P), dtype=torch.float32, device=dU.device)
     ddata = torch.empty((batch, n_data), dtype=torch.float32, device=dU.device) if n_data else None
+    dw = torch.empty((batch, n_data), dtype=torch.float32, device=dU.device) if (n_data and need_dw) else None
     nbytes = ctypes.c_size_t()
     _check(lib.mesh_unitary_backward_workspace(ctypes.byref(desc), batch, ts, ctypes.byref(nbytes)))
     ws = torch.empty(max(1, nbytes.value), dtype=torch.uint8, device=dU.device)
     ds = 0 if data is None else data.shape[-1]
-    _check(lib.mesh_unitary_backward(ctypes.byref(desc), _ptr(theta), ts, _ptr(data), ds, batch, _ptr(dU),
-                                     _ptr(dtheta), _ptr(ddata), _ptr(ws), nbytes.value, _stream(stream)))
-    return dtheta, ddata
+    if w is None:
+        _check(lib.mesh_unitary_backward(ctypes.byref(desc), _ptr(theta), ts, _ptr(data), ds, batch, _ptr(dU),
+                                         _ptr(dtheta), _ptr(ddata), _ptr(ws), nbytes.value, _stream(stream)))
+    else:
+        _check(lib.mesh_unitary_weighted_backward(ctypes.byref(desc), _ptr(theta), ts, _ptr(data), ds, _ptr(w), batch,
+                                                  _ptr(dU), _ptr(dtheta), _ptr(ddata), _ptr(dw), _ptr(ws),
+                                                  nbytes.value, _stream(stream)))
+    return (dtheta, ddata, dw) if need_dw else (dtheta, ddata)
 
 
 def fidelity_kernel(input_state, Ua: torch.Tensor, Ub: torch.Tensor | None = None, out=None, stream=None):
@@ -221,9 +243,22 @@ class Plan:
     def workspace(self, batch: int, training: bool, device="cuda") -> torch.Tensor:
         return torch.empty(max(1, self.workspace_bytes(batch, training)), dtype=torch.uint8, device=device)
 
+    def _check_io(self, U: torch.Tensor, out: torch.Tensor | None, output: int):
+        """U complex64 [B, m, m]; out (if given) float32 (probabilities) or
+        complex64 (amplitudes) [B, n_outputs], contiguous, on U's device."""
+        _need(U, torch.complex64, "U")
+        if U.dim() != 3 or U.shape[1] != self.m or U.shape[2] != self.m:
+            raise ValueError(f"U must be [B, {self.m}, {self.m}], got {tuple(U.shape)}")
+        if out is not None:
+            _need(out, torch.complex64 if output == AMPS else torch.float32, "out")
+            if tuple(out.shape) != (U.shape[0], self.n_outputs):
+                raise ValueError(f"out must be [{U.shape[0]}, {self.n_outputs}], got {tuple(out.shape)}")
+            if out.device != U.device:
+                raise ValueError("U and out must be on the same device")
+
     def forward(self, U: torch.Tensor, output: int = PROBS, save_for_backward: bool = False,
                 workspace: torch.Tensor | None = None, out: torch.Tensor | None = None, stream=None):
-        _need(U, torch.complex64, "U")
+        self._check_io(U, out, output)
         B = U.shape[0]
         if workspace is None:
             workspace = self.workspace(B, save_for_backward, U.device)
@@ -314,7 +349,7 @@ class Plan:
 
     def forward_noalloc(self, U: torch.Tensor, out: torch.Tensor, output: int = PROBS, stream=None):
         """slos_forward_noalloc: the library's built-in scratch, no workspace."""
-        _need(U, torch.complex64, "U")
+        self._check_io(U, out, output)
         _check(load().slos_forward_noalloc(self._h, _ptr(U), U.shape[0], output, _ptr(out), _stream(stream)))
         return out
 

@@ -45,6 +45,11 @@ slos_status_t fail(slos_status_t st, const std::string &msg) {
             return fail(SLOS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__));     \
     } while (0)
 
+// Plan-time host-to-device copy; false on failure.
+static bool h2d(void *dst, const void *src, size_t bytes) {
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
 static int mmax_for(int m) {
     if (m <= 8) return 8;
     if (m <= 12) return 12;
@@ -346,8 +351,10 @@ static slos_status_t build_tables_unbunched(slos_plan_s *p) {
             free_tables(p);
             return fail(SLOS_ERR_OOM, "slos_plan_space: cannot allocate the transition tables");
         }
-        cudaMemcpy(LT.slots, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice);
-        cudaMemcpy(LT.ctab, ctab.data(), ctab.size() * 4, cudaMemcpyHostToDevice);
+        if (!h2d(LT.slots, slots.data(), slots.size() * 4) || !h2d(LT.ctab, ctab.data(), ctab.size() * 4)) {
+            free_tables(p);
+            return fail(SLOS_ERR_CUDA, "slos_plan_space: cannot upload the transition tables");
+        }
     }
     // final layer: prod t! = 1, so every weight is 1 / prod s!
     std::vector<float> w(p->F[n], p->inv_sfact);
@@ -365,8 +372,10 @@ static slos_status_t build_tables_unbunched(slos_plan_s *p) {
         free_tables(p);
         return fail(SLOS_ERR_OOM, "slos_plan_space: cannot allocate the weight tables");
     }
-    cudaMemcpy(p->tab.w, w.data(), w.size() * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(p->tab.occ, occ.data(), occ.size(), cudaMemcpyHostToDevice);
+    if (!h2d(p->tab.w, w.data(), w.size() * 4) || !h2d(p->tab.occ, occ.data(), occ.size())) {
+        free_tables(p);
+        return fail(SLOS_ERR_CUDA, "slos_plan_space: cannot upload the weight tables");
+    }
     p->tab.bytes = bytes;
     p->tab.enabled = true;
     return SLOS_OK;
@@ -410,8 +419,10 @@ static slos_status_t build_tables(slos_plan_s *p) {
             free_tables(p);
             return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the transition tables");
         }
-        cudaMemcpy(LT.slots, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice);
-        cudaMemcpy(LT.ctab, ctab.data(), ctab.size() * 4, cudaMemcpyHostToDevice);
+        if (!h2d(LT.slots, slots.data(), slots.size() * 4) || !h2d(LT.ctab, ctab.data(), ctab.size() * 4)) {
+            free_tables(p);
+            return fail(SLOS_ERR_CUDA, "slos_plan: cannot upload the transition tables");
+        }
     }
     // final-layer weights and threshold patterns
     {
@@ -444,18 +455,27 @@ static slos_status_t build_tables(slos_plan_s *p) {
             free_tables(p);
             return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the occupation table");
         }
-        cudaMemcpy(p->tab.occ, occ.data(), occ.size(), cudaMemcpyHostToDevice);
+        if (!h2d(p->tab.occ, occ.data(), occ.size())) {
+            free_tables(p);
+            return fail(SLOS_ERR_CUDA, "slos_plan: cannot upload the occupation table");
+        }
         if (cudaMalloc(&p->tab.w, w.size() * 4) != cudaSuccess) {
             free_tables(p);
             return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the weight table");
         }
-        cudaMemcpy(p->tab.w, w.data(), w.size() * 4, cudaMemcpyHostToDevice);
+        if (!h2d(p->tab.w, w.data(), w.size() * 4)) {
+            free_tables(p);
+            return fail(SLOS_ERR_CUDA, "slos_plan: cannot upload the weight table");
+        }
         if (p->det == SLOS_DETECT_THRESHOLD) {
             if (cudaMalloc(&p->tab.pat, pat.size() * 4) != cudaSuccess) {
                 free_tables(p);
                 return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the pattern table");
             }
-            cudaMemcpy(p->tab.pat, pat.data(), pat.size() * 4, cudaMemcpyHostToDevice);
+            if (!h2d(p->tab.pat, pat.data(), pat.size() * 4)) {
+                free_tables(p);
+                return fail(SLOS_ERR_CUDA, "slos_plan: cannot upload the pattern table");
+            }
         }
     }
     p->tab.bytes = bytes;
@@ -467,9 +487,9 @@ static slos_status_t build_tables(slos_plan_s *p) {
 // layer k, its highest occupied mode c and the rank of s - e_c in layer k-1
 // (the column recursion of the transfer matrix), and sqrt(prod t!) of the
 // final states.  Built for PNR table plans of at most kMaxEncodeStates
-// outputs; an allocation failure just leaves the feature off.
-static void build_encode_tables(slos_plan_s *p) {
-    if (!p->tab.enabled || p->det != SLOS_DETECT_PNR || p->K > kMaxEncodeStates) return;
+// outputs; an allocation or upload failure fails the plan.
+static slos_status_t build_encode_tables(slos_plan_s *p) {
+    if (!p->tab.enabled || p->det != SLOS_DETECT_PNR || p->K > kMaxEncodeStates) return SLOS_OK;
     const int m = p->m, n = p->n;
     const bool unb = p->space == SLOS_SPACE_UNBUNCHED;
     std::vector<float> g(p->F[n], 1.f);
@@ -509,15 +529,19 @@ static void build_encode_tables(slos_plan_s *p) {
             }
         }
         uint32_t *d = nullptr;
-        if (cudaMalloc(&d, info.size() * 4) != cudaSuccess) return;
-        cudaMemcpy(d, info.data(), info.size() * 4, cudaMemcpyHostToDevice);
-        p->tab.layer[k].colinfo = d;
+        if (cudaMalloc(&d, info.size() * 4) != cudaSuccess)
+            return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the amplitude-encoding tables");
+        p->tab.layer[k].colinfo = d;  // owned by the plan from here on (freed with its tables)
+        if (!h2d(d, info.data(), info.size() * 4))
+            return fail(SLOS_ERR_CUDA, "slos_plan: cannot upload the amplitude-encoding tables");
     }
     if (cudaMalloc(&p->tab.gfact, g.size() * 4) != cudaSuccess) {
         p->tab.gfact = nullptr;
-        return;
+        return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the amplitude-encoding weights");
     }
-    cudaMemcpy(p->tab.gfact, g.data(), g.size() * 4, cudaMemcpyHostToDevice);
+    if (!h2d(p->tab.gfact, g.data(), g.size() * 4))
+        return fail(SLOS_ERR_CUDA, "slos_plan: cannot upload the amplitude-encoding weights");
+    return SLOS_OK;
 }
 
 // Split-lattice tables (split.h) for Fock table plans of 8..16 modes: head
@@ -635,14 +659,13 @@ static bool build_fused_tables(slos_plan_s *p) {
         FL.fpad = fpad;
         if (cudaMalloc(&FL.rows, rows.size() * 4) != cudaSuccess || cudaMalloc(&FL.blk, blk.size() * 4) != cudaSuccess)
             return false;
-        cudaMemcpy(FL.rows, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice);
-        cudaMemcpy(FL.blk, blk.data(), blk.size() * 4, cudaMemcpyHostToDevice);
+        if (!h2d(FL.rows, rows.data(), rows.size() * 4) || !h2d(FL.blk, blk.data(), blk.size() * 4)) return false;
         if (k == n) {
             if (cudaMalloc(&p->tab.fused_id, id.size() * 4) != cudaSuccess ||
                 cudaMalloc(&p->tab.fused_w, wf.size() * 4) != cudaSuccess)
                 return false;
-            cudaMemcpy(p->tab.fused_id, id.data(), id.size() * 4, cudaMemcpyHostToDevice);
-            cudaMemcpy(p->tab.fused_w, wf.data(), wf.size() * 4, cudaMemcpyHostToDevice);
+            if (!h2d(p->tab.fused_id, id.data(), id.size() * 4) || !h2d(p->tab.fused_w, wf.data(), wf.size() * 4))
+                return false;
         }
         if (k > 1) pos[k - 1].clear();
     }
@@ -907,8 +930,9 @@ static slos_status_t check_mesh(const slos_mesh_desc_t *d, int batch) {
     return SLOS_OK;
 }
 
-slos_status_t mesh_unitary(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
-                           const float *data, int64_t data_stride_b, int batch, void *U, void *stream) {
+static slos_status_t mesh_forward_impl(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
+                                       const float *data, int64_t data_stride_b, const float *w, int batch, void *U,
+                                       void *stream) {
     slos_status_t st = check_mesh(desc, batch);
     if (st != SLOS_OK) return st;
     if (batch == 0) return SLOS_OK;
@@ -919,6 +943,7 @@ slos_status_t mesh_unitary(const slos_mesh_desc_t *desc, const float *theta, int
     a.theta_stride = theta_stride_b;
     a.data = desc->n_data > 0 ? data : nullptr;
     a.data_stride = data_stride_b;
+    a.data_w = desc->n_data > 0 ? w : nullptr;
     a.U = reinterpret_cast<float2 *>(U);
     a.m = desc->m;
     a.n_data = desc->n_data;
@@ -931,6 +956,18 @@ slos_status_t mesh_unitary(const slos_mesh_desc_t *desc, const float *theta, int
     return SLOS_OK;
 }
 
+slos_status_t mesh_unitary(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
+                           const float *data, int64_t data_stride_b, int batch, void *U, void *stream) {
+    return mesh_forward_impl(desc, theta, theta_stride_b, data, data_stride_b, nullptr, batch, U, stream);
+}
+
+slos_status_t mesh_unitary_weighted(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
+                                    const float *x, int64_t x_stride_b, const float *w, int batch, void *U,
+                                    void *stream) {
+    if (desc && desc->n_data > 0 && !w) return fail(SLOS_ERR_INVALID_ARG, "mesh_unitary_weighted: NULL w");
+    return mesh_forward_impl(desc, theta, theta_stride_b, x, x_stride_b, w, batch, U, stream);
+}
+
 slos_status_t mesh_unitary_backward_workspace(const slos_mesh_desc_t *desc, int batch, int64_t theta_stride_b,
                                               size_t *bytes) {
     slos_status_t st = check_mesh(desc, batch);
@@ -940,10 +977,10 @@ slos_status_t mesh_unitary_backward_workspace(const slos_mesh_desc_t *desc, int 
     return SLOS_OK;
 }
 
-slos_status_t mesh_unitary_backward(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
-                                    const float *data, int64_t data_stride_b, int batch, const void *dU,
-                                    float *dtheta, float *ddata, void *workspace, size_t workspace_bytes,
-                                    void *stream) {
+static slos_status_t mesh_backward_impl(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
+                                        const float *data, int64_t data_stride_b, const float *w, int batch,
+                                        const void *dU, float *dtheta, float *ddata, float *dw, void *workspace,
+                                        size_t workspace_bytes, void *stream) {
     slos_status_t st = check_mesh(desc, batch);
     if (st != SLOS_OK) return st;
     const int m = desc->m;
@@ -964,6 +1001,8 @@ slos_status_t mesh_unitary_backward(const slos_mesh_desc_t *desc, const float *t
     a.theta_stride = theta_stride_b;
     a.data = desc->n_data > 0 ? data : nullptr;
     a.data_stride = data_stride_b;
+    a.data_w = desc->n_data > 0 ? w : nullptr;
+    a.dw = desc->n_data > 0 ? dw : nullptr;
     a.dU = reinterpret_cast<const float2 *>(dU);
     a.dtheta = theta_stride_b == 0 ? reinterpret_cast<float *>(workspace) : dtheta;
     a.dtheta_stride = P;
@@ -977,6 +1016,23 @@ slos_status_t mesh_unitary_backward(const slos_mesh_desc_t *desc, const float *t
         SLOS_CUDA(mesh_backward_launch(a, theta_stride_b == 0 ? dtheta : nullptr, (cudaStream_t)stream));
     }
     return SLOS_OK;
+}
+
+slos_status_t mesh_unitary_backward(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
+                                    const float *data, int64_t data_stride_b, int batch, const void *dU,
+                                    float *dtheta, float *ddata, void *workspace, size_t workspace_bytes,
+                                    void *stream) {
+    return mesh_backward_impl(desc, theta, theta_stride_b, data, data_stride_b, nullptr, batch, dU, dtheta, ddata,
+                              nullptr, workspace, workspace_bytes, stream);
+}
+
+slos_status_t mesh_unitary_weighted_backward(const slos_mesh_desc_t *desc, const float *theta, int64_t theta_stride_b,
+                                             const float *x, int64_t x_stride_b, const float *w, int batch,
+                                             const void *dU, float *dtheta, float *dx, float *dw, void *workspace,
+                                             size_t workspace_bytes, void *stream) {
+    if (desc && desc->n_data > 0 && !w) return fail(SLOS_ERR_INVALID_ARG, "mesh_unitary_weighted_backward: NULL w");
+    return mesh_backward_impl(desc, theta, theta_stride_b, x, x_stride_b, w, batch, dU, dtheta, dx, dw, workspace,
+                              workspace_bytes, stream);
 }
 
 slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t detection, size_t mem_budget_bytes,
@@ -1073,7 +1129,11 @@ slos_status_t slos_plan_space(int m, int n, const int *input_state, slos_detecti
         delete p;
         return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the status word");
     }
-    cudaMemset(p->d_status, 0, 64);
+    if (cudaMemset(p->d_status, 0, 64) != cudaSuccess) {
+        cudaFree(p->d_status);
+        delete p;
+        return fail(SLOS_ERR_CUDA, "slos_plan: cannot clear the status word");
+    }
     slos_status_t tst = build_tables(p);
     if (tst != SLOS_OK) {
         cudaFree(p->d_status);
@@ -1088,7 +1148,13 @@ slos_status_t slos_plan_space(int m, int n, const int *input_state, slos_detecti
         return tst;
     }
     choose_fused(p);
-    build_encode_tables(p);
+    tst = build_encode_tables(p);
+    if (tst != SLOS_OK) {
+        free_tables(p);
+        cudaFree(p->d_status);
+        delete p;
+        return tst;
+    }
     *out = p;
     return SLOS_OK;
 }

@@ -59,8 +59,8 @@ struct MziTab {
     float2 t00, t01, t10, t11, eth, eph;
 };
 
-__device__ __forceinline__ void fill_mzi_table(const float *th, const float *dd, int m, int n_data, int lane,
-                                               MziTab *tab, float2 *ed) {
+__device__ __forceinline__ void fill_mzi_table(const float *th, const float *dd, const float *dw, int m, int n_data,
+                                               int lane, MziTab *tab, float2 *ed) {
     const int nmzi = m * (m - 1) / 2;
     for (int idx = lane; idx < nmzi; idx += 32) {
         const Mzi z = make_mzi(th[2 * idx], th[2 * idx + 1]);
@@ -68,7 +68,7 @@ __device__ __forceinline__ void fill_mzi_table(const float *th, const float *dd,
     }
     for (int j = lane; j < n_data; j += 32) {
         float s, c;
-        sincosf(dd[j], &s, &c);
+        sincosf(dw ? dd[j] * dw[j] : dd[j], &s, &c);
         ed[j] = make_float2(c, s);
     }
     __syncwarp();
@@ -123,7 +123,7 @@ __global__ void mesh_fwd_kernel(MeshArgs a) {
     const int m = a.m;
     const float *th = a.theta + (int64_t)b * a.theta_stride;
     const float *dd = a.data ? a.data + (int64_t)b * a.data_stride : nullptr;
-    fill_mzi_table(th, dd, m, a.n_data, lane, sm[w].tab, sm[w].ed);
+    fill_mzi_table(th, dd, a.data_w, m, a.n_data, lane, sm[w].tab, sm[w].ed);
     float2 x[MMAX];
     mesh_column<MMAX>(sm[w].tab, sm[w].ed, m, a.n_data, a.data_col, lane, x);
     if (lane < m) {
@@ -157,7 +157,7 @@ __global__ void mesh_bwd_kernel(MeshBwdArgs a) {
     const float *dd = a.data ? a.data + (int64_t)b * a.data_stride : nullptr;
     float *gth = a.dtheta + (int64_t)b * a.dtheta_stride;
     float2 x[MMAX], mm[MMAX];
-    fill_mzi_table(th, dd, m, a.n_data, lane, sm.tab, sm.ed);
+    fill_mzi_table(th, dd, a.data_w, m, a.n_data, lane, sm.tab, sm.ed);
     mesh_column<MMAX>(sm.tab, sm.ed, m, a.n_data, a.data_col, lane, x);  // X = U, recomputed
 #pragma unroll
     for (int j = 0; j < MMAX; ++j) {
@@ -229,7 +229,12 @@ __global__ void mesh_bwd_kernel(MeshBwdArgs a) {
         float sum = 0.f;
         for (int l = 0; l < 32; ++l) sum += contrib[q * 33 + l];
         if (q < P) gth[q] = sum;
-        else a.ddata[(int64_t)b * a.n_data + (q - P)] = sum;
+        else {
+            // d/dx_j = d/dphi_j * w_j, d/dw_j = d/dphi_j * x_j (phi_j = x_j w_j)
+            const int j = q - P;
+            a.ddata[(int64_t)b * a.n_data + j] = a.data_w ? sum * a.data_w[j] : sum;
+            if (a.dw) a.dw[(int64_t)b * a.n_data + j] = sum * dd[j];
+        }
     }
 }
 

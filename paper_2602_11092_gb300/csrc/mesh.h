@@ -10,6 +10,7 @@ struct MeshArgs {
     int64_t theta_stride;
     const float *data;
     int64_t data_stride;
+    const float *data_w;  // per-mode weights: phase j = data_j * data_w[j] (null: the data are the phases)
     float2 *U;
     int m, n_data, data_col, B;
 };
@@ -19,6 +20,8 @@ struct MeshBwdArgs {
     int64_t theta_stride;
     const float *data;
     int64_t data_stride;
+    const float *data_w;  // as in MeshArgs
+    float *dw;            // [B][n_data] per-instance gradient of the weights (may be null)
     const float2 *dU;
     float *dtheta;     // [B][P] (per instance)
     int64_t dtheta_stride;

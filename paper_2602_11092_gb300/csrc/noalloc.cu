@@ -15,14 +15,22 @@
 // before any stream capture.  All calls share the one array and it keeps the
 // last call's contents; calls whose work overlaps on the GPU (concurrent
 // streams, or several host threads) race on it and must be serialised by the
-// caller.  The forward pass writes every scratch element it reads, so nothing
-// there needs clearing.
+// caller.  The forward pass writes every scratch element it reads except its
+// work-queue counters, which it zeroes itself at the start of every call.
+//
+// Device rule: the plan, U and out must all belong to the device that is
+// current when the entry point is called (the scratch address is that
+// device's); anything else is rejected with SLOS_ERR_INVALID_ARG.  The cached
+// address stays valid for the life of the process's context on that device:
+// after a cudaDeviceReset the entry point must not be called again in the
+// same process.
 #include <cuda_runtime.h>
 
 #include <mutex>
 #include <string>
 
 #include "../../include/slos.h"
+#include "plan.h"
 
 namespace slos {
 slos_status_t fail(slos_status_t st, const std::string &msg);
@@ -73,6 +81,22 @@ slos_status_t slos_forward_noalloc(slos_plan_t plan, const void *U, int batch, s
                               " bytes of scratch but the built-in scratch holds " +
                               std::to_string(kNoAllocScratchBytes) +
                               "; use a smaller batch or slos_forward with a caller workspace");
+    if (batch > 0) {
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device)
+            return slos::fail(SLOS_ERR_INVALID_ARG, "slos_forward_noalloc: the plan was built on device " +
+                                                        std::to_string(plan->device) + ", not the current device");
+        const void *ptrs[2] = {U, out};
+        for (const void *q : ptrs) {
+            cudaPointerAttributes at;
+            if (!q || cudaPointerGetAttributes(&at, q) != cudaSuccess ||
+                (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev) {
+                cudaGetLastError();  // clear a sticky lookup error, if any
+                return slos::fail(SLOS_ERR_INVALID_ARG,
+                                  "slos_forward_noalloc: U and out must be device memory of the current device");
+            }
+        }
+    }
     void *scratch = nullptr;
     st = scratch_address(&scratch);
     if (st != SLOS_OK) return st;

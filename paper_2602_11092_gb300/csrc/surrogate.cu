@@ -153,12 +153,15 @@ slos_status_t gemm(int epi, int M, int N, int K, const __nv_bfloat16 *A, int64_t
 }
 
 // ---------------------------------------------------------------- small kernels
-__global__ void features_kernel(const float *phases, int B, int P, __nv_bfloat16 *x) {
+// phase j of row b: in[b][j], or with H > 0 harmonics of nx inputs per row,
+// (j / nx + 1) * in[b][j % nx]
+__global__ void features_kernel(const float *in, int B, int P, int H, int nx, __nv_bfloat16 *x) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)B * P) return;
     const int64_t b = i / P, j = i % P;
+    const float phi = H > 0 ? (float)(j / nx + 1) * in[b * nx + j % nx] : in[i];
     float s, c;
-    sincosf(phases[i], &s, &c);
+    sincosf(phi, &s, &c);
     x[b * 2 * P + j] = __float2bfloat16(s);
     x[b * 2 * P + P + j] = __float2bfloat16(c);
 }
@@ -355,6 +358,7 @@ __global__ void gather_rows_kernel(const float *src, const int *rows, int W, flo
 // ======================================================================== model
 struct surr_model_s {
     int n_phases, in_dim, hidden, n_layers, K, max_batch;
+    int harmonics = 0;  // > 0: inputs are n_phases / harmonics values x, phases h x for h = 1..harmonics
     // parameters: layer l = 0..n_layers (last = output layer)
     std::vector<int> fan_in, fan_out;
     std::vector<float *> w, b, mw, vw, mb, vb, gw, gb;
@@ -525,12 +529,21 @@ slos_status_t surr_destroy(surr_model_t M) {
     return SLOS_OK;
 }
 
+slos_status_t surr_set_input_harmonics(surr_model_t M, int harmonics) {
+    if (!M) return fail(SLOS_ERR_INVALID_ARG, "surr_set_input_harmonics: NULL model");
+    if (harmonics < 0 || (harmonics > 0 && M->n_phases % harmonics))
+        return fail(SLOS_ERR_INVALID_ARG, "surr_set_input_harmonics: harmonics must divide n_phases");
+    M->harmonics = harmonics;
+    return SLOS_OK;
+}
+
 static slos_status_t forward_impl(surr_model_t M, const float *phases, int B, cudaStream_t s) {
     if (B <= 0 || B > M->max_batch || B % 8) return fail(SLOS_ERR_INVALID_ARG, "surrogate: batch must be in (0, max_batch], multiple of 8");
     const int64_t n = (int64_t)B * M->n_phases;
     {
         ProfScope ps("surr_features", 4.0 * n + 4.0 * n, s);
-        features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(phases, B, M->n_phases, M->x0);
+        features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+            phases, B, M->n_phases, M->harmonics, M->harmonics > 0 ? M->n_phases / M->harmonics : M->n_phases, M->x0);
     }
     slos_status_t st = launch_check("features");
     if (st) return st;

@@ -3,7 +3,8 @@ simulation; Sec. II-B: the quantum layer as a composable module).
 
 MeshFn  : (theta, data) -> U           via mesh_unitary / mesh_unitary_backward
 SlosFn  : U -> probabilities or amps   via slos_forward / slos_backward
-QuantumLayer: theta (trainable) and data phases x*w -> output distribution.
+QuantumLayer: theta (trainable) and data phases x*w (formed in the mesh kernel)
+-> output distribution.
 
 The Functions only marshal arguments; all arithmetic is in libslos.so.
 """
@@ -16,20 +17,27 @@ from . import binding as B
 
 class MeshFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, theta, data, m, batch, data_col):
+    def forward(ctx, theta, data, m, batch, data_col, w=None):
         theta = theta.contiguous()
         data = data.contiguous() if data is not None else None
-        U = B.mesh_unitary(m, theta, data, batch, data_col)
-        ctx.save_for_backward(theta, data if data is not None else torch.empty(0, device=theta.device))
-        ctx.m, ctx.batch, ctx.data_col, ctx.has_data = m, batch, data_col, data is not None
+        w = w.contiguous() if w is not None else None
+        U = B.mesh_unitary(m, theta, data, batch, data_col, w=w)
+        empty = torch.empty(0, device=theta.device)
+        ctx.save_for_backward(theta, data if data is not None else empty, w if w is not None else empty)
+        ctx.m, ctx.batch, ctx.data_col = m, batch, data_col
+        ctx.has_data, ctx.has_w = data is not None, w is not None
         return U
 
     @staticmethod
     def backward(ctx, dU):
-        theta, data = ctx.saved_tensors
+        theta, data, w = ctx.saved_tensors
         data = data if ctx.has_data else None
-        dtheta, ddata = B.mesh_unitary_backward(ctx.m, theta, data, ctx.batch, dU.contiguous(), ctx.data_col)
-        return dtheta, ddata, None, None, None
+        w = w if ctx.has_w else None
+        need_dw = w is not None and ctx.needs_input_grad[5]
+        res = B.mesh_unitary_backward(ctx.m, theta, data, ctx.batch, dU.contiguous(), ctx.data_col, w=w,
+                                      need_dw=need_dw)
+        dw = res[2].sum(0) if need_dw else None  # per-instance rows from the library, summed over the batch
+        return res[0], res[1], None, None, None, dw
 
 
 class SlosFn(torch.autograd.Function):
@@ -49,6 +57,9 @@ class SlosFn(torch.autograd.Function):
             d = dout[0]  # the same gradient row for every instance (stride 0)
         else:
             d = dout.contiguous()
+        if ctx.ws is None:
+            raise RuntimeError("SlosFn: a second backward through the same forward is not supported (its activations "
+                               "were released by the first backward); run the forward again")
         dU = ctx.plan.backward(U, d, ctx.ws, ctx.output)
         ctx.ws = None
         return dU, None, None
@@ -83,8 +94,9 @@ class RenormaliseFn(torch.autograd.Function):
         return ctx.plan.renormalise_backward(q, Z, dq.contiguous()), None
 
 
-def mesh_unitary(theta, data, m: int, batch: int, data_col: int | None = None):
-    return MeshFn.apply(theta, data, m, batch, m // 2 if data_col is None else data_col)
+def mesh_unitary(theta, data, m: int, batch: int, data_col: int | None = None, w=None):
+    """U(theta, data) with data phases data (or data * w, formed in the kernel)."""
+    return MeshFn.apply(theta, data, m, batch, m // 2 if data_col is None else data_col, w)
 
 
 def slos(U, plan: B.Plan, output: int = B.PROBS):
@@ -123,8 +135,8 @@ class QuantumLayer(torch.nn.Module):
         self.register_buffer("w", w.to(device=device, dtype=torch.float32))
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
-        data = (x * self.w[None, : x.shape[-1]]).to(torch.float32)
-        U = mesh_unitary(self.theta, data, self.m, x.shape[0])
+        x = x.to(torch.float32).contiguous()
+        U = mesh_unitary(self.theta, x, self.m, x.shape[0], w=self.w[: x.shape[-1]].contiguous())
         y = slos(U, self.plan, self.output)
         if self.renormalise:
             y = RenormaliseFn.apply(y, self.plan)
@@ -151,8 +163,8 @@ class FidelityKernel(torch.nn.Module):
         self.register_buffer("w", w.to(device=device, dtype=torch.float32))
 
     def unitaries(self, x: torch.Tensor) -> torch.Tensor:
-        data = (x * self.w[None, : x.shape[-1]]).to(torch.float32).contiguous()
-        return B.mesh_unitary(self.m, self.theta, data, x.shape[0])
+        x = x.to(torch.float32).contiguous()
+        return B.mesh_unitary(self.m, self.theta, x, x.shape[0], w=self.w[: x.shape[-1]].contiguous())
 
     @torch.no_grad()
     def forward(self, x1: torch.Tensor, x2: torch.Tensor | None = None) -> torch.Tensor:

@@ -16,6 +16,7 @@ _SIG = {
     "surr_sync_status": ([_vp], _int),
     "surr_create": ([_int, _int, _int, _int, _int, ctypes.c_ulonglong, ctypes.POINTER(_vp)], _int),
     "surr_destroy": ([_vp], _int),
+    "surr_set_input_harmonics": ([_vp, _int], _int),
     "surr_forward": ([_vp, _vp, _int, _vp, _vp], _int),
     "surr_train_step": ([_vp, _vp, _vp, _int, _f, _vp, _vp], _int),
     "surr_get_param": ([_vp, _int, _vp, _vp], _int),
@@ -82,6 +83,11 @@ class Surrogate:
             out = torch.empty((Bn, self.K), dtype=torch.float32, device=phases.device)
         B._check(lib().surr_forward(self._h, B._ptr(phases), Bn, B._ptr(out), B._stream(stream)))
         return out
+
+    def set_input_harmonics(self, harmonics: int):
+        """Inputs become n_phases / harmonics values x per row; the model's
+        phases h * x (h = 1..harmonics) are formed in its feature kernel."""
+        B._check(lib().surr_set_input_harmonics(self._h, int(harmonics)))
 
     def train_step(self, phases, target, lr, loss_rows=None, stream=None):
         B._check(lib().surr_train_step(self._h, B._ptr(phases), B._ptr(target), phases.shape[0], float(lr),
@@ -151,9 +157,10 @@ class SurrogateLayer:
         self.wdata = mb.w
         self.plan = B.Plan(self.m, self.s)
         self.K = self.plan.n_outputs
-        self.harmonics = torch.arange(1, 13, dtype=torch.float32, device=self.device)
-        self.model = Surrogate(n_phases=self.harmonics.numel() * self.m, hidden=hidden,
+        self.harmonics = 12
+        self.model = Surrogate(n_phases=self.harmonics * self.m, hidden=hidden,
                                n_hidden_layers=n_hidden_layers, n_outputs=self.K, max_batch=max_batch, seed=seed)
+        self.model.set_input_harmonics(self.harmonics)
         self.max_batch = max_batch
         occ, _ = B.device_index_table(self.m, self.n, 0, self.K, device=self.device)
         self.occ = occ
@@ -164,16 +171,14 @@ class SurrogateLayer:
         x = rng.standard_normal((count, self.m))
         return torch.tensor(x * self.wdata[None, :], dtype=torch.float32, device=self.device)
 
-    def phases(self, data: torch.Tensor) -> torch.Tensor:
-        """The model's 144 phase inputs: h * x_j for harmonics h = 1..12 of the
-        12 data phases (the model takes sin and cos of each).  The 132
-        trainable phases are the same for every sample and carry nothing; the
-        data phases sit in one column between the two halves of the mesh, so
-        every amplitude is a homogeneous polynomial of degree n = 6 in the
-        e^{i x_j} and each probability a trigonometric polynomial of degree
-        <= 6 in every x_j: its harmonics are the natural inputs."""
-        Bn = data.shape[0]
-        return (data[:, None, :] * self.harmonics[None, :, None]).reshape(Bn, -1).contiguous()
+    # The model's 144 phase inputs are h * x_j for the harmonics h = 1..12 of
+    # the 12 data phases x_j (it takes sin and cos of each), formed by the
+    # model's feature kernel from the data phases.  The 132 trainable phases
+    # are the same for every sample and carry nothing; the data phases sit in
+    # one column between the two halves of the mesh, so every amplitude is a
+    # homogeneous polynomial of degree n = 6 in the e^{i x_j} and each
+    # probability a trigonometric polynomial of degree <= 6 in every x_j: its
+    # harmonics are the natural inputs.
 
     def exact(self, data: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         U = B.mesh_unitary(self.m, self.theta, data.contiguous(), data.shape[0])
@@ -189,7 +194,7 @@ class SurrogateLayer:
             data = self.sample_data(batch, rng)
             p = self.exact(data)
             cur = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * it / steps))
-            self.model.train_step(self.phases(data), p, cur, losses)
+            self.model.train_step(data, p, cur, losses)
             if it % max(1, steps // 20) == 0 or it == steps - 1:
                 hist.append((it, float(losses.mean().item())))
         sync_status()
@@ -204,7 +209,7 @@ class SurrogateLayer:
             nb = min(batch, count - off)
             nb8 = (nb + 7) // 8 * 8
             data = self.sample_data(nb8, rng)
-            q = self.model.forward(self.phases(data))
+            q = self.model.forward(data)
             p = self.exact(data)
             rows = torch.arange(nb8, dtype=torch.int32, device=self.device)
             tv = torch.empty(nb8, dtype=torch.float32, device=self.device)
@@ -221,7 +226,7 @@ class SurrogateLayer:
         for every sample that failed either."""
         L = lib()
         Bn = data.shape[0]
-        q = self.model.forward(self.phases(data))
+        q = self.model.forward(data)
         U = B.mesh_unitary(self.m, self.theta, data, Bn)
         flag = torch.zeros(Bn, dtype=torch.int32, device=self.device)
         marg = torch.empty((Bn, self.m), dtype=torch.float32, device=self.device)

@@ -131,6 +131,49 @@ def test_uneven_full_workload_against_oracle(slos):
             assert np.abs(got[pos] - ref).max() <= P_TOL
 
 
+def test_uneven_workload_every_shape_against_oracle(slos):
+    """One instance of every (m, n, detection) shape of the 1024-instance
+    workload against the oracle.  Full outputs where the Fock space has at most
+    2e5 states (every PNR shape, and threshold shapes whose pattern sums the
+    oracle can form from the full distribution): max |dp| <= 1e-5 and
+    TV <= 1e-5.  Larger threshold shapes: 40 seeded patterns (and the first and
+    last) summed by the oracle state by state."""
+    inst, Us = workloads.uneven()
+    bp = make_plan(slos, inst)
+    ws = torch.empty(bp.workspace_bytes, dtype=torch.uint8, device="cuda")
+    out = torch.empty((bp.out_offsets[-1],), dtype=torch.float32, device="cuda")
+    bp.forward(pack(Us), out, ws)
+    bp.sync_status()
+    out = out.cpu().numpy()
+    first = {}
+    for i, it in enumerate(inst):
+        first.setdefault((it.m, it.n, it.threshold), i)
+    assert len(first) >= 70
+    rng = np.random.default_rng(11)
+    full = 0
+    for (m, n, thr), i in sorted(first.items()):
+        it = inst[i]
+        Uq = np.asarray(Us[i], dtype=np.complex64).astype(np.complex128)
+        got = out[bp.out_offsets[i]:bp.out_offsets[i + 1]].astype(np.float64)
+        K = workloads.fock_dim(m, n)
+        if K <= 200_000:
+            outs = oracle.enumerate_fock(m, n)
+            p = oracle.probabilities(Uq, it.s, outs)
+            ref = oracle.threshold_probs(p, outs, m, n) if thr else p
+            d = np.abs(got - ref)
+            assert d.max() <= P_TOL, (m, n, thr, d.max())
+            assert 0.5 * d.sum() <= 1e-5, (m, n, thr, 0.5 * d.sum())
+            full += 1
+        else:
+            assert thr
+            pats = oracle.threshold_patterns(m, n)
+            idx = np.unique(np.concatenate([[0, len(pats) - 1], rng.choice(len(pats), size=40, replace=False)]))
+            for j in idx:
+                ref = oracle.threshold_prob_of_pattern(Uq, it.s, pats[j])
+                assert abs(got[j] - ref) <= P_TOL, (m, n, j)
+    assert full >= 50
+
+
 def test_batched_graph_capture_and_replay(slos):
     rng = np.random.default_rng(8)
     inst = small_uneven(rng, 40)

@@ -104,6 +104,26 @@ def test_surrogate_gradients_match_cpu_mlp():
     assert np.array_equal(w0, params[0][0])
 
 
+def test_surrogate_input_harmonics_equal_explicit_phases():
+    """With input harmonics H the model forms its phases h * x_j (index
+    (h - 1) * n_x + j) itself: its outputs equal the same model fed those
+    phases directly (identical weights, bitwise up to the sin/cos argument)."""
+    from paper_2602_11092_gb300 import surrogate as S
+    rng = np.random.default_rng(31)
+    nx, H, K, Bn = 6, 4, 48, 16
+    a = S.Surrogate(n_phases=nx * H, hidden=64, n_hidden_layers=2, n_outputs=K, max_batch=Bn, seed=9)
+    b = S.Surrogate(n_phases=nx * H, hidden=64, n_hidden_layers=2, n_outputs=K, max_batch=Bn, seed=9)
+    b.set_input_harmonics(H)
+    x = rng.standard_normal((Bn, nx)).astype(np.float32)
+    phases = (np.arange(1, H + 1, dtype=np.float32)[None, :, None] * x[:, None, :]).reshape(Bn, -1)
+    qa = a.forward(torch.tensor(phases, device="cuda")).cpu().numpy()
+    qb = b.forward(torch.tensor(x, device="cuda")).cpu().numpy()
+    S.sync_status()
+    assert np.abs(qa - qb).max() <= 1e-6
+    with pytest.raises(Exception):
+        b.set_input_harmonics(5)  # must divide n_phases
+
+
 def test_surrogate_learns_a_small_map():
     """A few hundred Adam steps on a fixed random target reduce the KL loss."""
     from paper_2602_11092_gb300 import surrogate as S

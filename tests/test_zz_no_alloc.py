@@ -47,6 +47,65 @@ def test_noalloc_forward_matches_workspace_forward_twice(slos, m, s, B, detectio
         out = torch.zeros_like(ref)
         plan.forward_noalloc(U, out, output=slos.AMPS)
         assert (out - ref).abs().max().item() <= P_TOL
+    if m == 14:
+        # this plan is too large for the on-chip forward: its layers must have
+        # gone through the built-in scratch, layer by layer
+        slos.profile_reset()
+        slos.profile_enable(True)
+        plan.forward_noalloc(U, torch.empty_like(ref.real))
+        torch.cuda.synchronize()
+        names = set(slos.profile_collect())
+        slos.profile_enable(False)
+        assert "slos_fwd_final" in names and "slos_fwd_layer" in names, names
+        assert "slos_fwd_fused" not in names, names
+
+
+def test_noalloc_largest_batch_that_fits_the_scratch(slos):
+    """The batch whose forward workspace is just under the scratch size runs
+    and matches the workspace forward; one more instance is rejected when it
+    no longer fits."""
+    m, s = 14, [1, 0] * 7
+    plan = slos.Plan(m, s)
+    cap = slos.load().slos_noalloc_scratch_bytes()
+    lo, hi = 1, 4096
+    while lo < hi:  # largest B with workspace_bytes(B) <= cap
+        mid = (lo + hi + 1) // 2
+        if plan.workspace_bytes(mid, training=False) <= cap:
+            lo = mid
+        else:
+            hi = mid - 1
+    B = lo
+    assert plan.workspace_bytes(B, training=False) <= cap < plan.workspace_bytes(B + 32, training=False)
+    U = torch.tensor(workloads.haar_unitaries(m, B, np.random.default_rng(5)), dtype=torch.complex64, device="cuda")
+    ref = plan.forward(U)
+    out = torch.full_like(ref, float("nan"))
+    plan.forward_noalloc(U, out)
+    torch.cuda.synchronize()
+    assert (out - ref).abs().max().item() <= P_TOL
+    if plan.workspace_bytes(B + 1, training=False) > cap:
+        U1 = torch.zeros((B + 1, m, m), dtype=torch.complex64, device="cuda")
+        with pytest.raises(slos.SlosError):
+            plan.forward_noalloc(U1, torch.empty((B + 1, plan.n_outputs), device="cuda"))
+
+
+def test_noalloc_rejects_host_buffers_and_mismatched_outputs(slos):
+    """Outputs that are not device memory of the current device are refused
+    before any launch; a mismatched output dtype or shape is refused by the
+    binding."""
+    import ctypes
+    m, s = 6, [1, 1, 1, 0, 0, 0]
+    plan = slos.Plan(m, s)
+    U = torch.tensor(workloads.haar_unitaries(m, 2, np.random.default_rng(1)), dtype=torch.complex64, device="cuda")
+    host = np.zeros((2, plan.n_outputs), dtype=np.float32)
+    st = slos.load().slos_forward_noalloc(plan._h, ctypes.c_void_p(U.data_ptr()), 2, slos.PROBS,
+                                          ctypes.c_void_p(host.ctypes.data), None)
+    assert st == 1  # SLOS_ERR_INVALID_ARG
+    assert "device memory" in slos.load().slos_last_error().decode()
+    with pytest.raises(ValueError):
+        plan.forward_noalloc(U, torch.empty((2, plan.n_outputs), dtype=torch.float32, device="cuda"),
+                             output=slos.AMPS)
+    with pytest.raises(ValueError):
+        plan.forward_noalloc(U, torch.empty((2, plan.n_outputs - 1), dtype=torch.float32, device="cuda"))
 
 
 def test_noalloc_rejects_batches_beyond_the_scratch(slos):
