@@ -335,36 +335,58 @@ slos_status_t slos_host_unrank(int m, int k, int64_t rank, int *t);
  * be NULL.  SLOS_ERR_UNSUPPORTED when parent ranks do not fit 26 bits. */
 slos_status_t slos_host_transition_table(int m, int k, int32_t *rowptr, uint32_t *entries, int32_t *ctab);
 
-/* Host: the split-lattice tables that plans of 8..16 modes build once
- * (Sec. II-A.3's transition graph regrouped by head blocks).  The m modes are
- * split into head modes 0..h-1 and tail modes h..m-1; the states of layer k
- * with the same head occupations form one block of consecutive ranks.
- * Layer k (2 <= k <= n):
- *   counts   int64 [4]: forward blocks, backward blocks, forward chunks,
- *            backward chunks (always written).
- *   fdesc    int32 [blocks][4]: base rank, size, base rank of the same head in
- *            layer k-1, tail photons | occupied head modes << 8.
- *   fhead    uint32 [blocks][8]: (base rank of head t_H - e_j in layer k-1)
- *            << 5 | j for the occupied head modes j, ascending, then 0.
- *   fchunk   int32 [chunks]: block holding state 4 * chunk of layer k.
+/* Host: the split-lattice tables that plans of 8..16 modes build once for
+ * their backward layers (Sec. II-A.3's transition graph regrouped by head
+ * blocks).  The m modes are split into head modes 0..h-1 and tail modes
+ * h..m-1; the states of a layer with the same head occupations form one
+ * block of consecutive ranks.  Layer k (2 <= k <= n), whose parents are the
+ * states of layer k-1:
+ *   counts   int64 [2]: blocks, chunks (always written).
  *   bdesc    int32 [blocks][4]: the blocks of layer k-1: base rank, size, base
  *            rank of the same head in layer k, tail photons.
- *   bhead    int32 [blocks][8]: base rank in layer k of head t_H + e_j, j < h.
+ *   bhead    int32 [blocks][8]: base rank in layer k of head t_H + e_j, j < h,
+ *            then 0.
  *   bchunk   int32 [chunks]: block holding state 4 * chunk of layer k-1.
  * Any array may be NULL.  h: head modes (written).  SLOS_ERR_UNSUPPORTED
  * when the plan shape takes no split tables. */
-slos_status_t slos_host_split_layer(int m, int n, int k, int *h, int64_t *counts, int32_t *fdesc, uint32_t *fhead,
-                                    int32_t *fchunk, int32_t *bdesc, int32_t *bhead, int32_t *bchunk);
+slos_status_t slos_host_split_layer(int m, int n, int k, int *h, int64_t *counts, int32_t *bdesc, int32_t *bhead,
+                                    int32_t *bchunk);
 
-/* Host: the tail tables of the split lattice over the m - h tail modes, for
- * tail photon numbers rho = 0..n.  offsets int32 [3][n+1]: start of rho's
- * slot rows (uint32 units), slot-row width, start of rho's child rows (rows
- * of 8).  counts int64 [2]: slot entries, child entries (always written).
- * slots: (local parent position << 5) | (h + tail mode) per occupied tail
- * mode, padded with 24 (parent 0, the zero U row); ctab: uint16 local
- * position of t_L + e_j for j < m - h, then 0.  Any array may be NULL. */
-slos_status_t slos_host_split_tail(int m, int n, int *h, int32_t *offsets, int64_t *counts, uint32_t *slots,
-                                   uint16_t *ctab);
+/* Host: the tail child table of the split lattice over the m - h tail modes,
+ * for tail photon numbers rho = 0..n-1.  offsets int32 [n+1]: start of rho's
+ * child rows (rows of 8; offsets[n] = the row count).  count: child entries
+ * (always written).  ctab: uint16 local position of t_L + e_j within the
+ * tail lattice of rho + 1 photons for j < m - h, then 0.  Any array may be
+ * NULL. */
+slos_status_t slos_host_split_tail(int m, int n, int *h, int32_t *offsets, int64_t *count, uint16_t *ctab);
+
+/* Host: range check of a layer's transition tables as plans upload them
+ * (every plan runs it before uploading).  slots: uint32 [C(m+k-1,k)][kw],
+ * each (parent rank << 5) | mode for an occupied mode, or 24 (padding); every
+ * state needs at least one parent.  ctab: int32 [C(m+k-2,k-1)][m] child
+ * ranks.  SLOS_ERR_INTERNAL, naming the first bad entry, when an index is out
+ * of range. */
+slos_status_t slos_host_validate_tables(int m, int k, int kw, const uint32_t *slots, const int32_t *ctab);
+
+/* Host-side fault injection for tests; it makes host calls fail the way the
+ * real failure would, so no GPU is faulted.  SLOS_INJECT_ALLOC_FAIL: the
+ * value-th device allocation made while building plans from now on fails as
+ * out of memory (one shot; 0 = off).  SLOS_INJECT_STREAM_DEVICE: the device
+ * of any stream passed to slos_forward / slos_backward is reported as
+ * `value` (-1 = off), so a plan used with another device's stream is
+ * exercised; such calls return SLOS_ERR_INVALID_ARG before any launch.
+ * SLOS_INJECT_TABLE_BUDGET: while value != 0, every plan built finds its
+ * transition tables over the per-plan table budget, as plans too large for
+ * tables do, and so takes the arithmetic-index kernels (no tables, no split
+ * lattice, no on-chip forward); plans keep the mode they were built in.
+ * SLOS_INJECT_NONE clears all three. */
+typedef enum {
+    SLOS_INJECT_NONE = 0,
+    SLOS_INJECT_ALLOC_FAIL = 1,
+    SLOS_INJECT_STREAM_DEVICE = 2,
+    SLOS_INJECT_TABLE_BUDGET = 3
+} slos_inject_t;
+slos_status_t slos_inject_fault(slos_inject_t kind, int value);
 
 /* Device: for ranks [first, first + count) of layer k (k photons, m modes)
  * write the composition (uint8 [count][m]) and the parent index

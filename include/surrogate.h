@@ -96,7 +96,9 @@ slos_status_t surr_tv_rows(const float *q, const int *rows, const float *p, int 
 /* Cheap screen for every sample: the surrogate's mean photon number per mode,
  * sum_t q[b][t] t_j (occ: uint8 [K][m] occupations of the output states),
  * against the exact value sum_i |U[b][j][i]|^2 s_i (Sec. II-A.1); flag[b] is
- * set to 1 (never cleared) when some mode differs by more than tol.
+ * set to 1 (never cleared) when the differences summed over the modes exceed
+ * tol.  That sum is at most 2 n TV(exact, surrogate) for n photons, so with
+ * tol = 2 n t a flagged sample provably has TV > t.
  * input_state: host, m ints.  marg_scratch: float [B][m]. */
 slos_status_t surr_screen(const float *q, int B, int K, const uint8_t *occ, int m, const void *U, const int *input_state,
                           float tol, float *marg_scratch, int *flag, void *stream);

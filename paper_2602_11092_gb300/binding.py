@@ -77,8 +77,10 @@ _SIGNATURES = {
     "slos_host_unrank": ([_int, _int, _i64, ctypes.POINTER(_int)], _int),
     "slos_device_index_table": ([_int, _int, _i64, _i64, _vp, _vp, _vp], _int),
     "slos_host_transition_table": ([_int, _int, _vp, _vp, _vp], _int),
-    "slos_host_split_layer": ([_int, _int, _int, ctypes.POINTER(_int), _vp, _vp, _vp, _vp, _vp, _vp, _vp], _int),
-    "slos_host_split_tail": ([_int, _int, ctypes.POINTER(_int), _vp, _vp, _vp, _vp], _int),
+    "slos_host_validate_tables": ([_int, _int, _int, _vp, _vp], _int),
+    "slos_inject_fault": ([_int, _int], _int),
+    "slos_host_split_layer": ([_int, _int, _int, ctypes.POINTER(_int), _vp, _vp, _vp, _vp], _int),
+    "slos_host_split_tail": ([_int, _int, ctypes.POINTER(_int), _vp, _vp, _vp], _int),
     "slos_noalloc_scratch_bytes": ([], _sz),
     "slos_forward_noalloc": ([_vp, _vp, _int, _int, _vp, _vp], _int),
     "slos_profile_enable": ([_int], _int),
@@ -448,39 +450,33 @@ def host_transition_table(m: int, k: int):
 
 
 def host_split_layer(m: int, n: int, k: int):
-    """Split-lattice tables of layer k as numpy arrays (dict), built by the library."""
+    """Backward split-lattice tables of layer k (parents in layer k-1) as
+    numpy arrays (dict), built by the library."""
     import numpy as np
     lib = load()
     h = _int()
-    counts = np.zeros(4, dtype=np.int64)
-    _check(lib.slos_host_split_layer(m, n, k, ctypes.byref(h), counts.ctypes.data, None, None, None, None, None,
-                                     None))
-    nf, nb, nfc, nbc = (int(x) for x in counts)
-    out = {"h": h.value,
-           "fdesc": np.zeros((nf, 4), dtype=np.int32), "fhead": np.zeros((nf, 8), dtype=np.uint32),
-           "fchunk": np.zeros(nfc, dtype=np.int32),
-           "bdesc": np.zeros((nb, 4), dtype=np.int32), "bhead": np.zeros((nb, 8), dtype=np.int32),
+    counts = np.zeros(2, dtype=np.int64)
+    _check(lib.slos_host_split_layer(m, n, k, ctypes.byref(h), counts.ctypes.data, None, None, None))
+    nb, nbc = (int(x) for x in counts)
+    out = {"h": h.value, "bdesc": np.zeros((nb, 4), dtype=np.int32), "bhead": np.zeros((nb, 8), dtype=np.int32),
            "bchunk": np.zeros(nbc, dtype=np.int32)}
     _check(lib.slos_host_split_layer(m, n, k, ctypes.byref(h), counts.ctypes.data,
-                                     *(out[key].ctypes.data for key in ("fdesc", "fhead", "fchunk", "bdesc", "bhead",
-                                                                         "bchunk"))))
+                                     *(out[key].ctypes.data for key in ("bdesc", "bhead", "bchunk"))))
     return out
 
 
 def host_split_tail(m: int, n: int):
-    """Tail tables of the split lattice (dict of numpy arrays), built by the library."""
+    """Tail child table of the split lattice (dict of numpy arrays), built by the library."""
     import numpy as np
     lib = load()
     h = _int()
-    offsets = np.zeros(3 * (n + 1), dtype=np.int32)
-    counts = np.zeros(2, dtype=np.int64)
-    _check(lib.slos_host_split_tail(m, n, ctypes.byref(h), offsets.ctypes.data, counts.ctypes.data, None, None))
-    slots = np.zeros(int(counts[0]), dtype=np.uint32)
-    ctab = np.zeros(int(counts[1]), dtype=np.uint16)
-    _check(lib.slos_host_split_tail(m, n, ctypes.byref(h), offsets.ctypes.data, counts.ctypes.data,
-                                    slots.ctypes.data, ctab.ctypes.data))
-    off = offsets.reshape(3, n + 1)
-    return {"h": h.value, "soff": off[0], "tw": off[1], "coff": off[2], "slots": slots, "ctab": ctab}
+    offsets = np.zeros(n + 1, dtype=np.int32)
+    count = np.zeros(1, dtype=np.int64)
+    _check(lib.slos_host_split_tail(m, n, ctypes.byref(h), offsets.ctypes.data, count.ctypes.data, None))
+    ctab = np.zeros(int(count[0]), dtype=np.uint16)
+    _check(lib.slos_host_split_tail(m, n, ctypes.byref(h), offsets.ctypes.data, count.ctypes.data,
+                                    ctab.ctypes.data))
+    return {"h": h.value, "coff": offsets, "ctab": ctab}
 
 
 def device_index_table(m: int, k: int, first: int, count: int, device="cuda", stream=None):

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -107,12 +108,86 @@ static cudaError_t init_device_once(int dev) {
     if ((e = slos_init_m16()) != cudaSuccess) return e;
     if ((e = slos_init_m20()) != cudaSuccess) return e;
     if ((e = slos_init_m24()) != cudaSuccess) return e;
-    if ((e = slos_tab_init()) != cudaSuccess) return e;
     if ((e = slos_fused_init()) != cudaSuccess) return e;
-    if ((e = slos_split_init()) != cudaSuccess) return e;
     if ((e = slos_pair_init()) != cudaSuccess) return e;
     done[dev] = true;
     return cudaSuccess;
+}
+
+// ------------------------------------------------------------------ host fault injection
+// Test hooks (slos_inject_fault): they make host calls fail as the real
+// failure would, so error paths are exercised without faulting a GPU.
+static std::atomic<int> g_inject_alloc{0};         // n > 0: the n-th plan-time allocation from now fails
+static std::atomic<int> g_inject_stream_dev{-1};   // >= 0: stream device queries report this device
+static std::atomic<int> g_inject_table_budget{0};  // 1: every plan finds its table budget exceeded
+
+// Device allocation made while building a plan.
+static cudaError_t plan_malloc(void **ptr, size_t bytes) {
+    if (g_inject_alloc.load() > 0 && g_inject_alloc.fetch_sub(1) == 1) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+template <typename T>
+static cudaError_t plan_malloc(T **ptr, size_t bytes) {
+    return plan_malloc(reinterpret_cast<void **>(ptr), bytes);
+}
+
+// The stream must belong to the plan's device (its tables live there).  A
+// stream that is being captured into a graph is not asked (a device query
+// there ends the capture with an error), and a query that cannot answer is
+// not treated as a mismatch.
+static slos_status_t check_stream(const slos_plan_s *p, cudaStream_t s, const char *who) {
+    int dev = g_inject_stream_dev.load();
+    if (dev < 0) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return SLOS_OK;
+        }
+        if (cs != cudaStreamCaptureStatusNone) return SLOS_OK;
+        if (cudaStreamGetDevice(s, &dev) != cudaSuccess) {
+            cudaGetLastError();
+            return SLOS_OK;
+        }
+    }
+    if (dev != p->device)
+        return fail(SLOS_ERR_INVALID_ARG, std::string(who) + ": the stream belongs to device " + std::to_string(dev) +
+                                              " but the plan was built on device " + std::to_string(p->device));
+    return SLOS_OK;
+}
+
+// Every index of a layer's slot table and child table in range before upload:
+// a slot names a parent of layer k-1 and a mode, or is padding; every state
+// has at least one parent; a child entry names a state of layer k (or -1
+// where the lattice has no such child, if holes are allowed).
+static bool tables_in_range(int m, int64_t Fprev, int64_t Fk, int kw, const uint32_t *slots, const int32_t *ctab,
+                            bool holes, std::string *why) {
+    for (int64_t c = 0; c < Fk; ++c) {
+        int occ = 0;
+        for (int q = 0; q < kw; ++q) {
+            const uint32_t e = slots[(size_t)c * kw + q];
+            if (e == kSlotEmpty) continue;
+            if ((int)(e & 31u) >= m || (int64_t)(e >> 5) >= Fprev) {
+                *why = "slot " + std::to_string(q) + " of state " + std::to_string(c) + " out of range";
+                return false;
+            }
+            ++occ;
+        }
+        if (occ == 0) {
+            *why = "state " + std::to_string(c) + " has no parent";
+            return false;
+        }
+    }
+    for (int64_t i = 0; i < Fprev * m; ++i) {
+        const int32_t x = ctab[i];
+        if (x >= Fk || x < (holes ? -1 : 0)) {
+            *why = "child entry " + std::to_string(i) + " out of range";
+            return false;
+        }
+    }
+    return true;
 }
 
 // ------------------------------------------------------------------ host index
@@ -192,14 +267,10 @@ static void free_split_tables(slos_plan_s *p) {
     SplitTables *st = p->split;
     if (!st) return;
     for (auto &L : st->layer) {
-        cudaFree(L.fdesc);
-        cudaFree(L.fhead);
-        cudaFree(L.fchunk);
         cudaFree(L.bdesc);
         cudaFree(L.bhead);
         cudaFree(L.bchunk);
     }
-    cudaFree(st->tslots);
     cudaFree(st->tctab);
     delete st;
     p->split = nullptr;
@@ -215,14 +286,60 @@ static void free_tables(slos_plan_s *p) {
         L = LayerTables();
     }
     if (p->tab.w) cudaFree(p->tab.w);
-    if (p->tab.pat) cudaFree(p->tab.pat);
     if (p->tab.occ) cudaFree(p->tab.occ);
     if (p->tab.gfact) cudaFree(p->tab.gfact);
+    cudaFree(p->tab.lrank);
+    cudaFree(p->tab.lpat);
+    cudaFree(p->tab.lw);
+    cudaFree(p->tab.lseg);
+    p->tab.lrank = p->tab.lpat = p->tab.lseg = nullptr;
+    p->tab.lw = nullptr;
+    p->tab.nseg = 0;
     p->tab.gfact = nullptr;
     p->tab.w = nullptr;
-    p->tab.pat = nullptr;
     p->tab.occ = nullptr;
     p->tab.enabled = false;
+}
+
+// Threshold detection: list position of every final state (n photons, m
+// modes) in the pattern-grouped order of tables.h.  A state with support b
+// (j = |b| modes) sits at
+//     base_j + colex(b) C(n-1, j-1) + rank(u),  u = t - 1_b on the modes of b,
+// where base_j counts the states of the patterns with fewer modes and rank(u)
+// is u's descending-lex rank among the compositions of n - j over j modes.
+// Also the work items of the final layer: runs of whole patterns of about
+// kThreshSegStates states (at least one pattern), so that one warp sums each
+// pattern.
+constexpr int kThreshSegStates = 48;
+static void threshold_list_host(int m, int n, std::vector<int32_t> &pos, std::vector<int32_t> &seg) {
+    const int64_t Fn = binom_host(m + n - 1, n);
+    const int jmax = std::min(m, n);
+    std::vector<int64_t> base(jmax + 2, 0);
+    for (int j = 1; j <= jmax; ++j) base[j + 1] = base[j] + binom_host(m, j) * binom_host(n - 1, j - 1);
+    pos.assign(Fn, 0);
+    std::vector<int> bar(m + 1), t(m + 1), u(m + 1);
+    uint64_t z = 0;
+    for (int b = 0; b < m - 1; ++b) z |= 1ull << b;
+    for (int64_t c = 0; c < Fn; ++c) {
+        bars_of(z, m, n + m - 1, bar.data(), t.data());
+        int j = 0;
+        int64_t colex = 0;
+        for (int q = 0; q < m; ++q)
+            if (t[q] > 0) {
+                u[j] = t[q] - 1;
+                ++j;
+                colex += binom_host(q, j);
+            }
+        pos[c] = (int32_t)(base[j] + colex * binom_host(n - 1, j - 1) + host_rank(j, u.data()));
+        z = next_comb_host(z);
+    }
+    seg.clear();
+    for (int j = 1; j <= jmax; ++j) {
+        const int64_t cnt = binom_host(n - 1, j - 1), npat = binom_host(m, j);
+        const int64_t per = std::max<int64_t>(1, kThreshSegStates / cnt);
+        for (int64_t q = 0; q < npat; q += per) seg.push_back((int32_t)(base[j] + q * cnt));
+    }
+    seg.push_back((int32_t)Fn);
 }
 
 // Transition graph of layer k (k photons, m modes) on the host: CSR parent
@@ -346,8 +463,15 @@ static slos_status_t build_tables_unbunched(slos_plan_s *p) {
         }
         LayerTables &LT = p->tab.layer[k];
         LT.kw = kw;
-        if (cudaMalloc(&LT.slots, slots.size() * 4) != cudaSuccess ||
-            cudaMalloc(&LT.ctab, ctab.size() * 4) != cudaSuccess) {
+        {
+            std::string why;
+            if (!tables_in_range(m, p->F[k - 1], p->F[k], kw, slots.data(), ctab.data(), true, &why)) {
+                free_tables(p);
+                return fail(SLOS_ERR_INTERNAL, "slos_plan_space: layer " + std::to_string(k) + ": " + why);
+            }
+        }
+        if (plan_malloc(&LT.slots, slots.size() * 4) != cudaSuccess ||
+            plan_malloc(&LT.ctab, ctab.size() * 4) != cudaSuccess) {
             free_tables(p);
             return fail(SLOS_ERR_OOM, "slos_plan_space: cannot allocate the transition tables");
         }
@@ -368,7 +492,7 @@ static slos_status_t build_tables_unbunched(slos_plan_s *p) {
             ++c;
         } while (next_subset(S, m));
     }
-    if (cudaMalloc(&p->tab.w, w.size() * 4) != cudaSuccess || cudaMalloc(&p->tab.occ, occ.size()) != cudaSuccess) {
+    if (plan_malloc(&p->tab.w, w.size() * 4) != cudaSuccess || plan_malloc(&p->tab.occ, occ.size()) != cudaSuccess) {
         free_tables(p);
         return fail(SLOS_ERR_OOM, "slos_plan_space: cannot allocate the weight tables");
     }
@@ -392,9 +516,13 @@ static slos_status_t build_tables(slos_plan_s *p) {
         bytes += 4 * (size_t)p->F[k] * slot_width(m, k) + 4 * (size_t)m * p->F[k - 1];
     }
     bytes += 8 * (size_t)p->F[n] + (size_t)p->K * m;
-    if (bytes > kTableBudgetBytes) return SLOS_OK;
+    if (p->det == SLOS_DETECT_THRESHOLD) bytes += 12 * (size_t)p->F[n];  // list-order tables
+    if (bytes > kTableBudgetBytes || g_inject_table_budget.load()) return SLOS_OK;  // arithmetic-index kernels
     p->tab.layer.assign(n + 1, LayerTables());
     std::vector<int> bar(m + 1), t(m + 1);
+    const bool thresh = p->det == SLOS_DETECT_THRESHOLD;
+    std::vector<int32_t> lpos, lseg;
+    if (thresh) threshold_list_host(m, n, lpos, lseg);
     auto init_mask = [&](int k) {
         // first state (k, 0, ..., 0): all bars at the end of the string
         uint64_t z = 0;
@@ -414,8 +542,22 @@ static slos_status_t build_tables(slos_plan_s *p) {
             for (int32_t q = rowptr[c]; q < rowptr[c + 1]; ++q)
                 slots[(size_t)c * kw + (q - rowptr[c])] = ((entries[q] >> 6) << 5) | ((entries[q] >> 1) & 31u);
         LT.kw = kw;
-        if (cudaMalloc(&LT.slots, slots.size() * 4) != cudaSuccess ||
-            cudaMalloc(&LT.ctab, ctab.size() * 4) != cudaSuccess) {
+        {
+            std::string why;
+            if (!tables_in_range(m, p->F[k - 1], p->F[k], kw, slots.data(), ctab.data(), false, &why)) {
+                free_tables(p);
+                return fail(SLOS_ERR_INTERNAL, "slos_plan: layer " + std::to_string(k) + ": " + why);
+            }
+        }
+        if (thresh && k == n) {
+            // the final layer's rows in list order
+            std::vector<uint32_t> rows(slots.size());
+            for (int64_t c = 0; c < p->F[n]; ++c)
+                memcpy(&rows[(size_t)lpos[c] * kw], &slots[(size_t)c * kw], kw * sizeof(uint32_t));
+            slots.swap(rows);
+        }
+        if (plan_malloc(&LT.slots, slots.size() * 4) != cudaSuccess ||
+            plan_malloc(&LT.ctab, ctab.size() * 4) != cudaSuccess) {
             free_tables(p);
             return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the transition tables");
         }
@@ -451,7 +593,7 @@ static slos_status_t build_tables(slos_plan_s *p) {
                 for (int j = 0; j < m; ++j) occ[(size_t)pat[c] * m + j] = (uint8_t)((supp >> j) & 1u);
             z = next_comb_host(z);
         }
-        if (cudaMalloc(&p->tab.occ, occ.size()) != cudaSuccess) {
+        if (plan_malloc(&p->tab.occ, occ.size()) != cudaSuccess) {
             free_tables(p);
             return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the occupation table");
         }
@@ -459,7 +601,7 @@ static slos_status_t build_tables(slos_plan_s *p) {
             free_tables(p);
             return fail(SLOS_ERR_CUDA, "slos_plan: cannot upload the occupation table");
         }
-        if (cudaMalloc(&p->tab.w, w.size() * 4) != cudaSuccess) {
+        if (plan_malloc(&p->tab.w, w.size() * 4) != cudaSuccess) {
             free_tables(p);
             return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the weight table");
         }
@@ -467,14 +609,32 @@ static slos_status_t build_tables(slos_plan_s *p) {
             free_tables(p);
             return fail(SLOS_ERR_CUDA, "slos_plan: cannot upload the weight table");
         }
-        if (p->det == SLOS_DETECT_THRESHOLD) {
-            if (cudaMalloc(&p->tab.pat, pat.size() * 4) != cudaSuccess) {
-                free_tables(p);
-                return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the pattern table");
+        if (thresh) {
+            std::vector<int32_t> lrank(p->F[n]), lpat(p->F[n]);
+            std::vector<float> lw(p->F[n]);
+            for (int64_t c = 0; c < p->F[n]; ++c) {
+                lrank[lpos[c]] = (int32_t)c;
+                lpat[lpos[c]] = pat[c];
+                lw[lpos[c]] = w[c];
             }
-            if (!h2d(p->tab.pat, pat.data(), pat.size() * 4)) {
+            // every pattern lies inside one work item
+            for (size_t i = 0; i + 1 < lseg.size(); ++i)
+                if (lseg[i] >= lseg[i + 1] || (lseg[i] > 0 && lpat[lseg[i]] == lpat[lseg[i] - 1])) {
+                    free_tables(p);
+                    return fail(SLOS_ERR_INTERNAL, "slos_plan: threshold work items split a pattern");
+                }
+            p->tab.nseg = (int)lseg.size() - 1;
+            if (plan_malloc(&p->tab.lrank, lrank.size() * 4) != cudaSuccess ||
+                plan_malloc(&p->tab.lpat, lpat.size() * 4) != cudaSuccess ||
+                plan_malloc(&p->tab.lw, lw.size() * 4) != cudaSuccess ||
+                plan_malloc(&p->tab.lseg, lseg.size() * 4) != cudaSuccess) {
                 free_tables(p);
-                return fail(SLOS_ERR_CUDA, "slos_plan: cannot upload the pattern table");
+                return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the threshold list tables");
+            }
+            if (!h2d(p->tab.lrank, lrank.data(), lrank.size() * 4) || !h2d(p->tab.lpat, lpat.data(), lpat.size() * 4) ||
+                !h2d(p->tab.lw, lw.data(), lw.size() * 4) || !h2d(p->tab.lseg, lseg.data(), lseg.size() * 4)) {
+                free_tables(p);
+                return fail(SLOS_ERR_CUDA, "slos_plan: cannot upload the threshold list tables");
             }
         }
     }
@@ -529,13 +689,13 @@ static slos_status_t build_encode_tables(slos_plan_s *p) {
             }
         }
         uint32_t *d = nullptr;
-        if (cudaMalloc(&d, info.size() * 4) != cudaSuccess)
+        if (plan_malloc(&d, info.size() * 4) != cudaSuccess)
             return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the amplitude-encoding tables");
         p->tab.layer[k].colinfo = d;  // owned by the plan from here on (freed with its tables)
         if (!h2d(d, info.data(), info.size() * 4))
             return fail(SLOS_ERR_CUDA, "slos_plan: cannot upload the amplitude-encoding tables");
     }
-    if (cudaMalloc(&p->tab.gfact, g.size() * 4) != cudaSuccess) {
+    if (plan_malloc(&p->tab.gfact, g.size() * 4) != cudaSuccess) {
         p->tab.gfact = nullptr;
         return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the amplitude-encoding weights");
     }
@@ -550,7 +710,7 @@ template <typename T>
 static bool upload(T **dst, const std::vector<T> &v) {
     *dst = nullptr;
     if (v.empty()) return true;
-    if (cudaMalloc(dst, v.size() * sizeof(T)) != cudaSuccess) {
+    if (plan_malloc(dst, v.size() * sizeof(T)) != cudaSuccess) {
         *dst = nullptr;
         return false;
     }
@@ -567,31 +727,45 @@ static slos_status_t build_split_tables(slos_plan_s *p) {
     st->layer.assign(p->n + 1, SplitLayer());
     SplitTailHost tail;
     split_build_tail_host(p->m, h, p->n, tail);
-    memcpy(st->soff, tail.soff, sizeof(st->soff));
-    memcpy(st->tw, tail.tw, sizeof(st->tw));
+    {
+        // tail child rows: local children inside their tail lattices
+        const int mL = p->m - h;
+        for (int rho = 0; rho < p->n; ++rho) {
+            const int64_t cnt = binom_host(rho + mL - 1, mL - 1);
+            const int64_t chd = binom_host(rho + 1 + mL - 1, mL - 1);
+            for (int64_t i = 0; i < cnt * 8; ++i)
+                if ((i % 8) < mL && tail.ctab[(size_t)tail.coff[rho] * 8 + i] >= chd)
+                    return fail(SLOS_ERR_INTERNAL, "slos_plan: split tail child out of range");
+        }
+    }
     memcpy(st->coff, tail.coff, sizeof(st->coff));
-    bool ok = upload(&st->tslots, tail.slots) && upload(&st->tctab, tail.ctab);
-    st->bytes = tail.slots.size() * 4 + tail.ctab.size() * 2;
+    bool ok = upload(&st->tctab, tail.ctab);
+    st->bytes = tail.ctab.size() * 2;
     for (int k = 2; ok && k <= p->n; ++k) {
         SplitLayerHost L;
         split_build_layer_host(p->m, h, k, L);
-        // the blocks must tile both layers in rank order
+        // the parent blocks must tile layer k-1 in rank order, and every
+        // child block the kernel reads through them must lie inside layer k
+        const int mL = p->m - h;
+        auto tail_size = [&](int rho) { return rho < 0 ? (int64_t)0 : binom_host(rho + mL - 1, mL - 1); };
         int64_t next = 0;
-        for (size_t b = 0; b < L.fdesc.size() / 4; ++b) {
-            if (L.fdesc[4 * b] != next) return fail(SLOS_ERR_INTERNAL, "slos_plan: split blocks out of order");
-            next += L.fdesc[4 * b + 1];
+        for (size_t b = 0; b < L.bdesc.size() / 4; ++b) {
+            const int64_t base = L.bdesc[4 * b], size = L.bdesc[4 * b + 1], lc = L.bdesc[4 * b + 2];
+            const int rho = L.bdesc[4 * b + 3];
+            if (base != next || lc + tail_size(rho + 1) > p->F[k])
+                return fail(SLOS_ERR_INTERNAL, "slos_plan: split parent blocks out of range");
+            next += size;
+            for (int j = 0; j < h; ++j)
+                if ((int64_t)L.bhead[(size_t)b * kSplitMaxHead + j] + size > p->F[k])
+                    return fail(SLOS_ERR_INTERNAL, "slos_plan: split head-child block out of range");
         }
-        if (next != p->F[k]) return fail(SLOS_ERR_INTERNAL, "slos_plan: split blocks do not cover the layer");
+        if (next != p->F[k - 1]) return fail(SLOS_ERR_INTERNAL, "slos_plan: split parent blocks do not cover the layer");
         SplitLayer &D = st->layer[k];
-        D.nfblk = (int)(L.fdesc.size() / 4);
         D.nbblk = (int)(L.bdesc.size() / 4);
-        std::vector<int4> fd(D.nfblk), bd(D.nbblk);
-        memcpy(fd.data(), L.fdesc.data(), L.fdesc.size() * 4);
+        std::vector<int4> bd(D.nbblk);
         memcpy(bd.data(), L.bdesc.data(), L.bdesc.size() * 4);
-        ok = upload(&D.fdesc, fd) && upload(&D.fhead, L.fhead) && upload(&D.fchunk, L.fchunk) &&
-             upload(&D.bdesc, bd) && upload(&D.bhead, L.bhead) && upload(&D.bchunk, L.bchunk);
-        st->bytes += (L.fdesc.size() + L.fhead.size() + L.fchunk.size() + L.bdesc.size() + L.bhead.size() +
-                      L.bchunk.size()) * 4;
+        ok = upload(&D.bdesc, bd) && upload(&D.bhead, L.bhead) && upload(&D.bchunk, L.bchunk);
+        st->bytes += (L.bdesc.size() + L.bhead.size() + L.bchunk.size()) * 4;
     }
     if (!ok) return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate or upload the split-lattice tables");
     return SLOS_OK;
@@ -657,12 +831,12 @@ static bool build_fused_tables(slos_plan_s *p) {
         FusedLayer &FL = p->tab.fused[k];
         FL.nblk = (int)blk.size();
         FL.fpad = fpad;
-        if (cudaMalloc(&FL.rows, rows.size() * 4) != cudaSuccess || cudaMalloc(&FL.blk, blk.size() * 4) != cudaSuccess)
+        if (plan_malloc(&FL.rows, rows.size() * 4) != cudaSuccess || plan_malloc(&FL.blk, blk.size() * 4) != cudaSuccess)
             return false;
         if (!h2d(FL.rows, rows.data(), rows.size() * 4) || !h2d(FL.blk, blk.data(), blk.size() * 4)) return false;
         if (k == n) {
-            if (cudaMalloc(&p->tab.fused_id, id.size() * 4) != cudaSuccess ||
-                cudaMalloc(&p->tab.fused_w, wf.size() * 4) != cudaSuccess)
+            if (plan_malloc(&p->tab.fused_id, id.size() * 4) != cudaSuccess ||
+                plan_malloc(&p->tab.fused_w, wf.size() * 4) != cudaSuccess)
                 return false;
             if (!h2d(p->tab.fused_id, id.data(), id.size() * 4) || !h2d(p->tab.fused_w, wf.data(), wf.size() * 4))
                 return false;
@@ -742,16 +916,14 @@ static int bwd_tab_blocks(const slos_plan_s *p, int64_t parents, int NG, bool fi
     return (int)std::max<int64_t>(1, std::min(need, target));
 }
 
-// Split-lattice kernels: the forward walks CTA tiles of kSplitTile states,
-// the backward warp runs of kSplitRun parents; grids fill the resident blocks
-// their register budgets allow.
+// Split-lattice backward: warp runs of kSplitRun parents; the grid fills the
+// resident blocks its register budget allows.
 static int split_blocks(const slos_plan_s *p, int64_t items, int items_per_block, int NG, int per_sm) {
     const int64_t need = (items + items_per_block - 1) / items_per_block;
     const int64_t target = std::max<int64_t>(1, (int64_t)p->sm_count * per_sm / std::max(1, NG));
     return (int)std::max<int64_t>(1, std::min(need, target));
 }
 static int64_t split_runs(int64_t states) { return (states + kSplitRun - 1) / kSplitRun; }
-static int64_t split_tiles(int64_t states) { return (states + kSplitTile - 1) / kSplitTile; }
 
 constexpr int kChunkStore = 64;
 constexpr int kChunkFinal = 32;
@@ -777,10 +949,12 @@ static Layout make_layout(const slos_plan_s *p, int batch, bool training) {
     };
     L.counters = take(kCounters * sizeof(int));
     if (!training) {
-        // ping-pong: layer k in buffer (n-1-k) % 2
+        // ping-pong: layer k in buffer (n-1-k) % 2; a_n only for the
+        // threshold pattern sums of plans without tables
         size_t b0 = n >= 2 ? take(row * p->F[n - 1]) : SIZE_MAX;
         size_t b1 = n >= 3 ? take(row * p->F[n - 2]) : SIZE_MAX;
         for (int k = 1; k < n; ++k) L.layer[k] = ((n - 1 - k) % 2 == 0) ? b0 : b1;
+        if (p->det == SLOS_DETECT_THRESHOLD && !p->tab.enabled) L.layer[n] = take(row * p->F[n]);
     } else {
         // kept layers + one recompute segment: slot i of a segment holds the
         // i-th non-kept layer above the segment's kept base layer
@@ -1125,7 +1299,7 @@ slos_status_t slos_plan_space(int m, int n, const int *input_state, slos_detecti
         delete p;
         return fail(SLOS_ERR_CUDA, std::string("slos_plan: kernel attributes: ") + cudaGetErrorString(e));
     }
-    if (cudaMalloc(&p->d_status, 64) != cudaSuccess) {
+    if (plan_malloc(&p->d_status, 64) != cudaSuccess) {
         delete p;
         return fail(SLOS_ERR_OOM, "slos_plan: cannot allocate the status word");
     }
@@ -1232,7 +1406,7 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
     a.NG = NG;
     a.chunk = epi == EPI_STORE ? kChunkStore : kChunkFinal;
     a.inv_sfact = p->inv_sfact;
-    fill_pat_off(p, a.pat_off);
+    a.status = p->d_status;
     const int bx = blocks_for(p, a.Fk, a.chunk, NG);
     // layered-model bytes: read a_{k-1}, write a_k and/or the output
     double bytes = (k >= 2 ? 8.0 * a.Fprev : 0.0);
@@ -1244,53 +1418,29 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
         bytes += (epi == EPI_AMPS ? 8.0 : 4.0) * p->K + (save ? 8.0 * a.Fk : 0.0);
     }
     ProfScope ps(name, bytes * batch, s);
-    if (kSplitForward && p->split && k >= 2) {
-        const SplitTables &st = *p->split;
-        const SplitLayer &L = st.layer[k];
-        SplitFwdArgs sa;
-        memset(&sa, 0, sizeof(sa));
-        sa.prev = a.prev;
-        sa.next = a.next;
-        sa.U = U;
-        sa.out = out;
-        sa.w = p->tab.w;
-        sa.pat = p->tab.pat;
-        sa.desc = L.fdesc;
-        sa.head = L.fhead;
-        sa.chunk = L.fchunk;
-        sa.tslots = st.tslots;
-        memcpy(sa.soff, st.soff, sizeof(sa.soff));
-        memcpy(sa.tw, st.tw, sizeof(sa.tw));
-        sa.Fk = (int)p->F[k];
-        sa.Fprev = (int)p->F[k - 1];
-        sa.ntiles = (int)split_tiles(p->F[k]);
-        sa.K = p->K;
-        sa.m = p->m;
-        sa.col = a.col;
-        sa.B = batch;
-        SLOS_CUDA(slos_launch_fwd_split(sa, NG, epi, save, split_blocks(p, sa.ntiles, 1, NG, kSplitFwdMinBlocks), s));
-        return SLOS_OK;
-    }
     if (p->tab.enabled) {
-        TabArgs t;
+        TabArgs t{};
         t.slots = p->tab.layer[k].slots;
         t.kw = p->tab.layer[k].kw;
         t.w = p->tab.w;
-        t.pat = p->tab.pat;
         t.work = counter;
-        t.items_per_group = (int)((a.Fk + 32 * kWarpsPerBlock - 1) / (32 * kWarpsPerBlock));
-        if (kFwdPair) {
-            // warp items: one chunk of consecutive states of a group pair
-            const int64_t items = ((a.Fk + slos_pair_chunk() - 1) / slos_pair_chunk()) * ((NG + 1) / 2);
-            const int64_t blocks = (items + slos_pair_warps() - 1) / slos_pair_warps();
-            const int grid = (int)std::max<int64_t>(
-                1, std::min<int64_t>(blocks, (int64_t)p->sm_count * slos_pair_resident_blocks(p->m)));
-            SLOS_CUDA(slos_launch_fwd_pair(a, t, epi, save, grid, s));
-        } else {
-            const int64_t items = (int64_t)t.items_per_group * NG;
-            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)p->sm_count * fwd_tab_resident_blocks(epi)));
-            SLOS_CUDA(slos_launch_fwd_tab(a, t, epi, save, grid, s));
+        t.nseg = 0;
+        if (epi == EPI_THRESH) {
+            // the final layer in pattern-grouped list order (tables.h)
+            t.w = p->tab.lw;
+            t.lrank = p->tab.lrank;
+            t.lpat = p->tab.lpat;
+            t.lseg = p->tab.lseg;
+            t.nseg = p->tab.nseg;
         }
+        // warp items: one chunk of consecutive states (threshold: one run of
+        // whole patterns) of a group pair
+        const int64_t chunks = epi == EPI_THRESH ? t.nseg : (a.Fk + slos_pair_chunk() - 1) / slos_pair_chunk();
+        const int64_t items = chunks * ((NG + 1) / 2);
+        const int64_t blocks = (items + slos_pair_warps() - 1) / slos_pair_warps();
+        const int grid = (int)std::max<int64_t>(
+            1, std::min<int64_t>(blocks, (int64_t)p->sm_count * slos_pair_resident_blocks(p->m)));
+        SLOS_CUDA(slos_launch_fwd_pair(a, t, epi, save, grid, s));
     } else {
         SLOS_CUDA(launch_fwd(p->m, a, epi, save, bx, s));
     }
@@ -1307,6 +1457,10 @@ slos_status_t slos_forward(slos_plan_t p, const void *U, int batch, slos_output_
     if (batch == 0) return SLOS_OK;
     if (!U || !out) return fail(SLOS_ERR_INVALID_ARG, "slos_forward: NULL U or out");
     const bool save = save_for_backward != 0;
+    {
+        slos_status_t st = check_stream(p, (cudaStream_t)stream, "slos_forward");
+        if (st != SLOS_OK) return st;
+    }
     const Layout Ly = make_layout(p, batch, save);
     if (workspace_bytes < Ly.total || (Ly.total > 0 && !workspace))
         return fail(SLOS_ERR_INVALID_ARG, "slos_forward: workspace too small (" + std::to_string(workspace_bytes) +
@@ -1350,14 +1504,34 @@ slos_status_t slos_forward(slos_plan_t p, const void *U, int batch, slos_output_
         SLOS_CUDA(slos_launch_fused(fa, output == SLOS_OUT_AMPS ? EPI_AMPS : EPI_PROBS, s));
         return SLOS_OK;
     }
-    if (p->det == SLOS_DETECT_THRESHOLD) SLOS_CUDA(cudaMemsetAsync(out, 0, (size_t)batch * p->K * sizeof(float), s));
     SLOS_CUDA(cudaMemsetAsync(ws + Ly.counters, 0, kCounters * sizeof(int), s));
     for (int k = 1; k < n; ++k) {
         slos_status_t st = launch_layer_fwd(p, Ly, ws, Ud, batch, k, EPI_STORE, true, nullptr, s);
         if (st != SLOS_OK) return st;
     }
-    const int epi = p->det == SLOS_DETECT_THRESHOLD ? EPI_THRESH : (output == SLOS_OUT_AMPS ? EPI_AMPS : EPI_PROBS);
-    return launch_layer_fwd(p, Ly, ws, Ud, batch, n, epi, save, out, s);
+    if (p->det != SLOS_DETECT_THRESHOLD)
+        return launch_layer_fwd(p, Ly, ws, Ud, batch, n, output == SLOS_OUT_AMPS ? EPI_AMPS : EPI_PROBS, save, out, s);
+    // threshold: each pattern summed in a fixed order by one warp, during the
+    // final layer's walk (tables) or from the stored a_n (no tables)
+    if (p->tab.enabled) return launch_layer_fwd(p, Ly, ws, Ud, batch, n, EPI_THRESH, save, out, s);
+    slos_status_t st = launch_layer_fwd(p, Ly, ws, Ud, batch, n, EPI_STORE, true, nullptr, s);
+    if (st != SLOS_OK) return st;
+    ThreshArgs ta;
+    memset(&ta, 0, sizeof(ta));
+    ta.an = reinterpret_cast<const float2 *>(ws + Ly.layer[n]);
+    ta.out = reinterpret_cast<float *>(out);
+    ta.Fn = p->F[n];
+    ta.K = p->K;
+    ta.m = p->m;
+    ta.n = n;
+    ta.B = batch;
+    ta.NG = groups_for(batch);
+    ta.jmax = std::min(n, p->m);
+    ta.inv_sfact = p->inv_sfact;
+    ta.status = p->d_status;
+    ProfScope ps("slos_thresh_sum", (8.0 * p->F[n] + 4.0 * p->K) * batch, s);
+    SLOS_CUDA(slos_launch_thresh_sum(ta, s));
+    return SLOS_OK;
 }
 
 slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output_t output, const void *dout,
@@ -1369,6 +1543,10 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
     if (batch == 0) return SLOS_OK;
     if (!U || !dout || !dU) return fail(SLOS_ERR_INVALID_ARG, "slos_backward: NULL pointer");
     if (dout_stride_b < 0) return fail(SLOS_ERR_INVALID_ARG, "slos_backward: negative dout stride");
+    {
+        slos_status_t st = check_stream(p, (cudaStream_t)stream, "slos_backward");
+        if (st != SLOS_OK) return st;
+    }
     const Layout Ly = make_layout(p, batch, true);
     if (workspace_bytes < Ly.total || !workspace)
         return fail(SLOS_ERR_INVALID_ARG, "slos_backward: workspace too small (need the training size)");
@@ -1487,6 +1665,7 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
                 sa.m = m;
                 sa.col = a.col;
                 sa.B = batch;
+                sa.status = p->d_status;
                 SLOS_CUDA(slos_launch_bwd_split(sa, NG, k == n ? seed : SEED_G, st.h, Ly.bwd_blocks[k], s));
             } else if (p->tab.enabled)
                 SLOS_CUDA(launch_bwd_tab(m, a, p->tab.layer[k].ctab, k == n ? seed : SEED_G, Ly.bwd_blocks[k],
@@ -1528,6 +1707,9 @@ slos_status_t slos_sync_status(slos_plan_t p, void *stream) {
     SLOS_CUDA(cudaStreamSynchronize(s));
     if (h[0] == SLOS_ERR_TIMEOUT)
         return fail(SLOS_ERR_TIMEOUT, "a bounded wait between layers ran out (work item " + std::to_string(h[1]) + ")");
+    if (h[0] == kStatusBounds)
+        return fail(SLOS_ERR_INTERNAL, "a device bounds check failed: index " + std::to_string(h[1]) +
+                                           " past its layer (SLOS_DEBUG build)");
     if (h[0] != 0) return fail(SLOS_ERR_INTERNAL, "device status " + std::to_string(h[0]));
     return SLOS_OK;
 }
@@ -1571,8 +1753,8 @@ slos_status_t slos_host_transition_table(int m, int k, int32_t *rowptr, uint32_t
     return SLOS_OK;
 }
 
-slos_status_t slos_host_split_layer(int m, int n, int k, int *h, int64_t *counts, int32_t *fdesc, uint32_t *fhead,
-                                    int32_t *fchunk, int32_t *bdesc, int32_t *bhead, int32_t *bchunk) {
+slos_status_t slos_host_split_layer(int m, int n, int k, int *h, int64_t *counts, int32_t *bdesc, int32_t *bhead,
+                                    int32_t *bchunk) {
     int hh = 0;
     if (m < 2 || m > kMaxModes || n < 2 || n > kMaxPhotons || k < 2 || k > n || !split_eligible(m, n, &hh))
         return fail(SLOS_ERR_UNSUPPORTED, "slos_host_split_layer: no split tables for this shape");
@@ -1580,22 +1762,16 @@ slos_status_t slos_host_split_layer(int m, int n, int k, int *h, int64_t *counts
     split_build_layer_host(m, hh, k, L);
     if (h) *h = hh;
     if (counts) {
-        counts[0] = (int64_t)L.fdesc.size() / 4;
-        counts[1] = (int64_t)L.bdesc.size() / 4;
-        counts[2] = (int64_t)L.fchunk.size();
-        counts[3] = (int64_t)L.bchunk.size();
+        counts[0] = (int64_t)L.bdesc.size() / 4;
+        counts[1] = (int64_t)L.bchunk.size();
     }
-    if (fdesc) memcpy(fdesc, L.fdesc.data(), L.fdesc.size() * 4);
-    if (fhead) memcpy(fhead, L.fhead.data(), L.fhead.size() * 4);
-    if (fchunk) memcpy(fchunk, L.fchunk.data(), L.fchunk.size() * 4);
     if (bdesc) memcpy(bdesc, L.bdesc.data(), L.bdesc.size() * 4);
     if (bhead) memcpy(bhead, L.bhead.data(), L.bhead.size() * 4);
     if (bchunk) memcpy(bchunk, L.bchunk.data(), L.bchunk.size() * 4);
     return SLOS_OK;
 }
 
-slos_status_t slos_host_split_tail(int m, int n, int *h, int32_t *offsets, int64_t *counts, uint32_t *slots,
-                                   uint16_t *ctab) {
+slos_status_t slos_host_split_tail(int m, int n, int *h, int32_t *offsets, int64_t *count, uint16_t *ctab) {
     int hh = 0;
     if (m < 2 || m > kMaxModes || n < 2 || n > kMaxPhotons || !split_eligible(m, n, &hh))
         return fail(SLOS_ERR_UNSUPPORTED, "slos_host_split_tail: no split tables for this shape");
@@ -1603,18 +1779,33 @@ slos_status_t slos_host_split_tail(int m, int n, int *h, int32_t *offsets, int64
     split_build_tail_host(m, hh, n, T);
     if (h) *h = hh;
     if (offsets)
-        for (int r = 0; r <= n; ++r) {
-            offsets[r] = T.soff[r];
-            offsets[(n + 1) + r] = T.tw[r];
-            offsets[2 * (n + 1) + r] = T.coff[r];
-        }
-    if (counts) {
-        counts[0] = (int64_t)T.slots.size();
-        counts[1] = (int64_t)T.ctab.size();
-    }
-    if (slots) memcpy(slots, T.slots.data(), T.slots.size() * 4);
+        for (int r = 0; r <= n; ++r) offsets[r] = T.coff[r];
+    if (count) *count = (int64_t)T.ctab.size();
     if (ctab) memcpy(ctab, T.ctab.data(), T.ctab.size() * 2);
     return SLOS_OK;
+}
+
+slos_status_t slos_host_validate_tables(int m, int k, int kw, const uint32_t *slots, const int32_t *ctab) {
+    if (m < 2 || m > kMaxModes || k < 1 || k > kMaxPhotons || (kw != 4 && kw != 8 && kw != 12) || !slots || !ctab)
+        return fail(SLOS_ERR_INVALID_ARG, "slos_host_validate_tables: bad argument");
+    std::string why;
+    if (!tables_in_range(m, binom_host(m + k - 2, k - 1), binom_host(m + k - 1, k), kw, slots, ctab, false, &why))
+        return fail(SLOS_ERR_INTERNAL, "slos_host_validate_tables: " + why);
+    return SLOS_OK;
+}
+
+slos_status_t slos_inject_fault(slos_inject_t kind, int value) {
+    switch (kind) {
+        case SLOS_INJECT_NONE:
+            g_inject_alloc.store(0);
+            g_inject_stream_dev.store(-1);
+            g_inject_table_budget.store(0);
+            return SLOS_OK;
+        case SLOS_INJECT_ALLOC_FAIL: g_inject_alloc.store(value > 0 ? value : 0); return SLOS_OK;
+        case SLOS_INJECT_STREAM_DEVICE: g_inject_stream_dev.store(value >= 0 ? value : -1); return SLOS_OK;
+        case SLOS_INJECT_TABLE_BUDGET: g_inject_table_budget.store(value != 0 ? 1 : 0); return SLOS_OK;
+        default: return fail(SLOS_ERR_INVALID_ARG, "slos_inject_fault: unknown kind");
+    }
 }
 
 slos_status_t slos_device_index_table(int m, int k, int64_t first, int64_t count, uint8_t *compositions,

@@ -97,6 +97,24 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
+// ---------------------------------------------------------------- debug checks
+// SLOS_DEBUG builds bounds-check the gather indices of the hot-path kernels:
+// an index past its layer is recorded in the plan's status word (code
+// kStatusBounds, then the index) and replaced by 0, a valid row, so the
+// kernel finishes and the host reads the failure with slos_sync_status.
+// Nothing traps.  Release builds compile the checks away.
+constexpr int kStatusBounds = 7;
+#ifdef SLOS_DEBUG
+__device__ __forceinline__ uint32_t debug_index(uint32_t idx, uint32_t limit, int *status) {
+    if (idx < limit) return idx;
+    if (status && atomicCAS(status, 0, kStatusBounds) == 0) atomicExch(status + 1, (int)idx);
+    return 0u;
+}
+#define SLOS_IDX(idx, limit, status) ::slos::debug_index((idx), (limit), (status))
+#else
+#define SLOS_IDX(idx, limit, status) (idx)
+#endif
+
 // ---------------------------------------------------------------- L2 hints
 // L2 eviction-priority policies (createpolicy): parent rows are kept (each is
 // read by up to m children spread over the layer), rows that are only

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/slos.h"
 #include "profile.h"
 
@@ -33,7 +35,10 @@ std::vector<Rec> g_pool;  // reusable event pairs
 std::vector<Agg> g_aggs;
 }  // namespace
 
+// Every launch is also an NVTX range named after it (a no-op unless a
+// profiler that collects NVTX is attached).
 ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) : active_(false), stream_(s) {
+    nvtxRangePushA(name);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_enabled.load(std::memory_order_relaxed)) return;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -57,6 +62,7 @@ ProfScope::ProfScope(const char *name, double bytes, cudaStream_t s) : active_(f
 }
 
 ProfScope::~ProfScope() {
+    nvtxRangePop();
     if (!active_) return;
     std::lock_guard<std::mutex> lk(g_mu);
     if (idx_ < g_recs.size()) cudaEventRecord(g_recs[idx_].b, stream_);

@@ -19,8 +19,10 @@ enum Epilogue : int {
     EPI_STORE = 0,   // intermediate layer: write a_k
     EPI_PROBS = 1,   // final layer: p(t) = |a_n|^2 prod t! / prod s!  -> out [B][K]
     EPI_AMPS = 2,    // final layer: a_n * sqrt(prod t! / prod s!)     -> out [B][K] c64
-    EPI_THRESH = 3,  // final layer: q(pattern(t)) += p(t)                -> out [B][Kq]
+    EPI_THRESH = 3,  // final layer in list order: q(b) = sum of p(t) over the pattern's states -> out [B][Kq]
 };
+// (Threshold plans without tables store a_n with EPI_STORE; threshold.cu sums
+// the patterns.)
 
 // Output-gradient seed of the final backward layer.  The prep step folds the
 // weight w_t = prod t_j! / prod s_i! into it, so that
@@ -41,8 +43,19 @@ struct FwdArgs {
     int64_t Fk, Fprev, K;
     int m, k, col, B, NG, chunk;
     float inv_sfact;
-    int pat_off[kMaxPhotons + 2];  // threshold: first index of patterns with |b| = i
+    int *status;                   // plan status word (bounds checks of SLOS_DEBUG builds)
 };
+
+// Threshold outcomes from a stored a_n (threshold.cu).
+struct ThreshArgs {
+    const float2 *an;              // a_n: [NG][Fn][32]
+    float *out;                    // [B][K]
+    int64_t Fn, K;
+    int m, n, B, NG, jmax;         // jmax = min(n, m): pattern classes |b| = 1..jmax
+    float inv_sfact;
+    int *status;                   // plan status word (bounds checks of SLOS_DEBUG builds)
+};
+cudaError_t slos_launch_thresh_sum(const ThreshArgs &a, cudaStream_t s);
 
 struct BwdArgs {
     const float2 *aprev;  // a_{k-1}: [NG][Fprev][32]; unused when k == 1
@@ -108,14 +121,11 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_kernel(FwdArgs a) {
         const int64_t c0 = ch * a.chunk;
         const int64_t c1 = min(c0 + (int64_t)a.chunk, a.Fk);
         Z z = unrank_mask<MMAX, Z>(c0, m, L);
-        int run_pat = -1;
-        float run_val = 0.f;
         for (int64_t cb = c0; cb < c1; cb += C) {
             Z rem[C];
             int prevbar[C], S[C];
             float2 acc[C];
             float fp[C];
-            uint32_t supp[C];
             bool live[C];
 #pragma unroll
             for (int i = 0; i < C; ++i) {
@@ -126,7 +136,6 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_kernel(FwdArgs a) {
                 S[i] = 0;
                 acc[i] = make_float2(0.f, 0.f);
                 fp[i] = 1.f;
-                supp[i] = 0u;
             }
 #pragma unroll
             for (int i = 0; i < C; ++i)
@@ -147,10 +156,7 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_kernel(FwdArgs a) {
                             const float2 v = (a.k == 1) ? make_float2(1.f, 0.f)
                                                         : __ldg(prevg + (int64_t)(cb + i - S[i]) * kLanes);
                             acc[i] = cfma(u[j], v, acc[i]);
-                            if (EPI != EPI_STORE) {
-                                fp[i] *= c_fact.v[tj];
-                                supp[i] |= 1u << j;
-                            }
+                            if (EPI != EPI_STORE) fp[i] *= c_fact.v[tj];
                         }
                         if (j < m - 1) S[i] += (int)binom_m1(pb, m - 2 - j);
                     }
@@ -166,22 +172,8 @@ __global__ void __launch_bounds__(kThreads) slos_fwd_kernel(FwdArgs a) {
                 } else if (EPI == EPI_AMPS) {
                     float2 *t2 = reinterpret_cast<float2 *>(tile);
                     t2[lane * 33 + (int)(c - c0)] = cscale(acc[i], sqrtf(fp[i] * a.inv_sfact));
-                } else if (EPI == EPI_THRESH) {
-                    const float pr = fp[i] * a.inv_sfact * (acc[i].x * acc[i].x + acc[i].y * acc[i].y);
-                    const int pat = a.pat_off[__popc(supp[i])] + (int)colex_rank(supp[i]);
-                    if (pat != run_pat) {
-                        if (run_pat >= 0 && valid)
-                            atomicAdd(reinterpret_cast<float *>(a.out) + (int64_t)inst * a.K + run_pat, run_val);
-                        run_pat = pat;
-                        run_val = 0.f;
-                    }
-                    run_val += pr;
                 }
             }
-        }
-        if (EPI == EPI_THRESH) {
-            if (run_pat >= 0 && valid)
-                atomicAdd(reinterpret_cast<float *>(a.out) + (int64_t)inst * a.K + run_pat, run_val);
         }
         if (EPI == EPI_PROBS || EPI == EPI_AMPS) {
             __syncwarp();
@@ -694,8 +686,6 @@ cudaError_t launch_bwd_tab_t(const BwdArgs &a, const int32_t *ctab, int seed, in
             case 3: slos_fwd_kernel<MM, EPI_PROBS, true, kCFinal><<<grid, kThreads, sm, s>>>(a); break;              \
             case 4: slos_fwd_kernel<MM, EPI_AMPS, false, kCFinal><<<grid, kThreads, sm, s>>>(a); break;              \
             case 5: slos_fwd_kernel<MM, EPI_AMPS, true, kCFinal><<<grid, kThreads, sm, s>>>(a); break;               \
-            case 6: slos_fwd_kernel<MM, EPI_THRESH, false, kCFinal><<<grid, kThreads, 0, s>>>(a); break;             \
-            case 7: slos_fwd_kernel<MM, EPI_THRESH, true, kCFinal><<<grid, kThreads, 0, s>>>(a); break;              \
             default: return cudaErrorInvalidValue;                                                           \
         }                                                                                                    \
         return cudaGetLastError();                                                                           \

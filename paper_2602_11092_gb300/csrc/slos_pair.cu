@@ -113,12 +113,15 @@ __device__ __forceinline__ void tm_wait_ld4(uint32_t (&r)[N][4]) {
 // warp-uniform; padding slots (mode 24) read no parent row and multiply 0.
 template <int N, int KW>
 __device__ __forceinline__ void pair_sum(const uint32_t (&e)[KW], const float4 *prevh, uint32_t tq, uint32_t cmask,
-                                         uint64_t keep, float2 &acc0, float2 &acc1) {
+                                         uint64_t keep, uint32_t fprev, int *status, float2 &acc0, float2 &acc1) {
     float4 v[N];
     uint32_t u[N][4];
+    (void)fprev;
+    (void)status;
 #pragma unroll
     for (int q = 0; q < N; ++q)
-        v[q] = e[q] != kSlotEmpty ? ldg4_policy(prevh + ((e[q] >> 5) << 4), keep) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[q] = e[q] != kSlotEmpty ? ldg4_policy(prevh + (SLOS_IDX(e[q] >> 5, fprev, status) << 4), keep)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < N; ++q) tm_ld4(tq + 4u * (e[q] & cmask), u[q]);
     tm_wait_ld4<N>(u);
@@ -129,6 +132,16 @@ __device__ __forceinline__ void pair_sum(const uint32_t (&e)[KW], const float4 *
         acc0 = cfma(make_float2(__uint_as_float(u[q][0]), __uint_as_float(u[q][1])), make_float2(v[q].x, v[q].y), acc0);
         acc1 = cfma(make_float2(__uint_as_float(u[q][2]), __uint_as_float(u[q][3])), make_float2(v[q].z, v[q].w), acc1);
     }
+}
+
+// Threshold: pattern P's probability for the lane's two instances (one
+// plain store each: the pattern's states were all summed by this warp).
+__device__ __forceinline__ void pair_thresh_store(const FwdArgs &a, bool hvalid, int ginst, int P, float q0, float q1,
+                                                  uint64_t pol) {
+    if (P < 0 || !hvalid) return;
+    float *o = reinterpret_cast<float *>(a.out) + P;
+    if (ginst < a.B) stg_policy(o + (int64_t)ginst * a.K, q0, pol);
+    if (ginst + 1 < a.B) stg_policy(o + (int64_t)(ginst + 1) * a.K, q1, pol);
 }
 
 // Work order: each warp takes 32-state chunks of one group pair from a queue
@@ -163,7 +176,8 @@ __global__ void __launch_bounds__(kPairThreads, kPairMinBlocks) slos_fwd_pair_ke
     constexpr int TS = pair_tile_states(EPI);
     constexpr int TW = 64 * (TS + 1) + 1;  // tile words per warp
     float *tile = reinterpret_cast<float *>(smem_raw) + warp * (TW * (EPI == EPI_AMPS ? 2 : 1));
-    const int nchunks = (int)((a.Fk + kPairChunk - 1) / kPairChunk);
+    // items per pair: chunks of kPairChunk states, or (threshold) runs of whole patterns
+    const int nchunks = EPI == EPI_THRESH ? t.nseg : (int)((a.Fk + kPairChunk - 1) / kPairChunk);
     const int npairs = (a.NG + 1) / 2;
     const int total = nchunks * npairs;
     const bool first_layer = a.k == 1;
@@ -210,107 +224,118 @@ __global__ void __launch_bounds__(kPairThreads, kPairMinBlocks) slos_fwd_pair_ke
             nexth = reinterpret_cast<float4 *>(a.next + (size_t)gl * (size_t)a.Fk * kLanes) + sl;
         }
         const int ch = item - pair * nchunks;
-        const uint32_t c0 = (uint32_t)ch * (uint32_t)kPairChunk;
-        const int nc = (int)min((int64_t)kPairChunk, a.Fk - (int64_t)c0);
-        float wl = 0.f;
-        int patl = 0;
-        // slot row of state c0 + lane (lanes < nc), handed out by shuffles below
-        uint32_t sr[KW];
-#pragma unroll
-        for (int q = 0; q < KW; ++q) sr[q] = kSlotEmpty;
-        if (lane < nc) {
-#pragma unroll
-            for (int q4 = 0; q4 < KW / 4; ++q4) {
-                const uint4 w4 = __ldg(slots + (c0 + lane) * (KW / 4) + q4);
-                sr[4 * q4] = w4.x;
-                sr[4 * q4 + 1] = w4.y;
-                sr[4 * q4 + 2] = w4.z;
-                sr[4 * q4 + 3] = w4.w;
-            }
-            if (EPI != EPI_STORE) {
-                wl = __ldg(t.w + c0 + lane);
-                if (EPI == EPI_THRESH) patl = __ldg(t.pat + c0 + lane);
-            }
+        int lo, hi;
+        if (EPI == EPI_THRESH) {
+            lo = __ldg(t.lseg + ch);
+            hi = __ldg(t.lseg + ch + 1);
+        } else {
+            lo = ch * kPairChunk;
+            hi = (int)min((int64_t)(lo + kPairChunk), a.Fk);
         }
+        // threshold: the sum of the pattern being walked, for the lane's two instances
         int run_pat = -1;
         float run0 = 0.f, run1 = 0.f;
-        for (int ci = 0; ci < nc; ++ci) {
-            const uint32_t c = c0 + (uint32_t)ci;
-            uint32_t e[KW];
+        // one chunk per item, or (threshold) the item's chunks in turn
+        for (int cs = lo;;) {
+            const uint32_t c0 = (uint32_t)cs;
+            const int nc = min(kPairChunk, hi - cs);
+            float wl = 0.f;
+            int patl = 0, rkl = 0;
+            // slot row of state c0 + lane (lanes < nc), handed out by shuffles below
+            uint32_t sr[KW];
 #pragma unroll
-            for (int q = 0; q < KW; ++q) e[q] = __shfl_sync(0xffffffffu, sr[q], ci);
-            float2 acc0, acc1;
-            if (first_layer) {
-                uint32_t u[4][4];
-                tm_ld4(tq + 4u * (e[0] & cmask), u[0]);  // one photon: a_1(e_j) = U[j, c_1]
+            for (int q = 0; q < KW; ++q) sr[q] = kSlotEmpty;
+            if (lane < nc) {
 #pragma unroll
-                for (int q = 1; q < 4; ++q) u[q][0] = u[q][1] = u[q][2] = u[q][3] = 0u;
-                tm_wait_ld4<4>(u);
-                acc0 = make_float2(__uint_as_float(u[0][0]), __uint_as_float(u[0][1]));
-                acc1 = make_float2(__uint_as_float(u[0][2]), __uint_as_float(u[0][3]));
-            } else if (kSkip && e[4] == kSlotEmpty) {
-                pair_sum<4>(e, prevh, tq, cmask, keep, acc0, acc1);  // at most 4 occupied modes
-            } else if (kSkip && e[6] == kSlotEmpty) {
-                pair_sum<6>(e, prevh, tq, cmask, keep, acc0, acc1);
-            } else {
-                pair_sum<KW>(e, prevh, tq, cmask, keep, acc0, acc1);
+                for (int q4 = 0; q4 < KW / 4; ++q4) {
+                    const uint4 w4 = __ldg(slots + (c0 + lane) * (KW / 4) + q4);
+                    sr[4 * q4] = w4.x;
+                    sr[4 * q4 + 1] = w4.y;
+                    sr[4 * q4 + 2] = w4.z;
+                    sr[4 * q4 + 3] = w4.w;
+                }
+                if (EPI != EPI_STORE) wl = __ldg(t.w + c0 + lane);
+                if (EPI == EPI_THRESH) {
+                    patl = __ldg(t.lpat + c0 + lane);
+                    if (SAVE) rkl = __ldg(t.lrank + c0 + lane);
+                }
             }
-            if (hvalid) {
-                const float4 v = make_float4(acc0.x, acc0.y, acc1.x, acc1.y);
-                if (EPI == EPI_STORE) nexth[c << 4] = v;
-                else if (SAVE) stg4_policy(nexth + (c << 4), v, stream);
-            }
-            if (EPI != EPI_STORE) {
-                const float w = __shfl_sync(0xffffffffu, wl, ci);
-                const int r0 = (32 * h + 2 * sl) * (TS + 1) + h;  // tile word of instance 2 sl, state 0
-                if (EPI == EPI_PROBS) {
-                    tile[r0 + (ci & (TS - 1))] = w * (acc0.x * acc0.x + acc0.y * acc0.y);
-                    tile[r0 + (TS + 1) + (ci & (TS - 1))] = w * (acc1.x * acc1.x + acc1.y * acc1.y);
-                } else if (EPI == EPI_AMPS) {
-                    const float sw = sqrtf(w);
-                    reinterpret_cast<float2 *>(tile)[r0 + (ci & (TS - 1))] = cscale(acc0, sw);
-                    reinterpret_cast<float2 *>(tile)[r0 + (TS + 1) + (ci & (TS - 1))] = cscale(acc1, sw);
-                } else if (EPI == EPI_THRESH) {
-                    const int pat = __shfl_sync(0xffffffffu, patl, ci);
-                    if (pat != run_pat) {
-                        if (run_pat >= 0 && hvalid) {
-                            float *o = reinterpret_cast<float *>(a.out);
-                            if (ginst < a.B) atomicAdd(o + (int64_t)ginst * a.K + run_pat, run0);
-                            if (ginst + 1 < a.B) atomicAdd(o + (int64_t)(ginst + 1) * a.K + run_pat, run1);
+            for (int ci = 0; ci < nc; ++ci) {
+                const uint32_t c = c0 + (uint32_t)ci;
+                uint32_t e[KW];
+#pragma unroll
+                for (int q = 0; q < KW; ++q) e[q] = __shfl_sync(0xffffffffu, sr[q], ci);
+                float2 acc0, acc1;
+                if (first_layer) {
+                    uint32_t u[4][4];
+                    tm_ld4(tq + 4u * (e[0] & cmask), u[0]);  // one photon: a_1(e_j) = U[j, c_1]
+#pragma unroll
+                    for (int q = 1; q < 4; ++q) u[q][0] = u[q][1] = u[q][2] = u[q][3] = 0u;
+                    tm_wait_ld4<4>(u);
+                    acc0 = make_float2(__uint_as_float(u[0][0]), __uint_as_float(u[0][1]));
+                    acc1 = make_float2(__uint_as_float(u[0][2]), __uint_as_float(u[0][3]));
+                } else if (kSkip && e[4] == kSlotEmpty) {
+                    // at most 4 occupied modes
+                    pair_sum<4>(e, prevh, tq, cmask, keep, (uint32_t)a.Fprev, a.status, acc0, acc1);
+                } else if (kSkip && e[6] == kSlotEmpty) {
+                    pair_sum<6>(e, prevh, tq, cmask, keep, (uint32_t)a.Fprev, a.status, acc0, acc1);
+                } else {
+                    pair_sum<KW>(e, prevh, tq, cmask, keep, (uint32_t)a.Fprev, a.status, acc0, acc1);
+                }
+                // a_n kept for the backward: at the state's Fock rank
+                const uint32_t cr = (EPI == EPI_THRESH && SAVE) ? (uint32_t)__shfl_sync(0xffffffffu, rkl, ci) : c;
+                if (hvalid) {
+                    const float4 v = make_float4(acc0.x, acc0.y, acc1.x, acc1.y);
+                    if (EPI == EPI_STORE) nexth[c << 4] = v;
+                    else if (SAVE) stg4_policy(nexth + (cr << 4), v, stream);
+                }
+                if (EPI != EPI_STORE) {
+                    const float w = __shfl_sync(0xffffffffu, wl, ci);
+                    const int r0 = (32 * h + 2 * sl) * (TS + 1) + h;  // tile word of instance 2 sl, state 0
+                    if (EPI == EPI_PROBS) {
+                        tile[r0 + (ci & (TS - 1))] = w * (acc0.x * acc0.x + acc0.y * acc0.y);
+                        tile[r0 + (TS + 1) + (ci & (TS - 1))] = w * (acc1.x * acc1.x + acc1.y * acc1.y);
+                    } else if (EPI == EPI_AMPS) {
+                        const float sw = sqrtf(w);
+                        reinterpret_cast<float2 *>(tile)[r0 + (ci & (TS - 1))] = cscale(acc0, sw);
+                        reinterpret_cast<float2 *>(tile)[r0 + (TS + 1) + (ci & (TS - 1))] = cscale(acc1, sw);
+                    } else if (EPI == EPI_THRESH) {
+                        // the item holds whole patterns: each sum is complete when the pattern changes
+                        const int pat = __shfl_sync(0xffffffffu, patl, ci);
+                        if (pat != run_pat) {
+                            pair_thresh_store(a, hvalid, ginst, run_pat, run0, run1, stream);
+                            run_pat = pat;
+                            run0 = run1 = 0.f;
                         }
-                        run_pat = pat;
-                        run0 = run1 = 0.f;
-                    }
-                    run0 += w * (acc0.x * acc0.x + acc0.y * acc0.y);
-                    run1 += w * (acc1.x * acc1.x + acc1.y * acc1.y);
-                }
-            }
-            // a full tile (or the chunk's last states) goes out: TS consecutive
-            // outputs of 32 / TS instances per pass
-            if ((EPI == EPI_PROBS || EPI == EPI_AMPS) && ((ci & (TS - 1)) == TS - 1 || ci == nc - 1)) {
-                __syncwarp();
-                const int cb = ci & ~(TS - 1), cnt = ci - cb + 1;
-                const int il = lane & (TS - 1);
-                for (int i = lane / TS; i < 64; i += 32 / TS) {
-                    const int b = 2 * pair * kLanes + i;
-                    if (b < a.B && il < cnt) {
-                        const int64_t o = (int64_t)b * a.K + c0 + cb + il;
-                        const int wi = i * (TS + 1) + (i >> 5) + il;
-                        if (EPI == EPI_PROBS)
-                            stg_policy(reinterpret_cast<float *>(a.out) + o, tile[wi], stream);
-                        else
-                            stg_policy(reinterpret_cast<float2 *>(a.out) + o, reinterpret_cast<const float2 *>(tile)[wi],
-                                       stream);
+                        run0 += w * (acc0.x * acc0.x + acc0.y * acc0.y);
+                        run1 += w * (acc1.x * acc1.x + acc1.y * acc1.y);
                     }
                 }
-                __syncwarp();
+                // a full tile (or the chunk's last states) goes out: TS consecutive
+                // outputs of 32 / TS instances per pass
+                if ((EPI == EPI_PROBS || EPI == EPI_AMPS) && ((ci & (TS - 1)) == TS - 1 || ci == nc - 1)) {
+                    __syncwarp();
+                    const int cb = ci & ~(TS - 1), cnt = ci - cb + 1;
+                    const int il = lane & (TS - 1);
+                    for (int i = lane / TS; i < 64; i += 32 / TS) {
+                        const int b = 2 * pair * kLanes + i;
+                        if (b < a.B && il < cnt) {
+                            const int64_t o = (int64_t)b * a.K + c0 + cb + il;
+                            const int wi = i * (TS + 1) + (i >> 5) + il;
+                            if (EPI == EPI_PROBS)
+                                stg_policy(reinterpret_cast<float *>(a.out) + o, tile[wi], stream);
+                            else
+                                stg_policy(reinterpret_cast<float2 *>(a.out) + o,
+                                           reinterpret_cast<const float2 *>(tile)[wi], stream);
+                        }
+                    }
+                    __syncwarp();
+                }
             }
+            cs += kPairChunk;
+            if (EPI != EPI_THRESH || cs >= hi) break;
         }
-        if (EPI == EPI_THRESH && run_pat >= 0 && hvalid) {
-            float *o = reinterpret_cast<float *>(a.out);
-            if (ginst < a.B) atomicAdd(o + (int64_t)ginst * a.K + run_pat, run0);
-            if (ginst + 1 < a.B) atomicAdd(o + (int64_t)(ginst + 1) * a.K + run_pat, run1);
-        }
+        if (EPI == EPI_THRESH) pair_thresh_store(a, hvalid, ginst, run_pat, run0, run1, stream);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

@@ -1,15 +1,9 @@
 // SLOS layers on the head/tail split of the Fock lattice (split.h).
 //
-// Forward, layer k:  a_k(t) = sum_{j: t_j > 0} U[j, c_k] a_{k-1}(t - e_j)
-// (Sec. II-A.2/II-A.3).  Each warp owns a group of 32 instances (lane =
-// instance, layout [F_k][32] complex64, one coalesced 256-byte row per state)
-// and walks a chunk of 32 consecutive states.  Within a head block the
-// head-mode parents of state c are rows c + (parent block base - block base),
-// and their U factors are loaded into registers once per block; the tail
-// parents come from the block's tail slot row (one 16- or 32-byte broadcast
-// load per state) and take U from shared memory.  A per-block switch on the
-// number of occupied head modes selects a body whose head loop is fully
-// unrolled, so the head slots need neither padding nor per-state decoding.
+// The forward layers do not use the split: a head-block walk that takes
+// the head parents at fixed offsets measured slower on GB300 than the
+// two-group slot-table walk of slos_pair.cu, whose slot rows are shared by
+// both instance groups of a warp.
 //
 // Backward, layer k:  for every parent t' of layer k-1
 //      G_{k-1}(t') = sum_j conj(U[j, c_k]) G_k(t' + e_j)
@@ -67,49 +61,6 @@ bool split_eligible(int m, int n, int *h_out) {
 void split_build_layer_host(int m, int h, int k, SplitLayerHost &out) {
     const int mL = m - h;
     std::vector<int> full(m, 0);
-    // forward: head compositions of at most k photons, as (h+1)-compositions
-    // of k whose last part is the tail photon count
-    {
-        out.fdesc.clear();
-        out.fhead.clear();
-        std::vector<int> tc(h + 1, 0);
-        tc[0] = k;
-        do {
-            const int rho = tc[h];
-            std::fill(full.begin(), full.end(), 0);
-            for (int j = 0; j < h; ++j) full[j] = tc[j];
-            full[h] = rho;
-            const int64_t base = host_rank(m, full.data());
-            const int64_t size = binom_host(rho + mL - 1, mL - 1);
-            int64_t zbase = 0;
-            if (rho >= 1) {
-                full[h] = rho - 1;
-                zbase = host_rank(m, full.data());
-                full[h] = rho;
-            }
-            uint32_t heads[kSplitMaxHead] = {0};
-            int qh = 0;
-            for (int j = 0; j < h; ++j) {
-                if (tc[j] == 0) continue;
-                full[j] -= 1;
-                heads[qh++] = ((uint32_t)host_rank(m, full.data()) << 5) | (uint32_t)j;
-                full[j] += 1;
-            }
-            out.fdesc.push_back((int32_t)base);
-            out.fdesc.push_back((int32_t)size);
-            out.fdesc.push_back((int32_t)zbase);
-            out.fdesc.push_back(rho | (qh << 8));
-            for (int q = 0; q < kSplitMaxHead; ++q) out.fhead.push_back(heads[q]);
-        } while (next_comp_desc(tc));
-        const int64_t Fk = binom_host(m + k - 1, k);
-        out.fchunk.assign((size_t)((Fk + kSplitRun - 1) / kSplitRun), 0);
-        const size_t nb = out.fdesc.size() / 4;
-        for (size_t b = 0; b < nb; ++b) {
-            const int64_t lo = out.fdesc[4 * b], hi = lo + out.fdesc[4 * b + 1];
-            for (int64_t c0 = (lo + kSplitRun - 1) / kSplitRun * kSplitRun; c0 < hi; c0 += kSplitRun)
-                out.fchunk[(size_t)(c0 / kSplitRun)] = (int32_t)b;
-        }
-    }
     // backward: head compositions of at most k-1 photons (the parents)
     {
         out.bdesc.clear();
@@ -153,218 +104,25 @@ void split_build_layer_host(int m, int h, int k, SplitLayerHost &out) {
 
 void split_build_tail_host(int m, int h, int n, SplitTailHost &out) {
     const int mL = m - h;
-    out.slots.clear();
     out.ctab.clear();
     std::vector<int> t(mL, 0);
     for (int rho = 0; rho <= n; ++rho) {
-        const int tw = rho == 0 ? 0 : ((std::min(mL, rho) + 3) & ~3);
-        out.tw[rho] = tw;
-        out.soff[rho] = (int)out.slots.size();
         out.coff[rho] = (int)(out.ctab.size() / 8);
+        if (rho == n) break;  // the last layer's states have no children
         std::fill(t.begin(), t.end(), 0);
         t[0] = rho;
         do {
-            if (tw > 0) {
-                int q = 0;
-                for (int j = 0; j < mL; ++j) {
-                    if (t[j] == 0) continue;
-                    t[j] -= 1;
-                    out.slots.push_back(((uint32_t)host_rank(mL, t.data()) << 5) | (uint32_t)(h + j));
+            for (int j = 0; j < 8; ++j) {
+                uint16_t v = 0;
+                if (j < mL) {
                     t[j] += 1;
-                    ++q;
+                    v = (uint16_t)host_rank(mL, t.data());
+                    t[j] -= 1;
                 }
-                for (; q < tw; ++q) out.slots.push_back(kSlotEmpty);
-            }
-            if (rho < n) {
-                for (int j = 0; j < 8; ++j) {
-                    uint16_t v = 0;
-                    if (j < mL) {
-                        t[j] += 1;
-                        v = (uint16_t)host_rank(mL, t.data());
-                        t[j] -= 1;
-                    }
-                    out.ctab.push_back(v);
-                }
+                out.ctab.push_back(v);
             }
         } while (mL > 1 && next_comp_desc(t));
     }
-}
-
-// ============================================================ forward kernel
-size_t split_fwd_smem_bytes(int epi) {
-    const size_t cells = (size_t)32 * (kSplitTile + 1);
-    return epi == EPI_PROBS ? cells * sizeof(float) : (epi == EPI_AMPS ? cells * sizeof(float2) : 0);
-}
-
-struct SplitFwdCtx {
-    const float2 *prevg;  // a_{k-1} of the warp's group, lane offset included
-    float2 *nextg;        // a_k of the group (or null)
-    const float2 *usl;    // this lane's column of the staged U rows
-    float *tile;          // the CTA's [32 instances][kSplitTile + 1] output tile
-    int t0;               // first state of the CTA tile
-    int c0;               // first state of the warp's run
-    float wl;             // final weight of state c0 + lane (lanes < kSplitRun)
-    int patl;             // threshold pattern of state c0 + lane
-    int run_pat;
-    float run_val;
-    int64_t orow;         // this lane's output row offset (inst * K)
-    bool valid;
-};
-
-// Sum over the first N tail slots: parent rows issued together, then the
-// products with the staged U rows.
-template <int N, int KW>
-__device__ __forceinline__ float2 split_tail_sum(const uint32_t (&e)[KW], const float2 *lprev, const float2 *usl,
-                                                 float2 acc) {
-    float2 v[N];
-#pragma unroll
-    for (int q = 0; q < N; ++q) v[q] = __ldg(lprev + ((e[q] >> 5) << 5));
-#pragma unroll
-    for (int q = 0; q < N; ++q) acc = cfma(usl[(e[q] & 31u) * 32u], v[q], acc);
-    return acc;
-}
-
-template <int EPI, bool SAVE>
-__device__ __forceinline__ void split_emit(const SplitFwdArgs &a, SplitFwdCtx &x, int c, float2 acc) {
-    if (SAVE || EPI == EPI_STORE) x.nextg[(uint32_t)c << 5] = acc;
-    if (EPI == EPI_STORE) return;
-    const int lane = threadIdx.x & 31;
-    const int ci = c - x.t0;
-    const float w = __shfl_sync(0xffffffffu, x.wl, c - x.c0);
-    if (EPI == EPI_PROBS) {
-        x.tile[lane * (kSplitTile + 1) + ci] = w * (acc.x * acc.x + acc.y * acc.y);
-    } else if (EPI == EPI_AMPS) {
-        reinterpret_cast<float2 *>(x.tile)[lane * (kSplitTile + 1) + ci] = cscale(acc, sqrtf(w));
-    } else if (EPI == EPI_THRESH) {
-        const int pat = __shfl_sync(0xffffffffu, x.patl, c - x.c0);
-        const float pr = w * (acc.x * acc.x + acc.y * acc.y);
-        if (pat != x.run_pat) {
-            if (x.run_pat >= 0 && x.valid) atomicAdd(reinterpret_cast<float *>(a.out) + x.orow + x.run_pat, x.run_val);
-            x.run_pat = pat;
-            x.run_val = 0.f;
-        }
-        x.run_val += pr;
-    }
-}
-
-// States [c, stop) of head block b (descriptor d) with QH occupied head modes.
-template <int QH, int EPI, bool SAVE>
-__device__ __forceinline__ void split_walk(const SplitFwdArgs &a, SplitFwdCtx &x, const int4 d, int b, int c,
-                                           int stop) {
-    int hoff[QH > 0 ? QH : 1];
-    float2 uh[QH > 0 ? QH : 1];
-#pragma unroll
-    for (int q = 0; q < QH; ++q) {
-        const uint32_t e = __ldg(a.head + (size_t)b * kSplitMaxHead + q);
-        hoff[q] = (int)(e >> 5) - d.x;  // head parent of state c: row c + hoff[q]
-        uh[q] = x.usl[(e & 31u) * 32u];
-    }
-    const int rho = d.w & 255;
-    const int W = a.tw[rho];
-    const uint4 *trow = reinterpret_cast<const uint4 *>(a.tslots + a.soff[rho] + (size_t)(c - d.x) * W);
-    const float2 *lprev = x.prevg + ((uint32_t)d.z << 5);
-    for (; c < stop; ++c) {
-        float2 v[QH > 0 ? QH : 1];
-#pragma unroll
-        for (int q = 0; q < QH; ++q) v[q] = __ldg(x.prevg + ((uint32_t)(c + hoff[q]) << 5));
-        float2 acc = make_float2(0.f, 0.f);
-        if (W == 4) {
-            const uint4 r = __ldg(trow);
-            const uint32_t e[4] = {r.x, r.y, r.z, r.w};
-            acc = split_tail_sum<4, 4>(e, lprev, x.usl, acc);
-            trow += 1;
-        } else if (W == 8) {
-            const uint4 r0 = __ldg(trow), r1 = __ldg(trow + 1);
-            const uint32_t e[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-            // the state is the warp's (lane = instance): a uniform branch skips padding
-            if (e[4] == kSlotEmpty) acc = split_tail_sum<4, 8>(e, lprev, x.usl, acc);
-            else if (e[6] == kSlotEmpty) acc = split_tail_sum<6, 8>(e, lprev, x.usl, acc);
-            else acc = split_tail_sum<8, 8>(e, lprev, x.usl, acc);
-            trow += 2;
-        }
-#pragma unroll
-        for (int q = 0; q < QH; ++q) acc = cfma(uh[q], v[q], acc);
-        split_emit<EPI, SAVE>(a, x, c, acc);
-    }
-}
-
-template <int EPI, bool SAVE>
-__global__ void __launch_bounds__(kSplitFwdWarps * 32, kSplitFwdMinBlocks) slos_fwd_split_kernel(SplitFwdArgs a) {
-    __shared__ float2 us[kMaxModes + 1][32];
-    extern __shared__ float4 smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int grp = blockIdx.y;
-    const int inst = grp * kLanes + lane;
-    const bool valid = inst < a.B;
-    for (int j = warp; j < a.m; j += kSplitFwdWarps)
-        us[j][lane] = valid ? a.U[((int64_t)inst * a.m + j) * a.m + a.col] : make_float2(0.f, 0.f);
-    if (warp == 0) us[kMaxModes][lane] = make_float2(0.f, 0.f);
-    __syncthreads();
-
-    SplitFwdCtx x;
-    x.prevg = a.prev + (size_t)grp * (size_t)a.Fprev * kLanes + lane;
-    x.nextg = (SAVE || EPI == EPI_STORE) ? a.next + (size_t)grp * (size_t)a.Fk * kLanes + lane : nullptr;
-    x.usl = &us[0][lane];
-    x.tile = reinterpret_cast<float *>(smem_raw);
-    x.valid = valid;
-    x.orow = (int64_t)inst * a.K;
-    x.run_pat = -1;
-    x.run_val = 0.f;
-    x.wl = 0.f;
-    x.patl = 0;
-    // the CTA walks tiles of kSplitTile consecutive states, warp w the run of
-    // kSplitRun states at w * kSplitRun, so the states in flight across the
-    // grid stay a compact rank window (their parents share L2 lines)
-    for (int tl = blockIdx.x; tl < a.ntiles; tl += gridDim.x) {
-        const int t0 = tl * kSplitTile;
-        const int c0 = t0 + warp * kSplitRun;
-        const int cend = min(c0 + kSplitRun, a.Fk);
-        x.t0 = t0;
-        x.c0 = c0;
-        if (c0 < cend) {
-            if (EPI != EPI_STORE) {
-                x.wl = c0 + lane < cend ? __ldg(a.w + c0 + lane) : 0.f;
-                if (EPI == EPI_THRESH) x.patl = c0 + lane < cend ? __ldg(a.pat + c0 + lane) : 0;
-            }
-            int b = __ldg(a.chunk + c0 / kSplitRun);
-            for (int c = c0; c < cend; ++b) {
-                const int4 d = __ldg(reinterpret_cast<const int4 *>(a.desc) + b);
-                const int stop = min(d.x + d.y, cend);
-                switch ((d.w >> 8) & 15) {
-                    case 0: split_walk<0, EPI, SAVE>(a, x, d, b, c, stop); break;
-                    case 1: split_walk<1, EPI, SAVE>(a, x, d, b, c, stop); break;
-                    case 2: split_walk<2, EPI, SAVE>(a, x, d, b, c, stop); break;
-                    case 3: split_walk<3, EPI, SAVE>(a, x, d, b, c, stop); break;
-                    case 4: split_walk<4, EPI, SAVE>(a, x, d, b, c, stop); break;
-                    case 5: split_walk<5, EPI, SAVE>(a, x, d, b, c, stop); break;
-                    case 6: split_walk<6, EPI, SAVE>(a, x, d, b, c, stop); break;
-                    case 7: split_walk<7, EPI, SAVE>(a, x, d, b, c, stop); break;
-                    default: split_walk<8, EPI, SAVE>(a, x, d, b, c, stop); break;
-                }
-                c = stop;
-            }
-        }
-        if (EPI == EPI_PROBS || EPI == EPI_AMPS) {
-            // the tile: instance i's kSplitTile consecutive outputs in one 128/256-byte store
-            __syncthreads();
-            const int nc = min(kSplitTile, a.Fk - t0);
-            for (int i = warp; i < kLanes; i += kSplitFwdWarps) {
-                const int ii = grp * kLanes + i;
-                if (ii < a.B && lane < nc) {
-                    const int64_t o = (int64_t)ii * a.K + t0 + lane;
-                    if (EPI == EPI_PROBS)
-                        reinterpret_cast<float *>(a.out)[o] = x.tile[i * (kSplitTile + 1) + lane];
-                    else
-                        reinterpret_cast<float2 *>(a.out)[o] =
-                            reinterpret_cast<const float2 *>(x.tile)[i * (kSplitTile + 1) + lane];
-                }
-            }
-            __syncthreads();
-        }
-    }
-    if (EPI == EPI_THRESH && x.run_pat >= 0 && valid)
-        atomicAdd(reinterpret_cast<float *>(a.out) + x.orow + x.run_pat, x.run_val);
 }
 
 // ============================================================ backward kernel
@@ -396,7 +154,11 @@ __device__ __forceinline__ uint32_t crow16(const uint4 &r) {
 }
 
 template <int SEED>
-__device__ __forceinline__ float2 split_child(const float2 *srcb, const float *seedb, uint32_t x) {
+__device__ __forceinline__ float2 split_child(const float2 *srcb, const float *seedb, uint32_t x, uint32_t fk,
+                                              int *status) {
+    (void)fk;
+    (void)status;
+    x = SLOS_IDX(x, fk, status);
     float2 g = __ldg(srcb + (x << 5));
     if (SEED == SEED_T) g = cscale(g, __ldg(seedb + (x << 5)));
     if (SEED == SEED_BCAST) g = cscale(g, __ldg(seedb + x));
@@ -504,22 +266,22 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
                 float2 g[4];
                 // head modes 0..3, 4..H-1
 #pragma unroll
-                for (int j = 0; j < 4; ++j) g[j] = split_child<SEED>(srcb, seedb, (uint32_t)(c + hoff[j]));
+                for (int j = 0; j < 4; ++j) g[j] = split_child<SEED>(srcb, seedb, (uint32_t)(c + hoff[j]), (uint32_t)a.Fk, a.status);
                 split_bwd_batch<4>(tq, 0, 32, g, av, gacc);
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    g[j] = (4 + j < H) ? split_child<SEED>(srcb, seedb, (uint32_t)(c + hoff[4 + j])) : make_float2(0.f, 0.f);
+                    g[j] = (4 + j < H) ? split_child<SEED>(srcb, seedb, (uint32_t)(c + hoff[4 + j]), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
                 split_bwd_batch<H - 4>(tq, 8, 40, g, av, gacc);
                 // tail modes 0..3, 4..7 (positions from the tail child row)
-                g[0] = mL > 0 ? split_child<SEED>(srcb, seedb, lc + crow16<0>(cr)) : make_float2(0.f, 0.f);
-                g[1] = mL > 1 ? split_child<SEED>(srcb, seedb, lc + crow16<1>(cr)) : make_float2(0.f, 0.f);
-                g[2] = mL > 2 ? split_child<SEED>(srcb, seedb, lc + crow16<2>(cr)) : make_float2(0.f, 0.f);
-                g[3] = mL > 3 ? split_child<SEED>(srcb, seedb, lc + crow16<3>(cr)) : make_float2(0.f, 0.f);
+                g[0] = mL > 0 ? split_child<SEED>(srcb, seedb, lc + crow16<0>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
+                g[1] = mL > 1 ? split_child<SEED>(srcb, seedb, lc + crow16<1>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
+                g[2] = mL > 2 ? split_child<SEED>(srcb, seedb, lc + crow16<2>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
+                g[3] = mL > 3 ? split_child<SEED>(srcb, seedb, lc + crow16<3>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
                 split_bwd_batch<4>(tq, 16, 48, g, av, gacc);
-                g[0] = mL > 4 ? split_child<SEED>(srcb, seedb, lc + crow16<4>(cr)) : make_float2(0.f, 0.f);
-                g[1] = mL > 5 ? split_child<SEED>(srcb, seedb, lc + crow16<5>(cr)) : make_float2(0.f, 0.f);
-                g[2] = mL > 6 ? split_child<SEED>(srcb, seedb, lc + crow16<6>(cr)) : make_float2(0.f, 0.f);
-                g[3] = mL > 7 ? split_child<SEED>(srcb, seedb, lc + crow16<7>(cr)) : make_float2(0.f, 0.f);
+                g[0] = mL > 4 ? split_child<SEED>(srcb, seedb, lc + crow16<4>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
+                g[1] = mL > 5 ? split_child<SEED>(srcb, seedb, lc + crow16<5>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
+                g[2] = mL > 6 ? split_child<SEED>(srcb, seedb, lc + crow16<6>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
+                g[3] = mL > 7 ? split_child<SEED>(srcb, seedb, lc + crow16<7>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
                 split_bwd_batch<4>(tq, 24, 56, g, av, gacc);
                 Gprevb[(uint32_t)c << 5] = gacc;
             }
@@ -561,36 +323,6 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
 }
 
 // ============================================================ launchers
-cudaError_t slos_split_init() {
-    cudaError_t e;
-    const int sp = (int)split_fwd_smem_bytes(EPI_PROBS), sa = (int)split_fwd_smem_bytes(EPI_AMPS);
-    if ((e = cudaFuncSetAttribute(slos_fwd_split_kernel<EPI_PROBS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sp)))
-        return e;
-    if ((e = cudaFuncSetAttribute(slos_fwd_split_kernel<EPI_PROBS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sp)))
-        return e;
-    if ((e = cudaFuncSetAttribute(slos_fwd_split_kernel<EPI_AMPS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa)))
-        return e;
-    return cudaFuncSetAttribute(slos_fwd_split_kernel<EPI_AMPS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sa);
-}
-
-cudaError_t slos_launch_fwd_split(const SplitFwdArgs &a, int NG, int epi, bool save, int blocks_x, cudaStream_t s) {
-    const dim3 grid(blocks_x, NG);
-    const int th = kSplitFwdWarps * 32;
-    const size_t sm = split_fwd_smem_bytes(epi);
-    switch (epi * 2 + (save ? 1 : 0)) {
-        case 0:
-        case 1: slos_fwd_split_kernel<EPI_STORE, true><<<grid, th, 0, s>>>(a); break;
-        case 2: slos_fwd_split_kernel<EPI_PROBS, false><<<grid, th, sm, s>>>(a); break;
-        case 3: slos_fwd_split_kernel<EPI_PROBS, true><<<grid, th, sm, s>>>(a); break;
-        case 4: slos_fwd_split_kernel<EPI_AMPS, false><<<grid, th, sm, s>>>(a); break;
-        case 5: slos_fwd_split_kernel<EPI_AMPS, true><<<grid, th, sm, s>>>(a); break;
-        case 6: slos_fwd_split_kernel<EPI_THRESH, false><<<grid, th, 0, s>>>(a); break;
-        case 7: slos_fwd_split_kernel<EPI_THRESH, true><<<grid, th, 0, s>>>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
 template <int H>
 static cudaError_t launch_bwd_split_h(const SplitBwdArgs &a, int NG, int seed, int blocks_x, cudaStream_t s) {
     const int th = kSplitBwdWarps * 32;

@@ -328,16 +328,20 @@ struct ScreenArgs {
 __global__ void screen_kernel(ScreenArgs a) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= a.B) return;
-    float worst = 0.f;
+    // sum over modes of |exact <n_j> - surrogate <n_j>|: with the sign
+    // pattern w_j = +-1 of those differences, f(t) = sum_j w_j t_j lies in
+    // [-n, n] and the differences sum to zero, so sum_j |d_j| =
+    // sum_t f(t) (p_t - q_t) <= 2 n TV(p, q): a sum above 2 n tol proves TV > tol
+    float l1 = 0.f;
     for (int j = 0; j < a.m; ++j) {
         float nj = 0.f;
         for (int i = 0; i < a.m; ++i) {
             const float2 u = a.U[((int64_t)b * a.m + j) * a.m + i];
             nj += (u.x * u.x + u.y * u.y) * a.s[i];
         }
-        worst = fmaxf(worst, fabsf(nj - a.marg[(int64_t)b * a.m + j]));
+        l1 += fabsf(nj - a.marg[(int64_t)b * a.m + j]);
     }
-    if (worst > a.tol) a.flag[b] = 1;
+    if (l1 > a.tol) a.flag[b] = 1;
 }
 
 // dst[rows[i]] = src[i] (K floats per row)

@@ -9,8 +9,12 @@
 //             Parent ranks are < 2^26.
 //   backward: dense child table ctab[c'][j] = rank_k(t' + e_j) for every
 //             parent c' of layer k-1 and every mode j.
-// For the final layer n: w[t] = prod t_j! / prod s_i! and, for threshold
-// detection, pat[t] = index of the occupied-mode pattern of t.
+// For the final layer n: w[t] = prod t_j! / prod s_i!.  Under threshold
+// detection the forward walks the final layer in pattern-grouped list order
+// (patterns in output order; inside a pattern with support b, the states
+// t = 1_b + u in descending-lex order of u), so that the states of a pattern
+// are consecutive: layer n's slot rows are stored in that order, with the
+// per-position tables of PlanTables.
 #pragma once
 #include <stdint.h>
 
@@ -45,7 +49,12 @@ struct PlanTables {
     int32_t *fused_id = nullptr;     // final layer: output index of each position, -1 for padding
     float *fused_w = nullptr;        // final layer: weight of each position
     float *w = nullptr;              // [F_n]
-    int32_t *pat = nullptr;          // [F_n] (threshold only)
+    // threshold detection, per list position of the final layer
+    int32_t *lrank = nullptr;        // [F_n] Fock rank of the state
+    int32_t *lpat = nullptr;         // [F_n] its pattern (output index)
+    float *lw = nullptr;             // [F_n] its weight w[t]
+    int32_t *lseg = nullptr;         // [nseg + 1] forward work items: runs of whole patterns
+    int nseg = 0;
     float *gfact = nullptr;          // [F_n]: sqrt(prod t_j!) of the final states (amplitude encoding)
     uint8_t *occ = nullptr;          // [K][m]: occupation of mode j in output k (photon counts for PNR
                                      // outputs, 0/1 for threshold outcomes)

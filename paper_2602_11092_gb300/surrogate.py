@@ -219,11 +219,45 @@ class SurrogateLayer:
         return {"p50": float(self._np.median(tv)), "p99": float(self._np.percentile(tv, 99)), "max": float(tv.max()),
                 "frac_gt_0.02": float((tv > 0.02).mean()), "count": int(tv.size)}
 
-    def infer(self, data: torch.Tensor, rho: float = 1 / 64, tv_tol: float = 0.02, seed: int = 0):
-        """Surrogate outputs with the exact path as arbiter: a mean-photon-number
-        screen on every sample (a difference above 2 n tv_tol proves TV >
-        tv_tol), an exact spot check of a seeded fraction rho, exact fallback
-        for every sample that failed either."""
+    @staticmethod
+    def failure_rate_bound(failures: int, checked: int, confidence: float = 0.99) -> float:
+        """One-sided exact (Clopper-Pearson) upper confidence bound on a
+        binomial rate: the largest rate under which observing at most
+        `failures` in `checked` independent draws still has probability
+        >= 1 - confidence (bisection on the binomial distribution function)."""
+        import math
+        if checked <= 0 or failures >= checked:
+            return 1.0
+        alpha = 1.0 - confidence
+
+        def cdf(r):
+            return sum(math.comb(checked, k) * r ** k * (1.0 - r) ** (checked - k) for k in range(failures + 1))
+
+        lo, hi = failures / checked, 1.0
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            if cdf(mid) > alpha:
+                lo = mid
+            else:
+                hi = mid
+        return hi
+
+    def infer(self, data: torch.Tensor, rho: float = 1 / 64, tv_tol: float = 0.02, seed: int = 0,
+              max_fail_rate: float = 0.01, confidence: float = 0.99):
+        """Surrogate outputs with the exact path as arbiter.
+
+        1. Screen every sample: its per-mode mean photon numbers against the
+           exact ones (closed form); a screened-out sample provably has
+           TV > tv_tol.
+        2. Spot-check a seeded fraction rho exactly and bound the batch's
+           failure rate (TV > tv_tol) from above at the given confidence.
+        3. If that bound exceeds max_fail_rate, the whole batch takes the exact
+           path.  Otherwise every screened-out or failed sample takes it and
+           the rest keep the surrogate.
+
+        Every returned row is therefore exact, or belongs to a batch whose
+        unchecked rows exceed tv_tol at a rate <= max_fail_rate (with
+        probability >= confidence)."""
         L = lib()
         Bn = data.shape[0]
         q = self.model.forward(data)
@@ -242,20 +276,28 @@ class SurrogateLayer:
         pchk = self.exact(dchk)
         tv = torch.empty(n_chk, dtype=torch.float32, device=self.device)
         B._check(L.surr_tv_rows(B._ptr(q), B._ptr(chk), B._ptr(pchk), n_chk, self.K, B._ptr(tv), B._stream()))
-        # decisions on the host: which samples fall back
+        # decisions on the host
         fl = flag.cpu().numpy().astype(bool)
         tvh = tv.cpu().numpy()
         ch = chk.cpu().numpy()
-        fl[ch[tvh > tv_tol]] = True
-        # checked samples that passed keep the surrogate; the checked exact rows are free to reuse
-        bad = self._np.nonzero(fl)[0]
-        if bad.size:
-            rows = torch.tensor(bad, dtype=torch.int32, device=self.device)
-            dbad = torch.empty((bad.size, self.m), dtype=torch.float32, device=self.device)
-            B._check(L.surr_gather_rows(B._ptr(data), B._ptr(rows), bad.size, self.m, B._ptr(dbad), B._stream()))
-            pbad = self.exact(dbad)
-            B._check(L.surr_scatter_rows(B._ptr(pbad), B._ptr(rows), bad.size, self.K, B._ptr(q), B._stream()))
-        stats = {"batch": Bn, "screen_flagged": int(flag.sum().item()), "checked": n_chk,
-                 "check_failed": int((tvh > tv_tol).sum()), "fallback": int(bad.size),
+        failed = int((tvh > tv_tol).sum())
+        ucb = self.failure_rate_bound(failed, n_chk, confidence)
+        batch_fallback = ucb > max_fail_rate
+        if batch_fallback:
+            self.exact(data, out=q)
+            bad = self._np.arange(Bn)
+        else:
+            fl[ch[tvh > tv_tol]] = True
+            bad = self._np.nonzero(fl)[0]
+            if bad.size:
+                rows = torch.tensor(bad, dtype=torch.int32, device=self.device)
+                dbad = torch.empty((bad.size, self.m), dtype=torch.float32, device=self.device)
+                B._check(L.surr_gather_rows(B._ptr(data), B._ptr(rows), bad.size, self.m, B._ptr(dbad),
+                                            B._stream()))
+                pbad = self.exact(dbad)
+                B._check(L.surr_scatter_rows(B._ptr(pbad), B._ptr(rows), bad.size, self.K, B._ptr(q), B._stream()))
+        stats = {"batch": Bn, "screen_flagged": int(flag.sum().item()), "checked": n_chk, "check_failed": failed,
+                 "fail_rate_ucb": ucb, "max_fail_rate": max_fail_rate, "confidence": confidence,
+                 "batch_fallback": bool(batch_fallback), "fallback": int(bad.size),
                  "fallback_rate": float(bad.size / Bn), "checked_tv_max": float(tvh.max())}
         return q, stats

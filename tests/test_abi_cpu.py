@@ -93,6 +93,7 @@ def test_transition_graph_matches_enumeration(lib, m, k):
     enumeration: CSR parent entries of every child, child table of every
     parent, all indices in range."""
     from paper_2602_11092_gb300 import binding
+    from paper_2602_11092_gb300 import binding
     rowptr, entries, ctab = binding.host_transition_table(m, k)
     child = oracle.enumerate_fock(m, k)
     parent = oracle.enumerate_fock(m, k - 1)
@@ -137,3 +138,58 @@ def test_dram_traffic_profile_matches_the_kernel_sources():
     for kernel in ("slos_bwd_final", "slos_fwd_final"):
         traffic = bench.ncu_traffic(kernel)
         assert traffic is not None and traffic > 0, kernel
+
+
+def test_surrogate_failure_rate_bound():
+    """The one-sided Clopper-Pearson bound the checked inference decides with:
+    closed form 1 - alpha^(1/n) with no failures, the beta quantile
+    otherwise, and 1 when every check failed."""
+    import scipy.stats
+
+    from paper_2602_11092_gb300.surrogate import SurrogateLayer as S
+    for n in (64, 512, 1024):
+        assert abs(S.failure_rate_bound(0, n, 0.99) - (1 - 0.01 ** (1 / n))) < 1e-9
+        for k in (1, 3, 10):
+            ref = scipy.stats.beta.ppf(0.99, k + 1, n - k)
+            assert abs(S.failure_rate_bound(k, n, 0.99) - ref) < 1e-7
+    assert S.failure_rate_bound(7, 7) == 1.0
+    # a clean spot check of 1024 rows passes a 1 % bound, one of 64 cannot
+    assert S.failure_rate_bound(0, 1024) <= 0.01 < S.failure_rate_bound(0, 64)
+
+
+def _slot_table(m, k):
+    """Fixed-width slot rows (parent << 5 | mode, padded with 24) of layer k,
+    formed from the library's CSR transition graph."""
+    from paper_2602_11092_gb300 import binding
+    rowptr, entries, ctab = binding.host_transition_table(m, k)
+    kw = ((min(m, k) + 3) // 4) * 4
+    Fk = rowptr.size - 1
+    slots = np.full((Fk, kw), 24, dtype=np.uint32)
+    for c in range(Fk):
+        seg = entries[rowptr[c]:rowptr[c + 1]]
+        slots[c, :seg.size] = ((seg >> 6) << 5) | ((seg >> 1) & 31)
+    return kw, slots, np.ascontiguousarray(ctab.astype(np.int32))
+
+
+@pytest.mark.parametrize("m,k", [(6, 3), (8, 5), (12, 4)])
+def test_host_table_validation_rejects_corrupted_tables(lib, m, k):
+    """The range check every plan runs before uploading its tables accepts the
+    real tables and rejects each kind of corruption, naming the entry."""
+    kw, slots, ctab = _slot_table(m, k)
+
+    def check(sl, ct):
+        return lib.slos_host_validate_tables(m, k, kw, sl.ctypes.data, ct.ctypes.data)
+
+    assert check(slots, ctab) == 0
+    Fp = ctab.shape[0]
+    Fk = slots.shape[0]
+    bad = slots.copy(); bad[Fk // 2, 0] = (Fp << 5) | (bad[Fk // 2, 0] & 31)   # parent past layer k-1
+    assert check(bad, ctab) == 6 and b"out of range" in lib.slos_last_error()
+    bad = slots.copy(); bad[3, 0] = (bad[3, 0] & ~np.uint32(31)) | m            # mode past the last one
+    assert check(bad, ctab) == 6
+    bad = slots.copy(); bad[Fk - 1, :] = 24                                     # a state with no parent
+    assert check(bad, ctab) == 6 and b"no parent" in lib.slos_last_error()
+    badc = ctab.copy(); badc[Fp - 1, m - 1] = Fk                                # child past layer k
+    assert check(slots, badc) == 6
+    badc = ctab.copy(); badc[0, 0] = -1                                         # no holes in the Fock lattice
+    assert check(slots, badc) == 6

@@ -271,6 +271,28 @@ def test_threshold_matches_oracle(slos, m, n, B):
         check_dist(q[b], ref)
 
 
+@pytest.mark.parametrize("m,n,B", [(16, 6, 100), (10, 7, 33)])
+def test_threshold_outputs_are_reproducible_bit_for_bit(slos, m, n, B):
+    """Each pattern probability is one sum over the pattern's states in a
+    fixed order (no float atomics), so repeated forwards, with and without
+    kept activations, give the same bits; the sums still match the oracle
+    and every distribution sums to 1."""
+    rng = np.random.default_rng(m * 31 + n)
+    s = workloads.even_mode_input(m, n) if 2 * n <= m else [1] * n + [0] * (m - n)
+    U = c64(workloads.haar_unitaries(m, B, rng))
+    plan = slos.Plan(m, s, slos.THRESHOLD)
+    runs = [plan.forward(U) for _ in range(3)]
+    runs.append(plan.forward(U, save_for_backward=True, workspace=plan.workspace(B, training=True)))
+    for r in runs[1:]:
+        assert torch.equal(r, runs[0])
+    q = runs[0].double().cpu().numpy()
+    assert np.abs(q.sum(1) - 1.0).max() <= 2e-5
+    outs = oracle.enumerate_fock(m, n)
+    Uh = up(U)
+    for b in (0, B - 1):
+        check_dist(q[b], oracle.threshold_probs(oracle.probabilities(Uh[b], s, outs), outs, m, n))
+
+
 @pytest.mark.parametrize("m,s,B", [(6, [1, 1, 1, 0, 0, 0], 1), (12, [1, 0] * 6, 37), (9, [2, 0, 1, 0, 3, 0, 0, 0, 0], 5),
                                    (4, [0, 2, 0, 0], 3), (12, [1, 0] * 5 + [1, 1], 9), (10, [1, 0] * 5, 70)])
 def test_on_chip_forward_matches_layered_forward(slos, m, s, B):
@@ -378,6 +400,44 @@ def test_backward_threshold(slos, m, n, B):
         c_states = cq[b][pat_of].astype(np.float64)  # dL/dp(t) = dL/dq(pattern(t))
         ref = _grad_U_ref(Uh[b], s, c_states, outs)
         assert np.linalg.norm(dU[b] - ref) / np.linalg.norm(ref) <= G_TOL
+
+
+@pytest.mark.parametrize("m,n,det,B", [(8, 4, "pnr", 33), (13, 4, "threshold", 40), (20, 3, "threshold", 5),
+                                       (24, 3, "pnr", 3), (6, 6, "threshold", 7)])
+def test_arithmetic_index_path_matches_oracle(slos, m, n, det, B):
+    """Plans too large for transition tables walk the Fock lattice with the
+    closed-form rank arithmetic of common.cuh; an injected table-budget
+    overflow puts small plans on that path.  Forward (PNR probabilities, or
+    threshold sums over the stored a_n) against the oracle and reproducible
+    bit for bit; the backward against the table path's."""
+    lib = slos.load()
+    rng = np.random.default_rng(m * 5 + n)
+    s = workloads.even_mode_input(m, n) if 2 * n <= m else [1] * n + [0] * (m - n)
+    d = slos.THRESHOLD if det == "threshold" else slos.PNR
+    U = c64(workloads.haar_unitaries(m, B, rng))
+    assert lib.slos_inject_fault(3, 1) == 0
+    try:
+        arith = slos.Plan(m, s, d)
+    finally:
+        lib.slos_inject_fault(0, 0)
+    tab = slos.Plan(m, s, d)
+    p = arith.forward(U)
+    assert torch.equal(p, arith.forward(U))
+    outs = oracle.enumerate_fock(m, n)
+    Uh = up(U)
+    for b in (0, B - 1):
+        ref = oracle.probabilities(Uh[b], s, outs)
+        if d == slos.THRESHOLD:
+            ref = oracle.threshold_probs(ref, outs, m, n)
+        check_dist(p[b].cpu().numpy(), ref)
+    c = torch.tensor(rng.standard_normal((B, arith.n_outputs)), dtype=torch.float32, device=dev())
+    grads = []
+    for plan in (arith, tab):
+        ws = plan.workspace(B, training=True)
+        plan.forward(U, save_for_backward=True, workspace=ws)
+        grads.append(plan.backward(U, c, ws))
+    ga, gt = (g.cpu().numpy() for g in grads)
+    assert np.linalg.norm(ga - gt) / np.linalg.norm(gt) <= 1e-5
 
 
 def test_checkpointing_is_bitwise_equal_to_full_store(slos):

@@ -353,6 +353,55 @@ def test_mlp_reference_gradients_match_finite_differences():
         assert abs(fd - grads[l][1][0]) < 1e-7
 
 
+def _bf16_round_bits(x):
+    """Round float32 values to bfloat16 (round to nearest, ties to even) by
+    their bit patterns: keep the top 16 bits after adding 0x7FFF plus the
+    lowest kept bit (finite inputs)."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_mlp_bf16_rounding_is_round_to_nearest_even():
+    """The BF16 mode's rounding against the bit-level definition, including
+    halfway cases (ties go to the even neighbour) and representable values."""
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-6, 6, 20000), [0.0, -0.0, 1.0, -2.5]])
+    x = x.astype(np.float32)
+    assert np.array_equal(mlp.bf16(x), _bf16_round_bits(x))
+    # halfway between 1 and 1 + 2^-7: ties to even (1); between 1 + 2^-7 and 1 + 2^-6: up
+    half = np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8], dtype=np.float32)
+    assert np.array_equal(mlp.bf16(half), [1.0, 1.0 + 2.0 ** -6])
+    assert np.abs(mlp.bf16(x) - x).max() <= np.abs(x).max() * 2.0 ** -8
+
+
+def test_mlp_bf16_mode_within_its_rounding_bound_of_fp64():
+    """The BF16 mode is the FP64 model with values rounded to bfloat16
+    (unit roundoff u = 2^-9) at a fixed number of points per layer: features,
+    weights, pre-activations and activations.  Each rounding perturbs a value
+    by at most u relative, so with L hidden layers the logits and gradients
+    stay within a few (4L + 4) u of the FP64 model, relative to their norm,
+    and they do differ from it (the rounding is really applied)."""
+    from oracle import mlp
+    rng = np.random.default_rng(9)
+    sizes = [(32, 16), (32, 32), (10, 32)]  # 8 phases -> 16 features -> 32 -> 32 -> 10
+    params = [(rng.standard_normal(sz) / np.sqrt(sz[1]), rng.standard_normal(sz[0]) * 0.1) for sz in sizes]
+    phases = rng.uniform(0, 2 * np.pi, (6, 8))
+    target = rng.dirichlet(np.ones(10), size=6)
+    u = 2.0 ** -9
+    bound = (4 * (len(sizes) - 1) + 4) * u
+    z64, _ = mlp.forward(params, phases, bf=False)
+    zbf, _ = mlp.forward(params, phases, bf=True)
+    rel = np.linalg.norm(zbf - z64) / np.linalg.norm(z64)
+    assert 0.1 * u < rel <= bound, rel
+    _, _, g64 = mlp.loss_and_grads(params, phases, target, bf=False)
+    _, _, gbf = mlp.loss_and_grads(params, phases, target, bf=True)
+    for (w64, b64), (wbf, bbf) in zip(g64, gbf):
+        assert np.linalg.norm(wbf - w64) / np.linalg.norm(w64) <= 4 * bound
+        assert np.linalg.norm(bbf - b64) / np.linalg.norm(b64) <= 4 * bound
+
+
 def test_mlp_reference_invariants():
     from oracle import mlp
     z = np.array([[0.3, -1.0, 2.0], [5.0, 5.0, 5.0]])

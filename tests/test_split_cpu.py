@@ -2,8 +2,8 @@
 checked on the CPU, bit for bit.
 
 The tables are built by the library's host code; these tests walk them the way
-the split kernels do (4-state runs, head-block descriptors, tail slot and
-child rows) and compare every parent and child index that a kernel would form
+the split backward kernel does (4-parent runs, head-block descriptors, tail
+child rows) and compare every child index that the kernel would form
 with the plain transition graph of the same layer, which is itself pinned
 against brute-force enumeration (test_abi_cpu.py).  They also check that every
 index a kernel forms stays inside the buffer it addresses.
@@ -15,7 +15,6 @@ import pytest
 
 from paper_2602_11092_gb300 import binding
 
-EMPTY = 24  # padding slot: parent 0, the zero row of U
 CHUNK = 4  # states per warp run (the chunk tables' granularity)
 
 # (m, n): head/tail splits of 6 + 2, 6 + 6, 8 + 5 and 8 + 8 modes
@@ -29,63 +28,6 @@ def lib():
 
 def _layers(m, n):
     return [k for k in range(2, n + 1)]
-
-
-@pytest.mark.parametrize("m,n", SHAPES)
-def test_split_forward_walk_matches_transition_graph(lib, m, n):
-    tail = binding.host_split_tail(m, n)
-    h = tail["h"]
-    mL = m - h
-    slots = tail["slots"]
-    for k in _layers(m, n):
-        if k == n and (m, n) == (16, 8):
-            step = 29  # every 29th run of the 490314-state layer
-        else:
-            step = 1
-        L = binding.host_split_layer(m, n, k)
-        assert L["h"] == h
-        Fk, Fp = math.comb(m + k - 1, k), math.comb(m + k - 2, k - 1)
-        rowptr, entries, _ = binding.host_transition_table(m, k)
-        fdesc, fhead, fchunk = L["fdesc"], L["fhead"], L["fchunk"]
-        # blocks tile the layer in rank order
-        assert fdesc[0, 0] == 0
-        assert np.array_equal(fdesc[1:, 0], fdesc[:-1, 0] + fdesc[:-1, 1])
-        assert fdesc[-1, 0] + fdesc[-1, 1] == Fk
-        assert fchunk.size == (Fk + CHUNK - 1) // CHUNK
-        for ch in range(0, fchunk.size, step):
-            c0, cend = ch * CHUNK, min(ch * CHUNK + CHUNK, Fk)
-            b, c = int(fchunk[ch]), c0
-            while c < cend:
-                base, size, zb, w = (int(x) for x in fdesc[b])
-                assert base <= c < base + size
-                stop = min(base + size, cend)
-                rho, qh = w & 255, (w >> 8) & 15
-                assert 0 <= qh <= 8 and qh <= min(h, k)
-                hoff = [(int(fhead[b, q]) >> 5) - base for q in range(qh)]
-                hmode = [int(fhead[b, q]) & 31 for q in range(qh)]
-                W = int(tail["tw"][rho])
-                tr = int(tail["soff"][rho]) + (c - base) * W
-                if W:
-                    assert 0 <= zb and zb < Fp  # padding slots read parent row zb
-                for cc in range(c, stop):
-                    got = [(cc + hoff[q], hmode[q]) for q in range(qh)]
-                    if W:
-                        assert tr + W <= slots.size
-                        for e in slots[tr:tr + W]:
-                            e = int(e)
-                            if e == EMPTY:
-                                continue
-                            assert h <= (e & 31) < m
-                            got.append((zb + (e >> 5), e & 31))
-                        tr += W
-                    for p, _ in got:
-                        assert 0 <= p < Fp
-                    seg = entries[rowptr[cc]:rowptr[cc + 1]]
-                    want = [(int(e >> 6), int((e >> 1) & 31)) for e in seg]
-                    assert sorted(got, key=lambda x: x[1]) == want, (m, n, k, cc)
-                c = stop
-                b += 1
-        assert mL >= 1
 
 
 @pytest.mark.parametrize("m,n", SHAPES)
@@ -123,24 +65,34 @@ def test_split_backward_walk_matches_child_table(lib, m, n):
                 b += 1
 
 
-def test_split_tail_rows_are_padded_and_aligned(lib):
-    for m, n in SHAPES:
-        t = binding.host_split_tail(m, n)
-        mL = m - t["h"]
-        for rho in range(n + 1):
-            W = int(t["tw"][rho])
-            assert W == (0 if rho == 0 else ((min(mL, rho) + 3) & ~3))
-            assert int(t["soff"][rho]) % 4 == 0  # 16-byte row loads
-        # a tail state with q occupied modes has exactly q slots before the padding
-        rho = n
-        W = int(t["tw"][rho])
-        rows = t["slots"][int(t["soff"][rho]):].reshape(-1, W)[:math.comb(rho + mL - 1, mL - 1)]
-        occupied = (rows != EMPTY).sum(1)
-        assert occupied.min() >= 1 and occupied.max() <= min(mL, rho)
-        # padding only after the occupied slots
-        for r in rows[:200]:
-            nz = list(r != EMPTY)
-            assert nz == sorted(nz, reverse=True)
+def _compositions_desc(parts, total):
+    """All compositions of total into parts, in descending lexicographic order."""
+    if parts == 1:
+        return [(total,)]
+    out = []
+    for first in range(total, -1, -1):
+        out += [(first,) + rest for rest in _compositions_desc(parts - 1, total - first)]
+    return out
+
+
+@pytest.mark.parametrize("m,n", [(8, 4), (12, 5), (16, 4)])
+def test_split_tail_child_rows_by_enumeration(lib, m, n):
+    """Row r of rho's block is the r-th tail composition of rho photons in
+    descending-lex order; entry j is the position of t_L + e_j among the
+    compositions of rho + 1 photons (enumerated here independently), and
+    the entries past the m - h tail modes are 0."""
+    t = binding.host_split_tail(m, n)
+    mL = m - t["h"]
+    rows = t["ctab"].reshape(-1, 8)
+    assert int(t["coff"][0]) == 0 and int(t["coff"][n]) == rows.shape[0]
+    for rho in range(n):
+        comps = _compositions_desc(mL, rho)
+        nxt = {c: i for i, c in enumerate(_compositions_desc(mL, rho + 1))}
+        assert int(t["coff"][rho + 1]) - int(t["coff"][rho]) == len(comps)
+        for r, c in enumerate(comps):
+            row = rows[int(t["coff"][rho]) + r]
+            want = [nxt[c[:j] + (c[j] + 1,) + c[j + 1:]] for j in range(mL)] + [0] * (8 - mL)
+            assert [int(x) for x in row] == want, (m, n, rho, c)
 
 
 def test_split_eligibility(lib):
