@@ -15,10 +15,13 @@
 // the output) is stored with its states sorted, stably, by q rounded up to
 // even: a section of rows 2, 4, ..., 12 slots wide, so that no state pays
 // for the widest one.  A layer's "position" of a state is its place in that
-// order; the next layer's slots and the pattern lists use positions.  The
-// modes in a final state's slots are its occupied-mode pattern (threshold
-// detection); its weight prod t_j! / prod s_i! is a per-position table
-// built with the slots.
+// order; the next layer's slots use positions.  Under threshold detection
+// the final layer's positions are its pattern-grouped list order instead
+// (patterns in output order, a pattern's states consecutive; it agrees with
+// the sections, since the patterns come by increasing |b|), and a work item
+// of that layer is a run of whole patterns, so one warp sums each pattern in
+// a fixed order and stores it once.  A final state's weight
+// prod t_j! / prod s_i! is a per-position table built with the slots.
 // Work item = (lane group, layer k, chunk of consecutive Fock states).  Items are listed layer by
 // layer (all layer-1 items of every lane group, then all layer-2 items, ...),
 // largest lane groups first inside a layer (longest-processing-time order).
@@ -61,7 +64,6 @@ struct BShape {
     int64_t F[kMaxPhotons + 1];
     int64_t slot_off[kMaxPhotons + 1];  // element offset of layer k's slots in the table buffer
     int64_t w_off;                      // final-layer weights prod t! / prod s! (float) [F_n]
-    int64_t plist_off;                  // threshold: final states grouped by pattern [F_n]
     int kw[kMaxPhotons + 1];            // widest slot row of layer k (even, <= 12)
     // Layer k is stored in sections of states with 2s+1 or 2s+2 occupied
     // modes (s = 0 .. kBSec-1), each section with rows of 2s+2 slots;
@@ -79,13 +81,12 @@ struct BShape {
 struct BLaneGroup {
     int shape;
     int inst[kBLanes];    // global instance index per lane, -1 = empty lane
-    int64_t buf[2];       // workspace byte offsets of the two layer buffers; buf[1] also holds
-                          // the final layer's per-state probabilities under threshold detection
+    int64_t buf[2];       // workspace byte offsets of the two layer buffers
 };
 
 struct BDesc {
     int lg;      // lane group
-    int k;       // layer (n + 1: pattern sums of a threshold shape)
+    int k;       // layer
     int dep;     // descriptor of layer k-1 of the same lane group (-1 for k = 1)
     int nchunks;
 };
@@ -164,14 +165,15 @@ __global__ void __launch_bounds__(256) section_pass_kernel(const BShape sh, int 
 //   (position of t - e_j in layer k-1 << 5) | j
 // for the occupied modes j of t in mode order, then padding; ppos maps the
 // parent layer's ranks to positions (null: unsorted).  For the final layer
-// also w[position] = prod t_j! / prod s_i! and, under threshold detection,
-// the state's place in the pattern-grouped list: patterns in output order
-// (|b|, then colex), and inside a pattern the states t with support b in
-// descending-lex order of t - 1_b, a composition of n - |b| photons over
-// |b| modes, ranked with the same bar formula.
+// also w[position] = prod t_j! / prod s_i!.  With `listed` (the final layer
+// of a threshold shape) the position is the state's place in the
+// pattern-grouped list: patterns in output order (|b|, then colex), and
+// inside a pattern the states t with support b in descending-lex order of
+// t - 1_b, a composition of n - |b| photons over |b| modes, ranked with the
+// same bar formula.
 template <int MMAX>
 __global__ void build_slots_kernel(const BShape sh, int k, uint32_t *tab, const int *ppos, const int *cpos,
-                                   float *w, uint32_t *plist) {
+                                   float *w, bool listed) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= sh.F[k]) return;
     const int m = sh.m;
@@ -201,11 +203,22 @@ __global__ void build_slots_kernel(const BShape sh, int k, uint32_t *tab, const 
     }
     const int nb = q;
     int64_t at = c;
+    if (listed) {
+        const int np = k - nb, Lp = np + nb - 1;
+        int64_t r = 0;
+        int cum = 0;
+        for (int b = 0; b + 1 < nb; ++b) {
+            cum += tb[b] - 1;
+            r += (int64_t)binom(Lp - 1 - b - cum, nb - 1 - b);
+        }
+        at = sh.pat_base[nb] + (int64_t)colex_rank(supp) * sh.pat_cnt[nb] + r;
+    } else if (cpos) {
+        at = cpos[c];
+    }
     uint32_t *dst;
     int width;
-    if (cpos) {
+    if (cpos || listed) {
         const int sec = (nb + 1) / 2 - 1;
-        at = cpos[c];
         width = 2 * sec + 2;
         dst = tab + sh.sec_off[k][sec] + (at - sh.sec_pos[k][sec]) * width;
     } else {
@@ -215,17 +228,6 @@ __global__ void build_slots_kernel(const BShape sh, int k, uint32_t *tab, const 
     for (int i = 0; i < nb; ++i) dst[i] = e[i];
     for (int i = nb; i < width; ++i) dst[i] = kSlotEmpty;
     if (w) w[at] = fprod * sh.inv_sfact;
-    if (plist) {
-        const int np = k - nb, Lp = np + nb - 1;
-        int64_t r = 0;
-        int cum = 0;
-        for (int b = 0; b + 1 < nb; ++b) {
-            cum += tb[b] - 1;
-            r += (int64_t)binom(Lp - 1 - b - cum, nb - 1 - b);
-        }
-        const int64_t pl = sh.pat_base[nb] + (int64_t)colex_rank(supp) * sh.pat_cnt[nb] + r;
-        plist[pl] = (uint32_t)at;
-    }
 }
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -234,92 +236,101 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
     return v;
 }
 
-enum BOut { B_NEXT = 0, B_PNR = 1, B_SCRATCH = 2 };
-
-// Positions c0 + half, c0 + half + 2, ... < c1 of one section of a layer
-// (rows of KW slots from tab, the first row being position pos0) for the 16
-// instances of a lane group (lane il of each half-warp).  us: this warp's
-// staged column of U, row j = U[j][col] per lane (row kBMax zero); prev:
-// layer k-1 of this lane (rows of 16 complex64).  Parent rows are plain
+// Amplitude of position c of one section of a layer (rows of KW slots from
+// tab, the first row being position pos0) for the lane's instance.  us: this
+// warp's staged column of U, row j = U[j][col] per lane (row kBMax zero);
+// prev: layer k-1 of this lane (rows of 16 complex64).  Parent rows are plain
 // (L1-cached) loads: the wait on layer k-1's completion counter has ordered
 // them after its writes.
 template <int KW>
+__device__ __forceinline__ float2 b_state_amp(const uint32_t *__restrict__ tab, int pos0, int c, const float2 *us,
+                                              const char *prev, bool first_layer) {
+    uint32_t e[KW];
+    const uint32_t row = (uint32_t)(c - pos0) * KW;
+    if (KW % 4 == 0) {
+        const uint4 *t4 = reinterpret_cast<const uint4 *>(tab + row);
+#pragma unroll
+        for (int q4 = 0; q4 < KW / 4; ++q4) {
+            const uint4 w4 = __ldg(t4 + q4);
+            e[4 * q4] = w4.x;
+            e[4 * q4 + 1] = w4.y;
+            e[4 * q4 + 2] = w4.z;
+            e[4 * q4 + 3] = w4.w;
+        }
+    } else {
+        const uint2 *t2 = reinterpret_cast<const uint2 *>(tab + row);
+#pragma unroll
+        for (int q2 = 0; q2 < KW / 2; ++q2) {
+            const uint2 w2 = __ldg(t2 + q2);
+            e[2 * q2] = w2.x;
+            e[2 * q2 + 1] = w2.y;
+        }
+    }
+    if (first_layer) return us[(e[0] & 31u) * kBLanes];  // one photon: a_1(e_j) = U[j][col]
+    float2 v[KW];
+#pragma unroll
+    for (int q = 0; q < KW; ++q) v[q] = *reinterpret_cast<const float2 *>(prev + (size_t)(e[q] & ~31u) * 4u);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < KW; ++q) acc = cfma(us[(e[q] & 31u) * kBLanes], v[q], acc);
+    return acc;
+}
+
+// Positions c0 + half, c0 + half + 2, ... < c1 of one section for the 16
+// instances of a lane group (lane il of each half-warp): the next layer's
+// amplitudes, or the PNR output probabilities (Fock order).
+template <int KW>
 __device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int pos0, int c0, int c1, int half,
-                                           const float2 *us, const char *prev, bool first_layer, int kind,
-                                           float2 *next, float *outp, float *scr, const float *__restrict__ wtab) {
+                                           const float2 *us, const char *prev, bool first_layer, bool last,
+                                           float2 *next, float *outp, const float *__restrict__ wtab) {
     // positions fit in 32 bits (at most C(31, 12) < 2^28 per layer)
     for (int c = c0 + half; c < c1; c += 2) {
-        uint32_t e[KW];
-        const uint32_t row = (uint32_t)(c - pos0) * KW;
-        if (KW % 4 == 0) {
-            const uint4 *t4 = reinterpret_cast<const uint4 *>(tab + row);
-#pragma unroll
-            for (int q4 = 0; q4 < KW / 4; ++q4) {
-                const uint4 w4 = __ldg(t4 + q4);
-                e[4 * q4] = w4.x;
-                e[4 * q4 + 1] = w4.y;
-                e[4 * q4 + 2] = w4.z;
-                e[4 * q4 + 3] = w4.w;
-            }
-        } else {
-            const uint2 *t2 = reinterpret_cast<const uint2 *>(tab + row);
-#pragma unroll
-            for (int q2 = 0; q2 < KW / 2; ++q2) {
-                const uint2 w2 = __ldg(t2 + q2);
-                e[2 * q2] = w2.x;
-                e[2 * q2 + 1] = w2.y;
-            }
-        }
-        float2 acc;
-        if (first_layer) {
-            acc = us[(e[0] & 31u) * kBLanes];  // one photon: a_1(e_j) = U[j][col]
-        } else {
-            float2 v[KW];
-#pragma unroll
-            for (int q = 0; q < KW; ++q) v[q] = *reinterpret_cast<const float2 *>(prev + (size_t)(e[q] & ~31u) * 4u);
-            acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int q = 0; q < KW; ++q) acc = cfma(us[(e[q] & 31u) * kBLanes], v[q], acc);
-        }
-        if (kind == B_NEXT) {
-            next[(uint32_t)c * kBLanes] = acc;
-        } else {
-            const float pr = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
-            if (kind == B_SCRATCH) scr[(uint32_t)c * kBLanes] = pr;
-            else if (outp) outp[c] = pr;
-        }
+        const float2 acc = b_state_amp<KW>(tab, pos0, c, us, prev, first_layer);
+        if (!last) next[(uint32_t)c * kBLanes] = acc;
+        else if (outp) outp[c] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
     }
 }
 
-// Threshold detection: out[P] = sum of the final-layer probabilities of the
-// states of pattern P, for the patterns whose first list position lies in
-// [s0, s1).  Half-warp `half` takes every other such pattern; the sum runs
-// in list order, so it does not depend on the launch shape.
-__device__ __forceinline__ void pattern_sums(const BShape &sh, const uint32_t *__restrict__ plist, const float *scr,
-                                             float *outp, int64_t s0, int64_t s1, int half) {
-    for (int j = 1; j <= sh.nclass; ++j) {
-        const int64_t cnt = sh.pat_cnt[j];
-        const int64_t b0 = sh.pat_base[j];
-        const int64_t b1 = b0 + (int64_t)(sh.pat_off[j + 1] - sh.pat_off[j]) * cnt;
-        if (b1 <= s0 || b0 >= s1) continue;
-        const int64_t lo = max(s0, b0) - b0, hi = min(s1, b1) - b0;
-        const int64_t q0 = (lo + cnt - 1) / cnt, q1 = (hi + cnt - 1) / cnt;
-        for (int64_t qq = q0 + half; qq < q1; qq += 2) {
-            const uint32_t *lst = plist + b0 + qq * cnt;
-            float sum = 0.f;
-            for (int64_t r = 0; r < cnt; r += 4) {
-                uint32_t id[4];
-                float v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) id[u] = r + u < cnt ? __ldg(lst + r + u) : 0xFFFFFFFFu;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = id[u] != 0xFFFFFFFFu ? scr[(size_t)id[u] * kBLanes] : 0.f;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) sum += v[u];
-            }
-            if (outp) outp[sh.pat_off[j] + qq] = sum;
+// Threshold detection, final layer in list order: patterns [P0, P1) of
+// class j (cnt states each, the first at list position base), whose output
+// indices start at pat_first.  Each pattern's probability is one sum in
+// list order: with one state per pattern the half-warps take alternate
+// patterns; otherwise they take alternate states of each pattern and add
+// their two partial sums.  The sum does not depend on the launch shape.
+template <int KW>
+__device__ __forceinline__ void thresh_patterns(const uint32_t *__restrict__ tab, int pos0, int64_t base, int cnt,
+                                                int64_t P0, int64_t P1, int pat_first, int half, const float2 *us,
+                                                const char *prev, bool first_layer, float *outp,
+                                                const float *__restrict__ wtab) {
+    if (cnt == 1) {
+        for (int64_t P = P0 + half; P < P1; P += 2) {
+            const int c = (int)(base + P);
+            const float2 acc = b_state_amp<KW>(tab, pos0, c, us, prev, first_layer);
+            if (outp) outp[pat_first + P] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
         }
+        return;
     }
+    for (int64_t P = P0; P < P1; ++P) {
+        const int c0 = (int)(base + P * cnt);
+        float sum = 0.f;
+        for (int c = c0 + half; c < c0 + cnt; c += 2) {
+            const float2 acc = b_state_amp<KW>(tab, pos0, c, us, prev, first_layer);
+            sum += __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+        }
+        sum += __shfl_xor_sync(0xffffffffu, sum, 16);
+        if (half == 0 && outp) outp[pat_first + P] = sum;
+    }
+}
+
+// Work items of class j of a threshold final layer: runs of whole patterns
+// of about `chunk` states.
+__host__ __device__ __forceinline__ int64_t thresh_per_item(const BShape &sh, int j, int chunk) {
+    const int64_t per = chunk / sh.pat_cnt[j];
+    return per > 0 ? per : 1;
+}
+__host__ __device__ __forceinline__ int64_t thresh_items(const BShape &sh, int j, int chunk) {
+    const int64_t npat = sh.pat_off[j + 1] - sh.pat_off[j];
+    return (npat + thresh_per_item(sh, j, chunk) - 1) / thresh_per_item(sh, j, chunk);
 }
 
 // MINB: resident 256-thread blocks per SM the register allocation is sized for
@@ -377,48 +388,70 @@ __global__ void __launch_bounds__(256, MINB) slos_batched_kernel(BArgs a) {
         }
         const int inst = g.inst[il];
         const bool valid = inst >= 0;
-        const int64_t c0 = chunk_id * a.chunk;
         float *outp = valid ? a.out + a.out_off[inst] : nullptr;
-        float *scr = reinterpret_cast<float *>(a.ws + g.buf[1]) + il;
-        if (k == n + 1) {
-            const int64_t c1 = min(c0 + (int64_t)a.chunk, sh.F[n]);
-            pattern_sums(sh, a.slots + sh.plist_off, scr, outp, c0, c1, half);
-        } else {
+        {
             const int m = sh.m;
             const int col = sh.cols[k - 1];
             __syncwarp();
             for (int j = half; j < m; j += 2)
                 us[j * kBLanes + il] = valid ? a.U[a.u_off[inst] + (int64_t)j * m + col] : make_float2(0.f, 0.f);
             __syncwarp();
-            // the item's section: chunks are counted section by section, so no
-            // item straddles two widths
-            int sec = 0;
-            int64_t rem = chunk_id;
-            for (; sec < kBSec - 1; ++sec) {
-                const int64_t nch = (sh.sec_pos[k][sec + 1] - sh.sec_pos[k][sec] + a.chunk - 1) / a.chunk;
-                if (rem < nch) break;
-                rem -= nch;
-            }
-            const int p0 = sh.sec_pos[k][sec];
-            const int lo = p0 + (int)rem * a.chunk;
-            const int hi = min(lo + a.chunk, sh.sec_pos[k][sec + 1]);
             const char *prev = a.ws + g.buf[(n - 1 - (k - 1)) & 1] + il * sizeof(float2);
-            float2 *next = reinterpret_cast<float2 *>(a.ws + g.buf[(n - 1 - k) & 1]) + il;
-            const int kind = k < n ? B_NEXT : (sh.det == SLOS_DETECT_THRESHOLD ? B_SCRATCH : B_PNR);
             const uint32_t *tab = a.slots + sh.slot_off[k];
             const float *wtab = reinterpret_cast<const float *>(a.slots + sh.w_off);
             const float2 *usl = us + il;
-            const uint32_t *st = tab + sh.sec_off[k][sec];
-#define SLOS_B_SEC(W) fwd_states<W>(st, p0, lo, hi, half, usl, prev, k == 1, kind, next, outp, scr, wtab)
-            switch (sec) {
-                case 0: SLOS_B_SEC(2); break;
-                case 1: SLOS_B_SEC(4); break;
-                case 2: SLOS_B_SEC(6); break;
-                case 3: SLOS_B_SEC(8); break;
-                case 4: SLOS_B_SEC(10); break;
-                default: SLOS_B_SEC(12); break;
-            }
+            if (k == n && sh.det == SLOS_DETECT_THRESHOLD) {
+                // the item's class and run of patterns (items counted class by class)
+                int j = 1;
+                int64_t rem = chunk_id;
+                for (; j < sh.nclass; ++j) {
+                    const int64_t nit = thresh_items(sh, j, a.chunk);
+                    if (rem < nit) break;
+                    rem -= nit;
+                }
+                const int64_t per = thresh_per_item(sh, j, a.chunk);
+                const int64_t P0 = rem * per;
+                const int64_t P1 = min(P0 + per, (int64_t)(sh.pat_off[j + 1] - sh.pat_off[j]));
+                const int sec = (j + 1) / 2 - 1;
+                const int p0 = sh.sec_pos[k][sec];
+                const uint32_t *st = tab + sh.sec_off[k][sec];
+#define SLOS_B_THR(W) \
+    thresh_patterns<W>(st, p0, sh.pat_base[j], sh.pat_cnt[j], P0, P1, sh.pat_off[j], half, usl, prev, k == 1, outp, wtab)
+                switch (sec) {
+                    case 0: SLOS_B_THR(2); break;
+                    case 1: SLOS_B_THR(4); break;
+                    case 2: SLOS_B_THR(6); break;
+                    case 3: SLOS_B_THR(8); break;
+                    case 4: SLOS_B_THR(10); break;
+                    default: SLOS_B_THR(12); break;
+                }
+#undef SLOS_B_THR
+            } else {
+                // the item's section: chunks are counted section by section, so no
+                // item straddles two widths
+                int sec = 0;
+                int64_t rem = chunk_id;
+                for (; sec < kBSec - 1; ++sec) {
+                    const int64_t nch = (sh.sec_pos[k][sec + 1] - sh.sec_pos[k][sec] + a.chunk - 1) / a.chunk;
+                    if (rem < nch) break;
+                    rem -= nch;
+                }
+                const int p0 = sh.sec_pos[k][sec];
+                const int lo = p0 + (int)rem * a.chunk;
+                const int hi = min(lo + a.chunk, sh.sec_pos[k][sec + 1]);
+                float2 *next = reinterpret_cast<float2 *>(a.ws + g.buf[(n - 1 - k) & 1]) + il;
+                const uint32_t *st = tab + sh.sec_off[k][sec];
+#define SLOS_B_SEC(W) fwd_states<W>(st, p0, lo, hi, half, usl, prev, k == 1, k == n, next, outp, wtab)
+                switch (sec) {
+                    case 0: SLOS_B_SEC(2); break;
+                    case 1: SLOS_B_SEC(4); break;
+                    case 2: SLOS_B_SEC(6); break;
+                    case 3: SLOS_B_SEC(8); break;
+                    case 4: SLOS_B_SEC(10); break;
+                    default: SLOS_B_SEC(12); break;
+                }
 #undef SLOS_B_SEC
+            }
         }
         __threadfence();
         __syncwarp();
@@ -488,32 +521,33 @@ static slos_status_t build_items(BatchedPlan *b, int chunk) {
     int kmax = 0;
     for (auto &sh : b->shapes) kmax = std::max(kmax, sh.n);
     std::vector<BDesc> desc;
-    std::vector<int> idx_of((size_t)b->lgs.size() * (kmax + 2), -1);
-    for (int k = 1; k <= kmax + 1; ++k) {
+    std::vector<int> idx_of((size_t)b->lgs.size() * (kmax + 1), -1);
+    for (int k = 1; k <= kmax; ++k) {
         std::vector<D> layer;
         for (size_t l = 0; l < b->lgs.size(); ++l) {
             const BShape &sh = b->shapes[b->lgs[l].shape];
-            const bool sums = k == sh.n + 1 && sh.det == SLOS_DETECT_THRESHOLD;  // pattern sums
-            if (k > sh.n && !sums) continue;
-            const int64_t states = sums ? sh.F[sh.n] : sh.F[k];
+            if (k > sh.n) continue;
             D x;
             x.d.lg = (int)l;
             x.d.k = k;
             x.d.dep = -1;
-            x.d.nchunks = (int)((states + chunk - 1) / chunk);
-            if (!sums) {  // layer items never straddle a section (slot width)
-                int64_t nch = 0;
+            int64_t nch = 0;
+            if (k == sh.n && sh.det == SLOS_DETECT_THRESHOLD) {
+                // runs of whole patterns, class by class
+                for (int j = 1; j <= sh.nclass; ++j) nch += thresh_items(sh, j, chunk);
+            } else {
+                // items never straddle a section (slot width)
                 for (int sec = 0; sec < kBSec; ++sec)
                     nch += (sh.sec_pos[k][sec + 1] - sh.sec_pos[k][sec] + chunk - 1) / chunk;
-                x.d.nchunks = (int)nch;
             }
-            x.work = sums ? states : states * std::min(sh.m, k);
+            x.d.nchunks = (int)nch;
+            x.work = sh.F[k] * std::min(sh.m, k);
             layer.push_back(x);
         }
         std::stable_sort(layer.begin(), layer.end(), [](const D &a, const D &c) { return a.work > c.work; });
         for (auto &x : layer) {
-            x.d.dep = k > 1 ? idx_of[(size_t)x.d.lg * (kmax + 2) + k - 1] : -1;
-            idx_of[(size_t)x.d.lg * (kmax + 2) + k] = (int)desc.size();
+            x.d.dep = k > 1 ? idx_of[(size_t)x.d.lg * (kmax + 1) + k - 1] : -1;
+            idx_of[(size_t)x.d.lg * (kmax + 1) + k] = (int)desc.size();
             desc.push_back(x.d);
         }
     }
@@ -732,9 +766,7 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
                 g.inst[l] = q + l < members[si].size() ? members[si][q + l] : -1;
             const int64_t f1 = sh.n >= 2 ? sh.F[sh.n - 1] : 1;
             const int64_t f2 = sh.n >= 3 ? sh.F[sh.n - 2] : 1;
-            // buf[1]: layer n-2, then (threshold) the final layer's probabilities
-            size_t b1 = (size_t)f2 * kBLanes * sizeof(float2);
-            if (sh.det == SLOS_DETECT_THRESHOLD) b1 = std::max(b1, (size_t)sh.F[sh.n] * kBLanes * sizeof(float));
+            const size_t b1 = (size_t)f2 * kBLanes * sizeof(float2);
             g.buf[0] = (int64_t)off;
             off += align_up((size_t)f1 * kBLanes * sizeof(float2));
             g.buf[1] = (int64_t)off;
@@ -743,7 +775,7 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
         }
     }
     b->layer_bytes = off;
-    // tables: per shape, layers 1..n of slots, the final weights, the grouped list
+    // tables: per shape, layers 1..n of slots and the final weights
     int64_t tab_elems = 0;
     int64_t max_sorted = 0;  // largest sorted layer (plan-time scratch)
     for (auto &sh : b->shapes) {
@@ -771,11 +803,15 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
             }
             tab_elems += (off + 3) & ~int64_t(3);
         }
+        if (sh.det == SLOS_DETECT_THRESHOLD && sh.n >= 2)
+            for (int j = 1; j <= sh.nclass; j += 2)
+                if (sh.sec_pos[sh.n][(j - 1) / 2] != sh.pat_base[j]) {
+                    delete b;
+                    return fail(SLOS_ERR_INTERNAL, "slos_batched_plan: pattern classes do not match the sections");
+                }
         const int64_t fn4 = (sh.F[sh.n] + 3) & ~int64_t(3);
         sh.w_off = tab_elems;
         tab_elems += fn4;
-        sh.plist_off = tab_elems;
-        if (sh.det == SLOS_DETECT_THRESHOLD) tab_elems += fn4;
     }
     b->signature = sig.str();
     slos_plan_s *p = new slos_plan_s();
@@ -835,7 +871,8 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
             const int bs = 256;
             const unsigned grid = (unsigned)((sh.F[k] + bs - 1) / bs);
             int *cpos = nullptr;
-            if (layer_sorted(sh, k)) {
+            const bool listed = k == sh.n && sh.det == SLOS_DETECT_THRESHOLD;  // list order, no sort pass
+            if (layer_sorted(sh, k) && !listed) {
                 cpos = d_pos[k & 1];
                 section_pass_kernel<kBMax><<<grid, bs>>>(sh, k, d_cnt, nullptr, nullptr);
                 hcnt.resize((size_t)grid * kBSec);
@@ -861,8 +898,7 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
                 section_pass_kernel<kBMax><<<grid, bs>>>(sh, k, nullptr, d_base, cpos);
             }
             float *w = k == sh.n ? reinterpret_cast<float *>(b->d_slots + sh.w_off) : nullptr;
-            uint32_t *pl = (k == sh.n && sh.det == SLOS_DETECT_THRESHOLD) ? b->d_slots + sh.plist_off : nullptr;
-            build_slots_kernel<kBMax><<<grid, bs>>>(sh, k, b->d_slots + sh.slot_off[k], ppos, cpos, w, pl);
+            build_slots_kernel<kBMax><<<grid, bs>>>(sh, k, b->d_slots + sh.slot_off[k], ppos, cpos, w, listed);
             ppos = cpos;
         }
     }
