@@ -1639,9 +1639,13 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
         a.chunk = kChunkBwd;
         a.inv_sfact = p->inv_sfact;
         {
-            // layered-model bytes: read a_{k-1} and G_k (or a_n and dL/dout), write G_{k-1}
-            double bytes = (kp >= 1 ? 16.0 * a.Fprev : 0.0) + (k == n ? 12.0 : 8.0) * a.Fk;
-            ProfScope ps(k == n ? "slos_bwd_final" : "slos_bwd_layer", bytes * batch, s);
+            // layered-model bytes: read a_{k-1} and G_k (or a_n and the seed), write
+            // G_{k-1}; a seed shared by the batch is read once
+            double bytes = (kp >= 1 ? 16.0 * a.Fprev : 0.0) + 8.0 * a.Fk;
+            double shared = 0.0;
+            if (k == n && seed == SEED_T) bytes += 4.0 * a.Fk;
+            if (k == n && seed == SEED_BCAST) shared = 4.0 * a.Fk;
+            ProfScope ps(k == n ? "slos_bwd_final" : "slos_bwd_layer", bytes * batch + shared, s);
             if (p->split && k >= 2) {
                 const SplitTables &st = *p->split;
                 const SplitLayer &L = st.layer[k];

@@ -165,12 +165,20 @@ __device__ __forceinline__ float2 split_child(const float2 *srcb, const float *s
     return g;
 }
 
+// Tail child J of a parent (local position from the tail child row), 0 past
+// the plan's tail modes.
+template <int J, int SEED>
+__device__ __forceinline__ float2 tail_child(const float2 *srcb, const float *seedb, uint32_t lc, const uint4 &cr,
+                                             int mL, uint32_t fk, int *status) {
+    return mL > J ? split_child<SEED>(srcb, seedb, lc + crow16<J>(cr), fk, status) : make_float2(0.f, 0.f);
+}
+
 // One batch of (up to) 4 children of a parent: G_{k-1} += conj(U_j) g_j and
 // dU_j += conj(a_{k-1}) g_j, with dU_j and U_j in tensor-memory columns
 // [cd, cd + 8) and [cu, cu + 8) of the warp's lane quarter.  Modes past the
 // plan's last one hold U = 0 and g = 0.
 template <int N>
-__device__ __forceinline__ void split_bwd_batch(uint32_t tq, uint32_t cd, uint32_t cu, const float2 (&g)[4], float2 av,
+__device__ __forceinline__ void split_bwd_batch(uint32_t tq, uint32_t cd, uint32_t cu, const float2 *g, float2 av,
                                                 float2 &gacc) {
     uint32_t du[8], uu[8];
     tm_ld8(tq + cd, du);
@@ -242,6 +250,9 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
     const float *seedb = (SEED == SEED_T) ? reinterpret_cast<const float *>(a.seed) + gk
                                           : reinterpret_cast<const float *>(a.seed);
     const int wstride = gridDim.x * kSplitBwdWarps;
+    const uint32_t fk = (uint32_t)a.Fk;
+    int *const st = a.status;
+    const float2 z = make_float2(0.f, 0.f);
     for (int ch = blockIdx.x * kSplitBwdWarps + warp; ch < a.nruns; ch += wstride) {
         const int c0 = ch * kSplitRun;
         const int cend = min(c0 + kSplitRun, a.Fprev);
@@ -263,26 +274,23 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
                 const float2 av = __ldg(aprevb + ((uint32_t)c << 5));
                 const uint4 cr = __ldg(crow);
                 float2 gacc = make_float2(0.f, 0.f);
-                float2 g[4];
-                // head modes 0..3, 4..H-1
+                // every child of the parent first (16 loads in flight), then the four
+                // tensor-memory batches: head modes 0..3, 4..H-1, tail modes 0..3, 4..7
+                float2 g[16];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) g[j] = split_child<SEED>(srcb, seedb, (uint32_t)(c + hoff[j]), (uint32_t)a.Fk, a.status);
+                for (int j = 0; j < 8; ++j) g[j] = j < H ? split_child<SEED>(srcb, seedb, c + hoff[j], fk, st) : z;
+                g[8] = tail_child<0, SEED>(srcb, seedb, lc, cr, mL, fk, st);
+                g[9] = tail_child<1, SEED>(srcb, seedb, lc, cr, mL, fk, st);
+                g[10] = tail_child<2, SEED>(srcb, seedb, lc, cr, mL, fk, st);
+                g[11] = tail_child<3, SEED>(srcb, seedb, lc, cr, mL, fk, st);
+                g[12] = tail_child<4, SEED>(srcb, seedb, lc, cr, mL, fk, st);
+                g[13] = tail_child<5, SEED>(srcb, seedb, lc, cr, mL, fk, st);
+                g[14] = tail_child<6, SEED>(srcb, seedb, lc, cr, mL, fk, st);
+                g[15] = tail_child<7, SEED>(srcb, seedb, lc, cr, mL, fk, st);
                 split_bwd_batch<4>(tq, 0, 32, g, av, gacc);
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    g[j] = (4 + j < H) ? split_child<SEED>(srcb, seedb, (uint32_t)(c + hoff[4 + j]), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
-                split_bwd_batch<H - 4>(tq, 8, 40, g, av, gacc);
-                // tail modes 0..3, 4..7 (positions from the tail child row)
-                g[0] = mL > 0 ? split_child<SEED>(srcb, seedb, lc + crow16<0>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
-                g[1] = mL > 1 ? split_child<SEED>(srcb, seedb, lc + crow16<1>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
-                g[2] = mL > 2 ? split_child<SEED>(srcb, seedb, lc + crow16<2>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
-                g[3] = mL > 3 ? split_child<SEED>(srcb, seedb, lc + crow16<3>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
-                split_bwd_batch<4>(tq, 16, 48, g, av, gacc);
-                g[0] = mL > 4 ? split_child<SEED>(srcb, seedb, lc + crow16<4>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
-                g[1] = mL > 5 ? split_child<SEED>(srcb, seedb, lc + crow16<5>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
-                g[2] = mL > 6 ? split_child<SEED>(srcb, seedb, lc + crow16<6>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
-                g[3] = mL > 7 ? split_child<SEED>(srcb, seedb, lc + crow16<7>(cr), (uint32_t)a.Fk, a.status) : make_float2(0.f, 0.f);
-                split_bwd_batch<4>(tq, 24, 56, g, av, gacc);
+                split_bwd_batch<H - 4>(tq, 8, 40, g + 4, av, gacc);
+                split_bwd_batch<4>(tq, 16, 48, g + 8, av, gacc);
+                split_bwd_batch<4>(tq, 24, 56, g + 12, av, gacc);
                 Gprevb[(uint32_t)c << 5] = gacc;
             }
         }

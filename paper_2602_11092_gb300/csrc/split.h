@@ -85,8 +85,10 @@ struct SplitBwdArgs {
 
 // Resident blocks per SM the backward kernel's register budget is sized for.
 constexpr int kSplitBwdWarps = 4;
+// 5 (102 registers): the 16 child loads of a parent are all in flight before
+// the tensor-memory batches consume them, which 80 registers (6 blocks) spill
 #ifndef SLOS_SPLIT_BWD_MINB
-#define SLOS_SPLIT_BWD_MINB 6
+#define SLOS_SPLIT_BWD_MINB 5
 #endif
 constexpr int kSplitBwdMinBlocks = SLOS_SPLIT_BWD_MINB;
 
