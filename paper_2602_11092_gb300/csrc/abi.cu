@@ -1711,6 +1711,8 @@ slos_status_t slos_sync_status(slos_plan_t p, void *stream) {
     SLOS_CUDA(cudaStreamSynchronize(s));
     if (h[0] == SLOS_ERR_TIMEOUT)
         return fail(SLOS_ERR_TIMEOUT, "a bounded wait between layers ran out (work item " + std::to_string(h[1]) + ")");
+    if (h[2] != 0)
+        return fail(SLOS_ERR_TIMEOUT, "a tensor-core GEMM wait ran out (role " + std::to_string(h[2]) + ")");
     if (h[0] == kStatusBounds)
         return fail(SLOS_ERR_INTERNAL, "a device bounds check failed: index " + std::to_string(h[1]) +
                                            " past its layer (SLOS_DEBUG build)");

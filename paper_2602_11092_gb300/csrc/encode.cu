@@ -11,9 +11,29 @@
 // plan's fixed-width parent slots; the columns a per-state (s - e_c, c)
 // table.  Then one complex GEMM applies Phi to every input vector of the
 // batch (U is shared by the batch, as the layer's weights are).
+//
+// The GEMM runs on the tensor cores as one real GEMM with K' = 2K:
+//     [Yr | Yi](b, t) = sum_s  xr_s [Ar | Ai](s, t) + xi_s [-Ai | Ar](s, t),
+// x_s = X[b][s] / g_s, A = A_n, its output columns interleaved (2t = re,
+// 2t + 1 = im of output t) so the epilogue forms g_t (Yr + i Yi) and its
+// |.|^2 from adjacent columns of one row.  For FP32-accurate products in TF32
+// (the tensor core reads 10 mantissa bits) every operand value v is split
+// into hi = v rounded to TF32 and lo = v - hi, and the GEMM sums
+// A_hi B_hi + A_hi B_lo + A_lo B_hi (the three-product split-precision
+// scheme; the dropped lo lo term is ~2^-22 of the product), accumulating in
+// FP32, in chunks of 32 MMAs in tensor memory whose sums the epilogue adds
+// in FP32 registers with round-to-nearest (tc_gemm_chunked_kernel: the
+// tensor core's own accumulation over the whole K biased |psi|^2 low by
+// 4e-5).  The batch runs in chunks of kEncodeChunk rows, so the split copy of
+// X needs a fixed workspace.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
+#include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "../../include/slos.h"
@@ -21,6 +41,7 @@
 #include "plan.h"
 #include "profile.h"
 #include "tab_launch.h"
+#include "tc_gemm.cuh"
 
 namespace slos {
 slos_status_t fail(slos_status_t st, const std::string &msg);
@@ -62,62 +83,93 @@ __global__ void __launch_bounds__(kTransferThreads)
     cur[s * Fk + t] = acc;
 }
 
-// out[b][t] = g_t sum_s (X[b][s] / g_s) A[s][t]   (g = sqrt(prod t!));
-// 64 x 64 output tiles, 16 x 16 threads with 4 x 4 outputs each.
-constexpr int kGT = 64, kGK = 16;
+// TF32 split of an FP32 value: hi = v rounded to nearest TF32 (ties away),
+// lo = v - hi (exact in FP32).
+__device__ __forceinline__ void tf32_split(float v, float &hi, float &lo) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+    hi = __uint_as_float(h);
+    lo = v - hi;
+}
 
-__global__ void __launch_bounds__(256) encode_gemm_kernel(const float2 *X, const float2 *A, const float *g, int B,
-                                                          int64_t K, int probs, void *out) {
-    __shared__ float2 xs[kGT][kGK + 1];
-    __shared__ float2 as[kGK][kGT + 1];
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
-    const int64_t b0 = (int64_t)blockIdx.y * kGT, t0 = (int64_t)blockIdx.x * kGT;
-    float2 acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
-    for (int64_t k0 = 0; k0 < K; k0 += kGK) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int idx = tid + r * 256;  // 1024 = 64 x 16 elements of each tile
-            const int xr = idx / kGK, xc = idx % kGK;
-            const int64_t bb = b0 + xr, ss = k0 + xc;
-            float2 v = make_float2(0.f, 0.f);
-            if (bb < B && ss < K) v = cscale(X[bb * K + ss], 1.f / __ldg(g + ss));
-            xs[xr][xc] = v;
-            const int ar = idx / kGT, ac = idx % kGT;
-            const int64_t sa = k0 + ar, ta = t0 + ac;
-            as[ar][ac] = (sa < K && ta < K) ? A[sa * K + ta] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kGK; ++kk) {
-            float2 xv[4], av[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) xv[i] = xs[ty + 16 * i][kk];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) av[j] = as[kk][tx + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = cfma(xv[i], av[j], acc[i][j]);
-        }
-        __syncthreads();
+constexpr int kEncodeChunk = 4096;  // batch rows per GEMM launch
+constexpr int kEncodeKAlign = 32;   // K' padded to whole 128-byte TF32 stage rows
+
+// Real-form operand B of the GEMM, [N = 2K rows][K2 cols], K-major:
+//   row 2t:     cols s -> Ar[s][t],  K + s -> -Ai[s][t]
+//   row 2t + 1: cols s -> Ai[s][t],  K + s ->  Ar[s][t]
+// split into hi and lo copies; 32 x 32 tiles of A through shared memory, so
+// both the read (along t) and the writes (along s) are coalesced.
+__global__ void __launch_bounds__(256) encode_split_b_kernel(const float2 *A, int64_t K, int64_t K2, float *bhi,
+                                                             float *blo) {
+    __shared__ float2 tile[32][33];
+    const int64_t s0 = (int64_t)blockIdx.y * 32, t0 = (int64_t)blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t ss = s0 + i, tt = t0 + threadIdx.x;
+        tile[i][threadIdx.x] = (ss < K && tt < K) ? A[ss * K + tt] : make_float2(0.f, 0.f);
     }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t tt = t0 + i, ss = s0 + threadIdx.x;
+        if (tt >= K || ss >= K) continue;
+        const float2 v = tile[threadIdx.x][i];  // A[ss][tt]
+        const float vals[4] = {v.x, -v.y, v.y, v.x};  // (2t, s), (2t, K+s), (2t+1, s), (2t+1, K+s)
+        const int64_t o[4] = {2 * tt * K2 + ss, 2 * tt * K2 + K + ss, (2 * tt + 1) * K2 + ss, (2 * tt + 1) * K2 + K + ss};
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t bb = b0 + ty + 16 * i;
-        if (bb >= B) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t tt = t0 + tx + 16 * j;
-            if (tt >= K) continue;
-            const float2 v = cscale(acc[i][j], __ldg(g + tt));
-            if (probs) reinterpret_cast<float *>(out)[bb * K + tt] = v.x * v.x + v.y * v.y;
-            else reinterpret_cast<float2 *>(out)[bb * K + tt] = v;
+        for (int q = 0; q < 4; ++q) {
+            float h, l;
+            tf32_split(vals[q], h, l);
+            bhi[o[q]] = h;
+            blo[o[q]] = l;
         }
     }
+}
+
+// Real-form operand A of the GEMM for batch rows [b0, b0 + rows):
+// [rows][K2], cols s -> Re X[b][s] / g_s, K + s -> Im X[b][s] / g_s, the
+// padding columns 2K .. K2-1 zero; split into hi and lo copies.
+__global__ void __launch_bounds__(256) encode_split_a_kernel(const float2 *X, const float *g, int64_t b0, int rows,
+                                                             int64_t K, int64_t K2, float *ahi, float *alo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)rows * K2) return;
+    const int64_t r = i / K2, c = i % K2;
+    float v = 0.f;
+    if (c < 2 * K) {
+        const int64_t ss = c < K ? c : c - K;
+        const float2 x = X[(b0 + r) * K + ss];
+        v = (c < K ? x.x : x.y) / __ldg(g + ss);
+    }
+    float h, l;
+    tf32_split(v, h, l);
+    ahi[i] = h;
+    alo[i] = l;
+}
+
+// FP32 matrix [rows][cols] (row stride ld elements, a multiple of 4), box
+// 32 x box_rows, 128-byte swizzle: the TF32 operand layout of tc_gemm.cuh.
+static PFN_cuTensorMapEncodeTiled_v12000 encode_map_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *q = nullptr;
+        cudaDriverEntryPointQueryResult r;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &q, 12000, cudaEnableDefault, &r) ==
+                cudaSuccess &&
+            r == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(q);
+    });
+    return fn;
+}
+static bool make_map_f32(CUtensorMap *map, const float *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+    auto fn = encode_map_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+    cuuint32_t box[2] = {(cuuint32_t)tc::TcKind<1>::kElems, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 static bool encodable(const slos_plan_s *p) {
@@ -129,11 +181,19 @@ static bool encodable(const slos_plan_s *p) {
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+static int64_t encode_k2(const slos_plan_s *p) {
+    return (2 * p->K + kEncodeKAlign - 1) / kEncodeKAlign * kEncodeKAlign;
+}
+
+// workspace: the transfer matrices of layers n and n-1, then the split
+// operands B_hi, B_lo [2K][K2] and A_hi, A_lo [kEncodeChunk][K2]
 static size_t encode_bytes(const slos_plan_s *p) {
     const int n = p->n;
     const size_t a = (size_t)p->F[n] * p->F[n] * sizeof(float2);
     const size_t b = n >= 2 ? (size_t)p->F[n - 1] * p->F[n - 1] * sizeof(float2) : 0;
-    return align256(a) + align256(b);
+    const size_t bs = (size_t)2 * p->K * encode_k2(p) * sizeof(float);
+    const size_t as = (size_t)kEncodeChunk * encode_k2(p) * sizeof(float);
+    return align256(a) + align256(b) + 2 * align256(bs) + 2 * align256(as);
 }
 
 }  // namespace slos
@@ -160,7 +220,6 @@ slos_status_t slos_encoded_forward(slos_plan_t p, const void *U, const void *X, 
     if (batch < 0) return fail(SLOS_ERR_INVALID_ARG, "slos_encoded_forward: negative batch");
     if (output != SLOS_OUT_PROBS && output != SLOS_OUT_AMPS)
         return fail(SLOS_ERR_INVALID_ARG, "slos_encoded_forward: bad output");
-    if (batch > 65535 * kGT) return fail(SLOS_ERR_UNSUPPORTED, "slos_encoded_forward: batch too large");
     if (!U || (batch > 0 && (!X || !out))) return fail(SLOS_ERR_INVALID_ARG, "slos_encoded_forward: NULL pointer");
     if (!workspace || workspace_bytes < encode_bytes(p))
         return fail(SLOS_ERR_INVALID_ARG, "slos_encoded_forward: workspace too small (slos_encoded_workspace_bytes)");
@@ -189,13 +248,65 @@ slos_status_t slos_encoded_forward(slos_plan_t p, const void *U, const void *X, 
         }
     }
     if (batch == 0) return SLOS_OK;
-    const int64_t K = p->K;
-    ProfScope ps("slos_encode_gemm", 0.0, s);
-    dim3 grid((unsigned)((K + kGT - 1) / kGT), (unsigned)((batch + kGT - 1) / kGT));
-    encode_gemm_kernel<<<grid, dim3(16, 16), 0, s>>>(reinterpret_cast<const float2 *>(X), buf[0], p->tab.gfact, batch,
-                                                     K, output == SLOS_OUT_PROBS, out);
-    if ((e = cudaGetLastError()) != cudaSuccess)
-        return fail(SLOS_ERR_CUDA, std::string("slos_encoded_forward: ") + cudaGetErrorString(e));
+    const int64_t K = p->K, K2 = encode_k2(p);
+    const size_t bs = (size_t)2 * K * K2 * sizeof(float), as = (size_t)kEncodeChunk * K2 * sizeof(float);
+    char *w = ws + align256((size_t)p->F[n] * p->F[n] * sizeof(float2)) +
+              (n >= 2 ? align256((size_t)p->F[n - 1] * p->F[n - 1] * sizeof(float2)) : 0);
+    float *bhi = reinterpret_cast<float *>(w), *blo = reinterpret_cast<float *>(w + align256(bs));
+    float *ahi = reinterpret_cast<float *>(w + 2 * align256(bs));
+    float *alo = reinterpret_cast<float *>(w + 2 * align256(bs) + align256(as));
+    {
+        ProfScope ps("slos_encode_split", 0.0, s);
+        // B's padding columns stay zero: clear both copies, then fill
+        if ((e = cudaMemsetAsync(bhi, 0, 2 * align256(bs), s)) != cudaSuccess)
+            return fail(SLOS_ERR_CUDA, std::string("slos_encoded_forward: ") + cudaGetErrorString(e));
+        dim3 grid((unsigned)((K + 31) / 32), (unsigned)((K + 31) / 32));
+        encode_split_b_kernel<<<grid, dim3(32, 8), 0, s>>>(buf[0], K, K2, bhi, blo);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return fail(SLOS_ERR_CUDA, std::string("slos_encoded_forward: ") + cudaGetErrorString(e));
+    }
+    static bool attr_done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        if ((e = cudaFuncSetAttribute(tc::tc_gemm_chunked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tc::kCkSmem)) != cudaSuccess)
+            return fail(SLOS_ERR_CUDA, std::string("slos_encoded_forward: ") + cudaGetErrorString(e));
+        attr_done[dev] = true;
+    }
+    CUtensorMap mah, mal, mbh, mbl;
+    if (!make_map_f32(&mbh, bhi, 2 * K, K2, K2, tc::kCkBN) || !make_map_f32(&mbl, blo, 2 * K, K2, K2, tc::kCkBN) ||
+        !make_map_f32(&mah, ahi, kEncodeChunk, K2, K2, tc::BM) || !make_map_f32(&mal, alo, kEncodeChunk, K2, K2, tc::BM))
+        return fail(SLOS_ERR_CUDA, "slos_encoded_forward: cuTensorMapEncodeTiled failed");
+    const float2 *Xd = reinterpret_cast<const float2 *>(X);
+    for (int b0 = 0; b0 < batch; b0 += kEncodeChunk) {
+        const int rows = std::min(kEncodeChunk, batch - b0);
+        {
+            ProfScope ps("slos_encode_split", 0.0, s);
+            const int64_t cnt = (int64_t)rows * K2;
+            encode_split_a_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(Xd, p->tab.gfact, b0, rows, K, K2,
+                                                                                 ahi, alo);
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                return fail(SLOS_ERR_CUDA, std::string("slos_encoded_forward: ") + cudaGetErrorString(e));
+        }
+        tc::TcArgs g;
+        memset(&g, 0, sizeof(g));
+        g.M = rows;
+        g.N = (int)(2 * K);
+        g.K = (int)K2;
+        g.ldc = (int)K;
+        g.C = output == SLOS_OUT_AMPS ? (void *)(reinterpret_cast<float2 *>(out) + (int64_t)b0 * K)
+                                      : (void *)(reinterpret_cast<float *>(out) + (int64_t)b0 * K);
+        g.colscale = p->tab.gfact;
+        g.amps = output == SLOS_OUT_AMPS ? 1 : 0;
+        g.err = p->d_status + 2;
+        const int64_t tiles = (int64_t)((g.N + tc::kCkBN - 1) / tc::kCkBN) * ((rows + tc::BM - 1) / tc::BM);
+        const unsigned grid = (unsigned)std::min<int64_t>(tiles, p->sm_count);
+        ProfScope ps("slos_encode_gemm", 3.0 * 2.0 * rows * (double)g.N * (double)K2, s);  // flops
+        tc::tc_gemm_chunked_kernel<<<grid, tc::kCkThreads, tc::kCkSmem, s>>>(mah, mbh, mal, mbl, g);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return fail(SLOS_ERR_CUDA, std::string("slos_encoded_forward: ") + cudaGetErrorString(e));
+    }
     return SLOS_OK;
 }
 

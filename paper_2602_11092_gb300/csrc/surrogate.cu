@@ -134,6 +134,8 @@ slos_status_t gemm(int epi, int M, int N, int K, const __nv_bfloat16 *A, int64_t
     g.bias = bias;
     g.aux = aux;
     g.err = err_ptr();
+    g.colscale = nullptr;
+    g.amps = 0;
     // persistent CTAs, one per SM (the shared-memory ring allows no second)
     const int64_t tiles = (int64_t)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
     const unsigned grid = (unsigned)std::min<int64_t>(tiles, sm_count());

@@ -1,5 +1,9 @@
 // Tensor-core GEMM for sm_103a: C[M][N] = A[M][K] . B[N][K]^T, BF16 inputs
 // (both K-major), FP32 accumulation in tensor memory (TMEM), fused epilogues.
+// tc_gemm_chunked_kernel (end of the file) takes TF32 operands (FP32
+// storage, the tensor core reads 19 bits of each): a stage row is 128 bytes
+// either way (64 BF16 or 32 FP32 elements), four MMAs of 32 bytes of K each
+// (K = 16 or 8), so the ring, the swizzle and the descriptors are the same.
 // Two kernels share the pipeline below: tc_gemm_kernel (one tile per CTA) and
 // tc_gemm_persist_kernel (one CTA per SM over many tiles, two accumulators,
 // the epilogue of one tile overlapping the next tile's MMAs), which the
@@ -42,6 +46,8 @@ enum TcEpi : int {
     TC_GELU = 2,       // Z = acc + bias[n] (bf16, aux), C = gelu(Z) (bf16)
     TC_GELU_BWD = 3,   // C = acc * gelu'(Z), Z = aux (bf16 in), C bf16
     TC_F32_ACCUM = 4,  // C += acc                        (float)
+    TC_ENCODE = 5,     // columns (2t, 2t+1) = (re, im) of output t: psi = colscale[t] (re + i im);
+                       //   C float |psi|^2, or complex64 psi when amps (row stride ldc outputs)
 };
 
 struct TcArgs {
@@ -51,6 +57,8 @@ struct TcArgs {
     const float *bias;    // [N]
     __nv_bfloat16 *aux;   // [M][ldc] (Z for TC_GELU out, TC_GELU_BWD in)
     int *err;             // error word (device)
+    const float *colscale;  // TC_ENCODE: [N / 2]
+    int amps;               // TC_ENCODE: complex64 output
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -114,6 +122,12 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
         : "memory");
 }
+// Operand kinds: 0 = BF16, 1 = TF32; elements per 128-byte stage row.
+template <int KIND>
+struct TcKind {
+    static constexpr int kElems = KIND == 0 ? 64 : 32;
+};
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -151,6 +165,21 @@ __device__ __forceinline__ float gelu_grad(float z) {
 // accumulator values of row `row`, columns col0 .. col0 + 15.
 template <int EPI>
 __device__ __forceinline__ void tc_store16(const TcArgs &g, int row, int col0, float (&v)[16], bool vec) {
+    if (EPI == TC_ENCODE) {
+        if (row < g.M) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int t = col0 / 2 + i;
+                if (2 * t >= g.N) break;
+                const float c = g.colscale[t];
+                const float re = v[2 * i] * c, im = v[2 * i + 1] * c;
+                const int64_t o = (int64_t)row * g.ldc + t;
+                if (g.amps) reinterpret_cast<float2 *>(g.C)[o] = make_float2(re, im);
+                else reinterpret_cast<float *>(g.C)[o] = re * re + im * im;
+            }
+        }
+        return;
+    }
     if (row < g.M && col0 < g.N) {
         const int64_t o0 = (int64_t)row * g.ldc + col0;
         if (EPI == TC_F32_BIAS || EPI == TC_GELU) {
@@ -474,6 +503,210 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kPersistTmemCols)
                      : "memory");
+    }
+}
+
+}  // namespace tc
+}  // namespace slos
+
+namespace slos {
+namespace tc {
+
+// ---------------------------------------------------------------- chunked accumulation
+// tc_gemm_chunked_kernel: the persistent pipeline (128 x 256 tiles) with the
+// K sum taken in chunks of kChunkStages stages.  The tensor core's FP32
+// accumulation does not round to nearest: over the ~1500 MMAs of a long K its
+// errors pile up in one direction (measured: |psi|^2 of the amplitude-encoding
+// GEMM biased low by 4e-5 at K' = 3 x 4032).  Here each chunk accumulates
+// into one of two TMEM buffers while the epilogue warps move the other
+// buffer's finished chunk into FP32 registers (half a row, 128 columns, per
+// thread; round-to-nearest adds), so a truncation bias builds up only within
+// one chunk.  Roles: warp 0 TMA producer, warp 1 MMA issuer, warps 2-9
+// epilogue (TMEM lane quarter = warp % 4, columns 0-127 for warps 2-5 and
+// 128-255 for warps 6-9).  Waits are bounded as above.
+constexpr int kCkBN = 256;
+constexpr int kCkStages = 4;
+constexpr int kChunkStages = 8;  // 32 MMAs per chunk
+constexpr int kCkThreads = 320;
+constexpr int kCkEpiWarps = 8;
+constexpr int kCkATile = BM * 128, kCkBTile = kCkBN * 128;  // bytes: 128-byte rows
+constexpr int kCkStageBytes = kCkATile + kCkBTile;
+constexpr int kCkSmem = kCkStages * kCkStageBytes + 1024 + 256;
+constexpr uint32_t kCkTmemCols = 2 * kCkBN;
+// kind::tf32: A and B TF32 (bits 7-9 = 2, 10-12 = 2), otherwise as kIdesc.
+constexpr uint32_t kIdescTf32 =
+    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kCkBN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdescTf32), "r"(accumulate)
+        : "memory");
+}
+
+// TF32 operands in three K segments, A_hi B_hi + A_hi B_lo + A_lo B_hi, each
+// segment's tiles taken from the hi or lo copy of an operand (the
+// three-TF32-product scheme for FP32-accurate products); TC_ENCODE epilogue.
+static __global__ void __launch_bounds__(kCkThreads, 1)
+    tc_gemm_chunked_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                           const __grid_constant__ CUtensorMap ta_lo, const __grid_constant__ CUtensorMap tb_lo,
+                           TcArgs g) {
+    constexpr int KE = TcKind<1>::kElems;
+    extern __shared__ uint8_t smem_tc[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_tc) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = base;
+    uint8_t *sB = base + kCkStages * kCkATile;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + kCkStages * kCkBTile);
+    uint64_t *empty = full + kCkStages;
+    uint64_t *cfull = empty + kCkStages;  // [2] a chunk's MMAs are done
+    uint64_t *cempty = cfull + 2;         // [2] the epilogue has taken the chunk
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk1 = (g.K + KE - 1) / KE;
+    const int nk = 3 * nk1;
+    const int nchunks = (nk + kChunkStages - 1) / kChunkStages;
+    const int ntn = (g.N + kCkBN - 1) / kCkBN;
+    const int ntiles = ((g.M + BM - 1) / BM) * ntn;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kCkStages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(cfull + a, 1);
+            mbar_init(cempty + a, kCkEpiWarps);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kCkTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: every stage of every tile, in order
+            uint32_t it = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                const int m0 = (t / ntn) * BM, n0 = (t % ntn) * kCkBN;
+                for (int kt = 0; kt < nk; ++kt, ++it) {
+                    const int s = it % kCkStages;
+                    const uint32_t ph = (it / kCkStages) & 1;
+                    if (it >= (uint32_t)kCkStages && !mbar_wait(empty + s, ph ^ 1)) {
+                        atomicExch(g.err, 1);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    mbar_expect_tx(full + s, kCkStageBytes);
+                    const int seg = kt / nk1;  // 0: A_hi B_hi, 1: A_hi B_lo, 2: A_lo B_hi
+                    const int kx = (kt - seg * nk1) * KE;
+                    tma_load_2d(sA + s * kCkATile, seg == 2 ? &ta_lo : &ta, kx, m0, full + s);
+                    tma_load_2d(sB + s * kCkBTile, seg == 1 ? &tb_lo : &tb, kx, n0, full + s);
+                }
+            }
+            for (uint32_t q = (it > (uint32_t)kCkStages ? it - kCkStages : 0); q < it; ++q)
+                mbar_wait(full + (q % kCkStages), (q / kCkStages) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: chunk c of the CTA's walk goes to buffer c & 1
+            uint32_t it = 0, c = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                for (int ch = 0; ch < nchunks && !*abort_flag; ++ch, ++c) {
+                    const int b = c & 1;
+                    const uint32_t use = c >> 1;
+                    if (use > 0 && !mbar_wait(cempty + b, (use - 1) & 1)) {
+                        atomicExch(g.err, 4);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(b * kCkBN);
+                    const int k1 = min(nk, (ch + 1) * kChunkStages);
+                    for (int kt = ch * kChunkStages; kt < k1; ++kt, ++it) {
+                        const int s = it % kCkStages;
+                        const uint32_t ph = (it / kCkStages) & 1;
+                        if (*abort_flag || !mbar_wait(full + s, ph)) {
+                            atomicExch(g.err, 2);
+                            *abort_flag = 1;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(sA + s * kCkATile), b0 = smem_u32(sB + s * kCkBTile);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_tf32(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32),
+                                     (kt > ch * kChunkStages || kk > 0) ? 1u : 0u);
+                        mma_commit(empty + s);
+                    }
+                    if (*abort_flag) break;
+                    mma_commit(cfull + b);
+                }
+            }
+        }
+    } else {
+        // epilogue warps: each thread sums 128 columns of its row over the chunks
+        constexpr int HC = kCkBN / 2;
+        const int q = warp & 3;
+        const int hc = (warp - 2) >> 2;  // column half
+        uint32_t c = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            float acc[HC];
+#pragma unroll
+            for (int i = 0; i < HC; ++i) acc[i] = 0.f;
+            for (int ch = 0; ch < nchunks; ++ch, ++c) {
+                const int b = c & 1;
+                ok = __all_sync(0xffffffffu, !*abort_flag && mbar_wait(cfull + b, (c >> 1) & 1));
+                if (!ok) {
+                    if (lane == 0) {
+                        atomicExch(g.err, 3);
+                        *abort_flag = 1;
+                    }
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t src = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kCkBN + hc * HC);
+#pragma unroll
+                for (int c16 = 0; c16 < HC; c16 += 16) {
+                    float v[16];
+                    tmem_ld16(src + (uint32_t)c16, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) acc[c16 + i] += v[i];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(cempty + b);
+            }
+            if (!ok) break;
+            const int m0 = (t / ntn) * BM, n0 = (t % ntn) * kCkBN + hc * HC;
+            const int row = m0 + q * 32 + lane;
+#pragma unroll
+            for (int c16 = 0; c16 < HC; c16 += 16) {
+                float v[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = acc[c16 + i];
+                tc_store16<TC_ENCODE>(g, row, n0 + c16, v, false);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCkTmemCols) : "memory");
     }
 }
 

@@ -40,6 +40,31 @@ def test_encoded_amplitudes_match_oracle(slos, m, n, space, B):
         assert np.abs(probs.sum(axis=1) - 1.0).max() <= 1e-4
 
 
+@pytest.mark.parametrize("m,n,B", [(8, 4, 4100), (10, 4, 130), (12, 2, 9000)])
+def test_encoded_tensor_core_gemm_chunks_and_ragged_tiles(slos, m, n, B):
+    """The GEMM runs on the tensor cores in TF32 with the three-product split
+    (batch chunks of 4096 rows, 128 x 256 output tiles over (re, im)
+    interleaved columns): batches past one chunk, output counts that leave a
+    partial tile (2K = 660, 1430, 156 columns), every row and output against
+    the oracle within the FP32 tolerance."""
+    rng = np.random.default_rng(300 + m + n)
+    plan = slos.Plan(m, [n] + [0] * (m - 1))
+    basis = oracle.enumerate_fock(m, n)
+    K = plan.n_outputs
+    U = workloads.haar_unitaries(m, 1, rng)[0].astype(np.complex64)
+    X = rand_states(rng, B, K)
+    Ut, Xt = torch.tensor(U, device="cuda"), torch.tensor(X, device="cuda")
+    amps = plan.encoded_forward(Ut, Xt, slos.AMPS)
+    probs = plan.encoded_forward(Ut, Xt, slos.PROBS)
+    plan.sync_status()
+    ref = oracle.encoded_amplitudes(U.astype(np.complex128), X.astype(np.complex128), basis)
+    assert np.abs(amps.cpu().numpy() - ref).max() <= P_TOL
+    p = probs.cpu().numpy()
+    assert np.abs(p - np.abs(ref) ** 2).max() <= P_TOL
+    assert 0.5 * np.abs(p - np.abs(ref) ** 2).sum(axis=1).max() <= 1e-5
+    assert torch.equal(probs, plan.encoded_forward(Ut, Xt, slos.PROBS))  # fixed summation order
+
+
 def test_encoded_basis_state_equals_plain_forward(slos):
     """x = |s> reproduces slos_forward's amplitudes for input s."""
     m, s = 10, [1, 0, 2, 0, 1, 0, 0, 0, 0, 0]
