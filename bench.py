@@ -720,7 +720,7 @@ def run_extras(B, dev, peak_hbm, args):
                                  "value": 4096 / (mse * 1e-3), "unit": "distributions/s", "ms_per_batch": mse,
                                  "gemm_tflops": 8.0 * 4096 * Ke * Ke / (mse * 1e-3) / 1e12,
                                  "gemm_ms": gemm_ms,
-                                 "tensor": {"bound": "tensor", "kernel": "tc_gemm_persist_kernel<TC_ENCODE, TF32, split>",
+                                 "tensor": {"bound": "tensor", "kernel": "tc_gemm_chunked_kernel (TF32, three-product split)",
                                             "achieved_tflops": tensor_tf, "peak_tflops": tf32_peak,
                                             "frac": (tensor_tf / tf32_peak) if tensor_tf else None,
                                             "peak_kind": "measured bf16 burst x nominal tf32/bf16 (1.1/2.25)",
