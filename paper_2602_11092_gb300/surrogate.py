@@ -246,58 +246,69 @@ class SurrogateLayer:
               max_fail_rate: float = 0.01, confidence: float = 0.99):
         """Surrogate outputs with the exact path as arbiter.
 
-        1. Screen every sample: its per-mode mean photon numbers against the
-           exact ones (closed form); a screened-out sample provably has
-           TV > tv_tol.
-        2. Spot-check a seeded fraction rho exactly and bound the batch's
-           failure rate (TV > tv_tol) from above at the given confidence.
-        3. If that bound exceeds max_fail_rate, the whole batch takes the exact
-           path.  Otherwise every screened-out or failed sample takes it and
-           the rest keep the surrogate.
+        1. Spot-check first: a seeded fraction rho of the samples runs through
+           both the surrogate and the exact path, and the batch's failure
+           rate (TV > tv_tol) is bounded from above at the given confidence.
+        2. If that bound exceeds max_fail_rate, the whole batch takes the exact
+           path; the surrogate never runs on the rest.
+        3. Otherwise the surrogate runs on every sample, and every sample is
+           screened: its per-mode mean photon numbers against the exact ones
+           (closed form); a screened-out sample provably has TV > tv_tol.
+           Screened-out and failed samples take the exact path (a failed
+           checked sample keeps its exact row), the rest keep the surrogate.
 
         Every returned row is therefore exact, or belongs to a batch whose
         unchecked rows exceed tv_tol at a rate <= max_fail_rate (with
-        probability >= confidence)."""
+        probability >= confidence).  When the surrogate cannot meet the bound
+        the call costs the exact path plus the checked fraction."""
         L = lib()
         Bn = data.shape[0]
-        q = self.model.forward(data)
-        U = B.mesh_unitary(self.m, self.theta, data, Bn)
-        flag = torch.zeros(Bn, dtype=torch.int32, device=self.device)
-        marg = torch.empty((Bn, self.m), dtype=torch.float32, device=self.device)
-        s_host = (ctypes.c_int * self.m)(*self.s)
-        B._check(L.surr_screen(B._ptr(q), Bn, self.K, B._ptr(self.occ), self.m, B._ptr(U), s_host,
-                               2.0 * self.n * tv_tol, B._ptr(marg), B._ptr(flag), B._stream()))
         rng = self._np.random.default_rng(seed)
         n_chk = max(1, int(round(rho * Bn)))
         chk = torch.tensor(self._np.sort(rng.choice(Bn, size=n_chk, replace=False)), dtype=torch.int32,
                            device=self.device)
         dchk = torch.empty((n_chk, self.m), dtype=torch.float32, device=self.device)
         B._check(L.surr_gather_rows(B._ptr(data), B._ptr(chk), n_chk, self.m, B._ptr(dchk), B._stream()))
+        qchk = self.model.forward(dchk)
         pchk = self.exact(dchk)
+        ident = torch.arange(n_chk, dtype=torch.int32, device=self.device)
         tv = torch.empty(n_chk, dtype=torch.float32, device=self.device)
-        B._check(L.surr_tv_rows(B._ptr(q), B._ptr(chk), B._ptr(pchk), n_chk, self.K, B._ptr(tv), B._stream()))
+        B._check(L.surr_tv_rows(B._ptr(qchk), B._ptr(ident), B._ptr(pchk), n_chk, self.K, B._ptr(tv), B._stream()))
         # decisions on the host
-        fl = flag.cpu().numpy().astype(bool)
         tvh = tv.cpu().numpy()
         ch = chk.cpu().numpy()
         failed = int((tvh > tv_tol).sum())
         ucb = self.failure_rate_bound(failed, n_chk, confidence)
         batch_fallback = ucb > max_fail_rate
+        screened = None
         if batch_fallback:
-            self.exact(data, out=q)
+            q = self.exact(data)
             bad = self._np.arange(Bn)
         else:
-            fl[ch[tvh > tv_tol]] = True
-            bad = self._np.nonzero(fl)[0]
-            if bad.size:
-                rows = torch.tensor(bad, dtype=torch.int32, device=self.device)
-                dbad = torch.empty((bad.size, self.m), dtype=torch.float32, device=self.device)
-                B._check(L.surr_gather_rows(B._ptr(data), B._ptr(rows), bad.size, self.m, B._ptr(dbad),
+            q = self.model.forward(data)
+            U = B.mesh_unitary(self.m, self.theta, data, Bn)
+            flag = torch.zeros(Bn, dtype=torch.int32, device=self.device)
+            marg = torch.empty((Bn, self.m), dtype=torch.float32, device=self.device)
+            s_host = (ctypes.c_int * self.m)(*self.s)
+            B._check(L.surr_screen(B._ptr(q), Bn, self.K, B._ptr(self.occ), self.m, B._ptr(U), s_host,
+                                   2.0 * self.n * tv_tol, B._ptr(marg), B._ptr(flag), B._stream()))
+            fl = flag.cpu().numpy().astype(bool)
+            screened = int(fl.sum())
+            # checked samples keep their exact rows; screened-out ones are recomputed
+            B._check(L.surr_scatter_rows(B._ptr(pchk), B._ptr(chk), n_chk, self.K, B._ptr(q), B._stream()))
+            fl[ch] = False
+            redo = self._np.nonzero(fl)[0]
+            if redo.size:
+                rows = torch.tensor(redo, dtype=torch.int32, device=self.device)
+                dbad = torch.empty((redo.size, self.m), dtype=torch.float32, device=self.device)
+                B._check(L.surr_gather_rows(B._ptr(data), B._ptr(rows), redo.size, self.m, B._ptr(dbad),
                                             B._stream()))
                 pbad = self.exact(dbad)
-                B._check(L.surr_scatter_rows(B._ptr(pbad), B._ptr(rows), bad.size, self.K, B._ptr(q), B._stream()))
-        stats = {"batch": Bn, "screen_flagged": int(flag.sum().item()), "checked": n_chk, "check_failed": failed,
+                B._check(L.surr_scatter_rows(B._ptr(pbad), B._ptr(rows), redo.size, self.K, B._ptr(q), B._stream()))
+            bad = self._np.union1d(redo, ch[tvh > tv_tol])
+        stats = {"batch": Bn, "screen_flagged": screened, "checked": n_chk, "check_failed": failed,
                  "fail_rate_ucb": ucb, "max_fail_rate": max_fail_rate, "confidence": confidence,
                  "batch_fallback": bool(batch_fallback), "fallback": int(bad.size),
-                 "fallback_rate": float(bad.size / Bn), "checked_tv_max": float(tvh.max())}
+                 "fallback_rate": float(bad.size / Bn), "checked_tv_max": float(tvh.max()),
+                 "surrogate_rows": n_chk + (0 if batch_fallback else Bn)}
         return q, stats
