@@ -797,8 +797,8 @@ def run_extras(B, dev, peak_hbm, args):
         exact_s = time.perf_counter() - t0
         out["surrogate"] = {
             "workload": "BF16 MLP 288 -> 4x2048 GELU -> 12376 softmax on the m=12 n=6 layer, trained on "
-                        f"{args.surrogate_samples} exact distributions; inference batch 65536, spot check 1/64 "
-                        "(1024 rows); the batch takes the exact path unless the 99 % upper bound on its rate of "
+                        f"{args.surrogate_samples} exact distributions; inference batch 65536, spot check of 1/64 "
+                        "(1024 rows) first; the batch takes the exact path unless the 99 % upper bound on its rate of "
                         "rows with TV > 0.02 is <= 1 %, screened-out and failed rows always do",
             "train_s": train_s, "train_loss": hist, "heldout_tv": ev, "inference": st,
             "guarantee": "every returned row is exact, or its batch passed the spot check (rate of rows with "
