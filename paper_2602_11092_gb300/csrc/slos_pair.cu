@@ -75,20 +75,28 @@ __device__ __forceinline__ void tm_ld4(uint32_t taddr, uint32_t (&r)[4]) {
 }
 // waits for the thread's outstanding tcgen05.ld; naming the loaded registers
 // keeps every use of them after the wait
+// waits again, naming one more group of 4 loaded registers (a wait covers
+// every prior load, so the extra waits return at once)
+__device__ __forceinline__ void tm_wait_tie4(uint32_t (&r)[4]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]));
+}
 template <int N>
 __device__ __forceinline__ void tm_wait_ld4(uint32_t (&r)[N][4]) {
-    static_assert(N == 4 || N == 6 || N == 8 || N == 12, "slot counts");
-    if constexpr (N == 4) {
+    static_assert(N == 4 || N == 5 || N == 6 || N == 7 || N == 8 || N == 12, "slot counts");
+
+    if constexpr (N == 4 || N == 5) {
         asm volatile("tcgen05.wait::ld.sync.aligned;"
                      : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[1][0]), "+r"(r[1][1]),
                        "+r"(r[1][2]), "+r"(r[1][3]), "+r"(r[2][0]), "+r"(r[2][1]), "+r"(r[2][2]), "+r"(r[2][3]),
                        "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[3][2]), "+r"(r[3][3]));
-    } else if constexpr (N == 6) {
+        if constexpr (N == 5) tm_wait_tie4(r[4]);
+    } else if constexpr (N == 6 || N == 7) {
         asm volatile("tcgen05.wait::ld.sync.aligned;"
                      : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[1][0]), "+r"(r[1][1]),
                        "+r"(r[1][2]), "+r"(r[1][3]), "+r"(r[2][0]), "+r"(r[2][1]), "+r"(r[2][2]), "+r"(r[2][3]),
                        "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[3][2]), "+r"(r[3][3]), "+r"(r[4][0]), "+r"(r[4][1]),
                        "+r"(r[4][2]), "+r"(r[4][3]), "+r"(r[5][0]), "+r"(r[5][1]), "+r"(r[5][2]), "+r"(r[5][3]));
+        if constexpr (N == 7) tm_wait_tie4(r[6]);
     } else {
         // 8 or 12 slots: wait in two calls of 4 / 6 named groups (a wait covers every prior load)
         asm volatile("tcgen05.wait::ld.sync.aligned;"
@@ -277,8 +285,12 @@ __global__ void __launch_bounds__(kPairThreads, kPairMinBlocks) slos_fwd_pair_ke
                 } else if (kSkip && e[4] == kSlotEmpty) {
                     // at most 4 occupied modes
                     pair_sum<4>(e, prevh, tq, cmask, keep, (uint32_t)a.Fprev, a.status, acc0, acc1);
+                } else if (kSkip && e[5] == kSlotEmpty) {
+                    pair_sum<5>(e, prevh, tq, cmask, keep, (uint32_t)a.Fprev, a.status, acc0, acc1);
                 } else if (kSkip && e[6] == kSlotEmpty) {
                     pair_sum<6>(e, prevh, tq, cmask, keep, (uint32_t)a.Fprev, a.status, acc0, acc1);
+                } else if (kSkip && e[7] == kSlotEmpty) {
+                    pair_sum<7>(e, prevh, tq, cmask, keep, (uint32_t)a.Fprev, a.status, acc0, acc1);
                 } else {
                     pair_sum<KW>(e, prevh, tq, cmask, keep, (uint32_t)a.Fprev, a.status, acc0, acc1);
                 }
