@@ -590,7 +590,9 @@ def uneven_bench(B, dev, stream, max_fock=None, reps=5, with_oracle=False):
     for it in inst:
         key = (it.m, it.n, it.threshold, tuple(it.s))
         groups[key] = groups.get(key, 0) + 1
+    # lane groups of 16 instances, a shape's last group of at most 8 instances 8 wide
     lane_groups = sum((c + 15) // 16 for c in groups.values())
+    lanes = sum(16 * (c // 16) + (0 if c % 16 == 0 else (8 if c % 16 <= 8 else 16)) for c in groups.values())
     hbm, hbm_kind = peaks()
     oracle_s = uneven_oracle_seconds(inst, Us) if with_oracle else None
     wl = (f"{len(inst)} instances, m in 8..20, n in 2..min(10, m/2), threshold for m>=16, one persistent launch"
@@ -602,8 +604,8 @@ def uneven_bench(B, dev, stream, max_fock=None, reps=5, with_oracle=False):
                       "unit": "GB/s", "frac": lb / (msb * 1e-3) / 1e9 / hbm, "peak_kind": hbm_kind, "traffic": None,
                       "bytes_per_launch": lb,
                       "bytes": "per instance: 16 B x sum_{k<n} |F_k| (each layer written and read once) + 4 B x outputs"},
-         "lane_fill": {"instances": len(inst), "lane_groups": lane_groups,
-                       "frac": len(inst) / (16.0 * lane_groups)}}
+         "lane_fill": {"instances": len(inst), "lane_groups": lane_groups, "lanes": lanes,
+                       "frac": len(inst) / float(lanes)}}
     if oracle_s is not None:
         import oracle
         r["oracle"] = {"value": len(inst) / oracle_s, "unit": "instances/s", "cores": oracle.default_threads(),

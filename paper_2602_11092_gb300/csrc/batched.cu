@@ -2,11 +2,13 @@
 // persistent kernel launch (graph-capturable), with launch shapes picked by
 // an autotuner.
 //
-// Instances with the same shape are packed 16 per "lane group"; a warp
-// serves one lane group and walks two Fock states at a time (half-warp h
-// takes every other state, lane & 15 is the instance), so the ~14 instances
-// a shape typically has in a 1024-instance batch fill most lanes.  Layer k of
-// a lane group lives in workspace as complex64 [F_k][16].  Each shape's
+// Instances with the same shape are packed 16 per "lane group", a shape's
+// last group of at most 8 instances 8 per group; a warp serves one lane group
+// and walks 32 / width Fock states at a time (part p of the warp takes every
+// (32 / width)-th state, lane % width is the instance), so the ~14 instances
+// a shape typically has in a 1024-instance batch fill most lanes and a shape
+// with a few instances does not walk idle lanes' rows.  Layer k of a lane
+// group lives in workspace as complex64 [F_k][width].  Each shape's
 // transition graph is built once on the GPU at plan time as parent slots:
 // slot = (parent position << 5) | j for every mode j with t_j > 0, padded
 // with a slot that reads a zero row of U (Sec. II-A.3: the transitions
@@ -80,6 +82,7 @@ struct BShape {
 
 struct BLaneGroup {
     int shape;
+    int width;            // instances per lane group: 16, or 8 for a shape's last <= 8 instances
     int inst[kBLanes];    // global instance index per lane, -1 = empty lane
     int64_t buf[2];       // workspace byte offsets of the two layer buffers
 };
@@ -239,10 +242,10 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 // Amplitude of position c of one section of a layer (rows of KW slots from
 // tab, the first row being position pos0) for the lane's instance.  us: this
 // warp's staged column of U, row j = U[j][col] per lane (row kBMax zero);
-// prev: layer k-1 of this lane (rows of 16 complex64).  Parent rows are plain
+// prev: layer k-1 of this lane (rows of LW complex64).  Parent rows are plain
 // (L1-cached) loads: the wait on layer k-1's completion counter has ordered
 // them after its writes.
-template <int KW>
+template <int KW, int LW>
 __device__ __forceinline__ float2 b_state_amp(const uint32_t *__restrict__ tab, int pos0, int c, const float2 *us,
                                               const char *prev, bool first_layer) {
     uint32_t e[KW];
@@ -268,25 +271,28 @@ __device__ __forceinline__ float2 b_state_amp(const uint32_t *__restrict__ tab, 
     }
     if (first_layer) return us[(e[0] & 31u) * kBLanes];  // one photon: a_1(e_j) = U[j][col]
     float2 v[KW];
+    // parent position (e >> 5) times the row of LW complex64
 #pragma unroll
-    for (int q = 0; q < KW; ++q) v[q] = *reinterpret_cast<const float2 *>(prev + (size_t)(e[q] & ~31u) * 4u);
+    for (int q = 0; q < KW; ++q)
+        v[q] = *reinterpret_cast<const float2 *>(prev + (size_t)(e[q] & ~31u) * (LW / 4));
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < KW; ++q) acc = cfma(us[(e[q] & 31u) * kBLanes], v[q], acc);
     return acc;
 }
 
-// Positions c0 + half, c0 + half + 2, ... < c1 of one section for the 16
-// instances of a lane group (lane il of each half-warp): the next layer's
-// amplitudes, or the PNR output probabilities (Fock order).
-template <int KW>
-__device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int pos0, int c0, int c1, int half,
+// Positions c0 + part, c0 + part + P, ... < c1 of one section (P = 32 / LW
+// parts of the warp, lane il of each part = instance il of the lane group):
+// the next layer's amplitudes, or the PNR output probabilities (Fock order).
+template <int KW, int LW>
+__device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int pos0, int c0, int c1, int part,
                                            const float2 *us, const char *prev, bool first_layer, bool last,
                                            float2 *next, float *outp, const float *__restrict__ wtab) {
+    constexpr int P = 32 / LW;
     // positions fit in 32 bits (at most C(31, 12) < 2^28 per layer)
-    for (int c = c0 + half; c < c1; c += 2) {
-        const float2 acc = b_state_amp<KW>(tab, pos0, c, us, prev, first_layer);
-        if (!last) next[(uint32_t)c * kBLanes] = acc;
+    for (int c = c0 + part; c < c1; c += P) {
+        const float2 acc = b_state_amp<KW, LW>(tab, pos0, c, us, prev, first_layer);
+        if (!last) next[(uint32_t)c * LW] = acc;
         else if (outp) outp[c] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
     }
 }
@@ -294,31 +300,34 @@ __device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int
 // Threshold detection, final layer in list order: patterns [P0, P1) of
 // class j (cnt states each, the first at list position base), whose output
 // indices start at pat_first.  Each pattern's probability is one sum in
-// list order: with one state per pattern the half-warps take alternate
-// patterns; otherwise they take alternate states of each pattern and add
-// their two partial sums.  The sum does not depend on the launch shape.
-template <int KW>
+// list order: with one state per pattern the parts of the warp take
+// patterns in turn; otherwise they take the states of each pattern in turn
+// and add their partial sums (lanes il, il + LW, ... in a fixed order).  The
+// sum does not depend on the launch shape.
+template <int KW, int LW>
 __device__ __forceinline__ void thresh_patterns(const uint32_t *__restrict__ tab, int pos0, int64_t base, int cnt,
-                                                int64_t P0, int64_t P1, int pat_first, int half, const float2 *us,
+                                                int64_t P0, int64_t P1, int pat_first, int part, const float2 *us,
                                                 const char *prev, bool first_layer, float *outp,
                                                 const float *__restrict__ wtab) {
+    constexpr int P = 32 / LW;
     if (cnt == 1) {
-        for (int64_t P = P0 + half; P < P1; P += 2) {
-            const int c = (int)(base + P);
-            const float2 acc = b_state_amp<KW>(tab, pos0, c, us, prev, first_layer);
-            if (outp) outp[pat_first + P] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+        for (int64_t Q = P0 + part; Q < P1; Q += P) {
+            const int c = (int)(base + Q);
+            const float2 acc = b_state_amp<KW, LW>(tab, pos0, c, us, prev, first_layer);
+            if (outp) outp[pat_first + Q] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
         }
         return;
     }
-    for (int64_t P = P0; P < P1; ++P) {
-        const int c0 = (int)(base + P * cnt);
+    for (int64_t Q = P0; Q < P1; ++Q) {
+        const int c0 = (int)(base + Q * cnt);
         float sum = 0.f;
-        for (int c = c0 + half; c < c0 + cnt; c += 2) {
-            const float2 acc = b_state_amp<KW>(tab, pos0, c, us, prev, first_layer);
+        for (int c = c0 + part; c < c0 + cnt; c += P) {
+            const float2 acc = b_state_amp<KW, LW>(tab, pos0, c, us, prev, first_layer);
             sum += __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
         }
+        if (P == 4) sum += __shfl_xor_sync(0xffffffffu, sum, 8);
         sum += __shfl_xor_sync(0xffffffffu, sum, 16);
-        if (half == 0 && outp) outp[pat_first + P] = sum;
+        if (part == 0 && outp) outp[pat_first + Q] = sum;
     }
 }
 
@@ -333,6 +342,84 @@ __host__ __device__ __forceinline__ int64_t thresh_items(const BShape &sh, int j
     return (npat + thresh_per_item(sh, j, chunk) - 1) / thresh_per_item(sh, j, chunk);
 }
 
+// One work item of lane group g (LW = its width: 16 or 8 instances): layer
+// k's positions of the item's section, or (threshold final layer) its run of
+// whole patterns.  The warp's 32 / LW parts take positions in turn; lane il
+// of each part is instance il of the lane group.
+template <int LW>
+__device__ __forceinline__ void b_item(const BArgs &a, const BLaneGroup &g, const BShape &sh, int k, int64_t chunk_id,
+                                       int lane, float2 *us) {
+    constexpr int P = 32 / LW;
+    const int part = lane / LW, il = lane % LW;
+    const int n = sh.n;
+    const int inst = g.inst[il];
+    const bool valid = inst >= 0;
+    float *outp = valid ? a.out + a.out_off[inst] : nullptr;
+    const int m = sh.m;
+    const int col = sh.cols[k - 1];
+    __syncwarp();
+    for (int j = part; j < m; j += P)
+        us[j * kBLanes + il] = valid ? a.U[a.u_off[inst] + (int64_t)j * m + col] : make_float2(0.f, 0.f);
+    __syncwarp();
+    const char *prev = a.ws + g.buf[(n - 1 - (k - 1)) & 1] + il * sizeof(float2);
+    const uint32_t *tab = a.slots + sh.slot_off[k];
+    const float *wtab = reinterpret_cast<const float *>(a.slots + sh.w_off);
+    const float2 *usl = us + il;
+    if (k == n && sh.det == SLOS_DETECT_THRESHOLD) {
+        // the item's class and run of patterns (items counted class by class)
+        int j = 1;
+        int64_t rem = chunk_id;
+        for (; j < sh.nclass; ++j) {
+            const int64_t nit = thresh_items(sh, j, a.chunk);
+            if (rem < nit) break;
+            rem -= nit;
+        }
+        const int64_t per = thresh_per_item(sh, j, a.chunk);
+        const int64_t P0 = rem * per;
+        const int64_t P1 = min(P0 + per, (int64_t)(sh.pat_off[j + 1] - sh.pat_off[j]));
+        const int sec = (j + 1) / 2 - 1;
+        const int p0 = sh.sec_pos[k][sec];
+        const uint32_t *st = tab + sh.sec_off[k][sec];
+#define SLOS_B_THR(W)                                                                                              \
+    thresh_patterns<W, LW>(st, p0, sh.pat_base[j], sh.pat_cnt[j], P0, P1, sh.pat_off[j], part, usl, prev, k == 1, \
+                           outp, wtab)
+        switch (sec) {
+            case 0: SLOS_B_THR(2); break;
+            case 1: SLOS_B_THR(4); break;
+            case 2: SLOS_B_THR(6); break;
+            case 3: SLOS_B_THR(8); break;
+            case 4: SLOS_B_THR(10); break;
+            default: SLOS_B_THR(12); break;
+        }
+#undef SLOS_B_THR
+    } else {
+        // the item's section: chunks are counted section by section, so no
+        // item straddles two widths
+        int sec = 0;
+        int64_t rem = chunk_id;
+        for (; sec < kBSec - 1; ++sec) {
+            const int64_t nch = (sh.sec_pos[k][sec + 1] - sh.sec_pos[k][sec] + a.chunk - 1) / a.chunk;
+            if (rem < nch) break;
+            rem -= nch;
+        }
+        const int p0 = sh.sec_pos[k][sec];
+        const int c0 = p0 + (int)rem * a.chunk;
+        const int c1 = min(c0 + a.chunk, sh.sec_pos[k][sec + 1]);
+        float2 *next = reinterpret_cast<float2 *>(a.ws + g.buf[(n - 1 - k) & 1]) + il;
+        const uint32_t *st = tab + sh.sec_off[k][sec];
+#define SLOS_B_SEC(W) fwd_states<W, LW>(st, p0, c0, c1, part, usl, prev, k == 1, k == n, next, outp, wtab)
+        switch (sec) {
+            case 0: SLOS_B_SEC(2); break;
+            case 1: SLOS_B_SEC(4); break;
+            case 2: SLOS_B_SEC(6); break;
+            case 3: SLOS_B_SEC(8); break;
+            case 4: SLOS_B_SEC(10); break;
+            default: SLOS_B_SEC(12); break;
+        }
+#undef SLOS_B_SEC
+    }
+}
+
 // MINB: resident 256-thread blocks per SM the register allocation is sized for
 // (a tuning dimension: fewer registers, more warps in flight).
 template <int MINB>
@@ -340,9 +427,8 @@ __global__ void __launch_bounds__(256, MINB) slos_batched_kernel(BArgs a) {
     extern __shared__ float2 us_all[];  // [warps][kBMax + 1][16]
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int half = lane >> 4, il = lane & 15;
     float2 *us = us_all + warp * ((kBMax + 1) * kBLanes);
-    if (half == 0) us[kBMax * kBLanes + il] = make_float2(0.f, 0.f);
+    if (lane < kBLanes) us[kBMax * kBLanes + lane] = make_float2(0.f, 0.f);
     int lo = 0;  // descriptor of the previous item: items are handed out in increasing order
     for (;;) {
         unsigned long long q = 0;
@@ -363,7 +449,7 @@ __global__ void __launch_bounds__(256, MINB) slos_batched_kernel(BArgs a) {
         const int64_t chunk_id = (int64_t)q - a.first_item[lo];
         const BLaneGroup &g = a.lgs[d.lg];
         const BShape &sh = a.shapes[g.shape];
-        const int n = sh.n, k = d.k;
+        const int k = d.k;
         if (d.dep >= 0) {
             const int need = a.desc[d.dep].nchunks;
             long long spins = 0;
@@ -386,73 +472,8 @@ __global__ void __launch_bounds__(256, MINB) slos_batched_kernel(BArgs a) {
             __syncwarp();
             __threadfence();
         }
-        const int inst = g.inst[il];
-        const bool valid = inst >= 0;
-        float *outp = valid ? a.out + a.out_off[inst] : nullptr;
-        {
-            const int m = sh.m;
-            const int col = sh.cols[k - 1];
-            __syncwarp();
-            for (int j = half; j < m; j += 2)
-                us[j * kBLanes + il] = valid ? a.U[a.u_off[inst] + (int64_t)j * m + col] : make_float2(0.f, 0.f);
-            __syncwarp();
-            const char *prev = a.ws + g.buf[(n - 1 - (k - 1)) & 1] + il * sizeof(float2);
-            const uint32_t *tab = a.slots + sh.slot_off[k];
-            const float *wtab = reinterpret_cast<const float *>(a.slots + sh.w_off);
-            const float2 *usl = us + il;
-            if (k == n && sh.det == SLOS_DETECT_THRESHOLD) {
-                // the item's class and run of patterns (items counted class by class)
-                int j = 1;
-                int64_t rem = chunk_id;
-                for (; j < sh.nclass; ++j) {
-                    const int64_t nit = thresh_items(sh, j, a.chunk);
-                    if (rem < nit) break;
-                    rem -= nit;
-                }
-                const int64_t per = thresh_per_item(sh, j, a.chunk);
-                const int64_t P0 = rem * per;
-                const int64_t P1 = min(P0 + per, (int64_t)(sh.pat_off[j + 1] - sh.pat_off[j]));
-                const int sec = (j + 1) / 2 - 1;
-                const int p0 = sh.sec_pos[k][sec];
-                const uint32_t *st = tab + sh.sec_off[k][sec];
-#define SLOS_B_THR(W) \
-    thresh_patterns<W>(st, p0, sh.pat_base[j], sh.pat_cnt[j], P0, P1, sh.pat_off[j], half, usl, prev, k == 1, outp, wtab)
-                switch (sec) {
-                    case 0: SLOS_B_THR(2); break;
-                    case 1: SLOS_B_THR(4); break;
-                    case 2: SLOS_B_THR(6); break;
-                    case 3: SLOS_B_THR(8); break;
-                    case 4: SLOS_B_THR(10); break;
-                    default: SLOS_B_THR(12); break;
-                }
-#undef SLOS_B_THR
-            } else {
-                // the item's section: chunks are counted section by section, so no
-                // item straddles two widths
-                int sec = 0;
-                int64_t rem = chunk_id;
-                for (; sec < kBSec - 1; ++sec) {
-                    const int64_t nch = (sh.sec_pos[k][sec + 1] - sh.sec_pos[k][sec] + a.chunk - 1) / a.chunk;
-                    if (rem < nch) break;
-                    rem -= nch;
-                }
-                const int p0 = sh.sec_pos[k][sec];
-                const int lo = p0 + (int)rem * a.chunk;
-                const int hi = min(lo + a.chunk, sh.sec_pos[k][sec + 1]);
-                float2 *next = reinterpret_cast<float2 *>(a.ws + g.buf[(n - 1 - k) & 1]) + il;
-                const uint32_t *st = tab + sh.sec_off[k][sec];
-#define SLOS_B_SEC(W) fwd_states<W>(st, p0, lo, hi, half, usl, prev, k == 1, k == n, next, outp, wtab)
-                switch (sec) {
-                    case 0: SLOS_B_SEC(2); break;
-                    case 1: SLOS_B_SEC(4); break;
-                    case 2: SLOS_B_SEC(6); break;
-                    case 3: SLOS_B_SEC(8); break;
-                    case 4: SLOS_B_SEC(10); break;
-                    default: SLOS_B_SEC(12); break;
-                }
-#undef SLOS_B_SEC
-            }
-        }
+        if (g.width == 8) b_item<8>(a, g, sh, k, chunk_id, lane, us);
+        else b_item<16>(a, g, sh, k, chunk_id, lane, us);
         __threadfence();
         __syncwarp();
         if (lane == 0) atomicAdd(a.done + lo, 1);
@@ -762,13 +783,15 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
         for (size_t q = 0; q < members[si].size(); q += kBLanes) {
             BLaneGroup g;
             g.shape = (int)si;
+            // a shape's last group of at most 8 instances takes 8 lanes: 64-byte rows, 4 states per warp step
+            g.width = members[si].size() - q <= 8 ? 8 : kBLanes;
             for (int l = 0; l < kBLanes; ++l)
-                g.inst[l] = q + l < members[si].size() ? members[si][q + l] : -1;
+                g.inst[l] = (l < g.width && q + l < members[si].size()) ? members[si][q + l] : -1;
             const int64_t f1 = sh.n >= 2 ? sh.F[sh.n - 1] : 1;
             const int64_t f2 = sh.n >= 3 ? sh.F[sh.n - 2] : 1;
-            const size_t b1 = (size_t)f2 * kBLanes * sizeof(float2);
+            const size_t b1 = (size_t)f2 * g.width * sizeof(float2);
             g.buf[0] = (int64_t)off;
-            off += align_up((size_t)f1 * kBLanes * sizeof(float2));
+            off += align_up((size_t)f1 * g.width * sizeof(float2));
             g.buf[1] = (int64_t)off;
             off += align_up(b1);
             b->lgs.push_back(g);
