@@ -590,9 +590,15 @@ def uneven_bench(B, dev, stream, max_fock=None, reps=5, with_oracle=False):
     for it in inst:
         key = (it.m, it.n, it.threshold, tuple(it.s))
         groups[key] = groups.get(key, 0) + 1
-    # lane groups of 16 instances, a shape's last group of at most 8 instances 8 wide
-    lane_groups = sum((c + 15) // 16 for c in groups.values())
-    lanes = sum(16 * (c // 16) + (0 if c % 16 == 0 else (8 if c % 16 <= 8 else 16)) for c in groups.values())
+    # lane groups as the plan forms them: 16 wide while more than 12 instances of a
+    # shape are left, then 8 and 4 wide
+    lane_groups = lanes = 0
+    for c in groups.values():
+        while c > 0:
+            w = 16 if c > 12 else (8 if c > 4 else 4)
+            lane_groups += 1
+            lanes += w
+            c -= min(c, w)
     hbm, hbm_kind = peaks()
     oracle_s = uneven_oracle_seconds(inst, Us) if with_oracle else None
     wl = (f"{len(inst)} instances, m in 8..20, n in 2..min(10, m/2), threshold for m>=16, one persistent launch"

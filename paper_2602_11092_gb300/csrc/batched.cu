@@ -3,7 +3,7 @@
 // an autotuner.
 //
 // Instances with the same shape are packed 16 per "lane group", a shape's
-// last group of at most 8 instances 8 per group; a warp serves one lane group
+// remaining instances in groups of 8 and 4 (9..12 left: 8 + 4); a warp serves one lane group
 // and walks 32 / width Fock states at a time (part p of the warp takes every
 // (32 / width)-th state, lane % width is the instance), so the ~14 instances
 // a shape typically has in a 1024-instance batch fill most lanes and a shape
@@ -82,7 +82,7 @@ struct BShape {
 
 struct BLaneGroup {
     int shape;
-    int width;            // instances per lane group: 16, or 8 for a shape's last <= 8 instances
+    int width;            // instances per lane group: 16, 8 or 4 (a shape's remainder after the 16s)
     int inst[kBLanes];    // global instance index per lane, -1 = empty lane
     int64_t buf[2];       // workspace byte offsets of the two layer buffers
 };
@@ -325,7 +325,8 @@ __device__ __forceinline__ void thresh_patterns(const uint32_t *__restrict__ tab
             const float2 acc = b_state_amp<KW, LW>(tab, pos0, c, us, prev, first_layer);
             sum += __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
         }
-        if (P == 4) sum += __shfl_xor_sync(0xffffffffu, sum, 8);
+        if (P == 8) sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+        if (P >= 4) sum += __shfl_xor_sync(0xffffffffu, sum, 8);
         sum += __shfl_xor_sync(0xffffffffu, sum, 16);
         if (part == 0 && outp) outp[pat_first + Q] = sum;
     }
@@ -472,7 +473,8 @@ __global__ void __launch_bounds__(256, MINB) slos_batched_kernel(BArgs a) {
             __syncwarp();
             __threadfence();
         }
-        if (g.width == 8) b_item<8>(a, g, sh, k, chunk_id, lane, us);
+        if (g.width == 4) b_item<4>(a, g, sh, k, chunk_id, lane, us);
+        else if (g.width == 8) b_item<8>(a, g, sh, k, chunk_id, lane, us);
         else b_item<16>(a, g, sh, k, chunk_id, lane, us);
         __threadfence();
         __syncwarp();
@@ -780,13 +782,16 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
     size_t off = 0;
     for (size_t si = 0; si < members.size(); ++si) {
         const BShape &sh = b->shapes[si];
-        for (size_t q = 0; q < members[si].size(); q += kBLanes) {
+        // groups of 16; the remainder r in 16-wide (r > 12), 8 + 4 (r = 9..12), 8 (r = 5..8) or 4 (r <= 4)
+        // groups, so few lanes sit idle (a group's cost is its lanes x its shape's states)
+        for (size_t q = 0; q < members[si].size();) {
             BLaneGroup g;
             g.shape = (int)si;
-            // a shape's last group of at most 8 instances takes 8 lanes: 64-byte rows, 4 states per warp step
-            g.width = members[si].size() - q <= 8 ? 8 : kBLanes;
+            const size_t r = members[si].size() - q;
+            g.width = r > 12 ? kBLanes : (r > 4 ? 8 : 4);
             for (int l = 0; l < kBLanes; ++l)
                 g.inst[l] = (l < g.width && q + l < members[si].size()) ? members[si][q + l] : -1;
+            q += g.width;
             const int64_t f1 = sh.n >= 2 ? sh.F[sh.n - 1] : 1;
             const int64_t f2 = sh.n >= 3 ? sh.F[sh.n - 2] : 1;
             const size_t b1 = (size_t)f2 * g.width * sizeof(float2);
