@@ -178,7 +178,9 @@ slos_status_t slos_workspace_bytes(slos_plan_t plan, int batch, int training, si
 /* Forward pass for a batch of unitaries (all with this plan's m, n, input).
  * out: PNR + SLOS_OUT_PROBS  -> float32 [batch][n_outputs] probabilities;
  *      PNR + SLOS_OUT_AMPS   -> complex64 [batch][n_outputs] amplitudes <t|U|s>;
- *      threshold (PROBS only) -> float32 [batch][n_outputs] q(b).
+ *      threshold (PROBS only) -> float32 [batch][n_outputs] q(b), each one sum
+ *      over the pattern's states in a fixed order (outputs reproducible bit
+ *      for bit; every output element is written, so out needs no clearing).
  * save_for_backward = 1 keeps the activations slos_backward needs inside
  * `workspace` (sized with training = 1); the caller must hand the same
  * workspace, untouched, to slos_backward. */
