@@ -58,7 +58,9 @@ constexpr int kBMax = 20;   // modes handled by the persistent kernel (m <= 20)
 constexpr int kBLanes = 16; // instances per lane group
 constexpr uint32_t kSlotEmpty = (uint32_t)kBMax;   // parent 0, mode kBMax (a zero row of U)
 constexpr int64_t kBMaxParent = int64_t(1) << 27;  // parent ranks in 27 bits
-constexpr int kBSec = 6;    // slot-row widths 2, 4, ..., 12 (at most 12 occupied modes)
+constexpr int kBSec = 12;   // one section per occupied-mode count 1..12
+// slot-row width of section s (q = s + 1 occupied modes): q rounded up to even
+__host__ __device__ constexpr int sec_width(int s) { return (s + 2) & ~1; }
 
 struct BShape {
     int m, n, det, K;
@@ -67,10 +69,12 @@ struct BShape {
     int64_t slot_off[kMaxPhotons + 1];  // element offset of layer k's slots in the table buffer
     int64_t w_off;                      // final-layer weights prod t! / prod s! (float) [F_n]
     int kw[kMaxPhotons + 1];            // widest slot row of layer k (even, <= 12)
-    // Layer k is stored in sections of states with 2s+1 or 2s+2 occupied
-    // modes (s = 0 .. kBSec-1), each section with rows of 2s+2 slots;
+    // Layer k is stored in sections of states with q = s + 1 occupied modes
+    // (s = 0 .. kBSec-1), each section with rows of sec_width(s) slots (q
+    // rounded up to even, for aligned vector loads; a walk reads q of them);
     // positions sec_pos[k][s] .. sec_pos[k][s+1]-1, rows from element
-    // sec_off[k][s] of the layer's table.  An unsorted layer is one section.
+    // sec_off[k][s] of the layer's table.  An unsorted layer is one section,
+    // s = kw - 1 (rows of kw slots, all of them walked).
     int sec_pos[kMaxPhotons + 1][kBSec + 1];
     int64_t sec_off[kMaxPhotons + 1][kBSec];
     float inv_sfact;
@@ -115,7 +119,7 @@ struct BArgs {
 };
 
 // Occupied modes of state c of layer k (descending-lex rank, bar unranking
-// of common.cuh) and the section it goes to: (q + 1) / 2 - 1.
+// of common.cuh) and the section it goes to: q - 1.
 template <int MMAX>
 __device__ __forceinline__ int state_section(const BShape &sh, int k, int64_t c) {
     const int m = sh.m, L = k + m - 1;
@@ -125,7 +129,7 @@ __device__ __forceinline__ int state_section(const BShape &sh, int k, int64_t c)
 #pragma unroll
     for (int j = 0; j < MMAX; ++j)
         if (j < m && occupation<MMAX>(j, m, L, p) > 0) ++q;
-    return (q + 1) / 2 - 1;
+    return q - 1;
 }
 
 // Stable partition of layer k by section, in two passes over blocks of 256
@@ -221,8 +225,8 @@ __global__ void build_slots_kernel(const BShape sh, int k, uint32_t *tab, const 
     uint32_t *dst;
     int width;
     if (cpos || listed) {
-        const int sec = (nb + 1) / 2 - 1;
-        width = 2 * sec + 2;
+        const int sec = nb - 1;
+        width = sec_width(sec);
         dst = tab + sh.sec_off[k][sec] + (at - sh.sec_pos[k][sec]) * width;
     } else {
         width = sh.kw[k];
@@ -240,12 +244,13 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 }
 
 // Amplitude of position c of one section of a layer (rows of KW slots from
-// tab, the first row being position pos0) for the lane's instance.  us: this
+// tab, the first row being position pos0; the first QV of them occupied) for
+// the lane's instance.  us: this
 // warp's staged column of U, row j = U[j][col] per lane (row kBMax zero);
 // prev: layer k-1 of this lane (rows of LW complex64).  Parent rows are plain
 // (L1-cached) loads: the wait on layer k-1's completion counter has ordered
 // them after its writes.
-template <int KW, int LW>
+template <int KW, int QV, int LW>
 __device__ __forceinline__ float2 b_state_amp(const uint32_t *__restrict__ tab, int pos0, int c, const float2 *us,
                                               const char *prev, bool first_layer) {
     uint32_t e[KW];
@@ -270,28 +275,28 @@ __device__ __forceinline__ float2 b_state_amp(const uint32_t *__restrict__ tab, 
         }
     }
     if (first_layer) return us[(e[0] & 31u) * kBLanes];  // one photon: a_1(e_j) = U[j][col]
-    float2 v[KW];
+    float2 v[QV];
     // parent position (e >> 5) times the row of LW complex64
 #pragma unroll
-    for (int q = 0; q < KW; ++q)
+    for (int q = 0; q < QV; ++q)
         v[q] = *reinterpret_cast<const float2 *>(prev + (size_t)(e[q] & ~31u) * (LW / 4));
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < KW; ++q) acc = cfma(us[(e[q] & 31u) * kBLanes], v[q], acc);
+    for (int q = 0; q < QV; ++q) acc = cfma(us[(e[q] & 31u) * kBLanes], v[q], acc);
     return acc;
 }
 
 // Positions c0 + part, c0 + part + P, ... < c1 of one section (P = 32 / LW
 // parts of the warp, lane il of each part = instance il of the lane group):
 // the next layer's amplitudes, or the PNR output probabilities (Fock order).
-template <int KW, int LW>
+template <int KW, int QV, int LW>
 __device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int pos0, int c0, int c1, int part,
                                            const float2 *us, const char *prev, bool first_layer, bool last,
                                            float2 *next, float *outp, const float *__restrict__ wtab) {
     constexpr int P = 32 / LW;
     // positions fit in 32 bits (at most C(31, 12) < 2^28 per layer)
     for (int c = c0 + part; c < c1; c += P) {
-        const float2 acc = b_state_amp<KW, LW>(tab, pos0, c, us, prev, first_layer);
+        const float2 acc = b_state_amp<KW, QV, LW>(tab, pos0, c, us, prev, first_layer);
         if (!last) next[(uint32_t)c * LW] = acc;
         else if (outp) outp[c] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
     }
@@ -304,7 +309,7 @@ __device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int
 // patterns in turn; otherwise they take the states of each pattern in turn
 // and add their partial sums (lanes il, il + LW, ... in a fixed order).  The
 // sum does not depend on the launch shape.
-template <int KW, int LW>
+template <int KW, int QV, int LW>
 __device__ __forceinline__ void thresh_patterns(const uint32_t *__restrict__ tab, int pos0, int64_t base, int cnt,
                                                 int64_t P0, int64_t P1, int pat_first, int part, const float2 *us,
                                                 const char *prev, bool first_layer, float *outp,
@@ -313,7 +318,7 @@ __device__ __forceinline__ void thresh_patterns(const uint32_t *__restrict__ tab
     if (cnt == 1) {
         for (int64_t Q = P0 + part; Q < P1; Q += P) {
             const int c = (int)(base + Q);
-            const float2 acc = b_state_amp<KW, LW>(tab, pos0, c, us, prev, first_layer);
+            const float2 acc = b_state_amp<KW, QV, LW>(tab, pos0, c, us, prev, first_layer);
             if (outp) outp[pat_first + Q] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
         }
         return;
@@ -322,7 +327,7 @@ __device__ __forceinline__ void thresh_patterns(const uint32_t *__restrict__ tab
         const int c0 = (int)(base + Q * cnt);
         float sum = 0.f;
         for (int c = c0 + part; c < c0 + cnt; c += P) {
-            const float2 acc = b_state_amp<KW, LW>(tab, pos0, c, us, prev, first_layer);
+            const float2 acc = b_state_amp<KW, QV, LW>(tab, pos0, c, us, prev, first_layer);
             sum += __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
         }
         if (P == 8) sum += __shfl_xor_sync(0xffffffffu, sum, 4);
@@ -378,19 +383,25 @@ __device__ __forceinline__ void b_item(const BArgs &a, const BLaneGroup &g, cons
         const int64_t per = thresh_per_item(sh, j, a.chunk);
         const int64_t P0 = rem * per;
         const int64_t P1 = min(P0 + per, (int64_t)(sh.pat_off[j + 1] - sh.pat_off[j]));
-        const int sec = (j + 1) / 2 - 1;
+        const int sec = j - 1;
         const int p0 = sh.sec_pos[k][sec];
         const uint32_t *st = tab + sh.sec_off[k][sec];
-#define SLOS_B_THR(W)                                                                                              \
-    thresh_patterns<W, LW>(st, p0, sh.pat_base[j], sh.pat_cnt[j], P0, P1, sh.pat_off[j], part, usl, prev, k == 1, \
-                           outp, wtab)
+#define SLOS_B_THR(W, Q)                                                                                         \
+    thresh_patterns<W, Q, LW>(st, p0, sh.pat_base[j], sh.pat_cnt[j], P0, P1, sh.pat_off[j], part, usl, prev, k == 1, \
+                              outp, wtab)
         switch (sec) {
-            case 0: SLOS_B_THR(2); break;
-            case 1: SLOS_B_THR(4); break;
-            case 2: SLOS_B_THR(6); break;
-            case 3: SLOS_B_THR(8); break;
-            case 4: SLOS_B_THR(10); break;
-            default: SLOS_B_THR(12); break;
+            case 0: SLOS_B_THR(2, 1); break;
+            case 1: SLOS_B_THR(2, 2); break;
+            case 2: SLOS_B_THR(4, 3); break;
+            case 3: SLOS_B_THR(4, 4); break;
+            case 4: SLOS_B_THR(6, 5); break;
+            case 5: SLOS_B_THR(6, 6); break;
+            case 6: SLOS_B_THR(8, 7); break;
+            case 7: SLOS_B_THR(8, 8); break;
+            case 8: SLOS_B_THR(10, 9); break;
+            case 9: SLOS_B_THR(10, 10); break;
+            case 10: SLOS_B_THR(12, 11); break;
+            default: SLOS_B_THR(12, 12); break;
         }
 #undef SLOS_B_THR
     } else {
@@ -408,14 +419,20 @@ __device__ __forceinline__ void b_item(const BArgs &a, const BLaneGroup &g, cons
         const int c1 = min(c0 + a.chunk, sh.sec_pos[k][sec + 1]);
         float2 *next = reinterpret_cast<float2 *>(a.ws + g.buf[(n - 1 - k) & 1]) + il;
         const uint32_t *st = tab + sh.sec_off[k][sec];
-#define SLOS_B_SEC(W) fwd_states<W, LW>(st, p0, c0, c1, part, usl, prev, k == 1, k == n, next, outp, wtab)
+#define SLOS_B_SEC(W, Q) fwd_states<W, Q, LW>(st, p0, c0, c1, part, usl, prev, k == 1, k == n, next, outp, wtab)
         switch (sec) {
-            case 0: SLOS_B_SEC(2); break;
-            case 1: SLOS_B_SEC(4); break;
-            case 2: SLOS_B_SEC(6); break;
-            case 3: SLOS_B_SEC(8); break;
-            case 4: SLOS_B_SEC(10); break;
-            default: SLOS_B_SEC(12); break;
+            case 0: SLOS_B_SEC(2, 1); break;
+            case 1: SLOS_B_SEC(2, 2); break;
+            case 2: SLOS_B_SEC(4, 3); break;
+            case 3: SLOS_B_SEC(4, 4); break;
+            case 4: SLOS_B_SEC(6, 5); break;
+            case 5: SLOS_B_SEC(6, 6); break;
+            case 6: SLOS_B_SEC(8, 7); break;
+            case 7: SLOS_B_SEC(8, 8); break;
+            case 8: SLOS_B_SEC(10, 9); break;
+            case 9: SLOS_B_SEC(10, 10); break;
+            case 10: SLOS_B_SEC(12, 11); break;
+            default: SLOS_B_SEC(12, 12); break;
         }
 #undef SLOS_B_SEC
     }
@@ -816,24 +833,23 @@ slos_status_t slos_batched_plan(int count, const int *m, const int *n, const int
                 max_sorted = std::max(max_sorted, sh.F[k]);
                 sh.sec_pos[k][0] = 0;
                 for (int sec = 0; sec < kBSec; ++sec) {
-                    int64_t cnt = 0;
-                    for (int q = 2 * sec + 1; q <= 2 * sec + 2 && q <= std::min(sh.m, k); ++q)
-                        cnt += binom_host(sh.m, q) * binom_host(k - 1, q - 1);
+                    const int q = sec + 1;
+                    const int64_t cnt = q <= std::min(sh.m, k) ? binom_host(sh.m, q) * binom_host(k - 1, q - 1) : 0;
                     sh.sec_pos[k][sec + 1] = sh.sec_pos[k][sec] + (int)cnt;
                     off = (off + 3) & ~int64_t(3);  // 16-byte aligned rows for the uint4 reads
                     sh.sec_off[k][sec] = off;
-                    off += cnt * (2 * sec + 2);
+                    off += cnt * sec_width(sec);
                 }
             } else {
-                const int su = sh.kw[k] / 2 - 1;
+                const int su = sh.kw[k] - 1;
                 for (int sec = 0; sec <= kBSec; ++sec) sh.sec_pos[k][sec] = sec <= su ? 0 : (int)sh.F[k];
                 off = sh.F[k] * sh.kw[k];
             }
             tab_elems += (off + 3) & ~int64_t(3);
         }
         if (sh.det == SLOS_DETECT_THRESHOLD && sh.n >= 2)
-            for (int j = 1; j <= sh.nclass; j += 2)
-                if (sh.sec_pos[sh.n][(j - 1) / 2] != sh.pat_base[j]) {
+            for (int j = 1; j <= sh.nclass; ++j)
+                if (sh.sec_pos[sh.n][j - 1] != sh.pat_base[j]) {
                     delete b;
                     return fail(SLOS_ERR_INTERNAL, "slos_batched_plan: pattern classes do not match the sections");
                 }
