@@ -792,40 +792,48 @@ static bool build_fused_tables(slos_plan_s *p) {
             while (occ[c] < kw && nat[(size_t)c * kw + occ[c]] != kSlotEmpty) ++occ[c];
             qmax = std::max(qmax, occ[c]);
         }
-        std::vector<std::vector<int64_t>> by_q(qmax + 1);
-        for (int64_t c = 0; c < Fk; ++c) by_q[occ[c]].push_back(c);
         pos[k].assign(Fk, -1);
         std::vector<uint32_t> rows, blk;
         std::vector<int32_t> id;
         std::vector<float> wf;
         int fpad = 0;
-        for (int q = 1; q <= qmax; ++q) {
-            const auto &list = by_q[q];
-            for (size_t b0 = 0; b0 < list.size(); b0 += 32) {
-                const size_t off = rows.size();
-                blk.push_back((uint32_t)(off << 4) | (uint32_t)q);
-                rows.resize(off + (size_t)q * 32, kSlotEmpty);
-                for (int l = 0; l < 32; ++l) {
-                    const int position = fpad + l;
-                    int32_t out_id = -1;
-                    float wv = 0.f;
-                    if (b0 + l < list.size()) {
-                        const int64_t c = list[b0 + l];
-                        pos[k][c] = position;
-                        for (int i = 0; i < q; ++i) {
-                            const uint32_t e = nat[(size_t)c * kw + i];
-                            const uint32_t pp = (uint32_t)pos[k - 1][e >> 5];
-                            rows[off + (size_t)i * 32 + l] = (pp << 5) | (e & 31u);
+        // The final layer is sorted within tiles of kFusedOutTile consecutive
+        // output indices, so the CTA's warps, which take blocks in order,
+        // write one region of each output row at a time and L2 sees whole
+        // sectors (sorted over the whole layer, partly written sectors were
+        // evicted and re-read: 1.7x the output bytes in DRAM traffic).
+        const int64_t tile = k == n ? kFusedOutTile : Fk;
+        for (int64_t t0 = 0; t0 < Fk; t0 += tile) {
+            std::vector<std::vector<int64_t>> by_q(qmax + 1);
+            for (int64_t c = t0; c < std::min(Fk, t0 + tile); ++c) by_q[occ[c]].push_back(c);
+            for (int q = 1; q <= qmax; ++q) {
+                const auto &list = by_q[q];
+                for (size_t b0 = 0; b0 < list.size(); b0 += 32) {
+                    const size_t off = rows.size();
+                    blk.push_back((uint32_t)(off << 4) | (uint32_t)q);
+                    rows.resize(off + (size_t)q * 32, kSlotEmpty);
+                    for (int l = 0; l < 32; ++l) {
+                        const int position = fpad + l;
+                        int32_t out_id = -1;
+                        float wv = 0.f;
+                        if (b0 + l < list.size()) {
+                            const int64_t c = list[b0 + l];
+                            pos[k][c] = position;
+                            for (int i = 0; i < q; ++i) {
+                                const uint32_t e = nat[(size_t)c * kw + i];
+                                const uint32_t pp = (uint32_t)pos[k - 1][e >> 5];
+                                rows[off + (size_t)i * 32 + l] = (pp << 5) | (e & 31u);
+                            }
+                            out_id = (int32_t)c;
+                            if (k == n) wv = wnat[c];
                         }
-                        out_id = (int32_t)c;
-                        if (k == n) wv = wnat[c];
+                        if (k == n) {
+                            id.push_back(out_id);
+                            wf.push_back(wv);
+                        }
                     }
-                    if (k == n) {
-                        id.push_back(out_id);
-                        wf.push_back(wv);
-                    }
+                    fpad += 32;
                 }
-                fpad += 32;
             }
         }
         FusedLayer &FL = p->tab.fused[k];

@@ -9,6 +9,9 @@ namespace slos {
 
 // Shared memory a fused CTA may use.
 constexpr size_t kFusedSmemLimit = 200 * 1024;
+// Sorted walk: the final layer is sorted by occupied modes within tiles of
+// this many consecutive output indices.
+constexpr int64_t kFusedOutTile = 4096;
 
 struct FusedArgs {
     const float2 *U;                          // [B][m][m]
