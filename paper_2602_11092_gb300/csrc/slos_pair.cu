@@ -328,17 +328,36 @@ __global__ void __launch_bounds__(kPairThreads, kPairMinBlocks) slos_fwd_pair_ke
                 if ((EPI == EPI_PROBS || EPI == EPI_AMPS) && ((ci & (TS - 1)) == TS - 1 || ci == nc - 1)) {
                     __syncwarp();
                     const int cb = ci & ~(TS - 1), cnt = ci - cb + 1;
-                    const int il = lane & (TS - 1);
-                    for (int i = lane / TS; i < 64; i += 32 / TS) {
-                        const int b = 2 * pair * kLanes + i;
-                        if (b < a.B && il < cnt) {
-                            const int64_t o = (int64_t)b * a.K + c0 + cb + il;
-                            const int wi = i * (TS + 1) + (i >> 5) + il;
-                            if (EPI == EPI_PROBS)
-                                stg_policy(reinterpret_cast<float *>(a.out) + o, tile[wi], stream);
-                            else
-                                stg_policy(reinterpret_cast<float2 *>(a.out) + o,
-                                           reinterpret_cast<const float2 *>(tile)[wi], stream);
+                    if (EPI == EPI_PROBS && TS == 16 && (a.K & 1) == 0 &&
+                        (reinterpret_cast<uintptr_t>(a.out) & 7) == 0) {
+                        // rows of an even length: two consecutive outputs per lane
+                        // (8-byte stores), 8 lanes per instance
+                        const int il2 = 2 * (lane & 7);
+                        for (int i = lane >> 3; i < 64; i += 4) {
+                            const int b = 2 * pair * kLanes + i;
+                            if (b < a.B && il2 < cnt) {
+                                float *o = reinterpret_cast<float *>(a.out) + (int64_t)b * a.K + c0 + cb + il2;
+                                const int wi = i * (TS + 1) + (i >> 5) + il2;
+                                if (il2 + 1 < cnt)
+                                    stg_policy(reinterpret_cast<float2 *>(o), make_float2(tile[wi], tile[wi + 1]),
+                                               stream);
+                                else
+                                    stg_policy(o, tile[wi], stream);
+                            }
+                        }
+                    } else {
+                        const int il = lane & (TS - 1);
+                        for (int i = lane / TS; i < 64; i += 32 / TS) {
+                            const int b = 2 * pair * kLanes + i;
+                            if (b < a.B && il < cnt) {
+                                const int64_t o = (int64_t)b * a.K + c0 + cb + il;
+                                const int wi = i * (TS + 1) + (i >> 5) + il;
+                                if (EPI == EPI_PROBS)
+                                    stg_policy(reinterpret_cast<float *>(a.out) + o, tile[wi], stream);
+                                else
+                                    stg_policy(reinterpret_cast<float2 *>(a.out) + o,
+                                               reinterpret_cast<const float2 *>(tile)[wi], stream);
+                            }
                         }
                     }
                     __syncwarp();
