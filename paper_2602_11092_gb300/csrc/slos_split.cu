@@ -165,6 +165,12 @@ __device__ __forceinline__ float2 split_child(const float2 *srcb, const float *s
     return g;
 }
 
+// The same for a runtime q.
+__device__ __forceinline__ uint32_t crow16_rt(const uint4 &r, int q) {
+    const uint32_t w = q < 2 ? r.x : (q < 4 ? r.y : (q < 6 ? r.z : r.w));
+    return (q & 1) ? (w >> 16) : (w & 0xffffu);
+}
+
 // Tail child J of a parent (local position from the tail child row), 0 past
 // the plan's tail modes.
 template <int J, int SEED>
@@ -330,16 +336,280 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
     }
 }
 
+// ============================================================ ring kernel
+// The final layer (seed rows a_n or the amplitude seed) with each parent's
+// rows staged through a per-warp ring of kRingDepth shared-memory stages
+// filled by cp.async: while a warp sums one parent, the 16 child rows, the
+// parent row and (batch-shared seed) the 16 seeds of the next parent are in
+// flight without holding registers.  A lane copies its own 8 bytes of every
+// row and reads back only those, so the rows need no warp synchronisation;
+// the seeds, fetched by lanes 0..15, are read by every lane after a
+// __syncwarp.  Measured on GB300 (m=16, n=8, batch 256): final layer 0.785 ->
+// 0.715 ms; the intermediate layers, whose child rows G_k mostly hit L2, ran
+// slower this way (0.326 -> 0.355 ms) and keep the register walk above.
+constexpr int kRingDepth = 2;
+constexpr int kRingRows = 18;                       // children 0..15, parent row, seeds
+constexpr int kRingStage = kRingRows * kLanes * 8;  // bytes per stage
+constexpr int kRingWarpBytes = kRingDepth * kRingStage;
+size_t split_ring_smem_bytes() { return (size_t)kSplitBwdWarps * kRingWarpBytes; }
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The issue cursor of a warp: runs of kSplitRun parents (ch, ch + stride, ...),
+// crossing head blocks where they must, with the head offsets of the block.
+struct RingCursor {
+    int ch, c, cend, stop, b;
+    int4 d;
+    const uint4 *crow;
+    int hoff[8];
+    int hl;  // lane l < 8: the head offset of mode l (for its seed)
+};
+__device__ __forceinline__ void ring_block(RingCursor &w, const SplitBwdArgs &a, int lane) {
+    w.d = __ldg(reinterpret_cast<const int4 *>(a.desc) + w.b);
+    w.stop = min(w.d.x + w.d.y, w.cend);
+    w.crow = reinterpret_cast<const uint4 *>(a.tctab) + a.coff[w.d.w] + (w.c - w.d.x);
+    const int4 h0 = __ldg(reinterpret_cast<const int4 *>(a.head) + 2 * w.b);
+    const int4 h1 = __ldg(reinterpret_cast<const int4 *>(a.head) + 2 * w.b + 1);
+    w.hoff[0] = h0.x - w.d.x;
+    w.hoff[1] = h0.y - w.d.x;
+    w.hoff[2] = h0.z - w.d.x;
+    w.hoff[3] = h0.w - w.d.x;
+    w.hoff[4] = h1.x - w.d.x;
+    w.hoff[5] = h1.y - w.d.x;
+    w.hoff[6] = h1.z - w.d.x;
+    w.hoff[7] = h1.w - w.d.x;
+    w.hl = __ldg(a.head + 8 * w.b + (lane & 7)) - w.d.x;
+}
+__device__ __forceinline__ bool ring_run(RingCursor &w, const SplitBwdArgs &a, int lane) {
+    if (w.ch >= a.nruns) return false;
+    w.c = w.ch * kSplitRun;
+    w.cend = min(w.c + kSplitRun, a.Fprev);
+    w.b = __ldg(a.chunk + w.ch);
+    ring_block(w, a, lane);
+    return true;
+}
+__device__ __forceinline__ bool ring_next(RingCursor &w, const SplitBwdArgs &a, int stride, int lane) {
+    ++w.c;
+    ++w.crow;
+    if (w.c >= w.cend) {
+        w.ch += stride;
+        return ring_run(w, a, lane);
+    }
+    if (w.c >= w.stop) {
+        ++w.b;
+        ring_block(w, a, lane);
+    }
+    return true;
+}
+
+// Copies of parent w.c into a stage (one commit group, possibly empty).
+template <int H, int SEED>
+__device__ __forceinline__ void ring_issue(const RingCursor &w, const uint4 &cr, uint32_t stage, int lane, int mL,
+                                           const float2 *srcb, const float2 *aprevb, const float *seedb,
+                                           uint32_t fk, int *st) {
+    (void)fk;
+    (void)st;
+    const uint32_t lo = stage + 8u * lane;
+#pragma unroll
+    for (int j = 0; j < H; ++j)
+        cp_async8(lo + j * 256, srcb + ((uint32_t)SLOS_IDX((uint32_t)(w.c + w.hoff[j]), fk, st) << 5));
+    const uint32_t lc = (uint32_t)w.d.z;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (q < mL) cp_async8(lo + (8 + q) * 256, srcb + (SLOS_IDX(lc + crow16_rt(cr, q), fk, st) << 5));
+    cp_async8(lo + 16 * 256, aprevb + ((uint32_t)w.c << 5));
+    if (SEED == SEED_BCAST) {
+        int x = -1;
+        if (lane < H) x = w.c + w.hl;
+        else if (lane >= 8 && lane < 8 + mL) x = (int)(lc + crow16_rt(cr, lane - 8));
+        if (x >= 0) cp_async4(stage + 17 * 256 + 4u * lane, seedb + x);
+    }
+}
+
+template <int H, int SEED>
+__global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_bwd_ring_kernel(SplitBwdArgs a) {
+    static_assert(SEED == SEED_G || SEED == SEED_BCAST || SEED == SEED_AMPS_T, "row seeds");
+    __shared__ float2 red[kSplitBwdWarps][32];
+    __shared__ uint32_t tmem_slot;
+    extern __shared__ float4 ring_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int grp = blockIdx.y;
+    const int inst = grp * kLanes + lane;
+    const bool valid = inst < a.B;
+    const int m = a.m;
+    const int mL = m - H;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         static_cast<uint32_t>(__cvta_generic_to_shared(&tmem_slot))),
+                     "r"(kSplitTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tq = tmem_slot + ((uint32_t)(warp * 32) << 16);
+    {
+        float z[16], uh[16], ut[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) z[i] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float2 u = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+            if (valid && j < H) u = a.U[((int64_t)inst * m + j) * m + a.col];
+            if (valid && j < mL) v = a.U[((int64_t)inst * m + H + j) * m + a.col];
+            uh[2 * j] = u.x;
+            uh[2 * j + 1] = u.y;
+            ut[2 * j] = v.x;
+            ut[2 * j + 1] = v.y;
+        }
+        tm_st16(tq, z);
+        tm_st16(tq + 16, z);
+        tm_st16(tq + 32, uh);
+        tm_st16(tq + 48, ut);
+    }
+    // the warp's stages; the rows and seed slots no copy ever fills (modes past
+    // the plan's) stay zero
+    char *wring = reinterpret_cast<char *>(ring_raw) + (size_t)warp * kRingWarpBytes;
+    const uint32_t wring_s = static_cast<uint32_t>(__cvta_generic_to_shared(wring));
+#pragma unroll
+    for (int s = 0; s < kRingDepth; ++s) {
+        float2 *st = reinterpret_cast<float2 *>(wring + s * kRingStage);
+        for (int j = H; j < 8; ++j) st[j * kLanes + lane] = make_float2(0.f, 0.f);
+        for (int q = mL; q < 8; ++q) st[(8 + q) * kLanes + lane] = make_float2(0.f, 0.f);
+        if (lane < 16) reinterpret_cast<float *>(st + 17 * kLanes)[lane] = 0.f;
+    }
+    __syncwarp();
+    const size_t gprev = (size_t)grp * (size_t)a.Fprev * kLanes + lane;
+    const size_t gk = (size_t)grp * (size_t)a.Fk * kLanes + lane;
+    const float2 *aprevb = a.aprev + gprev;
+    float2 *Gprevb = a.Gprev + gprev;
+    const float2 *srcb = (SEED == SEED_G) ? a.Gk + gk
+                         : (SEED == SEED_AMPS_T) ? reinterpret_cast<const float2 *>(a.seed) + gk : a.an + gk;
+    const float *seedb = reinterpret_cast<const float *>(a.seed);
+    const int stride = gridDim.x * kSplitBwdWarps;
+    const uint32_t fk = (uint32_t)a.Fk;
+    int *const st = a.status;
+
+    RingCursor cur;
+    cur.ch = blockIdx.x * kSplitBwdWarps + warp;
+    bool more = ring_run(cur, a, lane);
+    uint4 cr = more ? __ldg(cur.crow) : make_uint4(0, 0, 0, 0);
+    int cq[kRingDepth];  // parent of each stage in flight, oldest first
+    int inflight = 0;
+#pragma unroll
+    for (int s = 0; s < kRingDepth; ++s) {
+        cq[s] = -1;
+        if (more) {
+            ring_issue<H, SEED>(cur, cr, wring_s + s * kRingStage, lane, mL, srcb, aprevb, seedb, fk, st);
+            cq[s] = cur.c;
+            ++inflight;
+            more = ring_next(cur, a, stride, lane);
+            if (more) cr = __ldg(cur.crow);
+        }
+        cp_commit();
+    }
+    int s = 0;
+    while (inflight > 0) {
+        cp_wait<kRingDepth - 1>();
+        if (SEED == SEED_BCAST) __syncwarp();
+        const float2 *stg = reinterpret_cast<const float2 *>(wring + s * kRingStage) + lane;
+        const float2 av = stg[16 * kLanes];
+        float2 gacc = make_float2(0.f, 0.f);
+        const float4 *sd = reinterpret_cast<const float4 *>(wring + s * kRingStage + 17 * 256);
+        // four tensor-memory batches (head modes 0..3, 4..H-1, tail modes 0..3, 4..7),
+        // each reading its 4 children from the stage
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float2 g[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) g[i] = stg[(4 * q + i) * kLanes];
+            if (SEED == SEED_BCAST) {
+                const float4 v = sd[q];
+                g[0] = cscale(g[0], v.x);
+                g[1] = cscale(g[1], v.y);
+                g[2] = cscale(g[2], v.z);
+                g[3] = cscale(g[3], v.w);
+            }
+            if (q == 1)
+                split_bwd_batch<H - 4>(tq, 8, 40, g, av, gacc);
+            else
+                split_bwd_batch<4>(tq, 8 * q, 32 + 8 * q, g, av, gacc);
+        }
+        Gprevb[(uint32_t)cq[0] << 5] = gacc;
+        --inflight;
+        if (SEED == SEED_BCAST) __syncwarp();  // every lane has read this stage's seeds
+        // refill the stage just read with the parent kRingDepth ahead
+        const int cnew = more ? cur.c : -1;
+        if (more) {
+            ring_issue<H, SEED>(cur, cr, wring_s + s * kRingStage, lane, mL, srcb, aprevb, seedb, fk, st);
+            ++inflight;
+            more = ring_next(cur, a, stride, lane);
+            if (more) cr = __ldg(cur.crow);
+        }
+        cp_commit();
+#pragma unroll
+        for (int i = 0; i + 1 < kRingDepth; ++i) cq[i] = cq[i + 1];
+        cq[kRingDepth - 1] = cnew;
+        s = (s + 1 == kRingDepth) ? 0 : s + 1;
+    }
+    cp_wait<0>();
+    // reduce dU over the CTA's warps, one mode at a time
+    float2 *dst = a.dUpart + (((int64_t)grp * gridDim.x + blockIdx.x) * kLanes) * m;
+    {
+        float dh[16], dt[16];
+        tm_ld16(tq, dh);
+        tm_ld16(tq + 16, dt);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j < m) {
+                red[warp][lane] = j < H ? make_float2(dh[2 * j], dh[2 * j + 1])
+                                        : make_float2(dt[2 * (j - H)], dt[2 * (j - H) + 1]);
+                __syncthreads();
+                if (warp == 0) {
+                    float2 t = red[0][lane];
+#pragma unroll
+                    for (int w = 1; w < kSplitBwdWarps; ++w) {
+                        t.x += red[w][lane].x;
+                        t.y += red[w][lane].y;
+                    }
+                    dst[lane * m + j] = t;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot), "r"(kSplitTmemCols)
+                     : "memory");
+    }
+}
+
 // ============================================================ launchers
 template <int H>
 static cudaError_t launch_bwd_split_h(const SplitBwdArgs &a, int NG, int seed, int blocks_x, cudaStream_t s) {
     const int th = kSplitBwdWarps * 32;
     const dim3 grid(blocks_x, NG);
+    const size_t rs = split_ring_smem_bytes();
     switch (seed) {
         case SEED_G: slos_bwd_split_kernel<H, SEED_G><<<grid, th, 0, s>>>(a); break;
-        case SEED_BCAST: slos_bwd_split_kernel<H, SEED_BCAST><<<grid, th, 0, s>>>(a); break;
+        case SEED_BCAST: slos_bwd_ring_kernel<H, SEED_BCAST><<<grid, th, rs, s>>>(a); break;
         case SEED_T: slos_bwd_split_kernel<H, SEED_T><<<grid, th, 0, s>>>(a); break;
-        case SEED_AMPS_T: slos_bwd_split_kernel<H, SEED_AMPS_T><<<grid, th, 0, s>>>(a); break;
+        case SEED_AMPS_T: slos_bwd_ring_kernel<H, SEED_AMPS_T><<<grid, th, rs, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
