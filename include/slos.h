@@ -183,7 +183,9 @@ slos_status_t slos_workspace_bytes(slos_plan_t plan, int batch, int training, si
  *      for bit; every output element is written, so out needs no clearing).
  * save_for_backward = 1 keeps the activations slos_backward needs inside
  * `workspace` (sized with training = 1); the caller must hand the same
- * workspace, untouched, to slos_backward. */
+ * workspace, untouched, to slos_backward.  The workspace must start on a
+ * 256-byte boundary (as cudaMalloc and PyTorch allocations do); otherwise the
+ * call returns SLOS_ERR_INVALID_ARG before any launch. */
 slos_status_t slos_forward(slos_plan_t plan, const void *U, int batch, slos_output_t output, void *out,
                            int save_for_backward, void *workspace, size_t workspace_bytes, void *stream);
 

@@ -1473,6 +1473,8 @@ slos_status_t slos_forward(slos_plan_t p, const void *U, int batch, slos_output_
     if (workspace_bytes < Ly.total || (Ly.total > 0 && !workspace))
         return fail(SLOS_ERR_INVALID_ARG, "slos_forward: workspace too small (" + std::to_string(workspace_bytes) +
                                                " < " + std::to_string(Ly.total) + ")");
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign != 0)
+        return fail(SLOS_ERR_INVALID_ARG, "slos_forward: workspace must be 256-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     char *ws = reinterpret_cast<char *>(workspace);
     const float2 *Ud = reinterpret_cast<const float2 *>(U);
@@ -1558,6 +1560,8 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
     const Layout Ly = make_layout(p, batch, true);
     if (workspace_bytes < Ly.total || !workspace)
         return fail(SLOS_ERR_INVALID_ARG, "slos_backward: workspace too small (need the training size)");
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign != 0)
+        return fail(SLOS_ERR_INVALID_ARG, "slos_backward: workspace must be 256-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     char *ws = reinterpret_cast<char *>(workspace);
     const float2 *Ud = reinterpret_cast<const float2 *>(U);

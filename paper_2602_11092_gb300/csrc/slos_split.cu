@@ -341,10 +341,9 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
 // rows staged through a per-warp ring of kRingDepth shared-memory stages
 // filled by cp.async: while a warp sums one parent, the 16 child rows, the
 // parent row and (batch-shared seed) the 16 seeds of the next parent are in
-// flight without holding registers.  A lane copies its own 8 bytes of every
-// row and reads back only those, so the rows need no warp synchronisation;
-// the seeds, fetched by lanes 0..15, are read by every lane after a
-// __syncwarp.  Measured on GB300 (m=16, n=8, batch 256): final layer 0.785 ->
+// flight without holding registers.  Rows move in 16-byte copies that skip
+// L1 (a half-warp per row), so every lane reads its own instance of each row
+// after a __syncwarp; the seeds are fetched by lanes 0..15.  Measured on GB300 (m=16, n=8, batch 256): final layer 0.785 ->
 // 0.715 ms; the intermediate layers, whose child rows G_k mostly hit L2, ran
 // slower this way (0.326 -> 0.355 ms) and keep the register walk above.
 constexpr int kRingDepth = 2;
@@ -355,6 +354,9 @@ size_t split_ring_smem_bytes() { return (size_t)kSplitBwdWarps * kRingWarpBytes;
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
@@ -412,22 +414,37 @@ __device__ __forceinline__ bool ring_next(RingCursor &w, const SplitBwdArgs &a, 
     return true;
 }
 
-// Copies of parent w.c into a stage (one commit group, possibly empty).
+// Copies of parent w.c into a stage (one commit group, possibly empty): each
+// 16-byte copy (L2 only) moves 4 instances, so a half-warp moves a 256-byte
+// row and the warp two rows per instruction: rows 2i (lanes 0..15) and 2i + 1
+// (lanes 16..31).  Rows of modes past the plan's are never copied.
 template <int H, int SEED>
 __device__ __forceinline__ void ring_issue(const RingCursor &w, const uint4 &cr, uint32_t stage, int lane, int mL,
-                                           const float2 *srcb, const float2 *aprevb, const float *seedb,
-                                           uint32_t fk, int *st) {
+                                           const char *srcg, const char *aprevg, const float *seedb, uint32_t fk,
+                                           int *st) {
     (void)fk;
     (void)st;
-    const uint32_t lo = stage + 8u * lane;
+    const int hi = lane >> 4;
+    const uint32_t lo16 = 16u * (lane & 15);
 #pragma unroll
-    for (int j = 0; j < H; ++j)
-        cp_async8(lo + j * 256, srcb + ((uint32_t)SLOS_IDX((uint32_t)(w.c + w.hoff[j]), fk, st) << 5));
+    for (int i = 0; i < 4; ++i) {  // head rows 2i, 2i + 1
+        const int j = 2 * i + hi;
+        if (j < H) {
+            const uint32_t x = SLOS_IDX((uint32_t)(w.c + (hi ? w.hoff[2 * i + 1] : w.hoff[2 * i])), fk, st);
+            cp_async16(stage + j * 256 + lo16, srcg + ((size_t)x << 8) + lo16);
+        }
+    }
     const uint32_t lc = (uint32_t)w.d.z;
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-        if (q < mL) cp_async8(lo + (8 + q) * 256, srcb + (SLOS_IDX(lc + crow16_rt(cr, q), fk, st) << 5));
-    cp_async8(lo + 16 * 256, aprevb + ((uint32_t)w.c << 5));
+    for (int i = 0; i < 4; ++i) {  // tail rows 8 + 2i, 9 + 2i
+        const int q = 2 * i + hi;
+        if (q < mL) {
+            const uint32_t wd = i == 0 ? cr.x : (i == 1 ? cr.y : (i == 2 ? cr.z : cr.w));
+            const uint32_t x = SLOS_IDX(lc + (hi ? (wd >> 16) : (wd & 0xffffu)), fk, st);
+            cp_async16(stage + (8 + q) * 256 + lo16, srcg + ((size_t)x << 8) + lo16);
+        }
+    }
+    if (!hi) cp_async16(stage + 16 * 256 + lo16, aprevg + ((size_t)w.c << 8) + lo16);
     if (SEED == SEED_BCAST) {
         int x = -1;
         if (lane < H) x = w.c + w.hl;
@@ -492,11 +509,13 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
     }
     __syncwarp();
     const size_t gprev = (size_t)grp * (size_t)a.Fprev * kLanes + lane;
-    const size_t gk = (size_t)grp * (size_t)a.Fk * kLanes + lane;
-    const float2 *aprevb = a.aprev + gprev;
     float2 *Gprevb = a.Gprev + gprev;
-    const float2 *srcb = (SEED == SEED_G) ? a.Gk + gk
-                         : (SEED == SEED_AMPS_T) ? reinterpret_cast<const float2 *>(a.seed) + gk : a.an + gk;
+    // group bases (bytes): rows of 32 instances, 256 bytes each
+    const size_t gk0 = (size_t)grp * (size_t)a.Fk * kLanes;
+    const char *srcg = reinterpret_cast<const char *>(
+        (SEED == SEED_G) ? a.Gk + gk0
+                         : (SEED == SEED_AMPS_T) ? reinterpret_cast<const float2 *>(a.seed) + gk0 : a.an + gk0);
+    const char *aprevg = reinterpret_cast<const char *>(a.aprev + (size_t)grp * (size_t)a.Fprev * kLanes);
     const float *seedb = reinterpret_cast<const float *>(a.seed);
     const int stride = gridDim.x * kSplitBwdWarps;
     const uint32_t fk = (uint32_t)a.Fk;
@@ -512,7 +531,7 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
     for (int s = 0; s < kRingDepth; ++s) {
         cq[s] = -1;
         if (more) {
-            ring_issue<H, SEED>(cur, cr, wring_s + s * kRingStage, lane, mL, srcb, aprevb, seedb, fk, st);
+            ring_issue<H, SEED>(cur, cr, wring_s + s * kRingStage, lane, mL, srcg, aprevg, seedb, fk, st);
             cq[s] = cur.c;
             ++inflight;
             more = ring_next(cur, a, stride, lane);
@@ -523,7 +542,7 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
     int s = 0;
     while (inflight > 0) {
         cp_wait<kRingDepth - 1>();
-        if (SEED == SEED_BCAST) __syncwarp();
+        __syncwarp();  // rows and seeds were copied by other lanes
         const float2 *stg = reinterpret_cast<const float2 *>(wring + s * kRingStage) + lane;
         const float2 av = stg[16 * kLanes];
         float2 gacc = make_float2(0.f, 0.f);
@@ -549,11 +568,11 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
         }
         Gprevb[(uint32_t)cq[0] << 5] = gacc;
         --inflight;
-        if (SEED == SEED_BCAST) __syncwarp();  // every lane has read this stage's seeds
+        __syncwarp();  // every lane has read this stage
         // refill the stage just read with the parent kRingDepth ahead
         const int cnew = more ? cur.c : -1;
         if (more) {
-            ring_issue<H, SEED>(cur, cr, wring_s + s * kRingStage, lane, mL, srcb, aprevb, seedb, fk, st);
+            ring_issue<H, SEED>(cur, cr, wring_s + s * kRingStage, lane, mL, srcg, aprevg, seedb, fk, st);
             ++inflight;
             more = ring_next(cur, a, stride, lane);
             if (more) cr = __ldg(cur.crow);

@@ -44,6 +44,27 @@ def test_injected_allocation_failure_fails_the_plan_cleanly(slos):
     assert torch.equal(p, ref)
 
 
+def test_misaligned_workspace_is_rejected_before_any_launch(slos):
+    # the layer kernels move 16-byte pieces of the workspace; a workspace that
+    # does not start on a 256-byte boundary is refused on the host
+    plan = slos.Plan(8, workloads.even_mode_input(8, 4))
+    U = _U(8, 33, 4)
+    need = plan.workspace_bytes(33, training=True)
+    raw = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    ws = raw[8:8 + need]
+    out = torch.full((33, plan.n_outputs), -1.0, device="cuda")
+    n0 = slos.launch_count()
+    with pytest.raises(slos.SlosError) as e:
+        plan.forward(U, save_for_backward=True, workspace=ws, out=out)
+    assert e.value.status == 1 and "aligned" in str(e.value)
+    with pytest.raises(slos.SlosError) as e:
+        plan.backward(U, torch.ones(plan.n_outputs, device="cuda"), ws)
+    assert e.value.status == 1 and "aligned" in str(e.value)
+    assert slos.launch_count() == n0
+    torch.cuda.synchronize()
+    assert (out == -1.0).all()
+
+
 def test_stream_of_another_device_is_rejected_before_any_launch(slos):
     lib = slos.load()
     plan = slos.Plan(8, workloads.even_mode_input(8, 4))
