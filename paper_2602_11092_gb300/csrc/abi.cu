@@ -21,6 +21,7 @@
 #include "profile.h"
 #include "slos_kernels.cuh"
 #include "fused.h"
+#include "prefix.h"
 #include "split.h"
 #include "tab_launch.h"
 
@@ -110,6 +111,7 @@ static cudaError_t init_device_once(int dev) {
     if ((e = slos_init_m24()) != cudaSuccess) return e;
     if ((e = slos_fused_init()) != cudaSuccess) return e;
     if ((e = slos_pair_init()) != cudaSuccess) return e;
+    if ((e = slos_prefix_init()) != cudaSuccess) return e;
     done[dev] = true;
     return cudaSuccess;
 }
@@ -1330,6 +1332,8 @@ slos_status_t slos_plan_space(int m, int n, const int *input_state, slos_detecti
         return tst;
     }
     choose_fused(p);
+    // the small leading layers on chip (Fock-space table plans: the child tables have no holes)
+    p->prefix_L = (p->tab.enabled && p->space == SLOS_SPACE_FOCK) ? slos_prefix_layers(p->m, p->n, p->F.data()) : 0;
     tst = build_encode_tables(p);
     if (tst != SLOS_OK) {
         free_tables(p);
@@ -1455,6 +1459,44 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
     return SLOS_OK;
 }
 
+static PrefixArgs prefix_args(const slos_plan_s *p, const float2 *U, int batch) {
+    PrefixArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    const int L = p->prefix_L;
+    pa.U = U;
+    for (int k = 0; k <= L; ++k) pa.F[k] = (int)p->F[k];
+    for (int k = 1; k <= L; ++k) {
+        pa.slots[k] = p->tab.layer[k].slots;
+        pa.kw[k] = p->tab.layer[k].kw;
+        pa.ctab[k] = p->tab.layer[k].ctab;
+        pa.cols[k - 1] = p->cols[k - 1];
+    }
+    pa.cap[0] = pa.cap[1] = 1;
+    for (int k = 1; k <= L; ++k) pa.cap[k & 1] = std::max(pa.cap[k & 1], (int)p->F[k]);
+    for (int k = 0; k < L; ++k) pa.asum += (int)p->F[k];
+    pa.m = p->m;
+    pa.L = L;
+    pa.B = batch;
+    pa.NI = slos_prefix_ni(p->m, L, p->F.data(), batch, p->sm_count);
+    return pa;
+}
+
+// Layers 1..prefix_L in one on-chip launch; writes layer k to the workspace
+// when bit k of `want` is set.
+static slos_status_t launch_prefix_fwd(const slos_plan_s *p, const Layout &Ly, char *ws, const float2 *U, int batch,
+                                       uint32_t want, const char *name, cudaStream_t s) {
+    PrefixArgs pa = prefix_args(p, U, batch);
+    double bytes = 8.0 * p->m * p->m;
+    for (int k = 1; k <= pa.L; ++k)
+        if ((want >> k) & 1u) {
+            pa.out[k] = reinterpret_cast<float2 *>(ws + Ly.layer[k]);
+            bytes += 8.0 * p->F[k];
+        }
+    ProfScope ps(name, bytes * batch, s);
+    SLOS_CUDA(slos_launch_prefix_fwd(pa, s));
+    return SLOS_OK;
+}
+
 slos_status_t slos_forward(slos_plan_t p, const void *U, int batch, slos_output_t output, void *out,
                            int save_for_backward, void *workspace, size_t workspace_bytes, void *stream) {
     if (!p || p->kind != 0) return fail(SLOS_ERR_INVALID_ARG, "slos_forward: not a single-shape plan");
@@ -1515,7 +1557,18 @@ slos_status_t slos_forward(slos_plan_t p, const void *U, int batch, slos_output_
         return SLOS_OK;
     }
     SLOS_CUDA(cudaMemsetAsync(ws + Ly.counters, 0, kCounters * sizeof(int), s));
-    for (int k = 1; k < n; ++k) {
+    int k0 = 1;
+    if (p->prefix_L >= 2) {
+        // kept layers of the prefix and its last layer (which layer L + 1 reads)
+        const int L = p->prefix_L;
+        uint32_t want = 1u << L;
+        for (int k = 1; k < L; ++k)
+            if (save && p->stored[k]) want |= 1u << k;
+        slos_status_t st = launch_prefix_fwd(p, Ly, ws, Ud, batch, want, "slos_fwd_prefix", s);
+        if (st != SLOS_OK) return st;
+        k0 = L + 1;
+    }
+    for (int k = k0; k < n; ++k) {
         slos_status_t st = launch_layer_fwd(p, Ly, ws, Ud, batch, k, EPI_STORE, true, nullptr, s);
         if (st != SLOS_OK) return st;
     }
@@ -1617,17 +1670,40 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
     int have_base = -1;  // segment currently recomputed (its kept base layer)
     ReduceArgs ra;
     memset(&ra, 0, sizeof(ra));
+    const int L = p->prefix_L;
     for (int k = n; k >= 1; --k) {
         const int kp = k - 1;
+        if (L >= 2 && k <= L) {
+            // layers L..1 on chip: a_1..a_{L-1} recomputed, G_L read, one dU row per layer
+            PrefixArgs pa = prefix_args(p, Ud, batch);
+            pa.GL = reinterpret_cast<const float2 *>(ws + Ly.g[(n - 1 - L) % 2]);
+            for (int q = 1; q <= L; ++q) {
+                pa.dUpart[q] = reinterpret_cast<float2 *>(ws + Ly.dupart[q]);
+                ra.part[q] = pa.dUpart[q];
+                ra.blocks[q] = 1;
+                ra.cols[q] = p->cols[q - 1];
+            }
+            ProfScope ps("slos_bwd_prefix", (8.0 * p->F[L] + 8.0 * p->m * p->m) * batch, s);
+            SLOS_CUDA(slos_launch_prefix_bwd(pa, s));
+            break;
+        }
         if (kp >= 1 && !p->stored[kp]) {
             int base = kp;
             while (base >= 1 && !p->stored[base]) --base;
             if (base != have_base) {
                 int top = kp;
                 while (top + 1 < n && !p->stored[top + 1]) ++top;
-                for (int q = base + 1; q <= top; ++q) {
-                    slos_status_t st = launch_layer_fwd(p, Ly, ws, Ud, batch, q, EPI_STORE, true, nullptr, s, true);
+                if (L >= 2 && top == L) {
+                    // the segment ends at the prefix's last layer: only a_L is needed
+                    // above the prefix, recomputed on chip from U
+                    slos_status_t st = launch_prefix_fwd(p, Ly, ws, Ud, batch, 1u << L, "slos_fwd_recompute", s);
                     if (st != SLOS_OK) return st;
+                } else {
+                    for (int q = base + 1; q <= top; ++q) {
+                        slos_status_t st =
+                            launch_layer_fwd(p, Ly, ws, Ud, batch, q, EPI_STORE, true, nullptr, s, true);
+                        if (st != SLOS_OK) return st;
+                    }
                 }
                 have_base = base;
             }
@@ -1702,7 +1778,7 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
     const int64_t tot = (int64_t)batch * m * m;
     {
         double bytes = 0.0;
-        for (int k = 1; k <= n; ++k) bytes += 8.0 * NG * Ly.bwd_blocks[k] * kLanes * m;
+        for (int k = 1; k <= n; ++k) bytes += 8.0 * NG * ra.blocks[k] * kLanes * m;
         ProfScope ps("slos_dU_reduce", bytes + 8.0 * tot, s);
         dU_layer_sum_kernel<<<dim3(n, NG, (kLanes * m + 31) / 32), 256, 0, s>>>(ra);
         SLOS_CUDA(cudaGetLastError());

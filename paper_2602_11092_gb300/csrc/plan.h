@@ -76,6 +76,7 @@ struct slos_plan_s {
     int fused_threads = 512;    // its CTA size
     int fused_cap[2] = {1, 1};  // its buffer capacities (states per instance, even / odd layers)
     bool fused_sorted = false;  // walks the sorted layout (tab.fused) instead of Fock order
+    int prefix_L = 0;           // layers 1..prefix_L run on chip in one launch each way (0: none)
     slos::BatchedPlan *batched;
     slos::SplitTables *split = nullptr;  // split-lattice tables (null: slot-table kernels only)
 };
