@@ -53,7 +53,7 @@ def peaks():
 
 
 SLOS_KERNEL_FILES = ("abi.cu", "common.cuh", "plan.h", "slos_kernels.cuh", "slos_m16.cu", "slos_pair.cu",
-                     "tab_launch.h", "tables.h", "slos_split.cu", "split.h")
+                     "tab_launch.h", "tables.h", "slos_split.cu", "split.h", "slos_prefix.cu", "prefix.h")
 
 
 def csrc_hash() -> str:

@@ -599,3 +599,32 @@ def test_repeated_runs_are_bitwise_identical(slos):
         runs.append(res)
     for x, y in zip(*runs):
         assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("B", [5, 1301])
+def test_on_chip_prefix_layers_forward_and_backward(slos, B):
+    # m=8, n=5: layers 1..4 run in one on-chip launch each way; B = 1301 takes
+    # four instances per CTA with a last CTA of one instance
+    m, s = 8, [1, 0, 1, 0, 1, 0, 1, 1]
+    rng = np.random.default_rng(40 + B)
+    U = c64(workloads.haar_unitaries(m, B, rng))
+    plan = slos.Plan(m, s)
+    K = plan.n_outputs
+    c = rng.standard_normal(K).astype(np.float32)
+    ws = plan.workspace(B, training=True)
+    slos.profile_reset()
+    slos.profile_enable(True)
+    p = plan.forward(U, save_for_backward=True, workspace=ws)
+    dU = plan.backward(U, torch.tensor(c, device=dev()), ws)
+    torch.cuda.synchronize()
+    names = set(slos.profile_collect())
+    slos.profile_enable(False)
+    assert "slos_fwd_prefix" in names and "slos_bwd_prefix" in names, names
+    p, dU = p.cpu().numpy(), dU.cpu().numpy()
+    outs = oracle.enumerate_fock(m, sum(s))
+    Uh = up(U)
+    for b in sorted({0, 1, B // 2, B - 2, B - 1}):
+        check_dist(p[b], oracle.probabilities(Uh[b], s, outs))
+        ref = _grad_U_ref(Uh[b], s, c.astype(np.float64), outs)
+        rel = np.linalg.norm(dU[b] - ref) / np.linalg.norm(ref)
+        assert rel <= G_TOL, f"instance {b}: rel err {rel:.2e}"
