@@ -553,15 +553,17 @@ def uneven_oracle_seconds(inst, Us, sample=20000):
     return sum(workloads.fock_dim(it.m, it.n) * per_out[it.n] for it in inst)
 
 
-def uneven_bench(B, dev, stream, max_fock=None, reps=5, with_oracle=False):
+def uneven_bench(B, dev, stream, max_fock=None, reps=5, with_oracle=False, min_fock=None):
     """The 1024-instance uneven workload (m in 8..20, n in 2..min(10, m/2),
     threshold detection for m >= 16) in one persistent launch, autotuned;
-    max_fock keeps only the instances with at most that many output states
-    (small cases for profiling)."""
+    max_fock / min_fock keep only the instances with at most / at least that
+    many output states (cases for profiling)."""
     import torch
     inst, Us = workloads.uneven()
-    if max_fock is not None:
-        keep = [i for i, it in enumerate(inst) if workloads.fock_dim(it.m, it.n) <= max_fock]
+    if max_fock is not None or min_fock is not None:
+        keep = [i for i, it in enumerate(inst)
+                if (max_fock is None or workloads.fock_dim(it.m, it.n) <= max_fock)
+                and (min_fock is None or workloads.fock_dim(it.m, it.n) >= min_fock)]
         inst, Us = [inst[i] for i in keep], [Us[i] for i in keep]
     bp = B.BatchedPlan([it.m for it in inst], [it.n for it in inst], [it.s for it in inst],
                        [B.THRESHOLD if it.threshold else B.PNR for it in inst])
@@ -834,13 +836,15 @@ def main():
     ap.add_argument("--uneven-only", type=int, default=None, metavar="MAX_STATES",
                     help="run only the uneven-batch launch, on the instances with at most MAX_STATES "
                          "output states (small cases for ncu captures)")
+    ap.add_argument("--uneven-min", type=int, default=None, metavar="MIN_STATES",
+                    help="with --uneven-only: keep only the instances with at least MIN_STATES output states")
     args = ap.parse_args()
     if args.uneven_only is not None:
         import torch
         import paper_2602_11092_gb300 as pkg
         B = pkg.load()
         r = uneven_bench(B, torch.device("cuda", 0), torch.cuda.current_stream(), max_fock=args.uneven_only,
-                         reps=args.steps)
+                         reps=args.steps, min_fock=args.uneven_min)
         print(json.dumps(r))
         return 0
     global BATCH
