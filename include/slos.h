@@ -154,6 +154,16 @@ slos_status_t mesh_unitary_weighted_backward(const slos_mesh_desc_t *desc, const
                                              const void *dU, float *dtheta, float *dx, float *dw, void *workspace,
                                              size_t workspace_bytes, void *stream);
 
+/* Sum of per-instance gradient rows over the batch: out[p] = sum_b rows[b][p]
+ * for rows float32 device [batch][width] (row stride width), out float32
+ * device [width].  The chain rule for parameters every instance shares (the
+ * trainable phases of Sec. II-A.3, the encoding weights w of Sec. II-C.1),
+ * e.g. the per-instance dw of mesh_unitary_weighted_backward.  The order of
+ * the additions is fixed (the result does not depend on the launch); batch = 0
+ * writes zeros.  Returns SLOS_ERR_INVALID_ARG for NULL pointers or negative
+ * sizes. */
+slos_status_t mesh_sum_rows(const float *rows, int batch, int width, float *out, void *stream);
+
 slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t detection,
                         size_t mem_budget_bytes, slos_plan_t *out);
 

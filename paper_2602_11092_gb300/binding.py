@@ -48,6 +48,7 @@ _SIGNATURES = {
     "mesh_unitary_backward": ([ctypes.POINTER(MeshDesc), _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp, _vp, _sz, _vp],
                               _int),
     "mesh_unitary_weighted": ([ctypes.POINTER(MeshDesc), _vp, _i64, _vp, _i64, _vp, _int, _vp, _vp], _int),
+    "mesh_sum_rows": ([_vp, _int, _int, _vp, _vp], _int),
     "mesh_unitary_weighted_backward": ([ctypes.POINTER(MeshDesc), _vp, _i64, _vp, _i64, _vp, _int, _vp, _vp, _vp,
                                         _vp, _vp, _sz, _vp], _int),
     "slos_plan": ([_int, _int, ctypes.POINTER(_int), _int, _sz, ctypes.POINTER(_vp)], _int),
@@ -195,6 +196,18 @@ def mesh_unitary_backward(m: int, theta, data, batch: int, dU: torch.Tensor, dat
                                                   _ptr(dU), _ptr(dtheta), _ptr(ddata), _ptr(dw), _ptr(ws),
                                                   nbytes.value, _stream(stream)))
     return (dtheta, ddata, dw) if need_dw else (dtheta, ddata)
+
+
+def mesh_sum_rows(rows: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """mesh_sum_rows: float32 [batch, width] -> [width], the batch sum in a fixed order."""
+    _need(rows, torch.float32, "rows")
+    if rows.dim() != 2:
+        raise ValueError("rows must be [batch, width]")
+    batch, width = rows.shape
+    if out is None:
+        out = torch.empty(width, dtype=torch.float32, device=rows.device)
+    _check(load().mesh_sum_rows(_ptr(rows), batch, width, _ptr(out), _stream(stream)))
+    return out
 
 
 def fidelity_kernel(input_state, Ua: torch.Tensor, Ub: torch.Tensor | None = None, out=None, stream=None):

@@ -1219,6 +1219,16 @@ slos_status_t mesh_unitary_weighted_backward(const slos_mesh_desc_t *desc, const
                               workspace_bytes, stream);
 }
 
+slos_status_t mesh_sum_rows(const float *rows, int batch, int width, float *out, void *stream) {
+    if (batch < 0 || width < 0) return fail(SLOS_ERR_INVALID_ARG, "mesh_sum_rows: negative size");
+    if (width == 0) return SLOS_OK;
+    if (!out || (batch > 0 && !rows)) return fail(SLOS_ERR_INVALID_ARG, "mesh_sum_rows: NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    ProfScope ps("mesh_sum_rows", 4.0 * ((double)batch + 1.0) * width, s);
+    SLOS_CUDA(mesh_sum_rows_launch(rows, batch, width, out, s));
+    return SLOS_OK;
+}
+
 slos_status_t slos_plan(int m, int n, const int *input_state, slos_detection_t detection, size_t mem_budget_bytes,
                         slos_plan_t *out) {
     return slos_plan_space(m, n, input_state, detection, SLOS_SPACE_FOCK, mem_budget_bytes, out);

@@ -238,13 +238,34 @@ __global__ void mesh_bwd_kernel(MeshBwdArgs a) {
     }
 }
 
-// dtheta[p] = sum_b part[b][p], in batch order.
-__global__ void mesh_reduce_kernel(const float *part, int B, int P, float *out) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
+// out[p] = sum_b part[b][p] for rows b < B of P floats, in a fixed order: a
+// block takes 32 consecutive columns; warp w sums rows w, w + 8, w + 16, ...
+// in row order (coalesced 128-byte row pieces, several loads in flight), and
+// the 8 partial sums are added in warp order.
+constexpr int kReduceWarps = 8;
+__global__ void __launch_bounds__(kReduceWarps * 32) mesh_reduce_kernel(const float *part, int B, int P, float *out) {
+    __shared__ float red[kReduceWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = blockIdx.x * 32 + lane;
     float s = 0.f;
-    for (int b = 0; b < B; ++b) s += part[(int64_t)b * P + p];
-    out[p] = s;
+    if (p < P) {
+#pragma unroll 4
+        for (int b = warp; b < B; b += kReduceWarps) s += part[(int64_t)b * P + p];
+    }
+    red[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && p < P) {
+        float t = red[0][lane];
+#pragma unroll
+        for (int w = 1; w < kReduceWarps; ++w) t += red[w][lane];
+        out[p] = t;
+    }
+}
+
+cudaError_t mesh_sum_rows_launch(const float *part, int B, int P, float *out, cudaStream_t s) {
+    count_launch();
+    mesh_reduce_kernel<<<(P + 31) / 32, kReduceWarps * 32, 0, s>>>(part, B, P, out);
+    return cudaGetLastError();
 }
 
 template <int MMAX>
@@ -292,9 +313,7 @@ cudaError_t mesh_backward_launch(const MeshBwdArgs &a, float *dtheta_shared, cud
     if (e != cudaSuccess) return e;
     if (dtheta_shared) {
         const int P = a.m * (a.m - 1);
-        count_launch();
-        mesh_reduce_kernel<<<(P + 127) / 128, 128, 0, s>>>(a.dtheta, a.B, P, dtheta_shared);
-        e = cudaGetLastError();
+        e = mesh_sum_rows_launch(a.dtheta, a.B, P, dtheta_shared, s);
     }
     return e;
 }

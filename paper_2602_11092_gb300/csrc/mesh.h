@@ -32,5 +32,7 @@ struct MeshBwdArgs {
 cudaError_t mesh_forward_launch(const MeshArgs &a, cudaStream_t s);
 // dtheta_shared != null: a.dtheta holds per-instance rows, summed into it.
 cudaError_t mesh_backward_launch(const MeshBwdArgs &a, float *dtheta_shared, cudaStream_t s);
+// out[p] = sum over rows b < B of part[b][p] (rows of P floats), fixed order.
+cudaError_t mesh_sum_rows_launch(const float *part, int B, int P, float *out, cudaStream_t s);
 
 }  // namespace slos

@@ -36,7 +36,7 @@ class MeshFn(torch.autograd.Function):
         need_dw = w is not None and ctx.needs_input_grad[5]
         res = B.mesh_unitary_backward(ctx.m, theta, data, ctx.batch, dU.contiguous(), ctx.data_col, w=w,
                                       need_dw=need_dw)
-        dw = res[2].sum(0) if need_dw else None  # per-instance rows from the library, summed over the batch
+        dw = B.mesh_sum_rows(res[2]) if need_dw else None  # per-instance rows, summed over the batch by the library
         return res[0], res[1], None, None, None, dw
 
 

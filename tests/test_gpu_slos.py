@@ -146,6 +146,18 @@ def test_weighted_mesh_matches_oracle_and_chain_rule(slos, m, B, shared):
         assert np.linalg.norm(dw[b] - ref_dw) / np.linalg.norm(ref_dw) < 1e-4
 
 
+@pytest.mark.parametrize("B,P", [(256, 240), (33, 7), (1, 40), (0, 16)])
+def test_mesh_sum_rows_is_the_batch_sum(slos, B, P):
+    # the gradient of parameters shared by the batch: a fixed-order column sum
+    rng = np.random.default_rng(B + P)
+    rows = rng.standard_normal((B, P)).astype(np.float32)
+    t = torch.tensor(rows, device=dev()).reshape(B, P)
+    out = slos.mesh_sum_rows(t).cpu().numpy()
+    ref = rows.astype(np.float64).sum(0) if B else np.zeros(P)
+    assert np.abs(out - ref).max() <= 1e-5 * max(1.0, np.abs(rows).sum(0).max())
+    assert torch.equal(slos.mesh_sum_rows(t), slos.mesh_sum_rows(t))
+
+
 # ------------------------------------------------------------------ forward
 
 def test_tiny_config_probs_and_amps(slos):
