@@ -387,6 +387,14 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # launch shapes of the layer kernels picked by the library's autotuner for
+    # this batch (cached per device and shape; one process per GPU writes it)
+    B.mesh_unitary(M, theta, data, BATCH, out=U)
+    cache = os.environ.get("SLOS_AUTOTUNE_CACHE", os.path.join(ROOT, ".autotune_cache.json")) if world == 1 else None
+    t0 = time.perf_counter()
+    tuning = plan.autotune(U, cache_path=cache)
+    tuning["seconds"] = time.perf_counter() - t0
+
     for _ in range(max(3, args.warmup)):
         step(theta, data, c)
     plan.sync_status()
@@ -481,7 +489,8 @@ def run_gpu(args):
                                f"{plan.checkpoint_stride}",
                    "global_batch": BATCH * world, "per_gpu_batch": BATCH, "modes": M, "photons": N,
                    "fock_states": plan.n_outputs, "parallelism": f"replicas x{world}" if world > 1 else "single",
-                   "l2": "working set > L2 (probs 502 MB/step), no flush needed"},
+                   "l2": "working set > L2 (probs 502 MB/step), no flush needed",
+                   "autotune": tuning},
         "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": ncu_traffic(name),
                      "launches_per_step": nl / args.steps},

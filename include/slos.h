@@ -293,6 +293,29 @@ slos_status_t slos_encoded_workspace_bytes(slos_plan_t plan, size_t *bytes);
 slos_status_t slos_encoded_forward(slos_plan_t plan, const void *U, const void *X, int batch, slos_output_t output,
                                    void *out, void *workspace, size_t workspace_bytes, void *stream);
 
+/* Launch-shape autotuner of a single-shape plan for one batch size (the
+ * paper has no counterpart; the recursion it times is the one of Sec.
+ * II-A.2).  Times a training pair (slos_forward with activations saved, then
+ * slos_backward with the shared output gradient dout_shared float32 [n_outputs])
+ * for each candidate launch shape: the number L of leading layers run on chip
+ * (none, or 2 up to the largest that fits), the instances per CTA of those
+ * launches, and the blocks per SM of the forward and backward layer grids; the
+ * fastest is kept in the plan.  U, out (float32 [batch][n_outputs]), dU and
+ * workspace (the training size for `batch`) are the caller's, as for
+ * slos_forward / slos_backward, and are overwritten.  cache_path (may be
+ * NULL): a JSON-lines file keyed by device name, plan shape and batch; a
+ * cached entry is applied without timing, a new result is appended.  Call it
+ * before a forward / backward pair, not between the two.  Synchronises
+ * `stream`; not for stream capture. */
+slos_status_t slos_autotune(slos_plan_t plan, const void *U, int batch, void *out, const float *dout_shared, void *dU,
+                            void *workspace, size_t workspace_bytes, const char *cache_path, void *stream);
+
+/* The launch shapes a plan uses: prefix_layers = L (0: none), prefix_ni,
+ * fwd_blocks_per_sm, bwd_blocks_per_sm (0: the defaults, before tuning).
+ * Any pointer may be NULL. */
+slos_status_t slos_plan_tuning(slos_plan_t plan, int *prefix_layers, int *prefix_ni, int *fwd_blocks_per_sm,
+                               int *bwd_blocks_per_sm);
+
 /* Reads the plan's device status word (waits for `stream`), clears it, and
  * returns SLOS_ERR_TIMEOUT / SLOS_ERR_INTERNAL if a kernel reported one. */
 slos_status_t slos_sync_status(slos_plan_t plan, void *stream);

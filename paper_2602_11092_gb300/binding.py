@@ -48,6 +48,9 @@ _SIGNATURES = {
     "mesh_unitary_backward": ([ctypes.POINTER(MeshDesc), _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp, _vp, _sz, _vp],
                               _int),
     "mesh_unitary_weighted": ([ctypes.POINTER(MeshDesc), _vp, _i64, _vp, _i64, _vp, _int, _vp, _vp], _int),
+    "slos_autotune": ([_vp, _vp, _int, _vp, _vp, _vp, _vp, _sz, ctypes.c_char_p, _vp], _int),
+    "slos_plan_tuning": ([_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int),
+                          ctypes.POINTER(_int)], _int),
     "mesh_sum_rows": ([_vp, _int, _int, _vp, _vp], _int),
     "mesh_unitary_weighted_backward": ([ctypes.POINTER(MeshDesc), _vp, _i64, _vp, _i64, _vp, _int, _vp, _vp, _vp,
                                         _vp, _vp, _sz, _vp], _int),
@@ -383,6 +386,26 @@ class Plan:
 
     def sync_status(self, stream=None):
         _check(load().slos_sync_status(self._h, _stream(stream)))
+
+    def autotune(self, U: torch.Tensor, cache_path: str | None = None, stream=None) -> dict:
+        """slos_autotune for U's batch: times forward(save) + backward over the
+        candidate launch shapes (buffers allocated here) and keeps the fastest."""
+        _need(U, torch.complex64, "U")
+        B = U.shape[0]
+        ws = self.workspace(B, training=True, device=U.device)
+        out = torch.empty((B, self.n_outputs), dtype=torch.float32, device=U.device)
+        dout = torch.ones(self.n_outputs, dtype=torch.float32, device=U.device)
+        dU = torch.empty_like(U)
+        path = cache_path.encode() if cache_path else None
+        _check(load().slos_autotune(self._h, _ptr(U), B, _ptr(out), _ptr(dout), _ptr(dU), _ptr(ws), ws.numel(), path,
+                                    _stream(stream)))
+        return self.tuning()
+
+    def tuning(self) -> dict:
+        v = [_int() for _ in range(4)]
+        _check(load().slos_plan_tuning(self._h, *[ctypes.byref(x) for x in v]))
+        return {"prefix_layers": v[0].value, "prefix_ni": v[1].value, "fwd_blocks_per_sm": v[2].value,
+                "bwd_blocks_per_sm": v[3].value}
 
     def __del__(self):
         h = getattr(self, "_h", None)

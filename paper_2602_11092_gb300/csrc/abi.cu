@@ -9,8 +9,10 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <fstream>
 #include <mutex>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -1460,8 +1462,9 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
         const int64_t chunks = epi == EPI_THRESH ? t.nseg : (a.Fk + slos_pair_chunk() - 1) / slos_pair_chunk();
         const int64_t items = chunks * ((NG + 1) / 2);
         const int64_t blocks = (items + slos_pair_warps() - 1) / slos_pair_warps();
-        const int grid = (int)std::max<int64_t>(
-            1, std::min<int64_t>(blocks, (int64_t)p->sm_count * slos_pair_resident_blocks(p->m)));
+        const int res = slos_pair_resident_blocks(p->m);
+        const int bps = p->tune_fwd_bps > 0 ? std::min(p->tune_fwd_bps, res) : res;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)p->sm_count * bps));
         SLOS_CUDA(slos_launch_fwd_pair(a, t, epi, save, grid, s));
     } else {
         SLOS_CUDA(launch_fwd(p->m, a, epi, save, bx, s));
@@ -1469,10 +1472,13 @@ static slos_status_t launch_layer_fwd(slos_plan_s *p, const Layout &Ly, char *ws
     return SLOS_OK;
 }
 
+// Prefix depth in use: the tuned one, else the largest that fits.
+static int prefix_layers(const slos_plan_s *p) { return p->tune_prefix_L >= 0 ? p->tune_prefix_L : p->prefix_L; }
+
 static PrefixArgs prefix_args(const slos_plan_s *p, const float2 *U, int batch) {
     PrefixArgs pa;
     memset(&pa, 0, sizeof(pa));
-    const int L = p->prefix_L;
+    const int L = prefix_layers(p);
     pa.U = U;
     for (int k = 0; k <= L; ++k) pa.F[k] = (int)p->F[k];
     for (int k = 1; k <= L; ++k) {
@@ -1488,6 +1494,8 @@ static PrefixArgs prefix_args(const slos_plan_s *p, const float2 *U, int batch) 
     pa.L = L;
     pa.B = batch;
     pa.NI = slos_prefix_ni(p->m, L, p->F.data(), batch, p->sm_count);
+    if (p->tune_prefix_ni > 0 && slos_prefix_bwd_smem(p->tune_prefix_ni, L, p->F.data()) <= kPrefixSmemLimit)
+        pa.NI = p->tune_prefix_ni;
     return pa;
 }
 
@@ -1568,9 +1576,9 @@ slos_status_t slos_forward(slos_plan_t p, const void *U, int batch, slos_output_
     }
     SLOS_CUDA(cudaMemsetAsync(ws + Ly.counters, 0, kCounters * sizeof(int), s));
     int k0 = 1;
-    if (p->prefix_L >= 2) {
+    if (prefix_layers(p) >= 2) {
         // kept layers of the prefix and its last layer (which layer L + 1 reads)
-        const int L = p->prefix_L;
+        const int L = prefix_layers(p);
         uint32_t want = 1u << L;
         for (int k = 1; k < L; ++k)
             if (save && p->stored[k]) want |= 1u << k;
@@ -1680,9 +1688,10 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
     int have_base = -1;  // segment currently recomputed (its kept base layer)
     ReduceArgs ra;
     memset(&ra, 0, sizeof(ra));
-    const int L = p->prefix_L;
+    const int L = prefix_layers(p);
     for (int k = n; k >= 1; --k) {
         const int kp = k - 1;
+        int bx = Ly.bwd_blocks[k];  // CTAs per group of this layer's launch (dU partial rows)
         if (L >= 2 && k <= L) {
             // layers L..1 on chip: a_1..a_{L-1} recomputed, G_L read, one dU row per layer
             PrefixArgs pa = prefix_args(p, Ud, batch);
@@ -1768,7 +1777,10 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
                 sa.col = a.col;
                 sa.B = batch;
                 sa.status = p->d_status;
-                SLOS_CUDA(slos_launch_bwd_split(sa, NG, k == n ? seed : SEED_G, st.h, Ly.bwd_blocks[k], s));
+                // a tuned grid is never wider than the layout's dU partial rows
+                if (p->tune_bwd_bps > 0)
+                    bx = std::min(bx, split_blocks(p, sa.nruns, kSplitBwdWarps, NG, p->tune_bwd_bps));
+                SLOS_CUDA(slos_launch_bwd_split(sa, NG, k == n ? seed : SEED_G, st.h, bx, s));
             } else if (p->tab.enabled)
                 SLOS_CUDA(launch_bwd_tab(m, a, p->tab.layer[k].ctab, k == n ? seed : SEED_G, Ly.bwd_blocks[k],
                                          p->space == SLOS_SPACE_UNBUNCHED, s));
@@ -1776,7 +1788,7 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
                 SLOS_CUDA(launch_bwd(m, a, k == n ? seed : SEED_G, Ly.bwd_blocks[k], s));
         }
         ra.part[k] = a.dUpart;
-        ra.blocks[k] = Ly.bwd_blocks[k];
+        ra.blocks[k] = bx;
         ra.cols[k] = a.col;
     }
     ra.n = n;
@@ -1796,6 +1808,136 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
         dU_assemble_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ra);
         SLOS_CUDA(cudaGetLastError());
     }
+    return SLOS_OK;
+}
+
+// ------------------------------------------------------------------ single-shape autotuner
+// Key of a single-shape plan's tuned launch shapes: device, shape and batch.
+static std::string tune_key(const slos_plan_s *p, int batch) {
+    cudaDeviceProp prop;
+    std::string dev = cudaGetDeviceProperties(&prop, p->device) == cudaSuccess ? prop.name : "unknown";
+    std::ostringstream k;
+    k << dev << "|single:m" << p->m << ",n" << p->n << ",s";
+    for (int v : p->s) k << v << ".";
+    k << ",det" << (int)p->det << ",space" << p->space << ",stride" << p->stride << ",batch" << batch;
+    return k.str();
+}
+
+// Integer field `name` of one JSON line of the cache; false when absent.
+static bool json_int(const std::string &line, const char *name, int *v) {
+    const std::string pat = std::string("\"") + name + "\": ";
+    const size_t i = line.find(pat);
+    if (i == std::string::npos) return false;
+    *v = atoi(line.c_str() + i + pat.size());
+    return true;
+}
+
+static bool tune_lookup(const char *path, const std::string &key, int out[4]) {
+    std::ifstream f(path);
+    if (!f) return false;
+    std::string line;
+    bool found = false;
+    const std::string kq = "\"key\": \"" + key + "\"";
+    while (std::getline(f, line)) {
+        if (line.find(kq) == std::string::npos) continue;
+        int v[4];
+        if (json_int(line, "prefix_layers", &v[0]) && json_int(line, "prefix_ni", &v[1]) &&
+            json_int(line, "fwd_blocks_per_sm", &v[2]) && json_int(line, "bwd_blocks_per_sm", &v[3])) {
+            memcpy(out, v, sizeof(v));
+            found = true;  // the last entry for the key wins
+        }
+    }
+    return found;
+}
+
+static void tune_apply(slos_plan_s *p, const int t[4]) {
+    p->tune_prefix_L = t[0];
+    p->tune_prefix_ni = t[1];
+    p->tune_fwd_bps = t[2];
+    p->tune_bwd_bps = t[3];
+}
+
+slos_status_t slos_autotune(slos_plan_t p, const void *U, int batch, void *out, const float *dout_shared, void *dU,
+                            void *workspace, size_t workspace_bytes, const char *cache_path, void *stream) {
+    if (!p || p->kind != 0) return fail(SLOS_ERR_INVALID_ARG, "slos_autotune: not a single-shape plan");
+    if (batch <= 0 || !U || !out || !dout_shared || !dU || !workspace)
+        return fail(SLOS_ERR_INVALID_ARG, "slos_autotune: empty batch or NULL pointer");
+    const std::string key = tune_key(p, batch);
+    int best_t[4] = {-1, 0, 0, 0};
+    if (cache_path && tune_lookup(cache_path, key, best_t)) {
+        tune_apply(p, best_t);
+        return SLOS_OK;
+    }
+    // candidates: prefix depth (none, or 2..largest), its instances per CTA,
+    // and the grid widths of the forward and backward layer launches
+    std::vector<int> Ls = {0};
+    for (int L = 2; L <= p->prefix_L; ++L) Ls.push_back(L);
+    const int res = slos_pair_resident_blocks(p->m);
+    const int fwd_opts[] = {res, std::max(1, res - 2)};
+    const int bwd_opts[] = {kSplitBwdMinBlocks, kSplitBwdMinBlocks - 1};
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(SLOS_ERR_CUDA, "slos_autotune: cannot create events");
+    }
+    slos_status_t st = SLOS_OK;
+    float best = 1e30f;
+    auto run = [&](void) -> slos_status_t {
+        slos_status_t r = slos_forward(p, U, batch, SLOS_OUT_PROBS, out, 1, workspace, workspace_bytes, stream);
+        if (r != SLOS_OK) return r;
+        return slos_backward(p, U, batch, SLOS_OUT_PROBS, dout_shared, 0, dU, workspace, workspace_bytes, stream);
+    };
+    for (int L : Ls) {
+        for (int ni : {1, 2, 4}) {
+            if (L == 0 && ni > 1) continue;
+            if (L > 0 && (ni > batch || slos_prefix_bwd_smem(ni, L, p->F.data()) > kPrefixSmemLimit)) continue;
+            for (int fb : fwd_opts) {
+                for (int bb : bwd_opts) {
+                    const int t[4] = {L, L > 0 ? ni : 0, fb, bb};
+                    tune_apply(p, t);
+                    if ((st = run()) != SLOS_OK) goto done;  // warm-up
+                    cudaEventRecord(e0, s);
+                    for (int r = 0; r < 2 && st == SLOS_OK; ++r) st = run();
+                    if (st != SLOS_OK) goto done;
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        st = fail(SLOS_ERR_CUDA, "slos_autotune: synchronisation failed");
+                        goto done;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms *= 0.5f;
+                    if (ms < best) {
+                        best = ms;
+                        memcpy(best_t, t, sizeof(t));
+                    }
+                }
+            }
+        }
+    }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tune_apply(p, best_t);
+    if (st != SLOS_OK) return st;
+    if (cache_path) {
+        std::ofstream f(cache_path, std::ios::app);
+        if (f)
+            f << "{\"key\": \"" << key << "\", \"prefix_layers\": " << best_t[0] << ", \"prefix_ni\": " << best_t[1]
+              << ", \"fwd_blocks_per_sm\": " << best_t[2] << ", \"bwd_blocks_per_sm\": " << best_t[3]
+              << ", \"ms\": " << best << "}\n";
+    }
+    return SLOS_OK;
+}
+
+slos_status_t slos_plan_tuning(slos_plan_t p, int *prefix_layers_out, int *prefix_ni, int *fwd_blocks_per_sm,
+                               int *bwd_blocks_per_sm) {
+    if (!p || p->kind != 0) return fail(SLOS_ERR_INVALID_ARG, "slos_plan_tuning: not a single-shape plan");
+    if (prefix_layers_out) *prefix_layers_out = prefix_layers(p);
+    if (prefix_ni) *prefix_ni = p->tune_prefix_ni;
+    if (fwd_blocks_per_sm) *fwd_blocks_per_sm = p->tune_fwd_bps;
+    if (bwd_blocks_per_sm) *bwd_blocks_per_sm = p->tune_bwd_bps;
     return SLOS_OK;
 }
 

@@ -77,6 +77,11 @@ struct slos_plan_s {
     int fused_cap[2] = {1, 1};  // its buffer capacities (states per instance, even / odd layers)
     bool fused_sorted = false;  // walks the sorted layout (tab.fused) instead of Fock order
     int prefix_L = 0;           // layers 1..prefix_L run on chip in one launch each way (0: none)
+    // launch shapes picked by slos_autotune (negative / zero: the defaults)
+    int tune_prefix_L = -1;     // prefix depth: 0 (none) or 2..prefix_L
+    int tune_prefix_ni = 0;     // prefix instances per CTA: 1, 2 or 4
+    int tune_fwd_bps = 0;       // forward layer grid: blocks per SM (at most the resident count)
+    int tune_bwd_bps = 0;       // backward layer grid: blocks per SM (at most the layout's)
     slos::BatchedPlan *batched;
     slos::SplitTables *split = nullptr;  // split-lattice tables (null: slot-table kernels only)
 };

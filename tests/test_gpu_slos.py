@@ -640,3 +640,31 @@ def test_on_chip_prefix_layers_forward_and_backward(slos, B):
         ref = _grad_U_ref(Uh[b], s, c.astype(np.float64), outs)
         rel = np.linalg.norm(dU[b] - ref) / np.linalg.norm(ref)
         assert rel <= G_TOL, f"instance {b}: rel err {rel:.2e}"
+
+
+def test_autotune_picks_a_shape_caches_it_and_keeps_parity(slos, tmp_path):
+    m, s, B = 8, [1, 0, 1, 0, 1, 0, 1, 1], 40
+    rng = np.random.default_rng(77)
+    U = c64(workloads.haar_unitaries(m, B, rng))
+    cache = str(tmp_path / "tune.json")
+    plan = slos.Plan(m, s)
+    t = plan.autotune(U, cache_path=cache)
+    assert t["prefix_layers"] in (0, 2, 3, 4)
+    assert t["fwd_blocks_per_sm"] > 0 and t["bwd_blocks_per_sm"] > 0
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and "single:m8,n5" in lines[0]
+    # a second plan of the same shape takes the cached entry without timing
+    plan2 = slos.Plan(m, s)
+    assert plan2.autotune(U, cache_path=cache) == t
+    assert len(open(cache).read().splitlines()) == 1
+    K = plan2.n_outputs
+    c = rng.standard_normal(K).astype(np.float32)
+    ws = plan2.workspace(B, training=True)
+    p = plan2.forward(U, save_for_backward=True, workspace=ws).cpu().numpy()
+    dU = plan2.backward(U, torch.tensor(c, device=dev()), ws).cpu().numpy()
+    outs = oracle.enumerate_fock(m, sum(s))
+    Uh = up(U)
+    for b in (0, B - 1):
+        check_dist(p[b], oracle.probabilities(Uh[b], s, outs))
+        ref = _grad_U_ref(Uh[b], s, c.astype(np.float64), outs)
+        assert np.linalg.norm(dU[b] - ref) / np.linalg.norm(ref) <= G_TOL
