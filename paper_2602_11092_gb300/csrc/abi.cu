@@ -1661,7 +1661,10 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
         pa.outT = ws + (bcast ? Ly.dpw : Ly.seedT);
         ProfScope ps("slos_seed_prep", bcast ? 8.0 * p->F[n]
                                             : (double)batch * ((pa.kind == 1 ? 16.0 : 8.0) * p->F[n]), s);
-        if (p->space == SLOS_SPACE_UNBUNCHED) {
+        // plans with tables read the final-layer weights prod t! / prod s! from
+        // the plan's table instead of unranking every state (threshold plans
+        // also need the pattern of each state and keep the arithmetic kernel)
+        if (p->space == SLOS_SPACE_UNBUNCHED || (p->tab.enabled && pa.kind != 2)) {
             SeedTabArgs sa;
             sa.dout = dout;
             sa.stride = dout_stride_b;
