@@ -243,36 +243,37 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
     return v;
 }
 
-// Amplitude of position c of one section of a layer (rows of KW slots from
-// tab, the first row being position pos0; the first QV of them occupied) for
-// the lane's instance.  us: this
-// warp's staged column of U, row j = U[j][col] per lane (row kBMax zero);
-// prev: layer k-1 of this lane (rows of LW complex64).  Parent rows are plain
-// (L1-cached) loads: the wait on layer k-1's completion counter has ordered
-// them after its writes.
+// Slot rows of up to kBStage consecutive positions are staged per warp in
+// shared memory by one coalesced warp-wide copy, so a walk step waits for
+// one global round trip (its parent rows) instead of two (slot row, then
+// parent rows).
+constexpr int kBStage = 32;
+constexpr int kBSlotWords = kBStage * 12;                      // widest rows: 12 slots
+constexpr int kBWarpF2 = (kBMax + 1) * kBLanes + kBSlotWords / 2;  // per-warp shared memory, float2 units
+
+__device__ __forceinline__ void stage_rows(const uint32_t *__restrict__ src, int nwords, uint32_t *dst, int lane) {
+    __syncwarp();
+#pragma unroll 4
+    for (int i = lane; i < nwords; i += 32) dst[i] = __ldg(src + i);
+    __syncwarp();
+}
+
+// Amplitude of one state from its staged slot row srow (KW slots, the first
+// QV of them occupied) for the lane's instance.  us: this warp's staged
+// column of U, row j = U[j][col] per lane (row kBMax zero); prev: layer k-1
+// of this lane (rows of LW complex64).  Parent rows are plain (L1-cached)
+// loads: the wait on layer k-1's completion counter has ordered them after
+// its writes.
 template <int KW, int QV, int LW>
-__device__ __forceinline__ float2 b_state_amp(const uint32_t *__restrict__ tab, int pos0, int c, const float2 *us,
-                                              const char *prev, bool first_layer) {
+__device__ __forceinline__ float2 b_state_amp(const uint32_t *srow, const float2 *us, const char *prev,
+                                              bool first_layer) {
     uint32_t e[KW];
-    const uint32_t row = (uint32_t)(c - pos0) * KW;
-    if (KW % 4 == 0) {
-        const uint4 *t4 = reinterpret_cast<const uint4 *>(tab + row);
+    const uint2 *s2 = reinterpret_cast<const uint2 *>(srow);  // rows of an even number of slots: 8-byte aligned
 #pragma unroll
-        for (int q4 = 0; q4 < KW / 4; ++q4) {
-            const uint4 w4 = __ldg(t4 + q4);
-            e[4 * q4] = w4.x;
-            e[4 * q4 + 1] = w4.y;
-            e[4 * q4 + 2] = w4.z;
-            e[4 * q4 + 3] = w4.w;
-        }
-    } else {
-        const uint2 *t2 = reinterpret_cast<const uint2 *>(tab + row);
-#pragma unroll
-        for (int q2 = 0; q2 < KW / 2; ++q2) {
-            const uint2 w2 = __ldg(t2 + q2);
-            e[2 * q2] = w2.x;
-            e[2 * q2 + 1] = w2.y;
-        }
+    for (int q2 = 0; q2 < KW / 2; ++q2) {
+        const uint2 w2 = s2[q2];
+        e[2 * q2] = w2.x;
+        e[2 * q2 + 1] = w2.y;
     }
     if (first_layer) return us[(e[0] & 31u) * kBLanes];  // one photon: a_1(e_j) = U[j][col]
     float2 v[QV];
@@ -289,16 +290,23 @@ __device__ __forceinline__ float2 b_state_amp(const uint32_t *__restrict__ tab, 
 // Positions c0 + part, c0 + part + P, ... < c1 of one section (P = 32 / LW
 // parts of the warp, lane il of each part = instance il of the lane group):
 // the next layer's amplitudes, or the PNR output probabilities (Fock order).
+// Staged kBStage positions at a time (a multiple of P, so each part keeps its
+// positions).
 template <int KW, int QV, int LW>
 __device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int pos0, int c0, int c1, int part,
-                                           const float2 *us, const char *prev, bool first_layer, bool last,
-                                           float2 *next, float *outp, const float *__restrict__ wtab) {
+                                           int lane, uint32_t *sbuf, const float2 *us, const char *prev,
+                                           bool first_layer, bool last, float2 *next, float *outp,
+                                           const float *__restrict__ wtab) {
     constexpr int P = 32 / LW;
     // positions fit in 32 bits (at most C(31, 12) < 2^28 per layer)
-    for (int c = c0 + part; c < c1; c += P) {
-        const float2 acc = b_state_amp<KW, QV, LW>(tab, pos0, c, us, prev, first_layer);
-        if (!last) next[(uint32_t)c * LW] = acc;
-        else if (outp) outp[c] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+    for (int cb = c0; cb < c1; cb += kBStage) {
+        const int nb = min(kBStage, c1 - cb);
+        stage_rows(tab + (size_t)(cb - pos0) * KW, nb * KW, sbuf, lane);
+        for (int c = cb + part; c < cb + nb; c += P) {
+            const float2 acc = b_state_amp<KW, QV, LW>(sbuf + (c - cb) * KW, us, prev, first_layer);
+            if (!last) next[(uint32_t)c * LW] = acc;
+            else if (outp) outp[c] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+        }
     }
 }
 
@@ -307,33 +315,65 @@ __device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int
 // indices start at pat_first.  Each pattern's probability is one sum in
 // list order: with one state per pattern the parts of the warp take
 // patterns in turn; otherwise they take the states of each pattern in turn
-// and add their partial sums (lanes il, il + LW, ... in a fixed order).  The
-// sum does not depend on the launch shape.
+// (part p: states p, p + P, ... of the pattern) and add their partial sums
+// (lanes il, il + LW, ... in a fixed order).  The sum does not depend on the
+// launch shape or on how the slot rows are staged: windows of whole patterns
+// (cnt <= kBStage) or, for larger patterns, pieces of kBStage states, which
+// keep each part's states and their order.
 template <int KW, int QV, int LW>
 __device__ __forceinline__ void thresh_patterns(const uint32_t *__restrict__ tab, int pos0, int64_t base, int cnt,
-                                                int64_t P0, int64_t P1, int pat_first, int part, const float2 *us,
-                                                const char *prev, bool first_layer, float *outp,
-                                                const float *__restrict__ wtab) {
+                                                int64_t P0, int64_t P1, int pat_first, int part, int lane,
+                                                uint32_t *sbuf, const float2 *us, const char *prev, bool first_layer,
+                                                float *outp, const float *__restrict__ wtab) {
     constexpr int P = 32 / LW;
     if (cnt == 1) {
-        for (int64_t Q = P0 + part; Q < P1; Q += P) {
-            const int c = (int)(base + Q);
-            const float2 acc = b_state_amp<KW, QV, LW>(tab, pos0, c, us, prev, first_layer);
-            if (outp) outp[pat_first + Q] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+        const int q0 = (int)(base + P0), q1 = (int)(base + P1);
+        for (int cb = q0; cb < q1; cb += kBStage) {
+            const int nb = min(kBStage, q1 - cb);
+            stage_rows(tab + (size_t)(cb - pos0) * KW, nb * KW, sbuf, lane);
+            for (int c = cb + part; c < cb + nb; c += P) {
+                const float2 acc = b_state_amp<KW, QV, LW>(sbuf + (c - cb) * KW, us, prev, first_layer);
+                if (outp) outp[pat_first + (c - base)] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+            }
+        }
+        return;
+    }
+    auto combine_store = [&](float sum, int64_t Q) {
+        if (P == 8) sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+        if (P >= 4) sum += __shfl_xor_sync(0xffffffffu, sum, 8);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 16);
+        if (part == 0 && outp) outp[pat_first + Q] = sum;
+    };
+    if (cnt <= kBStage) {
+        const int per = kBStage / cnt;  // whole patterns per window
+        for (int64_t Qw = P0; Qw < P1; Qw += per) {
+            const int np = (int)min((int64_t)per, P1 - Qw);
+            const int cw = (int)(base + Qw * cnt);
+            stage_rows(tab + (size_t)(cw - pos0) * KW, np * cnt * KW, sbuf, lane);
+            for (int64_t Q = Qw; Q < Qw + np; ++Q) {
+                const int c0 = (int)(base + Q * cnt);
+                float sum = 0.f;
+                for (int c = c0 + part; c < c0 + cnt; c += P) {
+                    const float2 acc = b_state_amp<KW, QV, LW>(sbuf + (c - cw) * KW, us, prev, first_layer);
+                    sum += __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+                }
+                combine_store(sum, Q);
+            }
         }
         return;
     }
     for (int64_t Q = P0; Q < P1; ++Q) {
         const int c0 = (int)(base + Q * cnt);
         float sum = 0.f;
-        for (int c = c0 + part; c < c0 + cnt; c += P) {
-            const float2 acc = b_state_amp<KW, QV, LW>(tab, pos0, c, us, prev, first_layer);
-            sum += __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+        for (int piece = 0; piece < cnt; piece += kBStage) {
+            const int cs = c0 + piece, nb = min(kBStage, cnt - piece);
+            stage_rows(tab + (size_t)(cs - pos0) * KW, nb * KW, sbuf, lane);
+            for (int c = cs + part; c < cs + nb; c += P) {
+                const float2 acc = b_state_amp<KW, QV, LW>(sbuf + (c - cs) * KW, us, prev, first_layer);
+                sum += __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+            }
         }
-        if (P == 8) sum += __shfl_xor_sync(0xffffffffu, sum, 4);
-        if (P >= 4) sum += __shfl_xor_sync(0xffffffffu, sum, 8);
-        sum += __shfl_xor_sync(0xffffffffu, sum, 16);
-        if (part == 0 && outp) outp[pat_first + Q] = sum;
+        combine_store(sum, Q);
     }
 }
 
@@ -354,7 +394,7 @@ __host__ __device__ __forceinline__ int64_t thresh_items(const BShape &sh, int j
 // of each part is instance il of the lane group.
 template <int LW>
 __device__ __forceinline__ void b_item(const BArgs &a, const BLaneGroup &g, const BShape &sh, int k, int64_t chunk_id,
-                                       int lane, float2 *us) {
+                                       int lane, float2 *us, uint32_t *sbuf) {
     constexpr int P = 32 / LW;
     const int part = lane / LW, il = lane % LW;
     const int n = sh.n;
@@ -387,8 +427,8 @@ __device__ __forceinline__ void b_item(const BArgs &a, const BLaneGroup &g, cons
         const int p0 = sh.sec_pos[k][sec];
         const uint32_t *st = tab + sh.sec_off[k][sec];
 #define SLOS_B_THR(W, Q)                                                                                         \
-    thresh_patterns<W, Q, LW>(st, p0, sh.pat_base[j], sh.pat_cnt[j], P0, P1, sh.pat_off[j], part, usl, prev, k == 1, \
-                              outp, wtab)
+    thresh_patterns<W, Q, LW>(st, p0, sh.pat_base[j], sh.pat_cnt[j], P0, P1, sh.pat_off[j], part, lane, sbuf, usl, \
+                              prev, k == 1, outp, wtab)
         switch (sec) {
             case 0: SLOS_B_THR(2, 1); break;
             case 1: SLOS_B_THR(2, 2); break;
@@ -419,7 +459,8 @@ __device__ __forceinline__ void b_item(const BArgs &a, const BLaneGroup &g, cons
         const int c1 = min(c0 + a.chunk, sh.sec_pos[k][sec + 1]);
         float2 *next = reinterpret_cast<float2 *>(a.ws + g.buf[(n - 1 - k) & 1]) + il;
         const uint32_t *st = tab + sh.sec_off[k][sec];
-#define SLOS_B_SEC(W, Q) fwd_states<W, Q, LW>(st, p0, c0, c1, part, usl, prev, k == 1, k == n, next, outp, wtab)
+#define SLOS_B_SEC(W, Q) \
+    fwd_states<W, Q, LW>(st, p0, c0, c1, part, lane, sbuf, usl, prev, k == 1, k == n, next, outp, wtab)
         switch (sec) {
             case 0: SLOS_B_SEC(2, 1); break;
             case 1: SLOS_B_SEC(2, 2); break;
@@ -442,10 +483,11 @@ __device__ __forceinline__ void b_item(const BArgs &a, const BLaneGroup &g, cons
 // (a tuning dimension: fewer registers, more warps in flight).
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) slos_batched_kernel(BArgs a) {
-    extern __shared__ float2 us_all[];  // [warps][kBMax + 1][16]
+    extern __shared__ float2 us_all[];  // per warp: U column [kBMax + 1][16], then kBSlotWords staged slots
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    float2 *us = us_all + warp * ((kBMax + 1) * kBLanes);
+    float2 *us = us_all + warp * kBWarpF2;
+    uint32_t *sbuf = reinterpret_cast<uint32_t *>(us + (kBMax + 1) * kBLanes);
     if (lane < kBLanes) us[kBMax * kBLanes + lane] = make_float2(0.f, 0.f);
     int lo = 0;  // descriptor of the previous item: items are handed out in increasing order
     for (;;) {
@@ -490,9 +532,9 @@ __global__ void __launch_bounds__(256, MINB) slos_batched_kernel(BArgs a) {
             __syncwarp();
             __threadfence();
         }
-        if (g.width == 4) b_item<4>(a, g, sh, k, chunk_id, lane, us);
-        else if (g.width == 8) b_item<8>(a, g, sh, k, chunk_id, lane, us);
-        else b_item<16>(a, g, sh, k, chunk_id, lane, us);
+        if (g.width == 4) b_item<4>(a, g, sh, k, chunk_id, lane, us, sbuf);
+        else if (g.width == 8) b_item<8>(a, g, sh, k, chunk_id, lane, us, sbuf);
+        else b_item<16>(a, g, sh, k, chunk_id, lane, us, sbuf);
         __threadfence();
         __syncwarp();
         if (lane == 0) atomicAdd(a.done + lo, 1);
@@ -654,7 +696,7 @@ static slos_status_t batched_launch(slos_plan_s *p, const void *U, float *out, v
         a.spin_limit = 5000;
     }
     const int warps = threads / 32;
-    const size_t smem = (size_t)warps * (kBMax + 1) * kBLanes * sizeof(float2);
+    const size_t smem = (size_t)warps * kBWarpF2 * sizeof(float2);
     const int grid = std::max(1, p->sm_count * bps);
     double bytes = 0.0;
     for (int i = 0; i < b->count; ++i) bytes += 4.0 * (b->out_off[i + 1] - b->out_off[i]);
@@ -1014,7 +1056,7 @@ slos_status_t slos_batched_autotune(slos_plan_t p, const void *U_packed, float *
         for (int th : thread_opts) {
             int nb = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_kernel(mbv), th,
-                                                          (size_t)(th / 32) * (kBMax + 1) * kBLanes * sizeof(float2));
+                                                          (size_t)(th / 32) * kBWarpF2 * sizeof(float2));
             // a persistent grid must be fully resident: all of it, or one block per SM less
             for (int bps = std::max(1, nb - 1); bps <= nb; ++bps) {
                 for (int ch : chunks) {
