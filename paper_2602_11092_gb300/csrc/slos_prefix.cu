@@ -225,12 +225,31 @@ __global__ void __launch_bounds__(kPrefixThreads, 2) slos_bwd_prefix_kernel(Pref
             for (int t = threadIdx.x; t < Fp; t += blockDim.x) {
                 const float2 av = ak[t];
                 float2 gacc = make_float2(0.f, 0.f);
+                // child ranks of parent t: rows of m entries, read as int4 when m % 4 == 0
+                if (m % 4 == 0) {
+                    const int4 *c4 = reinterpret_cast<const int4 *>(ct + (size_t)t * m);
 #pragma unroll
-                for (int j = 0; j < MM; ++j) {
-                    if (j < m) {
-                        const float2 g = gi[__ldg(ct + (size_t)t * m + j)];
-                        gacc = cfma_conj_a(u[j], g, gacc);
-                        du[j] = cfma_conj_a(av, g, du[j]);
+                    for (int j4 = 0; j4 < MM / 4; ++j4) {
+                        if (4 * j4 < m) {
+                            const int4 v = __ldg(c4 + j4);
+                            const int cx[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                            for (int i4 = 0; i4 < 4; ++i4) {
+                                const int j = 4 * j4 + i4;
+                                const float2 g = gi[cx[i4]];
+                                gacc = cfma_conj_a(u[j], g, gacc);
+                                du[j] = cfma_conj_a(av, g, du[j]);
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < MM; ++j) {
+                        if (j < m) {
+                            const float2 g = gi[__ldg(ct + (size_t)t * m + j)];
+                            gacc = cfma_conj_a(u[j], g, gacc);
+                            du[j] = cfma_conj_a(av, g, du[j]);
+                        }
                     }
                 }
                 if (k >= 2) gp[(size_t)i * capp + t] = gacc;
