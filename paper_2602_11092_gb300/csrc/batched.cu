@@ -248,14 +248,53 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 // one global round trip (its parent rows) instead of two (slot row, then
 // parent rows).
 constexpr int kBStage = 32;
-constexpr int kBSlotWords = kBStage * 12;                      // widest rows: 12 slots
-constexpr int kBWarpF2 = (kBMax + 1) * kBLanes + kBSlotWords / 2;  // per-warp shared memory, float2 units
+constexpr int kBSlotWords = kBStage * 12;                     // widest rows: 12 slots
+constexpr int kBWarpF2 = (kBMax + 1) * kBLanes + kBSlotWords;  // per warp: U column, two staging buffers (float2 units)
 
-__device__ __forceinline__ void stage_rows(const uint32_t *__restrict__ src, int nwords, uint32_t *dst, int lane) {
+__device__ __forceinline__ void b_cp4(uint32_t *dst, const uint32_t *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+template <int N>
+__device__ __forceinline__ void b_cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The slot rows of positions [start, start + n) into dst, as one cp.async group.
+__device__ __forceinline__ void stage_issue(const uint32_t *__restrict__ tab, int pos0, int KW, int start, int n,
+                                            uint32_t *dst, int lane) {
+    const uint32_t *src = tab + (size_t)(start - pos0) * KW;
+    for (int i = lane; i < n * KW; i += 32) b_cp4(dst + i, src + i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Walk of nwin windows of consecutive positions (win(i, start, n) gives window
+// i), each one's slot rows staged in one of the warp's two buffers while the
+// previous window is walked: proc(i, start, n, rows) runs once the rows are in.
+template <typename Win, typename Proc>
+__device__ __forceinline__ void staged_walk(int nwin, Win win, Proc proc, const uint32_t *__restrict__ tab, int pos0,
+                                            int KW, uint32_t *sbuf, int lane) {
+    if (nwin <= 0) return;
+    int s0, n0;
+    win(0, s0, n0);
     __syncwarp();
-#pragma unroll 4
-    for (int i = lane; i < nwords; i += 32) dst[i] = __ldg(src + i);
-    __syncwarp();
+    stage_issue(tab, pos0, KW, s0, n0, sbuf, lane);
+    for (int i = 0; i < nwin; ++i) {
+        int s, n;
+        win(i, s, n);
+        if (i + 1 < nwin) {
+            int s1, n1;
+            win(i + 1, s1, n1);
+            stage_issue(tab, pos0, KW, s1, n1, sbuf + ((i + 1) & 1) * kBSlotWords, lane);
+            b_cp_wait<1>();
+        } else {
+            b_cp_wait<0>();
+        }
+        __syncwarp();  // every lane's copies of window i are in
+        proc(i, s, n, sbuf + (i & 1) * kBSlotWords);
+        __syncwarp();  // window i read before its buffer takes window i + 2
+    }
 }
 
 // Amplitude of one state from its staged slot row srow (KW slots, the first
@@ -290,7 +329,7 @@ __device__ __forceinline__ float2 b_state_amp(const uint32_t *srow, const float2
 // Positions c0 + part, c0 + part + P, ... < c1 of one section (P = 32 / LW
 // parts of the warp, lane il of each part = instance il of the lane group):
 // the next layer's amplitudes, or the PNR output probabilities (Fock order).
-// Staged kBStage positions at a time (a multiple of P, so each part keeps its
+// Windows of kBStage positions (a multiple of P, so each part keeps its
 // positions).
 template <int KW, int QV, int LW>
 __device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int pos0, int c0, int c1, int part,
@@ -299,15 +338,20 @@ __device__ __forceinline__ void fwd_states(const uint32_t *__restrict__ tab, int
                                            const float *__restrict__ wtab) {
     constexpr int P = 32 / LW;
     // positions fit in 32 bits (at most C(31, 12) < 2^28 per layer)
-    for (int cb = c0; cb < c1; cb += kBStage) {
-        const int nb = min(kBStage, c1 - cb);
-        stage_rows(tab + (size_t)(cb - pos0) * KW, nb * KW, sbuf, lane);
-        for (int c = cb + part; c < cb + nb; c += P) {
-            const float2 acc = b_state_amp<KW, QV, LW>(sbuf + (c - cb) * KW, us, prev, first_layer);
-            if (!last) next[(uint32_t)c * LW] = acc;
-            else if (outp) outp[c] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
-        }
-    }
+    staged_walk(
+        (c1 - c0 + kBStage - 1) / kBStage,
+        [&](int i, int &st, int &nb) {
+            st = c0 + i * kBStage;
+            nb = min(kBStage, c1 - st);
+        },
+        [&](int, int cb, int nb, const uint32_t *rows) {
+            for (int c = cb + part; c < cb + nb; c += P) {
+                const float2 acc = b_state_amp<KW, QV, LW>(rows + (c - cb) * KW, us, prev, first_layer);
+                if (!last) next[(uint32_t)c * LW] = acc;
+                else if (outp) outp[c] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+            }
+        },
+        tab, pos0, KW, sbuf, lane);
 }
 
 // Threshold detection, final layer in list order: patterns [P0, P1) of
@@ -326,55 +370,72 @@ __device__ __forceinline__ void thresh_patterns(const uint32_t *__restrict__ tab
                                                 uint32_t *sbuf, const float2 *us, const char *prev, bool first_layer,
                                                 float *outp, const float *__restrict__ wtab) {
     constexpr int P = 32 / LW;
-    if (cnt == 1) {
-        const int q0 = (int)(base + P0), q1 = (int)(base + P1);
-        for (int cb = q0; cb < q1; cb += kBStage) {
-            const int nb = min(kBStage, q1 - cb);
-            stage_rows(tab + (size_t)(cb - pos0) * KW, nb * KW, sbuf, lane);
-            for (int c = cb + part; c < cb + nb; c += P) {
-                const float2 acc = b_state_amp<KW, QV, LW>(sbuf + (c - cb) * KW, us, prev, first_layer);
-                if (outp) outp[pat_first + (c - base)] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
-            }
-        }
-        return;
-    }
     auto combine_store = [&](float sum, int64_t Q) {
         if (P == 8) sum += __shfl_xor_sync(0xffffffffu, sum, 4);
         if (P >= 4) sum += __shfl_xor_sync(0xffffffffu, sum, 8);
         sum += __shfl_xor_sync(0xffffffffu, sum, 16);
         if (part == 0 && outp) outp[pat_first + Q] = sum;
     };
-    if (cnt <= kBStage) {
-        const int per = kBStage / cnt;  // whole patterns per window
-        for (int64_t Qw = P0; Qw < P1; Qw += per) {
-            const int np = (int)min((int64_t)per, P1 - Qw);
-            const int cw = (int)(base + Qw * cnt);
-            stage_rows(tab + (size_t)(cw - pos0) * KW, np * cnt * KW, sbuf, lane);
-            for (int64_t Q = Qw; Q < Qw + np; ++Q) {
-                const int c0 = (int)(base + Q * cnt);
-                float sum = 0.f;
-                for (int c = c0 + part; c < c0 + cnt; c += P) {
-                    const float2 acc = b_state_amp<KW, QV, LW>(sbuf + (c - cw) * KW, us, prev, first_layer);
-                    sum += __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+    if (cnt == 1) {
+        const int q0 = (int)(base + P0), q1 = (int)(base + P1);
+        staged_walk(
+            (q1 - q0 + kBStage - 1) / kBStage,
+            [&](int i, int &st, int &nb) {
+                st = q0 + i * kBStage;
+                nb = min(kBStage, q1 - st);
+            },
+            [&](int, int cb, int nb, const uint32_t *rows) {
+                for (int c = cb + part; c < cb + nb; c += P) {
+                    const float2 acc = b_state_amp<KW, QV, LW>(rows + (c - cb) * KW, us, prev, first_layer);
+                    if (outp) outp[pat_first + (c - base)] = __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
                 }
-                combine_store(sum, Q);
-            }
-        }
+            },
+            tab, pos0, KW, sbuf, lane);
         return;
     }
-    for (int64_t Q = P0; Q < P1; ++Q) {
-        const int c0 = (int)(base + Q * cnt);
-        float sum = 0.f;
-        for (int piece = 0; piece < cnt; piece += kBStage) {
-            const int cs = c0 + piece, nb = min(kBStage, cnt - piece);
-            stage_rows(tab + (size_t)(cs - pos0) * KW, nb * KW, sbuf, lane);
+    if (cnt <= kBStage) {
+        const int per = kBStage / cnt;  // whole patterns per window
+        staged_walk(
+            (int)((P1 - P0 + per - 1) / per),
+            [&](int i, int &st, int &nb) {
+                const int64_t Qw = P0 + (int64_t)i * per;
+                st = (int)(base + Qw * cnt);
+                nb = (int)min((int64_t)per, P1 - Qw) * cnt;
+            },
+            [&](int i, int cw, int nb, const uint32_t *rows) {
+                const int64_t Qw = P0 + (int64_t)i * per;
+                for (int64_t Q = Qw; Q < Qw + nb / cnt; ++Q) {
+                    const int c0 = (int)(base + Q * cnt);
+                    float sum = 0.f;
+                    for (int c = c0 + part; c < c0 + cnt; c += P) {
+                        const float2 acc = b_state_amp<KW, QV, LW>(rows + (c - cw) * KW, us, prev, first_layer);
+                        sum += __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
+                    }
+                    combine_store(sum, Q);
+                }
+            },
+            tab, pos0, KW, sbuf, lane);
+        return;
+    }
+    const int npc = (cnt + kBStage - 1) / kBStage;  // pieces per pattern
+    float sum = 0.f;
+    staged_walk(
+        (int)(P1 - P0) * npc,
+        [&](int i, int &st, int &nb) {
+            const int64_t Q = P0 + i / npc;
+            const int piece = (i % npc) * kBStage;
+            st = (int)(base + Q * cnt) + piece;
+            nb = min(kBStage, cnt - piece);
+        },
+        [&](int i, int cs, int nb, const uint32_t *rows) {
+            if (i % npc == 0) sum = 0.f;
             for (int c = cs + part; c < cs + nb; c += P) {
-                const float2 acc = b_state_amp<KW, QV, LW>(sbuf + (c - cs) * KW, us, prev, first_layer);
+                const float2 acc = b_state_amp<KW, QV, LW>(rows + (c - cs) * KW, us, prev, first_layer);
                 sum += __ldg(wtab + c) * (acc.x * acc.x + acc.y * acc.y);
             }
-        }
-        combine_store(sum, Q);
-    }
+            if (i % npc == npc - 1) combine_store(sum, P0 + i / npc);
+        },
+        tab, pos0, KW, sbuf, lane);
 }
 
 // Work items of class j of a threshold final layer: runs of whole patterns
