@@ -56,9 +56,11 @@ size_t pair_smem_bytes(int epi) {
 // re/im), modes 0..15 in 64 columns, 0..23 in 128 (at most 4 CTAs per SM).
 constexpr int pair_tmem_cols(int m) { return m <= 16 ? 64 : 128; }
 
+// Parent rows: read-only, not allocated in L1 (one in ten would hit there; the
+// L1 data pipe is the busiest unit of the walk), kept in L2 by the policy.
 __device__ __forceinline__ float4 ldg4_policy(const float4 *ptr, uint64_t pol) {
     float4 v;
-    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
         : "l"(ptr), "l"(pol));
     return v;
