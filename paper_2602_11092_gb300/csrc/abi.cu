@@ -1709,7 +1709,12 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
             SLOS_CUDA(slos_launch_prefix_bwd(pa, s));
             break;
         }
-        if (kp >= 1 && !p->stored[kp]) {
+        // an intermediate split layer whose parent layer kp alone was not kept (kp - 1
+        // kept, kp + 1 kept): a_kp is formed per parent inside the backward launch from
+        // a_{kp-1} instead of being recomputed into the workspace and read back
+        const bool fuse_prev = p->split && k >= 2 && k < n && kp > L && kp >= 2 && !p->stored[kp] &&
+                               p->stored[kp - 1] && p->stored[kp + 1] && p->tab.layer[kp].kw == 8;
+        if (kp >= 1 && !p->stored[kp] && !fuse_prev) {
             int base = kp;
             while (base >= 1 && !p->stored[base]) --base;
             if (base != have_base) {
@@ -1783,7 +1788,13 @@ slos_status_t slos_backward(slos_plan_t p, const void *U, int batch, slos_output
                 // a tuned grid is never wider than the layout's dU partial rows
                 if (p->tune_bwd_bps > 0)
                     bx = std::min(bx, split_blocks(p, sa.nruns, kSplitBwdWarps, NG, p->tune_bwd_bps));
-                SLOS_CUDA(slos_launch_bwd_split(sa, NG, k == n ? seed : SEED_G, st.h, bx, s));
+                if (fuse_prev) {
+                    sa.pslots = p->tab.layer[kp].slots;
+                    sa.pprev = reinterpret_cast<const float2 *>(ws + Ly.layer[kp - 1]);
+                    sa.pcol = p->cols[kp - 1];
+                    sa.Fpp = (int)p->F[kp - 1];
+                }
+                SLOS_CUDA(slos_launch_bwd_split(sa, NG, k == n ? seed : SEED_G, st.h, bx, s, fuse_prev));
             } else if (p->tab.enabled)
                 SLOS_CUDA(launch_bwd_tab(m, a, p->tab.layer[k].ctab, k == n ? seed : SEED_G, Ly.bwd_blocks[k],
                                          p->space == SLOS_SPACE_UNBUNCHED, s));

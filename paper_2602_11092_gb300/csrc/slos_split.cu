@@ -205,10 +205,12 @@ __device__ __forceinline__ void split_bwd_batch(uint32_t tq, uint32_t cd, uint32
 // tail modes [16, 32); U[j, c_k] of the head modes [32, 48), tail [48, 64).
 constexpr int kSplitTmemCols = 64;
 
-template <int H, int SEED>
+template <int H, int SEED, bool FUSE = false>
 __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_bwd_split_kernel(SplitBwdArgs a) {
     constexpr int T = kSplitMaxTail;
     __shared__ float2 red[kSplitBwdWarps][32];
+    // FUSE: U[j, c_{k-1}] of the group's instances, row kMaxModes zero (padding slots)
+    __shared__ float2 upc[FUSE ? kMaxModes + 1 : 1][32];
     __shared__ uint32_t tmem_slot;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -217,6 +219,10 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
     const bool valid = inst < a.B;
     const int m = a.m;
     const int mL = m - H;
+    if (FUSE && warp == 1) {
+        for (int j = 0; j <= kMaxModes; ++j)
+            upc[j][lane] = (valid && j < m) ? a.U[((int64_t)inst * m + j) * m + a.pcol] : make_float2(0.f, 0.f);
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          static_cast<uint32_t>(__cvta_generic_to_shared(&tmem_slot))),
@@ -250,6 +256,7 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
     const size_t gprev = (size_t)grp * (size_t)a.Fprev * kLanes + lane;
     const size_t gk = (size_t)grp * (size_t)a.Fk * kLanes + lane;
     const float2 *aprevb = a.aprev + gprev;
+    const float2 *pprevb = FUSE ? a.pprev + (size_t)grp * (size_t)a.Fpp * kLanes + lane : nullptr;
     float2 *Gprevb = a.Gprev + gprev;
     const float2 *srcb = (SEED == SEED_G) ? a.Gk + gk
                          : (SEED == SEED_AMPS_T) ? reinterpret_cast<const float2 *>(a.seed) + gk : a.an + gk;
@@ -277,7 +284,19 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
             const uint4 *crow = reinterpret_cast<const uint4 *>(a.tctab) + a.coff[d.w] + (c - d.x);
             const uint32_t lc = (uint32_t)d.z;
             for (; c < stop; ++c, ++crow) {
-                const float2 av = __ldg(aprevb + ((uint32_t)c << 5));
+                float2 av;
+                if (FUSE) {
+                    // a_{k-1}(c) = sum over its parent slots of U[j, c_{k-1}] a_{k-2}(parent)
+                    const uint4 *sr = reinterpret_cast<const uint4 *>(a.pslots) + (size_t)c * 2;
+                    const uint4 s0 = __ldg(sr), s1 = __ldg(sr + 1);
+                    const uint32_t e[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+                    av = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        av = cfma(upc[e[q] & 31u][lane], __ldg(pprevb + ((e[q] >> 5) << 5)), av);
+                } else {
+                    av = __ldg(aprevb + ((uint32_t)c << 5));
+                }
                 const uint4 cr = __ldg(crow);
                 float2 gacc = make_float2(0.f, 0.f);
                 // every child of the parent first (16 loads in flight), then the four
@@ -620,10 +639,16 @@ __global__ void __launch_bounds__(kSplitBwdWarps * 32, kSplitBwdMinBlocks) slos_
 
 // ============================================================ launchers
 template <int H>
-static cudaError_t launch_bwd_split_h(const SplitBwdArgs &a, int NG, int seed, int blocks_x, cudaStream_t s) {
+static cudaError_t launch_bwd_split_h(const SplitBwdArgs &a, int NG, int seed, int blocks_x, cudaStream_t s,
+                                      bool fuse) {
     const int th = kSplitBwdWarps * 32;
     const dim3 grid(blocks_x, NG);
     const size_t rs = split_ring_smem_bytes();
+    if (fuse) {
+        if (seed != SEED_G) return cudaErrorInvalidValue;
+        slos_bwd_split_kernel<H, SEED_G, true><<<grid, th, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     switch (seed) {
         case SEED_G: slos_bwd_split_kernel<H, SEED_G><<<grid, th, 0, s>>>(a); break;
         case SEED_BCAST: slos_bwd_ring_kernel<H, SEED_BCAST><<<grid, th, rs, s>>>(a); break;
@@ -634,10 +659,11 @@ static cudaError_t launch_bwd_split_h(const SplitBwdArgs &a, int NG, int seed, i
     return cudaGetLastError();
 }
 
-cudaError_t slos_launch_bwd_split(const SplitBwdArgs &a, int NG, int seed, int h, int blocks_x, cudaStream_t s) {
+cudaError_t slos_launch_bwd_split(const SplitBwdArgs &a, int NG, int seed, int h, int blocks_x, cudaStream_t s,
+                                  bool fuse_prev) {
     switch (h) {
-        case 6: return launch_bwd_split_h<6>(a, NG, seed, blocks_x, s);
-        case 8: return launch_bwd_split_h<8>(a, NG, seed, blocks_x, s);
+        case 6: return launch_bwd_split_h<6>(a, NG, seed, blocks_x, s, fuse_prev);
+        case 8: return launch_bwd_split_h<8>(a, NG, seed, blocks_x, s, fuse_prev);
         default: return cudaErrorInvalidValue;
     }
 }

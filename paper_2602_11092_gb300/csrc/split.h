@@ -81,6 +81,12 @@ struct SplitBwdArgs {
     int Fk, Fprev, nruns;      // nruns: warp items of kSplitRun parents
     int *status;               // plan status word (bounds checks of SLOS_DEBUG builds)
     int m, col, B;
+    // a_{k-1} recomputed per parent from a_{k-2} instead of read (intermediate
+    // layers whose parent layer was not kept): layer k-1's parent slots (rows
+    // of 8), a_{k-2} [NG][F_{k-2}][32] and the input mode of photon k-1
+    const uint32_t *pslots;
+    const float2 *pprev;
+    int pcol, Fpp;
 };
 
 // Resident blocks per SM the backward kernel's register budget is sized for.
@@ -92,6 +98,7 @@ constexpr int kSplitBwdWarps = 4;
 #endif
 constexpr int kSplitBwdMinBlocks = SLOS_SPLIT_BWD_MINB;
 
-cudaError_t slos_launch_bwd_split(const SplitBwdArgs &a, int NG, int seed, int h, int blocks_x, cudaStream_t s);
+cudaError_t slos_launch_bwd_split(const SplitBwdArgs &a, int NG, int seed, int h, int blocks_x, cudaStream_t s,
+                                  bool fuse_prev = false);
 
 }  // namespace slos
